@@ -1,0 +1,759 @@
+/*
+ * FP64 CPU oracle for the stabilised FDTD-Esirkepov PIC time step of
+ * Godfrey & Vay, "Suppressing the Numerical Cherenkov Instability in FDTD PIC
+ * Codes" (arXiv 1401.0838).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline leg may load it. The CUDA library never links,
+ * includes or calls anything in this directory, and this file includes nothing
+ * from the CUDA library: the two share no code, headers or constants.
+ *
+ * Style: plain, slow and literal. Every pass is applied on its own (no fusion),
+ * there are no tiles, particles are visited one at a time, FP64 throughout,
+ * libm for sin/cos/asin/log/exp, compiled with -ffp-contract=off.
+ *
+ * Units: c = eps0 = mu0 = 1, particle mass m = 1, charge q = +-1. Positions are
+ * stored in grid units (x/dx), momenta as u = gamma*v. Fields live on the
+ * standard Yee staggering (periodic in every direction):
+ *   Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
+ *   Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k)
+ * and array element [(k*ny+j)*nx+i] holds the component at the position above.
+ * A 2D x-z run is the y-invariant case ny = 1, dy = 1.
+ *
+ * Parity pins for every function here are in tests/test_oracle_*.py. The
+ * readings taken where the paper is silent are listed in the file header of
+ * each section below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_GALERKIN 0
+#define ORC_UNIFORM 1
+#define ORC_MOMENTUM 2
+
+#define ORC_OK 0
+#define ORC_E_SINGULAR (-1)
+#define ORC_E_ARG (-2)
+
+/* ------------------------------------------------------------------------ */
+/* Parameters, fields and particles (the oracle's own types)                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int ndim;               /* 2 or 3 */
+  int nx, ny, nz;         /* ny = 1 in 2D */
+  double dx, dy, dz, dt;  /* dy = 1 in 2D */
+  int scheme;             /* gather: 0 Galerkin, 1 Uniform */
+  double psi_e[9];        /* 9-tap z-stencil of Psi_E(D_z), taps for offsets -4..4 */
+  double psi_b[9];        /* 9-tap z-stencil of Psi_B(D_z) */
+  int f_nbin;             /* bilinear passes per direction, per side */
+  int f_ncomp;            /* compensation passes per direction, per side */
+  double f_alpha;         /* compensation centre weight (3 in the paper's filter) */
+  int f_targets;          /* bit 0: filter J; bit 1: filter the gather copies */
+} orc_params;
+
+typedef struct {
+  double *ex, *ey, *ez, *bx, *by, *bz, *jx, *jy, *jz;
+} orc_fields;
+
+typedef struct {
+  long n;
+  double *x, *y, *z;    /* grid units, in [0, n) after every step; y unused in 2D */
+  double *ux, *uy, *uz; /* u = gamma v */
+  double *w;            /* number weight of the macro-particle */
+  double *q;            /* charge, -1 or +1 (mass 1) */
+} orc_particles;
+
+static long idx3(const orc_params* p, int i, int j, int k) {
+  return ((long)k * p->ny + j) * p->nx + i;
+}
+static int wrap(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+static double wrapf(double x, double n) {
+  double r = fmod(x, n);
+  if (r < 0) r += n;
+  if (r >= n) r -= n;
+  return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2, Eq. 3-5: field multipliers; s = k_z dz / 2, alpha = c dt / dz.     */
+/* k_z dt / 2 = alpha s and dz/dt = 1/alpha (c = 1).                          */
+/* The multiplier speed is c (tuned for infinite gamma, Sec. 3).             */
+/* ------------------------------------------------------------------------ */
+double orc_multiplier(int scheme, double alpha, double s) {
+  if (s == 0.0) return 1.0; /* limit s -> 0 of every form */
+  double sc = sin(alpha * s) * cos(alpha * s) / alpha;
+  switch (scheme) {
+    case ORC_GALERKIN: /* Eq. 3: ... csc^2(s) * s */
+      return sc * s / (sin(s) * sin(s));
+    case ORC_UNIFORM: /* Eq. 4: ... csc(s) */
+      return sc / sin(s);
+    case ORC_MOMENTUM: /* Eq. 5: ... cot(s) */
+      return sc * cos(s) / sin(s);
+    default:
+      return NAN;
+  }
+}
+
+/* Value of the polynomial sum_n c[n] xi^n, n = 0..4. */
+static double poly4(const double c[5], double xi) {
+  double r = 0.0, p = 1.0;
+  for (int n = 0; n < 5; ++n) {
+    r += c[n] * p;
+    p *= xi;
+  }
+  return r;
+}
+
+/*
+ * Sec. 2: (4,4) rational interpolation of the multiplier in xi = sin^2(s) on
+ * the nine nodes xi_j = j/8. Unknowns a0..a4 (Psi_E) and b1..b4 (Psi_B, with
+ * b0 = 1); the interpolation conditions Psi_E(xi_j) = M_j Psi_B(xi_j) are the
+ * linear system sum_n a_n xi^n - M_j sum_{n>=1} b_n xi^n = M_j, solved here by
+ * Gaussian elimination with partial pivoting.
+ * Degenerate case (reading): if the system is singular, the constant
+ * interpolant Psi_E = Psi_B = 1 is returned when it reproduces every node
+ * (Uniform at alpha = 1/2, where the multiplier is identically 1); any other
+ * singular case, or a Psi_B with a zero on [0,1], returns ORC_E_SINGULAR.
+ */
+int orc_rational_coeffs(int scheme, double alpha, double psi_e[5], double psi_b[5]) {
+  double A[9][10];
+  double m[9];
+  double amax = 0.0;
+  for (int j = 0; j < 9; ++j) {
+    double xi = j / 8.0;
+    double s = asin(sqrt(xi));
+    m[j] = orc_multiplier(scheme, alpha, s);
+    double p = 1.0;
+    for (int n = 0; n <= 4; ++n) {
+      A[j][n] = p;
+      if (n >= 1) A[j][4 + n] = -m[j] * p;
+      p *= xi;
+    }
+    A[j][9] = m[j];
+    for (int c = 0; c < 9; ++c) amax = fmax(amax, fabs(A[j][c]));
+  }
+  int singular = 0;
+  for (int c = 0; c < 9; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 9; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (fabs(A[piv][c]) <= 1e-12 * amax) {
+      singular = 1;
+      break;
+    }
+    if (piv != c)
+      for (int cc = 0; cc < 10; ++cc) {
+        double t = A[c][cc];
+        A[c][cc] = A[piv][cc];
+        A[piv][cc] = t;
+      }
+    for (int r = c + 1; r < 9; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int cc = c; cc < 10; ++cc) A[r][cc] -= f * A[c][cc];
+    }
+  }
+  if (singular) {
+    for (int j = 0; j < 9; ++j)
+      if (fabs(m[j] - 1.0) > 1e-12) return ORC_E_SINGULAR;
+    for (int n = 0; n < 5; ++n) psi_e[n] = psi_b[n] = (n == 0) ? 1.0 : 0.0;
+    return ORC_OK;
+  }
+  double sol[9];
+  for (int r = 8; r >= 0; --r) {
+    double acc = A[r][9];
+    for (int c = r + 1; c < 9; ++c) acc -= A[r][c] * sol[c];
+    sol[r] = acc / A[r][r];
+  }
+  for (int n = 0; n < 5; ++n) psi_e[n] = sol[n];
+  psi_b[0] = 1.0;
+  for (int n = 1; n < 5; ++n) psi_b[n] = sol[4 + n];
+  for (int t = 0; t <= 4096; ++t)
+    if (poly4(psi_b, t / 4096.0) <= 0.0) return ORC_E_SINGULAR;
+  return ORC_OK;
+}
+
+/*
+ * Sec. 2: xi corresponds to the operator D = -(1,-2,1)/4 along z, since
+ * D exp(i k z) = sin^2(k dz/2) exp(i k z). Psi(D) = sum_n a_n D^n is a 9-tap
+ * symmetric stencil; taps[m+4] multiplies f[k+m]. Built by repeated
+ * convolution of D with itself.
+ */
+void orc_psi_taps(const double a[5], double taps[9]) {
+  double pw[9] = {0, 0, 0, 0, 1, 0, 0, 0, 0}; /* D^0 */
+  const double d[3] = {-0.25, 0.5, -0.25};
+  for (int m = 0; m < 9; ++m) taps[m] = a[0] * pw[m];
+  for (int n = 1; n <= 4; ++n) {
+    double nx[9] = {0};
+    for (int m = 0; m < 9; ++m)
+      for (int t = -1; t <= 1; ++t) {
+        int mm = m + t;
+        if (mm >= 0 && mm < 9) nx[mm] += pw[m] * d[t + 1];
+      }
+    memcpy(pw, nx, sizeof pw);
+    for (int m = 0; m < 9; ++m) taps[m] += a[n] * pw[m];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Periodic convolutions along one axis (0 = x, 1 = y, 2 = z).               */
+/* ------------------------------------------------------------------------ */
+void orc_conv_axis(const orc_params* p, double* f, int axis, const double* taps, int half) {
+  long ncell = (long)p->nx * p->ny * p->nz;
+  double* out = (double*)malloc(sizeof(double) * ncell);
+  int n = axis == 0 ? p->nx : axis == 1 ? p->ny : p->nz;
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double acc = 0.0;
+        for (int m = -half; m <= half; ++m) {
+          int ii = i, jj = j, kk = k;
+          if (axis == 0) ii = wrap(i + m, n);
+          if (axis == 1) jj = wrap(j + m, n);
+          if (axis == 2) kk = wrap(k + m, n);
+          acc += taps[m + half] * f[idx3(p, ii, jj, kk)];
+        }
+        out[idx3(p, i, j, k)] = acc;
+      }
+  memcpy(f, out, sizeof(double) * ncell);
+  free(out);
+}
+
+/*
+ * Sec. 3 (Eq. 6) and Sec. 4: the digital filter is a number of bilinear
+ * (1/4, 1/2, 1/4) passes, transfer cos^2(s), and of compensation passes
+ * (-(a-1)/2, a, -(a-1)/2), transfer a - (a-1) cos(2s) (= 5 - 4cos^2 s for
+ * a = 3), along every direction of the grid. One bilinear and one
+ * compensation pass per direction is the square root of Eq. 6.
+ */
+void orc_filter(const orc_params* p, double* f) {
+  const double bil[3] = {0.25, 0.5, 0.25};
+  const double cmp[3] = {-(p->f_alpha - 1.0) / 2.0, p->f_alpha, -(p->f_alpha - 1.0) / 2.0};
+  int naxes[3] = {1, p->ndim == 3, 1};
+  for (int axis = 0; axis < 3; ++axis) {
+    if (!naxes[axis]) continue;
+    for (int r = 0; r < p->f_nbin; ++r) orc_conv_axis(p, f, axis, bil, 1);
+    for (int r = 0; r < p->f_ncomp; ++r) orc_conv_axis(p, f, axis, cmp, 1);
+  }
+}
+
+/*
+ * Sec. 2 (last paragraph) and Sec. 3: the copies of the fields that the
+ * particles see. Psi_E is applied to the transverse E components (Ex, Ey) and
+ * Psi_B to every other component (Ez, Bx, By, Bz); the 3D rule is used in 2D
+ * too (reading). Then the gather-side share of the digital filter. The Yee
+ * fields themselves are never modified.
+ * out[0..5] receive Ex, Ey, Ez, Bx, By, Bz copies.
+ */
+void orc_gather_copies(const orc_params* p, const orc_fields* F, double* out[6]) {
+  long ncell = (long)p->nx * p->ny * p->nz;
+  const double* src[6] = {F->ex, F->ey, F->ez, F->bx, F->by, F->bz};
+  for (int c = 0; c < 6; ++c) {
+    memcpy(out[c], src[c], sizeof(double) * ncell);
+    orc_conv_axis(p, out[c], 2, c < 2 ? p->psi_e : p->psi_b, 4);
+    if (p->f_targets & 2) orc_filter(p, out[c]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Yee solver (standard staggering, periodic)                                */
+/* ------------------------------------------------------------------------ */
+/* B -= h curl E */
+void orc_yee_b(const orc_params* p, orc_fields* F, double h) {
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        int ip = wrap(i + 1, p->nx), jp = wrap(j + 1, p->ny), kp = wrap(k + 1, p->nz);
+        long c = idx3(p, i, j, k);
+        double cex = (F->ez[idx3(p, i, jp, k)] - F->ez[c]) / p->dy - (F->ey[idx3(p, i, j, kp)] - F->ey[c]) / p->dz;
+        double cey = (F->ex[idx3(p, i, j, kp)] - F->ex[c]) / p->dz - (F->ez[idx3(p, ip, j, k)] - F->ez[c]) / p->dx;
+        double cez = (F->ey[idx3(p, ip, j, k)] - F->ey[c]) / p->dx - (F->ex[idx3(p, i, jp, k)] - F->ex[c]) / p->dy;
+        F->bx[c] -= h * cex;
+        F->by[c] -= h * cey;
+        F->bz[c] -= h * cez;
+      }
+}
+
+/* E += h (curl B - J) */
+void orc_yee_e(const orc_params* p, orc_fields* F, double h) {
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        int im = wrap(i - 1, p->nx), jm = wrap(j - 1, p->ny), km = wrap(k - 1, p->nz);
+        long c = idx3(p, i, j, k);
+        double cbx = (F->bz[c] - F->bz[idx3(p, i, jm, k)]) / p->dy - (F->by[c] - F->by[idx3(p, i, j, km)]) / p->dz;
+        double cby = (F->bx[c] - F->bx[idx3(p, i, j, km)]) / p->dz - (F->bz[c] - F->bz[idx3(p, im, j, k)]) / p->dx;
+        double cbz = (F->by[c] - F->by[idx3(p, im, j, k)]) / p->dx - (F->bx[c] - F->bx[idx3(p, i, jm, k)]) / p->dy;
+        F->ex[c] += h * (cbx - F->jx[c]);
+        F->ey[c] += h * (cby - F->jy[c]);
+        F->ez[c] += h * (cbz - F->jz[c]);
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Particle shapes and field gather (Sec. 2 Eq. 3-4; Sec. 3 last paragraph)  */
+/* ------------------------------------------------------------------------ */
+/* Linear spline S1(d) = max(0, 1-|d|). */
+static double S1(double d) {
+  double a = 1.0 - fabs(d);
+  return a > 0.0 ? a : 0.0;
+}
+
+/*
+ * Interpolate one component at grid-unit position (x[0..2]) with stagger
+ * st[axis] (0: nodes at integers, 1: nodes at half-integers) and spline order
+ * ord[axis] (1: S1 on the two nearest nodes, 0: S0, the width-1 box, i.e. the
+ * one node whose box [node-1/2, node+1/2) holds the position).
+ * Galerkin: order 0 along each direction in which the component is half
+ * staggered, order 1 along the others (the ratio of Eq. 3 to Eq. 4 is s/sin s,
+ * the ratio of the S0 and S1 transforms). Uniform: order 1 everywhere.
+ */
+static double gather1(const orc_params* p, const double* F, const double x[3], const int st[3], const int ord[3]) {
+  int n[3] = {p->nx, p->ny, p->nz};
+  int base[3], cnt[3];
+  double wt[3][2];
+  for (int a = 0; a < 3; ++a) {
+    if (a == 1 && p->ndim == 2) {
+      base[a] = 0;
+      cnt[a] = 1;
+      wt[a][0] = 1.0;
+      continue;
+    }
+    double xs = x[a] - 0.5 * st[a]; /* coordinate in units of this component's node lattice */
+    if (ord[a] == 1) {
+      double fl = floor(xs);
+      base[a] = (int)fl;
+      cnt[a] = 2;
+      wt[a][0] = S1(xs - fl);
+      wt[a][1] = S1(xs - (fl + 1.0));
+    } else {
+      base[a] = (int)floor(xs + 0.5);
+      cnt[a] = 1;
+      wt[a][0] = 1.0;
+    }
+  }
+  double acc = 0.0;
+  for (int c = 0; c < cnt[2]; ++c)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int a = 0; a < cnt[0]; ++a) {
+        long id = idx3(p, wrap(base[0] + a, n[0]), wrap(base[1] + b, n[1]), wrap(base[2] + c, n[2]));
+        acc += wt[0][a] * wt[1][b] * wt[2][c] * F[id];
+      }
+  return acc;
+}
+
+/* Stagger of Ex, Ey, Ez, Bx, By, Bz along x, y, z. */
+static const int STAG[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+/* Gather the six components from field arrays G[6] at particle position. */
+void orc_gather_point(const orc_params* p, double* const G[6], double x, double y, double z, double out[6]) {
+  double pos[3] = {x, y, z};
+  for (int c = 0; c < 6; ++c) {
+    int ord[3];
+    for (int a = 0; a < 3; ++a) ord[a] = (p->scheme == ORC_GALERKIN) ? 1 - STAG[c][a] : 1;
+    out[c] = gather1(p, G[c], pos, STAG[c], ord);
+  }
+}
+
+void orc_gather(const orc_params* p, double* const G[6], const double* x, const double* y, const double* z, long n,
+                double* out6[6]) {
+  for (long i = 0; i < n; ++i) {
+    double o[6];
+    orc_gather_point(p, G, x[i], p->ndim == 3 ? y[i] : 0.0, z[i], o);
+    for (int c = 0; c < 6; ++c) out6[c][i] = o[c];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Relativistic Boris push (Boris 1970; the paper does not state its pusher) */
+/* ------------------------------------------------------------------------ */
+void orc_boris(double q, double dt, const double E[3], const double B[3], double u[3]) {
+  double h = 0.5 * q * dt; /* q dt / (2 m), m = 1 */
+  double um[3] = {u[0] + h * E[0], u[1] + h * E[1], u[2] + h * E[2]};
+  double g = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+  double t[3] = {h * B[0] / g, h * B[1] / g, h * B[2] / g};
+  double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double s[3] = {2.0 * t[0] / (1.0 + tt), 2.0 * t[1] / (1.0 + tt), 2.0 * t[2] / (1.0 + tt)};
+  double up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]), um[1] + (um[2] * t[0] - um[0] * t[2]),
+                  um[2] + (um[0] * t[1] - um[1] * t[0])};
+  double upl[3] = {um[0] + (up[1] * s[2] - up[2] * s[1]), um[1] + (up[2] * s[0] - up[0] * s[2]),
+                   um[2] + (up[0] * s[1] - up[1] * s[0])};
+  for (int a = 0; a < 3; ++a) u[a] = upl[a] + h * E[a];
+}
+
+void orc_boris_many(const double* q, double dt, double* const E3[3], double* const B3[3], double* ux, double* uy,
+                    double* uz, long n) {
+  for (long i = 0; i < n; ++i) {
+    double E[3] = {E3[0][i], E3[1][i], E3[2][i]}, B[3] = {B3[0][i], B3[1][i], B3[2][i]};
+    double u[3] = {ux[i], uy[i], uz[i]};
+    orc_boris(q[i], dt, E, B, u);
+    ux[i] = u[0];
+    uy[i] = u[1];
+    uz[i] = u[2];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Esirkepov current deposition (Esirkepov 2001; cited in Sec. 2)            */
+/* ------------------------------------------------------------------------ */
+/*
+ * Charge density at node (i,j,k): rho = sum q w S1 S1 (S1) / dV, dV = dx dy dz.
+ * The weights W satisfy S1(x1)S1(z1) - S1(x0)S1(z0) = Wx + Wz (2D) and the
+ * currents follow from discrete continuity,
+ *   J_a(node + 1/2 e_a) - J_a(node - 1/2 e_a) = -(q w d_a / (dV dt)) W_a(node),
+ * summed from a node left of the footprint where J = 0. x0, x1 are unwrapped
+ * positions (grid units) before and after the move.
+ */
+#define FP 6 /* footprint window: enough nodes for |x1 - x0| < 1 */
+
+void orc_deposit_2d(const orc_params* p, orc_fields* F, double x0, double z0, double x1, double z1, double vy,
+                    double qw) {
+  double dV = p->dx * p->dy * p->dz;
+  int ia = (int)floor(fmin(x0, x1)) - 1;
+  int ka = (int)floor(fmin(z0, z1)) - 1;
+  double S0x[FP], dSx[FP], S0z[FP], dSz[FP];
+  for (int a = 0; a < FP; ++a) {
+    S0x[a] = S1((ia + a) - x0);
+    dSx[a] = S1((ia + a) - x1) - S0x[a];
+    S0z[a] = S1((ka + a) - z0);
+    dSz[a] = S1((ka + a) - z1) - S0z[a];
+  }
+  double cx = -qw * p->dx / (dV * p->dt);
+  double cz = -qw * p->dz / (dV * p->dt);
+  double cy = qw * vy / dV;
+  for (int b = 0; b < FP; ++b) { /* Jx(i+1/2, k): running sum over i */
+    double acc = 0.0;
+    for (int a = 0; a < FP; ++a) {
+      acc += dSx[a] * (S0z[b] + 0.5 * dSz[b]);
+      if (acc != 0.0) F->jx[idx3(p, wrap(ia + a, p->nx), 0, wrap(ka + b, p->nz))] += cx * acc;
+    }
+  }
+  for (int a = 0; a < FP; ++a) { /* Jz(i, k+1/2): running sum over k */
+    double acc = 0.0;
+    for (int b = 0; b < FP; ++b) {
+      acc += dSz[b] * (S0x[a] + 0.5 * dSx[a]);
+      if (acc != 0.0) F->jz[idx3(p, wrap(ia + a, p->nx), 0, wrap(ka + b, p->nz))] += cz * acc;
+    }
+  }
+  for (int b = 0; b < FP; ++b) /* Jy(i, k): out-of-plane weight */
+    for (int a = 0; a < FP; ++a) {
+      double wy = S0x[a] * S0z[b] + 0.5 * dSx[a] * S0z[b] + 0.5 * S0x[a] * dSz[b] + dSx[a] * dSz[b] / 3.0;
+      if (wy != 0.0) F->jy[idx3(p, wrap(ia + a, p->nx), 0, wrap(ka + b, p->nz))] += cy * wy;
+    }
+}
+
+void orc_deposit_3d(const orc_params* p, orc_fields* F, const double r0[3], const double r1[3], double qw) {
+  double dV = p->dx * p->dy * p->dz;
+  int n[3] = {p->nx, p->ny, p->nz};
+  double d[3] = {p->dx, p->dy, p->dz};
+  int lo[3];
+  double S0[3][FP], dS[3][FP];
+  for (int ax = 0; ax < 3; ++ax) {
+    lo[ax] = (int)floor(fmin(r0[ax], r1[ax])) - 1;
+    for (int a = 0; a < FP; ++a) {
+      S0[ax][a] = S1((lo[ax] + a) - r0[ax]);
+      dS[ax][a] = S1((lo[ax] + a) - r1[ax]) - S0[ax][a];
+    }
+  }
+  double* J[3] = {F->jx, F->jy, F->jz};
+  for (int ax = 0; ax < 3; ++ax) {
+    int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3; /* the two transverse axes */
+    double c = -qw * d[ax] / (dV * p->dt);
+    for (int t2 = 0; t2 < FP; ++t2)
+      for (int t1 = 0; t1 < FP; ++t1) {
+        /* transverse factor of W_ax: S0 S0 + dS S0/2 + S0 dS/2 + dS dS/3 */
+        double tr = S0[b1][t1] * S0[b2][t2] + 0.5 * dS[b1][t1] * S0[b2][t2] + 0.5 * S0[b1][t1] * dS[b2][t2] +
+                    dS[b1][t1] * dS[b2][t2] / 3.0;
+        double acc = 0.0;
+        for (int a = 0; a < FP; ++a) {
+          acc += dS[ax][a] * tr;
+          if (acc == 0.0) continue;
+          int node[3];
+          node[ax] = lo[ax] + a;
+          node[b1] = lo[b1] + t1;
+          node[b2] = lo[b2] + t2;
+          J[ax][idx3(p, wrap(node[0], n[0]), wrap(node[1], n[1]), wrap(node[2], n[2]))] += c * acc;
+        }
+      }
+  }
+}
+
+/* Node charge density with S1 shapes (used by the continuity and Gauss checks). */
+void orc_rho(const orc_params* p, const orc_particles* P, double* rho) {
+  long ncell = (long)p->nx * p->ny * p->nz;
+  double dV = p->dx * p->dy * p->dz;
+  memset(rho, 0, sizeof(double) * ncell);
+  for (long m = 0; m < P->n; ++m) {
+    double r[3] = {P->x[m], p->ndim == 3 ? P->y[m] : 0.0, P->z[m]};
+    int n[3] = {p->nx, p->ny, p->nz};
+    int b[3];
+    double wt[3][2];
+    for (int a = 0; a < 3; ++a) {
+      double fl = floor(r[a]);
+      b[a] = (int)fl;
+      wt[a][0] = S1(r[a] - fl);
+      wt[a][1] = S1(r[a] - (fl + 1.0));
+    }
+    int cy = p->ndim == 3 ? 2 : 1;
+    for (int c = 0; c < 2; ++c)
+      for (int bb = 0; bb < cy; ++bb)
+        for (int a = 0; a < 2; ++a) {
+          double wy = p->ndim == 3 ? wt[1][bb] : 1.0;
+          rho[idx3(p, wrap(b[0] + a, n[0]), wrap(b[1] + bb, n[1]), wrap(b[2] + c, n[2]))] +=
+              P->q[m] * P->w[m] * wt[0][a] * wy * wt[2][c] / dV;
+        }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One full time step, in the order the paper's loop implies                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * State in: x^n, u^{n-1/2}, E^n, B^n. State out: x^{n+1}, u^{n+1/2}, E^{n+1},
+ * B^{n+1}. J holds J^{n+1/2} (filtered) on return. B is advanced in two half
+ * steps around the E update, so that the particles see B at integer time (the
+ * cos(k_z dt/2) factor of Eq. 3-5).
+ */
+void orc_step(const orc_params* p, orc_fields* F, orc_particles* P) {
+  long ncell = (long)p->nx * p->ny * p->nz;
+  double* G[6];
+  for (int c = 0; c < 6; ++c) G[c] = (double*)malloc(sizeof(double) * ncell);
+  /* 1. corrected and filtered copies of the fields seen by the particles */
+  orc_gather_copies(p, F, G);
+  memset(F->jx, 0, sizeof(double) * ncell);
+  memset(F->jy, 0, sizeof(double) * ncell);
+  memset(F->jz, 0, sizeof(double) * ncell);
+  double nn[3] = {p->nx, p->ny, p->nz};
+  for (long m = 0; m < P->n; ++m) {
+    double x0 = P->x[m], y0 = p->ndim == 3 ? P->y[m] : 0.0, z0 = P->z[m];
+    /* 2. gather at x^n */
+    double f[6];
+    orc_gather_point(p, G, x0, y0, z0, f);
+    /* 3. Boris u^{n-1/2} -> u^{n+1/2} */
+    double u[3] = {P->ux[m], P->uy[m], P->uz[m]};
+    orc_boris(P->q[m], p->dt, f, f + 3, u);
+    P->ux[m] = u[0];
+    P->uy[m] = u[1];
+    P->uz[m] = u[2];
+    /* 4. move */
+    double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double x1 = x0 + p->dt * u[0] / gam / p->dx;
+    double y1 = y0 + p->dt * u[1] / gam / p->dy;
+    double z1 = z0 + p->dt * u[2] / gam / p->dz;
+    /* 5. Esirkepov deposition of J^{n+1/2} */
+    double qw = P->q[m] * P->w[m];
+    if (p->ndim == 2) {
+      orc_deposit_2d(p, F, x0, z0, x1, z1, u[1] / gam, qw);
+    } else {
+      double r0[3] = {x0, y0, z0}, r1[3] = {x1, y1, z1};
+      orc_deposit_3d(p, F, r0, r1, qw);
+    }
+    P->x[m] = wrapf(x1, nn[0]);
+    if (p->ndim == 3) P->y[m] = wrapf(y1, nn[1]);
+    P->z[m] = wrapf(z1, nn[2]);
+  }
+  /* 6. current filter */
+  if (p->f_targets & 1) {
+    orc_filter(p, F->jx);
+    orc_filter(p, F->jy);
+    orc_filter(p, F->jz);
+  }
+  /* 7. Yee: B half step, E full step with J, B half step */
+  orc_yee_b(p, F, 0.5 * p->dt);
+  orc_yee_e(p, F, p->dt);
+  orc_yee_b(p, F, 0.5 * p->dt);
+  for (int c = 0; c < 6; ++c) free(G[c]);
+}
+
+void orc_run(const orc_params* p, orc_fields* F, orc_particles* P, int nsteps) {
+  for (int s = 0; s < nsteps; ++s) orc_step(p, F, P);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics: energies (FP64)                                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * out[0] W_E = 1/2 sum E^2 dV, out[1] W_B = 1/2 sum B^2 dV,
+ * out[2] W_perp = 1/2 sum (Ex^2+Ey^2+Bx^2+By^2) dV,
+ * out[3] K = sum w (gamma - 1) (m = c = 1; u is at the half step),
+ * out[4] W_E + W_B + K.
+ */
+void orc_energy(const orc_params* p, const orc_fields* F, const orc_particles* P, double out[5]) {
+  long ncell = (long)p->nx * p->ny * p->nz;
+  double dV = p->dx * p->dy * p->dz;
+  double we = 0, wb = 0, wp = 0, k = 0;
+  for (long c = 0; c < ncell; ++c) {
+    double ex2 = F->ex[c] * F->ex[c], ey2 = F->ey[c] * F->ey[c], ez2 = F->ez[c] * F->ez[c];
+    double bx2 = F->bx[c] * F->bx[c], by2 = F->by[c] * F->by[c], bz2 = F->bz[c] * F->bz[c];
+    we += ex2 + ey2 + ez2;
+    wb += bx2 + by2 + bz2;
+    wp += ex2 + ey2 + bx2 + by2;
+  }
+  for (long m = 0; m < P->n; ++m) {
+    double u2 = P->ux[m] * P->ux[m] + P->uy[m] * P->uy[m] + P->uz[m] * P->uz[m];
+    k += P->w[m] * u2 / (sqrt(1.0 + u2) + 1.0); /* gamma - 1 without cancellation */
+  }
+  out[0] = 0.5 * we * dV;
+  out[1] = 0.5 * wb * dV;
+  out[2] = 0.5 * wp * dV;
+  out[3] = k;
+  out[4] = out[0] + out[1] + out[3];
+}
+
+/* Divergence of E at nodes (for the Gauss-law check). */
+void orc_div_e(const orc_params* p, const orc_fields* F, double* out) {
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        long c = idx3(p, i, j, k);
+        out[c] = (F->ex[c] - F->ex[idx3(p, wrap(i - 1, p->nx), j, k)]) / p->dx +
+                 (F->ey[c] - F->ey[idx3(p, i, wrap(j - 1, p->ny), k)]) / p->dy +
+                 (F->ez[c] - F->ez[idx3(p, i, j, wrap(k - 1, p->nz))]) / p->dz;
+      }
+}
+
+/* Divergence of B at cell centres (i+1/2, j+1/2, k+1/2). */
+void orc_div_b(const orc_params* p, const orc_fields* F, double* out) {
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        long c = idx3(p, i, j, k);
+        out[c] = (F->bx[idx3(p, wrap(i + 1, p->nx), j, k)] - F->bx[c]) / p->dx +
+                 (F->by[idx3(p, i, wrap(j + 1, p->ny), k)] - F->by[c]) / p->dy +
+                 (F->bz[idx3(p, i, j, wrap(k + 1, p->nz))] - F->bz[c]) / p->dz;
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the beam recipe     */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Uniform on (0,1) from 32 random bits: (r + 1/2) 2^-32, exact in FP64. */
+static double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
+
+typedef struct {
+  int ppc;              /* lattice points per cell per species */
+  double gamma;         /* drift Lorentz factor along +z */
+  double omega_p_dz;    /* total (both species) plasma frequency times dz / c */
+  double jitter;        /* uniform jitter half-width, cells */
+  double u_th;          /* Gaussian thermal spread of each u component */
+  double sigma_perp;    /* > 0: Gaussian transverse weight profile, cells (3D) */
+  uint64_t seed;
+} orc_beam;
+
+/* Lattice of ppc points per cell: counts per axis, as even as possible, z last. */
+void orc_lattice_dims(int ndim, int ppc, int out[3]) {
+  out[0] = out[1] = out[2] = 1;
+  if (ndim == 2) {
+    int best = 1;
+    for (int d = 1; d * d <= ppc; ++d)
+      if (ppc % d == 0) best = d;
+    out[0] = best;
+    out[2] = ppc / best;
+  } else {
+    int bx = 1, by = 1;
+    double bscore = 1e30;
+    for (int a = 1; a <= ppc; ++a)
+      for (int b = a; a * b <= ppc; ++b) {
+        if (ppc % (a * b)) continue;
+        int c = ppc / (a * b);
+        if (c < b) continue;
+        double score = (double)(c - a);
+        if (score < bscore) {
+          bscore = score;
+          bx = a;
+          by = b;
+        }
+      }
+    out[0] = bx;
+    out[1] = by;
+    out[2] = ppc / (bx * by);
+  }
+}
+
+/*
+ * Beam initial state (the synthetic stand-in for the paper's drifting beam):
+ * per cell and lattice point one electron (q = -1) and one positron (q = +1)
+ * at the same jittered position (so rho = 0 and E = B = 0 is a consistent
+ * start), each with its own thermal draw u = (N*u_th, N*u_th, u0 + N*u_th),
+ * u0 = sqrt(gamma^2 - 1). Particle id = (cell*ppc + point)*2 + species, and
+ * the arrays are filled in id order. Random numbers: Philox4x32-10 with key
+ * (seed lo, seed hi) and counter (point id lo, point id hi, stream, 0);
+ * stream 0 gives the jitter (outputs 0, 1, 2 for x, y, z), streams 1 and 2
+ * the thermal draws of species 0 and 1 by Box-Muller on outputs (0,1), (2,3).
+ * Weight w = omega_p^2 dV / (2 ppc), times exp(-r_perp^2 / (2 sigma^2)) with
+ * r_perp measured from the box axis (nx/2, ny/2) when sigma_perp > 0.
+ */
+void orc_init_beam(const orc_params* p, const orc_beam* b, orc_particles* P) {
+  int L[3];
+  orc_lattice_dims(p->ndim, b->ppc, L);
+  double u0 = sqrt(b->gamma * b->gamma - 1.0);
+  double wp = b->omega_p_dz / p->dz;
+  double w0 = wp * wp * p->dx * p->dy * p->dz / (2.0 * b->ppc);
+  uint32_t key[2] = {(uint32_t)(b->seed & 0xffffffffu), (uint32_t)(b->seed >> 32)};
+  long ncell = (long)p->nx * p->ny * p->nz;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long c = 0; c < ncell; ++c) {
+    int i = (int)(c % p->nx), j = (int)((c / p->nx) % p->ny), k = (int)(c / ((long)p->nx * p->ny));
+    for (int l = 0; l < b->ppc; ++l) {
+      int lx = l % L[0], ly = (l / L[0]) % L[1], lz = l / (L[0] * L[1]);
+      uint64_t pid = (uint64_t)c * b->ppc + l;
+      uint32_t ctr[4] = {(uint32_t)(pid & 0xffffffffu), (uint32_t)(pid >> 32), 0, 0};
+      uint32_t r[4];
+      orc_philox4x32_10(ctr, key, r);
+      double x = i + (lx + 0.5) / L[0] + b->jitter * (2.0 * u01(r[0]) - 1.0);
+      double y = p->ndim == 3 ? j + (ly + 0.5) / L[1] + b->jitter * (2.0 * u01(r[1]) - 1.0) : 0.0;
+      double z = k + (lz + 0.5) / L[2] + b->jitter * (2.0 * u01(r[2]) - 1.0);
+      x = wrapf(x, p->nx);
+      if (p->ndim == 3) y = wrapf(y, p->ny);
+      z = wrapf(z, p->nz);
+      double w = w0;
+      if (b->sigma_perp > 0) {
+        double rx = x - 0.5 * p->nx, ry = p->ndim == 3 ? y - 0.5 * p->ny : 0.0;
+        w = w0 * exp(-(rx * rx + ry * ry) / (2.0 * b->sigma_perp * b->sigma_perp));
+      }
+      for (int s = 0; s < 2; ++s) {
+        long m = (long)pid * 2 + s;
+        ctr[2] = (uint32_t)(1 + s);
+        orc_philox4x32_10(ctr, key, r);
+        double ra = sqrt(-2.0 * log(u01(r[0]))), ta = two_pi * u01(r[1]);
+        double rb = sqrt(-2.0 * log(u01(r[2]))), tb = two_pi * u01(r[3]);
+        P->x[m] = x;
+        if (p->ndim == 3) P->y[m] = y;
+        P->z[m] = z;
+        P->ux[m] = b->u_th * ra * cos(ta);
+        P->uy[m] = b->u_th * ra * sin(ta);
+        P->uz[m] = u0 + b->u_th * rb * cos(tb);
+        P->w[m] = w;
+        P->q[m] = s == 0 ? -1.0 : 1.0;
+      }
+    }
+  }
+}

@@ -1,0 +1,196 @@
+/*
+ * pic.h -- C ABI of a GB300 (sm_103a) implementation of the stabilised FDTD-Esirkepov
+ * particle-in-cell time step of Godfrey & Vay, "Suppressing the Numerical Cherenkov
+ * Instability in FDTD PIC Codes" (arXiv 1401.0838).
+ *
+ * One step (Sec. 2 and Sec. 3 of the paper, in the order its loop implies):
+ *   1. copies of E and B as seen by the particles: Psi_E(D_z) on Ex, Ey and Psi_B(D_z) on
+ *      Ez, Bx, By, Bz (Sec. 2, last paragraph), D = -(1,-2,1)/4 along z, then the gather share
+ *      of the binomial + compensation filter (Sec. 3, Eq. 6; Sec. 4);
+ *   2. gather at x^n with the Galerkin or Uniform shapes (Sec. 2, Eq. 3-4);
+ *   3. relativistic Boris push u^{n-1/2} -> u^{n+1/2};
+ *   4. move x^n -> x^{n+1};
+ *   5. Esirkepov current deposition J^{n+1/2} (cited in Sec. 2);
+ *   6. current filter (Eq. 6 / Sec. 4);
+ *   7. Yee update: B half step, E full step with -J, B half step.
+ *
+ * Conventions
+ *   - Units c = eps0 = mu0 = 1; particle mass 1; charges -1 (species 0, electrons) and
+ *     +1 (species 1, positrons). Positions are in grid units.
+ *   - Fields live on the standard periodic Yee mesh; element [(k*ny + j)*nx + i] of a field
+ *     array holds Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2), Bx(i,j+1/2,k+1/2),
+ *     By(i+1/2,j,k+1/2), Bz(i+1/2,j+1/2,k). A 2D run is x-z with ny = 1.
+ *   - Every function returns PIC_OK (0) or a negative PIC_E_* code; pic_last_error() gives text.
+ *   - The handle owns all device memory it allocates. Caller arrays are only read or written
+ *     during the call (device-side copies are ordered on the handle's stream) and never kept.
+ *   - pic_step and the state copies are asynchronous on the handle's stream. Errors raised by
+ *     kernels (bin overflow, a wait that timed out) are sticky and reported by the next
+ *     pic_sync, pic_energy or pic_get_state.
+ *   - A handle is not thread safe; different handles are independent.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_E_ARG (-1)        /* invalid argument or configuration */
+#define PIC_E_CFL (-2)        /* dt violates the Yee Courant limit */
+#define PIC_E_SINGULAR (-3)   /* rational interpolation singular / ill-conditioned */
+#define PIC_E_OOM (-4)        /* device or host allocation failed */
+#define PIC_E_CUDA (-5)       /* a CUDA runtime call failed */
+#define PIC_E_TIMEOUT (-6)    /* a bounded device wait gave up */
+#define PIC_E_NONFINITE (-7)  /* NaN/Inf found in the state */
+#define PIC_E_OVERFLOW (-8)   /* a cell's particle bin overflowed (raise bin_capacity) */
+#define PIC_E_STATE (-9)      /* call not valid in the handle's current state */
+
+#define PIC_GALERKIN 0
+#define PIC_UNIFORM 1
+#define PIC_MOMENTUM 2 /* multiplier only (pic_compute_correction_coeffs); no gather yet */
+
+#define PIC_FP32 0
+#define PIC_FP64 1
+
+#define PIC_FILTER_J 1      /* filter the deposited current */
+#define PIC_FILTER_GATHER 2 /* filter the field copies seen by the particles */
+
+#define PIC_HOST 0
+#define PIC_DEVICE 1
+
+typedef struct pic_handle pic_handle;
+
+/* Run configuration. pic_config_default() fills the values of the paper's 2D beam problem. */
+typedef struct pic_config {
+  int ndim;                 /* 2 (x-z, three velocity components) or 3 */
+  int nx, ny, nz;           /* cells per direction; ny is forced to 1 in 2D */
+  double dx, dy, dz, dt;    /* cell sizes and time step (c = 1); dy forced to 1 in 2D */
+  double gamma;             /* Lorentz factor of the beam drift along +z */
+  int scheme;               /* PIC_GALERKIN or PIC_UNIFORM field gather */
+  int shape_order;          /* 1 (linear particle shapes) */
+  int precision;            /* PIC_FP32 or PIC_FP64 (fields, particles and kernels) */
+  int ppc_per_species;      /* lattice points per cell per species of the initial beam */
+  double omega_p_dz;        /* total plasma frequency (both species) times dz / c */
+  double jitter;            /* uniform position jitter half-width, cells */
+  double u_th;              /* Gaussian spread of each momentum component (u = gamma v) */
+  double sigma_perp;        /* > 0: per-particle weight exp(-r_perp^2/(2 sigma^2)), cells */
+  int filter_nbin;          /* bilinear passes per direction per side (paper's WARP runs: 1) */
+  int filter_ncomp;         /* compensation passes per direction per side (paper: 1) */
+  double filter_comp_alpha; /* compensation centre weight a: taps (-(a-1)/2, a, -(a-1)/2) */
+  int filter_targets;       /* PIC_FILTER_J | PIC_FILTER_GATHER */
+  unsigned long long seed;  /* Philox4x32-10 key of the initial beam */
+  int init_beam;            /* 1: pic_create fills the seeded beam; 0: start empty */
+  int bin_capacity;         /* particle slots per cell per species; 0: automatic */
+  int track_ids;            /* 1: carry a 32-bit id per particle (for tests) */
+} pic_config;
+
+/* Energies, all FP64 sums over the whole grid / all particles (c = 1, m = 1). */
+typedef struct pic_energy_t {
+  double w_e;    /* 1/2 sum E^2 dV */
+  double w_b;    /* 1/2 sum B^2 dV (B at integer time) */
+  double w_perp; /* 1/2 sum (Ex^2 + Ey^2 + Bx^2 + By^2) dV: the growth-rate observable */
+  double k;      /* sum w (gamma - 1), u at the last half step */
+  double total;  /* w_e + w_b + k */
+  long long np;  /* number of particles */
+} pic_energy_t;
+
+/*
+ * State in the handle's native layout. Element type of the void* arrays is float (PIC_FP32
+ * handle) or double (PIC_FP64). `where` says whether every pointer is host or device memory.
+ * Particle i: cell index cell[i] = (k*ny + j)*nx + i, species[i] in {0, 1}, position
+ * (i + ox, j + oy, k + oz) with offsets in [0, 1), momentum u = (dux, duy, u_drift + duz) with
+ * u_drift = sqrt(gamma^2 - 1).
+ */
+typedef struct pic_state {
+  int where;                        /* PIC_HOST or PIC_DEVICE */
+  void *ex, *ey, *ez, *bx, *by, *bz; /* nx*ny*nz each; NULL skips that component */
+  long long np;                     /* set: particle count; get: in = array capacity, out = count */
+  int* cell;
+  int* species;
+  void *ox, *oy, *oz;               /* oy unused (may be NULL) in 2D */
+  void *dux, *duy, *duz;
+  void* w;                          /* per-particle weights; NULL: the uniform beam weight */
+  unsigned int* id;                 /* optional (NULL); kept only when track_ids = 1 */
+  double u_drift;                   /* filled by pic_get_state */
+} pic_state;
+
+/* Fills *cfg with the defaults: 2D 64x128, dx = dz = 1, dt = 0.5, gamma = 130, Galerkin, FP64,
+ * 4 particles/cell/species, omega_p dz = 0.3868, jitter 0.1, u_th 1e-4, filter (1, 1, a = 3)
+ * on J and on the gather copies, seed 1, init_beam 1. */
+void pic_config_default(pic_config* cfg);
+
+/*
+ * Correction coefficients (Sec. 2, Eq. 3-4 and the rational interpolation that follows):
+ * the (4,4) rational interpolant Psi_E(xi)/Psi_B(xi), xi = sin^2(k_z dz/2), of the Galerkin
+ * (Eq. 3) or Uniform (Eq. 4) multiplier (or Eq. 5 for PIC_MOMENTUM) at alpha = c dt / dz, on the
+ * nine nodes xi_j = j/8, with Psi_B(0) = 1. Coefficients are in powers of xi, constant first.
+ * Host only, FP64. Returns PIC_E_SINGULAR when the 9x9 system is singular and the multiplier is
+ * not constant, when its condition estimate exceeds 1e12, or when Psi_B has a zero on [0, 1];
+ * when the multiplier is identically 1 (Uniform at alpha = 1/2) it returns Psi_E = Psi_B = 1.
+ */
+int pic_compute_correction_coeffs(int scheme, double alpha, double psi_e[5], double psi_b[5]);
+
+/* Validates cfg (PIC_E_ARG, PIC_E_CFL: dt >= 1/sqrt(sum 1/d^2)), allocates device memory,
+ * fills the seeded beam (Philox4x32-10, counter = lattice point) when cfg->init_beam, zero fields.
+ * The correction starts off (Psi = 1); set it with pic_set_correction_stencil. */
+int pic_create(const pic_config* cfg, pic_handle** out);
+
+/* Uses `stream` (a cudaStream_t; NULL = the handle's own stream) for all later work. */
+int pic_set_stream(pic_handle* h, void* stream);
+
+/* Sets the Psi_E / Psi_B polynomial coefficients (Sec. 2), powers of xi, constant first.
+ * Both NULL turns the correction off (Psi = 1). The 9-tap z-stencils sum_n a_n D^n are built on
+ * the host in FP64 and combined with the gather filter taps. */
+int pic_set_correction_stencil(pic_handle* h, const double psi_e[5], const double psi_b[5]);
+
+/* Advances nsteps >= 0 time steps (asynchronous on the handle's stream). */
+int pic_step(pic_handle* h, int nsteps);
+
+/* Waits for the handle's stream and returns any sticky kernel error. */
+int pic_sync(pic_handle* h);
+
+/* Energies (FP64 device reductions); synchronises the stream. */
+int pic_energy(pic_handle* h, pic_energy_t* out);
+
+/* Current number of particles (synchronises). */
+int pic_num_particles(pic_handle* h, long long* np);
+
+/* Copies the state out (s->np in: capacity of the particle arrays; PIC_E_ARG when too small,
+ * with s->np set to the count needed). With every particle pointer NULL only the non-NULL fields
+ * are copied and s->np returns the particle count. Particles come out grouped by species, then by
+ * cell. Synchronises. */
+int pic_get_state(pic_handle* h, pic_state* s);
+
+/* Replaces the state: the fields that are non-NULL, and all particles (re-binned by cell on the
+ * device; offsets outside [0, 1) are folded into the cell index, periodically). s->np = -1 leaves
+ * the particles untouched; s->np = 0 removes them all. Without per-particle weights (sigma_perp
+ * <= 0) every particle carries the beam weight (omega_p_dz/dz)^2 dx dy dz / (2 ppc_per_species). */
+int pic_set_state(pic_handle* h, const pic_state* s);
+
+/* Test hooks. Copy out the six field copies the particles saw in the last step (after Psi and
+ * the gather filter; order Ex Ey Ez Bx By Bz) or the three components of the (filtered) current
+ * J^{n+1/2} of the last step. `out` holds 6 (resp. 3) pointers of nx*ny*nz elements. */
+int pic_debug_gather_copies(pic_handle* h, int where, void* const* out6);
+int pic_debug_current(pic_handle* h, int where, void* const* out3);
+
+/* Maximum instability growth rate (Fig. 2/4 captions: from the transverse field energy):
+ * Gamma = 1/2 d ln W / dt by an FP64 least-squares fit over the window from the first sample
+ * two decades above the noise floor (median of log10 W over the first tenth of the samples) to
+ * the first later sample within one decade of the maximum; if that window has fewer than 5
+ * samples, the steepest window of max(5, n/5) samples after the first tenth. Host only. */
+int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_out, int* i0, int* i1);
+
+/* Frees everything the handle owns. NULL is a no-op. */
+void pic_destroy(pic_handle* h);
+
+/* Text of the last error on this handle (never NULL). */
+const char* pic_last_error(const pic_handle* h);
+
+/* Static text for a PIC_E_* code. */
+const char* pic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

@@ -1,0 +1,231 @@
+"""Thin Python binding of the C ABI in include/pic.h (argument marshalling only).
+
+Every function keeps the C name. Arrays are passed as raw pointers: numpy arrays (host) or torch
+tensors (device or pinned host). No step of the PIC method runs here; if the CUDA library is not
+built the import fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpic_gb300.so")
+
+PIC_OK = 0
+PIC_E_ARG, PIC_E_CFL, PIC_E_SINGULAR, PIC_E_OOM, PIC_E_CUDA = -1, -2, -3, -4, -5
+PIC_E_TIMEOUT, PIC_E_NONFINITE, PIC_E_OVERFLOW, PIC_E_STATE = -6, -7, -8, -9
+PIC_GALERKIN, PIC_UNIFORM, PIC_MOMENTUM = 0, 1, 2
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_FILTER_J, PIC_FILTER_GATHER = 1, 2
+PIC_HOST, PIC_DEVICE = 0, 1
+
+# every symbol the header declares
+EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", "pic_set_stream",
+           "pic_set_correction_stencil", "pic_step", "pic_sync", "pic_energy", "pic_num_particles",
+           "pic_get_state", "pic_set_state", "pic_debug_gather_copies", "pic_debug_current",
+           "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror")
+
+
+class pic_config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("scheme", ctypes.c_int), ("shape_order", ctypes.c_int),
+                ("precision", ctypes.c_int), ("ppc_per_species", ctypes.c_int), ("omega_p_dz", ctypes.c_double),
+                ("jitter", ctypes.c_double), ("u_th", ctypes.c_double), ("sigma_perp", ctypes.c_double),
+                ("filter_nbin", ctypes.c_int), ("filter_ncomp", ctypes.c_int), ("filter_comp_alpha", ctypes.c_double),
+                ("filter_targets", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("init_beam", ctypes.c_int),
+                ("bin_capacity", ctypes.c_int), ("track_ids", ctypes.c_int)]
+
+
+class pic_energy_t(ctypes.Structure):
+    _fields_ = [("w_e", ctypes.c_double), ("w_b", ctypes.c_double), ("w_perp", ctypes.c_double),
+                ("k", ctypes.c_double), ("total", ctypes.c_double), ("np", ctypes.c_longlong)]
+
+
+class pic_state(ctypes.Structure):
+    _fields_ = [("where", ctypes.c_int)] + [(n, ctypes.c_void_p) for n in ("ex", "ey", "ez", "bx", "by", "bz")] + \
+               [("np", ctypes.c_longlong), ("cell", ctypes.c_void_p), ("species", ctypes.c_void_p)] + \
+               [(n, ctypes.c_void_p) for n in ("ox", "oy", "oz", "dux", "duy", "duz", "w", "id")] + \
+               [("u_drift", ctypes.c_double)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpic_gb300.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_1401_0838_gb300.build` "
+                               "(no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, V, I, D = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        DP = P(ctypes.c_double)
+        L.pic_config_default.argtypes = [P(pic_config)]
+        L.pic_config_default.restype = None
+        L.pic_compute_correction_coeffs.argtypes = [I, D, DP, DP]
+        L.pic_create.argtypes = [P(pic_config), P(V)]
+        L.pic_set_stream.argtypes = [V, V]
+        L.pic_set_correction_stencil.argtypes = [V, DP, DP]
+        L.pic_step.argtypes = [V, I]
+        L.pic_sync.argtypes = [V]
+        L.pic_energy.argtypes = [V, P(pic_energy_t)]
+        L.pic_num_particles.argtypes = [V, P(ctypes.c_longlong)]
+        L.pic_get_state.argtypes = [V, P(pic_state)]
+        L.pic_set_state.argtypes = [V, P(pic_state)]
+        L.pic_debug_gather_copies.argtypes = [V, I, P(V)]
+        L.pic_debug_current.argtypes = [V, I, P(V)]
+        L.pic_fit_growth_rate.argtypes = [DP, DP, I, DP, P(I), P(I)]
+        L.pic_destroy.argtypes = [V]
+        L.pic_destroy.restype = None
+        L.pic_last_error.argtypes = [V]
+        L.pic_last_error.restype = ctypes.c_char_p
+        L.pic_strerror.argtypes = [I]
+        L.pic_strerror.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("pic_config_default", "pic_destroy", "pic_last_error", "pic_strerror"):
+                getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc != PIC_OK:
+        msg = lib().pic_strerror(rc).decode()
+        if h is not None:
+            detail = lib().pic_last_error(h).decode()
+            if detail:
+                msg = f"{msg}: {detail}"
+        raise PicError(rc, msg)
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+# ------------------------------------------------------------------------------------------------
+# C ABI, same names
+# ------------------------------------------------------------------------------------------------
+def pic_config_default(**overrides) -> pic_config:
+    c = pic_config()
+    lib().pic_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def pic_compute_correction_coeffs(scheme: int, alpha: float):
+    pe = (ctypes.c_double * 5)()
+    pb = (ctypes.c_double * 5)()
+    _check(lib().pic_compute_correction_coeffs(scheme, alpha, pe, pb))
+    return np.array(pe[:]), np.array(pb[:])
+
+
+def pic_create(cfg: pic_config):
+    h = ctypes.c_void_p()
+    _check(lib().pic_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def pic_set_stream(h, stream_ptr: int | None):
+    _check(lib().pic_set_stream(h, stream_ptr), h)
+
+
+def pic_set_correction_stencil(h, psi_e=None, psi_b=None):
+    pe = None if psi_e is None else (ctypes.c_double * 5)(*[float(v) for v in psi_e])
+    pb = None if psi_b is None else (ctypes.c_double * 5)(*[float(v) for v in psi_b])
+    _check(lib().pic_set_correction_stencil(h, pe, pb), h)
+
+
+def pic_step(h, nsteps: int = 1):
+    _check(lib().pic_step(h, int(nsteps)), h)
+
+
+def pic_sync(h):
+    _check(lib().pic_sync(h), h)
+
+
+def pic_energy(h) -> dict:
+    e = pic_energy_t()
+    _check(lib().pic_energy(h, ctypes.byref(e)), h)
+    return {"w_e": e.w_e, "w_b": e.w_b, "w_perp": e.w_perp, "k": e.k, "total": e.total, "np": e.np}
+
+
+def pic_num_particles(h) -> int:
+    n = ctypes.c_longlong()
+    _check(lib().pic_num_particles(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def make_state(where: int, fields=None, particles=None) -> pic_state:
+    """pic_state from dicts of arrays: fields {ex..bz}, particles {cell, species, ox, oy, oz, dux, duy, duz, w, id}."""
+    s = pic_state()
+    s.where = where
+    for n in ("ex", "ey", "ez", "bx", "by", "bz"):
+        setattr(s, n, _ptr((fields or {}).get(n)))
+    p = particles or {}
+    s.np = len(p["cell"]) if "cell" in p else 0
+    for n in ("cell", "species", "ox", "oy", "oz", "dux", "duy", "duz", "w", "id"):
+        setattr(s, n, _ptr(p.get(n)))
+    return s
+
+
+def pic_set_state(h, state: pic_state):
+    _check(lib().pic_set_state(h, ctypes.byref(state)), h)
+
+
+def pic_get_state(h, state: pic_state) -> pic_state:
+    _check(lib().pic_get_state(h, ctypes.byref(state)), h)
+    return state
+
+
+def pic_debug_gather_copies(h, where: int, outs):
+    arr = (ctypes.c_void_p * 6)(*[_ptr(o) for o in outs])
+    _check(lib().pic_debug_gather_copies(h, where, arr), h)
+
+
+def pic_debug_current(h, where: int, outs):
+    arr = (ctypes.c_void_p * 3)(*[_ptr(o) for o in outs])
+    _check(lib().pic_debug_current(h, where, arr), h)
+
+
+def pic_fit_growth_rate(t, w):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = ctypes.c_double()
+    i0 = ctypes.c_int()
+    i1 = ctypes.c_int()
+    DP = ctypes.POINTER(ctypes.c_double)
+    _check(lib().pic_fit_growth_rate(t.ctypes.data_as(DP), w.ctypes.data_as(DP), len(t), ctypes.byref(g),
+                                     ctypes.byref(i0), ctypes.byref(i1)))
+    return g.value, i0.value, i1.value
+
+
+def pic_destroy(h):
+    if h is not None:
+        lib().pic_destroy(h)
+
+
+def pic_last_error(h) -> str:
+    return lib().pic_last_error(h).decode()
+
+
+def pic_strerror(code: int) -> str:
+    return lib().pic_strerror(code).decode()

@@ -1,0 +1,672 @@
+// C ABI (include/pic.h): handle management, the per-step launch sequence, state import/export
+// and diagnostics. All arithmetic of the step runs in the CUDA kernels of k_fields.cu and
+// k_particles.cu; this file only allocates, marshals and orders launches on one stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "common.cuh"
+#include "host_math.h"
+#include "launch.h"
+
+using namespace picgb;
+
+struct pic_handle {
+  pic_config cfg;
+  size_t es = 8;  // element size of fields and particle reals
+  cudaStream_t own = nullptr, stream = nullptr;
+  long long ncell = 0;
+  int cap = 0;
+  int ntx = 1, nty = 1, ntz = 1;
+  double u0 = 0, w0 = 0;
+  bool has_w = false, has_id = false;
+  std::vector<void*> allocs;
+  void* f[9] = {};   // ex ey ez bx by bz jx jy jz
+  void* g[6] = {};   // gather copies
+  void* jf[3] = {};  // filtered current (aliases f[6..8] when J is not filtered)
+  void* parr[2][2][8] = {};  // [species][buffer][ox oy oz dux duy duz w id]
+  int* cnt[2][2] = {};
+  int parity = 0;
+  int* d_err = nullptr;
+  double* d_acc = nullptr;  // 8 doubles of reduction scratch
+  long long* d_offs = nullptr;
+  long long* d_bsum = nullptr;
+  long long* d_total = nullptr;
+  // import / export staging (device)
+  void* stage[10] = {};
+  long long stage_n = 0;
+  // taps (FP64, host) of the copy and current stencils
+  double pe[5] = {1, 0, 0, 0, 0}, pb[5] = {1, 0, 0, 0, 0};
+  std::vector<double> zt_e, zt_b, xt_g, zt_j, xt_j;
+  std::string err;
+};
+
+namespace {
+
+int fail(pic_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(pic_handle* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? PIC_E_OOM : PIC_E_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                               \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+void* dalloc(pic_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return p;
+}
+
+void lattice_dims(int ndim, int ppc, int out[3]) {
+  out[0] = out[1] = out[2] = 1;
+  if (ndim == 2) {
+    int d = (int)floor(sqrt((double)ppc));
+    while (d > 1 && ppc % d) --d;
+    out[0] = d;
+    out[2] = ppc / d;
+    return;
+  }
+  // most even split a <= b <= c of ppc = a b c (smallest c - a)
+  int best = 1 << 30;
+  for (int a = 1; a * a * a <= ppc; ++a) {
+    if (ppc % a) continue;
+    for (int b = a; a * b * b <= ppc; ++b) {
+      if ((ppc / a) % b) continue;
+      int c = ppc / (a * b);
+      if (c - a < best) {
+        best = c - a;
+        out[0] = a;
+        out[1] = b;
+        out[2] = c;
+      }
+    }
+  }
+}
+
+void rebuild_taps(pic_handle* h) {
+  const pic_config& c = h->cfg;
+  std::vector<double> F = filter_taps(c.filter_nbin, c.filter_ncomp, c.filter_comp_alpha);
+  std::vector<double> one{1.0};
+  const std::vector<double>& Fg = (c.filter_targets & PIC_FILTER_GATHER) ? F : one;
+  const std::vector<double>& Fj = (c.filter_targets & PIC_FILTER_J) ? F : one;
+  double te[9], tb[9];
+  psi_stencil(h->pe, te);
+  psi_stencil(h->pb, tb);
+  h->zt_e = convolve(std::vector<double>(te, te + 9), Fg);
+  h->zt_b = convolve(std::vector<double>(tb, tb + 9), Fg);
+  h->xt_g = Fg;
+  h->zt_j = Fj;
+  h->xt_j = Fj;
+}
+
+template <typename T>
+RunDev<T> make_run(pic_handle* h, int parity) {
+  RunDev<T> r;
+  memset(&r, 0, sizeof r);
+  const pic_config& c = h->cfg;
+  r.ndim = c.ndim;
+  r.nx = c.nx;
+  r.ny = c.ny;
+  r.nz = c.nz;
+  r.ncell = h->ncell;
+  r.ntx = h->ntx;
+  r.nty = h->nty;
+  r.ntz = h->ntz;
+  r.cap = h->cap;
+  r.scheme = c.scheme;
+  r.dtdx = (T)(c.dt / c.dx);
+  r.dtdy = (T)(c.dt / c.dy);
+  r.dtdz = (T)(c.dt / c.dz);
+  r.u0 = (T)h->u0;
+  r.hq = (T)(0.5 * c.dt);
+  r.wconst = (T)h->w0;
+  const double dV = c.dx * c.dy * c.dz;
+  r.jfx = (T)(-c.dx / (dV * c.dt));
+  r.jfy = (T)(-c.dy / (dV * c.dt));
+  r.jfz = (T)(-c.dz / (dV * c.dt));
+  r.jfy2d = (T)(1.0 / dV);
+  for (int q = 0; q < 6; ++q) r.g[q] = (T*)h->g[q];
+  for (int q = 0; q < 3; ++q) r.j[q] = (T*)h->f[6 + q];
+  for (int s = 0; s < 2; ++s)
+    for (int io = 0; io < 2; ++io) {
+      int b = io == 0 ? parity : 1 - parity;
+      SpeciesBuf<T> sb;
+      sb.ox = (T*)h->parr[s][b][0];
+      sb.oy = (T*)h->parr[s][b][1];
+      sb.oz = (T*)h->parr[s][b][2];
+      sb.dux = (T*)h->parr[s][b][3];
+      sb.duy = (T*)h->parr[s][b][4];
+      sb.duz = (T*)h->parr[s][b][5];
+      sb.w = (T*)h->parr[s][b][6];
+      sb.id = (unsigned*)h->parr[s][b][7];
+      sb.cnt = h->cnt[s][b];
+      if (io == 0) r.in[s] = sb; else r.out[s] = sb;
+    }
+  r.err = h->d_err;
+  r.kin = nullptr;
+  return r;
+}
+
+template <typename T>
+SepArgs<T> sep_args(pic_handle* h, bool copies) {
+  SepArgs<T> a;
+  memset(&a, 0, sizeof a);
+  const pic_config& c = h->cfg;
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.nz = c.nz;
+  a.ndim = c.ndim;
+  auto put = [](T* dst, const std::vector<double>& v) {
+    for (size_t i = 0; i < v.size(); ++i) dst[i] = (T)v[i];
+  };
+  if (copies) {
+    a.ncomp = 6;
+    for (int q = 0; q < 6; ++q) {
+      a.src[q] = (const T*)h->f[q];
+      a.dst[q] = (T*)h->g[q];
+      a.zset[q] = q < 2 ? 0 : 1;  // Psi_E on Ex, Ey; Psi_B on Ez, Bx, By, Bz
+    }
+    a.hz[0] = (int)(h->zt_e.size() / 2);
+    a.hz[1] = (int)(h->zt_b.size() / 2);
+    put(a.zt[0], h->zt_e);
+    put(a.zt[1], h->zt_b);
+    a.hx = a.hy = (int)(h->xt_g.size() / 2);
+    put(a.xt, h->xt_g);
+    put(a.yt, h->xt_g);
+  } else {
+    a.ncomp = 3;
+    for (int q = 0; q < 3; ++q) {
+      a.src[q] = (const T*)h->f[6 + q];
+      a.dst[q] = (T*)h->jf[q];
+      a.zset[q] = 0;
+    }
+    a.hz[0] = a.hz[1] = (int)(h->zt_j.size() / 2);
+    put(a.zt[0], h->zt_j);
+    put(a.zt[1], h->zt_j);
+    a.hx = a.hy = (int)(h->xt_j.size() / 2);
+    put(a.xt, h->xt_j);
+    put(a.yt, h->xt_j);
+  }
+  return a;
+}
+
+template <typename T>
+YeeArgs<T> yee_args(pic_handle* h, double hstep) {
+  YeeArgs<T> a;
+  const pic_config& c = h->cfg;
+  a.ex = (T*)h->f[0];
+  a.ey = (T*)h->f[1];
+  a.ez = (T*)h->f[2];
+  a.bx = (T*)h->f[3];
+  a.by = (T*)h->f[4];
+  a.bz = (T*)h->f[5];
+  void* const* js = (h->cfg.filter_targets & PIC_FILTER_J) ? h->jf : h->f + 6;
+  a.jx = (const T*)js[0];
+  a.jy = (const T*)js[1];
+  a.jz = (const T*)js[2];
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.nz = c.nz;
+  a.cx = (T)(hstep / c.dx);
+  a.cy = (T)(hstep / c.dy);
+  a.cz = (T)(hstep / c.dz);
+  a.h = (T)hstep;
+  return a;
+}
+
+template <typename T>
+int step_once(pic_handle* h) {
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  // 1. field copies seen by the particles: Psi(D_z) and the gather filter
+  CK(launch_sep<T>(sep_args<T>(h, true), st), "copy stencil");
+  // 2-5. gather, Boris, move, Esirkepov, rebin
+  for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(h->f[6 + q], 0, fb, st), "zero J");
+  RunDev<T> r = make_run<T>(h, h->parity);
+  CK(launch_push<T>(r, h->has_w, h->has_id, st), "push");
+  // 6. current filter
+  if (h->cfg.filter_targets & PIC_FILTER_J) CK(launch_sep<T>(sep_args<T>(h, false), st), "current filter");
+  // 7. Yee: B half, E full, B half
+  const double dt = h->cfg.dt;
+  CK(launch_yee_b<T>(yee_args<T>(h, 0.5 * dt), st), "yee B");
+  CK(launch_yee_e<T>(yee_args<T>(h, dt), st), "yee E");
+  CK(launch_yee_b<T>(yee_args<T>(h, 0.5 * dt), st), "yee B");
+  h->parity ^= 1;
+  return PIC_OK;
+}
+
+int check_err(pic_handle* h) {
+  int e = 0;
+  CK(cudaStreamSynchronize(h->stream), "synchronize");
+  CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+  if (!e) return PIC_OK;
+  CK(cudaMemset(h->d_err, 0, sizeof(int)), "clear error flag");
+  if (e & ERR_OVERFLOW) return fail(h, PIC_E_OVERFLOW, "a cell's particle bin overflowed; raise bin_capacity");
+  if (e & ERR_NONFINITE) return fail(h, PIC_E_NONFINITE, "a particle became non-finite or moved more than a cell");
+  if (e & ERR_IMPORT) return fail(h, PIC_E_ARG, "imported particle with invalid cell or species");
+  if (e & ERR_TIMEOUT) return fail(h, PIC_E_TIMEOUT, "a bounded device wait gave up");
+  return fail(h, PIC_E_CUDA, "unknown device error flag");
+}
+
+template <typename T>
+int init_beam(pic_handle* h) {
+  const pic_config& c = h->cfg;
+  int lat[3];
+  lattice_dims(c.ndim, c.ppc_per_species, lat);
+  RunDev<T> r = make_run<T>(h, h->parity);
+  CK(launch_init_beam<T>(r, c.ppc_per_species, lat, h->u0, h->w0, c.jitter, c.u_th, c.sigma_perp, c.seed, h->stream),
+     "init beam");
+  return PIC_OK;
+}
+
+int ensure_stage(pic_handle* h, long long n) {
+  if (n <= h->stage_n) return PIC_OK;
+  for (int q = 0; q < 10; ++q)
+    if (h->stage[q]) {
+      cudaFree(h->stage[q]);
+      for (auto& p : h->allocs)
+        if (p == h->stage[q]) p = nullptr;
+      h->stage[q] = nullptr;
+    }
+  // cell, species, ox, oy, oz, dux, duy, duz, w, id
+  const size_t sz[10] = {4, 4, h->es, h->es, h->es, h->es, h->es, h->es, h->es, 4};
+  for (int q = 0; q < 10; ++q) {
+    h->stage[q] = dalloc(h, sz[q] * (size_t)n);
+    if (!h->stage[q]) return fail(h, PIC_E_OOM, "staging allocation failed");
+  }
+  h->stage_n = n;
+  return PIC_OK;
+}
+
+template <typename T>
+FlatDev<T> stage_view(pic_handle* h, long long n) {
+  FlatDev<T> f;
+  f.np = n;
+  f.cell = (int*)h->stage[0];
+  f.species = (int*)h->stage[1];
+  f.ox = (T*)h->stage[2];
+  f.oy = (T*)h->stage[3];
+  f.oz = (T*)h->stage[4];
+  f.dux = (T*)h->stage[5];
+  f.duy = (T*)h->stage[6];
+  f.duz = (T*)h->stage[7];
+  f.w = (T*)h->stage[8];
+  f.id = (unsigned*)h->stage[9];
+  return f;
+}
+
+template <typename T>
+int set_state_t(pic_handle* h, const pic_state* s) {
+  cudaStream_t st = h->stream;
+  const cudaMemcpyKind k = s->where == PIC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  void* const src[6] = {s->ex, s->ey, s->ez, s->bx, s->by, s->bz};
+  for (int q = 0; q < 6; ++q)
+    if (src[q]) CK(cudaMemcpyAsync(h->f[q], src[q], fb, k, st), "copy field in");
+  const long long n = s->np;
+  if (n == -1) return PIC_OK;  // fields only: particles untouched
+  if (n < 0) return fail(h, PIC_E_ARG, "negative particle count");
+  // particles: clear bins, stage, bin
+  for (int sp = 0; sp < 2; ++sp)
+    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
+  h->parity = 0;
+  if (n == 0) return PIC_OK;
+  if (!s->cell || !s->species || !s->ox || !s->oz || !s->dux || !s->duy || !s->duz ||
+      (h->cfg.ndim == 3 && !s->oy))
+    return fail(h, PIC_E_ARG, "missing particle array");
+  int rc = ensure_stage(h, n);
+  if (rc) return rc;
+  FlatDev<T> f = stage_view<T>(h, n);
+  CK(cudaMemcpyAsync(f.cell, s->cell, 4 * (size_t)n, k, st), "copy cell");
+  CK(cudaMemcpyAsync(f.species, s->species, 4 * (size_t)n, k, st), "copy species");
+  CK(cudaMemcpyAsync(f.ox, s->ox, sizeof(T) * n, k, st), "copy ox");
+  if (h->cfg.ndim == 3) CK(cudaMemcpyAsync(f.oy, s->oy, sizeof(T) * n, k, st), "copy oy");
+  else f.oy = nullptr;
+  CK(cudaMemcpyAsync(f.oz, s->oz, sizeof(T) * n, k, st), "copy oz");
+  CK(cudaMemcpyAsync(f.dux, s->dux, sizeof(T) * n, k, st), "copy dux");
+  CK(cudaMemcpyAsync(f.duy, s->duy, sizeof(T) * n, k, st), "copy duy");
+  CK(cudaMemcpyAsync(f.duz, s->duz, sizeof(T) * n, k, st), "copy duz");
+  if (s->w && h->has_w) CK(cudaMemcpyAsync(f.w, s->w, sizeof(T) * n, k, st), "copy w");
+  else f.w = nullptr;
+  if (s->id && h->has_id) CK(cudaMemcpyAsync(f.id, s->id, 4 * (size_t)n, k, st), "copy id");
+  else f.id = nullptr;
+  RunDev<T> r = make_run<T>(h, 0);
+  CK(launch_import<T>(r, f, st), "import");
+  return PIC_OK;
+}
+
+template <typename T>
+int count_particles(pic_handle* h, long long out[2]) {
+  for (int s = 0; s < 2; ++s) {
+    CK(launch_count_prefix(h->cnt[s][h->parity], h->ncell, h->cap, h->d_offs, h->d_bsum, h->d_total + s, h->stream),
+       "count prefix");
+  }
+  CK(cudaMemcpyAsync(out, h->d_total, 2 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream), "read counts");
+  CK(cudaStreamSynchronize(h->stream), "synchronize");
+  return PIC_OK;
+}
+
+template <typename T>
+int get_state_t(pic_handle* h, pic_state* s) {
+  int rc = check_err(h);
+  if (rc) return rc;
+  cudaStream_t st = h->stream;
+  const cudaMemcpyKind k = s->where == PIC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  void* const dst[6] = {s->ex, s->ey, s->ez, s->bx, s->by, s->bz};
+  for (int q = 0; q < 6; ++q)
+    if (dst[q]) CK(cudaMemcpyAsync(dst[q], h->f[q], fb, k, st), "copy field out");
+  s->u_drift = h->u0;
+  long long cnts[2];
+  rc = count_particles<T>(h, cnts);
+  if (rc) return rc;
+  const long long n = cnts[0] + cnts[1];
+  if (!s->cell && !s->species && !s->ox && !s->oy && !s->oz && !s->dux && !s->duy && !s->duz && !s->w && !s->id) {
+    s->np = n;  // fields only
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return check_err(h);
+  }
+  if (s->np < n) {
+    s->np = n;
+    return fail(h, PIC_E_ARG, "particle arrays too small (np updated to the required count)");
+  }
+  s->np = n;
+  if (n == 0) return PIC_OK;
+  rc = ensure_stage(h, n);
+  if (rc) return rc;
+  FlatDev<T> f = stage_view<T>(h, n);
+  if (h->cfg.ndim != 3) f.oy = nullptr;
+  RunDev<T> r = make_run<T>(h, h->parity);
+  long long base = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    CK(launch_count_prefix(h->cnt[sp][h->parity], h->ncell, h->cap, h->d_offs, h->d_bsum, h->d_total, st),
+       "count prefix");
+    CK(launch_export<T>(r, sp, h->d_offs, base, f, st), "export");
+    base += cnts[sp];
+  }
+  if (s->cell) CK(cudaMemcpyAsync(s->cell, f.cell, 4 * (size_t)n, k, st), "copy cell out");
+  if (s->species) CK(cudaMemcpyAsync(s->species, f.species, 4 * (size_t)n, k, st), "copy species out");
+  if (s->ox) CK(cudaMemcpyAsync(s->ox, f.ox, sizeof(T) * n, k, st), "copy ox out");
+  if (s->oy && f.oy) CK(cudaMemcpyAsync(s->oy, f.oy, sizeof(T) * n, k, st), "copy oy out");
+  if (s->oz) CK(cudaMemcpyAsync(s->oz, f.oz, sizeof(T) * n, k, st), "copy oz out");
+  if (s->dux) CK(cudaMemcpyAsync(s->dux, f.dux, sizeof(T) * n, k, st), "copy dux out");
+  if (s->duy) CK(cudaMemcpyAsync(s->duy, f.duy, sizeof(T) * n, k, st), "copy duy out");
+  if (s->duz) CK(cudaMemcpyAsync(s->duz, f.duz, sizeof(T) * n, k, st), "copy duz out");
+  if (s->w) CK(cudaMemcpyAsync(s->w, f.w, sizeof(T) * n, k, st), "copy w out");
+  if (s->id) CK(cudaMemcpyAsync(s->id, f.id, 4 * (size_t)n, k, st), "copy id out");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  return check_err(h);
+}
+
+template <typename T>
+int energy_t(pic_handle* h, pic_energy_t* out) {
+  cudaStream_t st = h->stream;
+  CK(cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), st), "zero accumulators");
+  const T* f6[6];
+  for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
+  CK(launch_field_energy<T>(f6, h->ncell, h->d_acc, st), "field energy");
+  RunDev<T> r = make_run<T>(h, h->parity);
+  CK(launch_kinetic<T>(r, h->d_acc + 3, st), "kinetic energy");
+  double acc[8];
+  CK(cudaMemcpyAsync(acc, h->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st), "read energies");
+  long long cnts[2];
+  int rc = count_particles<T>(h, cnts);
+  if (rc) return rc;
+  const pic_config& c = h->cfg;
+  const double dV = c.dx * c.dy * c.dz;
+  out->w_e = 0.5 * acc[0] * dV;
+  out->w_b = 0.5 * acc[1] * dV;
+  out->w_perp = 0.5 * acc[2] * dV;
+  out->k = acc[3];
+  out->total = out->w_e + out->w_b + out->k;
+  out->np = cnts[0] + cnts[1];
+  return check_err(h);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// Public ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+void pic_config_default(pic_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof *c);
+  c->ndim = 2;
+  c->nx = 64;
+  c->ny = 1;
+  c->nz = 128;
+  c->dx = c->dy = c->dz = 1.0;
+  c->dt = 0.5;
+  c->gamma = 130.0;
+  c->scheme = PIC_GALERKIN;
+  c->shape_order = 1;
+  c->precision = PIC_FP64;
+  c->ppc_per_species = 4;
+  c->omega_p_dz = 0.3868;
+  c->jitter = 0.1;
+  c->u_th = 1e-4;
+  c->sigma_perp = 0.0;
+  c->filter_nbin = 1;
+  c->filter_ncomp = 1;
+  c->filter_comp_alpha = 3.0;
+  c->filter_targets = PIC_FILTER_J | PIC_FILTER_GATHER;
+  c->seed = 1;
+  c->init_beam = 1;
+  c->bin_capacity = 0;
+  c->track_ids = 0;
+}
+
+int pic_compute_correction_coeffs(int scheme, double alpha, double psi_e[5], double psi_b[5]) {
+  if (!psi_e || !psi_b) return PIC_E_ARG;
+  return correction_coeffs(scheme, alpha, psi_e, psi_b);
+}
+
+int pic_create(const pic_config* cfg_in, pic_handle** out) {
+  if (!cfg_in || !out) return PIC_E_ARG;
+  *out = nullptr;
+  pic_config c = *cfg_in;
+  if (c.ndim == 2) {
+    c.ny = 1;
+    c.dy = 1.0;
+  }
+  if ((c.ndim != 2 && c.ndim != 3) || c.nx < 1 || c.ny < 1 || c.nz < 1 || !(c.dx > 0) || !(c.dy > 0) ||
+      !(c.dz > 0) || !(c.dt > 0) || !(c.gamma >= 1.0) || (c.scheme != PIC_GALERKIN && c.scheme != PIC_UNIFORM) ||
+      c.shape_order != 1 || (c.precision != PIC_FP32 && c.precision != PIC_FP64) || c.ppc_per_species < 0 ||
+      c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
+      (long long)c.nx * c.ny * c.nz > (1ll << 31) - 1)
+    return PIC_E_ARG;
+  const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
+  if (c.dt >= 1.0 / sqrt(inv)) return PIC_E_CFL;
+  pic_handle* h = new pic_handle();
+  h->cfg = c;
+  h->es = c.precision == PIC_FP32 ? 4 : 8;
+  h->ncell = (long long)c.nx * c.ny * c.nz;
+  push_tiles(c.ndim, c.nx, c.ny, c.nz, &h->ntx, &h->nty, &h->ntz);
+  h->u0 = sqrt(c.gamma * c.gamma - 1.0);
+  const double wp = c.omega_p_dz / c.dz;
+  h->w0 = c.ppc_per_species > 0 ? wp * wp * c.dx * c.dy * c.dz / (2.0 * c.ppc_per_species) : 0.0;
+  h->has_w = c.sigma_perp > 0;
+  h->has_id = c.track_ids != 0;
+  int cap = c.bin_capacity;
+  if (cap == 0) cap = c.ppc_per_species * 2 + 8;
+  cap = (cap + 7) / 8 * 8;
+  h->cap = cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete h;
+    return PIC_E_CUDA;
+  }
+  h->stream = h->own;
+  const size_t fb = (size_t)h->ncell * h->es;
+  bool ok = true;
+  for (int q = 0; q < 9 && ok; ++q) ok = (h->f[q] = dalloc(h, fb)) != nullptr;
+  for (int q = 0; q < 6 && ok; ++q) ok = (h->g[q] = dalloc(h, fb)) != nullptr;
+  for (int q = 0; q < 3 && ok; ++q) ok = (h->jf[q] = dalloc(h, fb)) != nullptr;
+  const size_t slots = (size_t)h->ncell * cap;
+  for (int s = 0; s < 2 && ok; ++s)
+    for (int b = 0; b < 2 && ok; ++b) {
+      for (int a = 0; a < 8 && ok; ++a) {
+        if (a == 1 && c.ndim == 2) continue;
+        if (a == 6 && !h->has_w) continue;
+        if (a == 7 && !h->has_id) continue;
+        ok = (h->parr[s][b][a] = dalloc(h, slots * (a == 7 ? 4 : h->es))) != nullptr;
+      }
+      if (ok) ok = (h->cnt[s][b] = (int*)dalloc(h, sizeof(int) * h->ncell)) != nullptr;
+    }
+  if (ok) ok = (h->d_err = (int*)dalloc(h, 16)) != nullptr;
+  if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
+  if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
+  if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
+  if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;
+  if (!ok) {
+    pic_destroy(h);
+    return PIC_E_OOM;
+  }
+  for (int q = 0; q < 9; ++q) cudaMemsetAsync(h->f[q], 0, fb, h->stream);
+  for (int s = 0; s < 2; ++s)
+    for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->cnt[s][b], 0, sizeof(int) * h->ncell, h->stream);
+  cudaMemsetAsync(h->d_err, 0, 16, h->stream);
+  rebuild_taps(h);
+  int rc = PIC_OK;
+  if (c.init_beam && c.ppc_per_species > 0)
+    rc = c.precision == PIC_FP32 ? init_beam<float>(h) : init_beam<double>(h);
+  if (rc == PIC_OK) rc = check_err(h);
+  if (rc != PIC_OK) {
+    pic_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_set_stream(pic_handle* h, void* stream) {
+  if (!h) return PIC_E_ARG;
+  h->stream = stream ? (cudaStream_t)stream : h->own;
+  return PIC_OK;
+}
+
+int pic_set_correction_stencil(pic_handle* h, const double psi_e[5], const double psi_b[5]) {
+  if (!h) return PIC_E_ARG;
+  if ((psi_e == nullptr) != (psi_b == nullptr)) return fail(h, PIC_E_ARG, "give both Psi_E and Psi_B, or neither");
+  for (int q = 0; q < 5; ++q) {
+    h->pe[q] = psi_e ? psi_e[q] : (q == 0 ? 1.0 : 0.0);
+    h->pb[q] = psi_b ? psi_b[q] : (q == 0 ? 1.0 : 0.0);
+    if (!isfinite(h->pe[q]) || !isfinite(h->pb[q])) return fail(h, PIC_E_ARG, "non-finite coefficient");
+  }
+  rebuild_taps(h);
+  return PIC_OK;
+}
+
+int pic_step(pic_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return PIC_E_ARG;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = h->es == 4 ? step_once<float>(h) : step_once<double>(h);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_sync(pic_handle* h) {
+  if (!h) return PIC_E_ARG;
+  return check_err(h);
+}
+
+int pic_energy(pic_handle* h, pic_energy_t* out) {
+  if (!h || !out) return PIC_E_ARG;
+  return h->es == 4 ? energy_t<float>(h, out) : energy_t<double>(h, out);
+}
+
+int pic_num_particles(pic_handle* h, long long* np) {
+  if (!h || !np) return PIC_E_ARG;
+  long long c[2];
+  int rc = h->es == 4 ? count_particles<float>(h, c) : count_particles<double>(h, c);
+  if (rc) return rc;
+  *np = c[0] + c[1];
+  return check_err(h);
+}
+
+int pic_get_state(pic_handle* h, pic_state* s) {
+  if (!h || !s || (s->where != PIC_HOST && s->where != PIC_DEVICE)) return PIC_E_ARG;
+  return h->es == 4 ? get_state_t<float>(h, s) : get_state_t<double>(h, s);
+}
+
+int pic_set_state(pic_handle* h, const pic_state* s) {
+  if (!h || !s || (s->where != PIC_HOST && s->where != PIC_DEVICE)) return PIC_E_ARG;
+  return h->es == 4 ? set_state_t<float>(h, s) : set_state_t<double>(h, s);
+}
+
+static int debug_copy(pic_handle* h, int where, void* const* out, void* const* src, int n) {
+  if (!h || !out || (where != PIC_HOST && where != PIC_DEVICE)) return PIC_E_ARG;
+  const cudaMemcpyKind k = where == PIC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  for (int q = 0; q < n; ++q)
+    if (out[q]) CK(cudaMemcpyAsync(out[q], src[q], (size_t)h->ncell * h->es, k, h->stream), "debug copy");
+  CK(cudaStreamSynchronize(h->stream), "synchronize");
+  return PIC_OK;
+}
+
+int pic_debug_gather_copies(pic_handle* h, int where, void* const* out6) {
+  if (!h) return PIC_E_ARG;
+  return debug_copy(h, where, out6, h->g, 6);
+}
+
+int pic_debug_current(pic_handle* h, int where, void* const* out3) {
+  if (!h) return PIC_E_ARG;
+  void* src[3] = {h->jf[0], h->jf[1], h->jf[2]};
+  if (!(h->cfg.filter_targets & PIC_FILTER_J))
+    for (int q = 0; q < 3; ++q) src[q] = h->f[6 + q];
+  return debug_copy(h, where, out3, src, 3);
+}
+
+int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_out, int* i0, int* i1) {
+  if (!t || !w || !gamma_out || n < 5) return PIC_E_ARG;
+  return growth_fit(t, w, n, gamma_out, i0, i1);
+}
+
+void pic_destroy(pic_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+const char* pic_last_error(const pic_handle* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+const char* pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_E_ARG: return "invalid argument";
+    case PIC_E_CFL: return "time step violates the Courant limit";
+    case PIC_E_SINGULAR: return "singular or ill-conditioned rational interpolation";
+    case PIC_E_OOM: return "out of memory";
+    case PIC_E_CUDA: return "CUDA error";
+    case PIC_E_TIMEOUT: return "device wait timed out";
+    case PIC_E_NONFINITE: return "non-finite state";
+    case PIC_E_OVERFLOW: return "particle bin overflow";
+    case PIC_E_STATE: return "invalid call for the handle's state";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

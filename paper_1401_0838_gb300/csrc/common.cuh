@@ -1,0 +1,101 @@
+// Internal definitions shared by the CUDA translation units of the PIC library.
+// Nothing here is part of the public C ABI (include/pic.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace picgb {
+
+// Sticky error bits written by kernels (read by the host at pic_sync / pic_energy).
+enum : int {
+  ERR_OVERFLOW = 1,   // a particle found its destination cell bin full and was dropped
+  ERR_NONFINITE = 2,  // a particle position or momentum became NaN/Inf or moved > 1 cell
+  ERR_IMPORT = 4,     // an imported particle had an invalid cell or species
+  ERR_TIMEOUT = 8,    // a bounded device wait gave up
+};
+
+constexpr int MAX_ZTAPS = 33;  // combined z stencil: Psi (9 taps) convolved with the filter
+constexpr int MAX_XTAPS = 25;  // filter stencil along x or y
+
+// One species' particle storage in one of the two ping-pong buffers. Slot s of the arrays
+// belongs to cell s / cap; cell c holds cnt[c] particles in slots [c*cap, c*cap + cnt[c]).
+template <typename T>
+struct SpeciesBuf {
+  T *ox, *oy, *oz;     // offsets in [0,1) inside the cell (oy unused in 2D)
+  T *dux, *duy, *duz;  // u - u0 z_hat
+  T* w;                // per-particle weight or nullptr
+  unsigned* id;        // particle id or nullptr
+  int* cnt;            // particles per cell
+};
+
+// Everything a kernel needs about one simulation (passed by value as a kernel parameter).
+template <typename T>
+struct RunDev {
+  int ndim, nx, ny, nz;
+  long long ncell;
+  int ntx, nty, ntz;  // particle tiles per direction
+  int cap;            // slots per cell per species
+  int scheme;         // 0 Galerkin, 1 Uniform
+  T dtdx, dtdy, dtdz; // dt / d (grid units per unit velocity)
+  T u0;               // drift momentum sqrt(gamma^2 - 1)
+  T hq;               // dt / 2 (Boris half-kick for unit charge and mass)
+  T wconst;           // weight when per-particle weights are absent
+  T jfx, jfy, jfz;    // -d_a / (dV dt): Esirkepov current per unit (q w) and unit W
+  T jfy2d;            // 1 / dV: 2D out-of-plane current per unit (q w v_y)
+  T* g[6];            // field copies seen by the particles (Ex Ey Ez Bx By Bz)
+  T* j[3];            // current accumulator
+  SpeciesBuf<T> in[2], out[2];
+  int* err;
+  double* kin;        // FP64 accumulator for sum w (gamma - 1) of this step (may be nullptr)
+};
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the multiply-xor round
+// function with multipliers 0xD2511F53, 0xCD9E8D57 and Weyl key increments 0x9E3779B9,
+// 0xBB67AE85.
+// ---------------------------------------------------------------------------------------------
+struct u32x4 {
+  uint32_t v[4];
+};
+
+__host__ __device__ inline u32x4 philox10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    uint64_t a = (uint64_t)0xD2511F53u * c.v[0];
+    uint64_t b = (uint64_t)0xCD9E8D57u * c.v[2];
+    u32x4 n;
+    n.v[0] = (uint32_t)(b >> 32) ^ c.v[1] ^ k0;
+    n.v[1] = (uint32_t)b;
+    n.v[2] = (uint32_t)(a >> 32) ^ c.v[3] ^ k1;
+    n.v[3] = (uint32_t)a;
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Small math helpers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T tri(T d) {  // linear spline max(0, 1 - |d|)
+  T a = T(1) - (d < T(0) ? -d : d);
+  return a > T(0) ? a : T(0);
+}
+
+__device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double dev_floor(double x) { return floor(x); }
+__device__ __forceinline__ float dev_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dev_sqrt(double x) { return sqrt(x); }
+
+__device__ __forceinline__ void flag_error(int* err, int bit) {
+  if (err) atomicOr(err, bit);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+}  // namespace picgb

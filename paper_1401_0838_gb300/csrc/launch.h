@@ -1,0 +1,73 @@
+// Host-side launchers of the CUDA kernels (internal; the public ABI is include/pic.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace picgb {
+
+// Flat (compact) particle arrays used by state import / export.
+template <typename T>
+struct FlatDev {
+  long long np;
+  int* cell;
+  int* species;
+  T *ox, *oy, *oz, *dux, *duy, *duz, *w;
+  unsigned* id;
+};
+
+// Separable periodic stencil over up to 6 components: out = X(Y(Z(in))) with per-component
+// z taps (one of two sets) and shared x / y taps. Taps are odd-length, centred.
+template <typename T>
+struct SepArgs {
+  const T* src[6];
+  T* dst[6];
+  int zset[6];
+  int ncomp;
+  int nx, ny, nz, ndim;
+  int hz[2], hx, hy;
+  T zt[2][MAX_ZTAPS];
+  T xt[MAX_XTAPS];
+  T yt[MAX_XTAPS];
+};
+
+template <typename T>
+struct YeeArgs {
+  T *ex, *ey, *ez, *bx, *by, *bz;
+  const T *jx, *jy, *jz;
+  int nx, ny, nz;
+  T cx, cy, cz;  // h / d for the curl differences (h = dt or dt/2)
+  T h;           // coefficient of J in the E update
+};
+
+void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);
+
+template <typename T>
+cudaError_t launch_push(const RunDev<T>& r, bool has_w, bool has_id, cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_beam(const RunDev<T>& r, int ppc, const int lat[3], double u0, double w0, double jitter,
+                             double u_th, double sigma_perp, unsigned long long seed, cudaStream_t st);
+template <typename T>
+cudaError_t launch_import(const RunDev<T>& r, const FlatDev<T>& f, cudaStream_t st);
+template <typename T>
+cudaError_t launch_export(const RunDev<T>& r, int s, const long long* offs, long long base, const FlatDev<T>& f,
+                          cudaStream_t st);
+cudaError_t launch_count_prefix(const int* cnt, long long ncell, int cap, long long* offs, long long* bsum,
+                                long long* total, cudaStream_t st);
+long long count_prefix_blocks(long long ncell);
+
+template <typename T>
+cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yee_b(const YeeArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yee_e(const YeeArgs<T>& a, cudaStream_t st);
+
+// out[0..2] += (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2) in FP64
+template <typename T>
+cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, cudaStream_t st);
+// out[0] += sum w (gamma - 1) over both species of the input buffers
+template <typename T>
+cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);
+
+}  // namespace picgb

@@ -1,0 +1,101 @@
+"""CPU checks of the C ABI: the library loads and exports every declared symbol; its host-only FP64
+functions (correction coefficients, growth fit, argument validation) agree with the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.fit import growth_rate
+
+P = pytest.importorskip("paper_1401_0838_gb300")
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(HEADER):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(HEADER, fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pic_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(P.EXPORTS) == declared
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("alpha", [0.1, 0.25, 0.3, 0.45, 0.55, 0.6, 0.7])
+def test_coefficients_match_oracle(scheme, alpha):
+    pe, pb = P.pic_compute_correction_coeffs(scheme, alpha)
+    st, oe, ob = O.rational_coeffs(scheme, alpha)
+    assert st == 0
+    # two different solvers (QR here, Gaussian elimination in the oracle) of a system with
+    # condition ~1e8: agreement to ~1e-16 * cond
+    np.testing.assert_allclose(pe, oe, rtol=2e-7, atol=2e-8)
+    np.testing.assert_allclose(pb, ob, rtol=2e-7, atol=2e-8)
+    # the multiplier they interpolate agrees to 1e-10 everywhere on [0, 1]
+    xi = np.linspace(0, 1, 101)
+    r1 = np.polyval(pe[::-1], xi) / np.polyval(pb[::-1], xi)
+    r2 = np.polyval(oe[::-1], xi) / np.polyval(ob[::-1], xi)
+    assert np.abs(r1 - r2).max() < 1e-9
+
+
+def test_coefficients_degenerate_and_errors():
+    pe, pb = P.pic_compute_correction_coeffs(1, 0.5)
+    assert list(pe) == [1, 0, 0, 0, 0] and list(pb) == [1, 0, 0, 0, 0]
+    with pytest.raises(P.PicError) as e:
+        P.pic_compute_correction_coeffs(0, -0.1)
+    assert e.value.code == P.PIC_E_ARG
+    with pytest.raises(P.PicError):
+        P.pic_compute_correction_coeffs(7, 0.5)
+
+
+def test_momentum_multiplier_coefficients():
+    # Eq. 5 is also interpolated (host only); its ratio reproduces the nine nodes
+    pe, pb = P.pic_compute_correction_coeffs(2, 0.5)
+    for j in range(9):
+        xi = j / 8
+        m = O.multiplier(2, 0.5, math.asin(math.sqrt(xi)))
+        assert abs(np.polyval(pe[::-1], xi) / np.polyval(pb[::-1], xi) - m) < 1e-10
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_growth_fit_matches_oracle(seed):
+    rng = np.random.default_rng(seed)
+    t = np.arange(150) * 0.7
+    g = rng.uniform(0.01, 0.05)
+    w = 1e-8 * (1 + 0.2 * rng.random(150)) + 1e-10 * np.exp(2 * g * t)
+    w = np.minimum(w, 10 ** rng.uniform(-2, 3))
+    a = P.pic_fit_growth_rate(t, w)
+    b = growth_rate(t, w)
+    assert a[1:] == b[1:]
+    assert abs(a[0] - b[0]) < 1e-12 * abs(b[0])
+
+
+def test_create_validates_before_touching_the_gpu():
+    cfg = P.pic_config_default(dt=0.71)  # 2D Courant limit 1/sqrt(2)
+    with pytest.raises(P.PicError) as e:
+        P.pic_create(cfg)
+    assert e.value.code == P.PIC_E_CFL
+    cfg = P.pic_config_default(ndim=4)
+    with pytest.raises(P.PicError) as e:
+        P.pic_create(cfg)
+    assert e.value.code == P.PIC_E_ARG
+    cfg = P.pic_config_default(ndim=3, nx=8, ny=8, nz=8, dt=0.58)  # 3D limit 1/sqrt(3)
+    with pytest.raises(P.PicError) as e:
+        P.pic_create(cfg)
+    assert e.value.code == P.PIC_E_CFL
+
+
+def test_destroy_null_is_noop():
+    P.lib().pic_destroy(None)

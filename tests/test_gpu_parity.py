@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: FP64 GPU vs FP64 oracle <= 1e-10 relative per step (atomic ordering is the only difference);
+FP32 GPU vs FP64 oracle <= 1e-5 relative per step. Particles are matched by id; positions are
+compared as absolute periodic differences in cells, the rest as relative L2 norms per array.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._pic import P, Pair, make_cfg, periodic_diff, rel_l2, uniform_weight
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-10, 0: 1e-5}
+FIELDS = ("ex", "ey", "ez", "bx", "by", "bz")
+
+
+def _coeffs(scheme, alpha):
+    return P.pic_compute_correction_coeffs(scheme, alpha)
+
+
+def _compare(pair, tol, fields=True, particles=True, field_floor=0.0):
+    f, p = pair.gpu_state()
+    out = {}
+    if fields:
+        for n in FIELDS:
+            e = rel_l2(f[n], pair.o.f[n], floor=field_floor)
+            out[n] = e
+            assert e <= tol, (n, e)
+    if particles and pair.npart:
+        o = pair.o
+        order = np.argsort(o.pid, kind="stable")
+        assert len(p["id"]) == len(order), (len(p["id"]), len(order))
+        np.testing.assert_array_equal(p["id"], o.pid[order])
+        nz, ny, nx = o.shape
+        dx = periodic_diff(p["x"], o.part["x"][order], nx)
+        dz = periodic_diff(p["z"], o.part["z"][order], nz)
+        pos_err = max(np.abs(dx).max(), np.abs(dz).max())
+        if pair.cfg.ndim == 3:
+            pos_err = max(pos_err, np.abs(periodic_diff(p["y"], o.part["y"][order], ny)).max())
+        out["pos"] = pos_err
+        assert pos_err <= tol, ("pos", pos_err)
+        for c in ("ux", "uy", "uz"):
+            e = rel_l2(p[c], o.part[c][order])
+            out[c] = e
+            assert e <= tol, (c, e)
+        np.testing.assert_array_equal(p["q"], o.part["q"][order])
+    return out
+
+
+def _random_pair(ndim, precision, scheme=0, nx=40, ny=12, nz=72, npart=20000, seed=0, psi=True, alpha=0.5,
+                 targets=3, nbin=1, ncomp=1, calpha=3.0, sigma=0.0, field_scale=2e-2):
+    dt = alpha if ndim == 2 else min(alpha, 0.55)
+    cfg = make_cfg(ndim=ndim, nx=nx, ny=ny, nz=nz, dt=dt, scheme=scheme, precision=precision, targets=targets,
+                   nbin=nbin, ncomp=ncomp, calpha=calpha, sigma_perp=sigma)
+    shape = (nz, ny if ndim == 3 else 1, nx)
+    fields = synth.random_fields(shape, seed=seed + 100, scale=field_scale, smooth=1)
+    part = synth.random_particles(ndim, nx, ny if ndim == 3 else 1, nz, npart, seed=seed + 200,
+                                  per_particle_weight=sigma > 0)
+    return Pair(cfg, psi=_coeffs(scheme, alpha) if psi else None, fields=fields, part=part)
+
+
+# ---------------------------------------------------------------------------------------------
+# stage-level parity
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("nbin,ncomp,calpha,targets", [(1, 1, 3.0, 3), (2, 1, 2.0, 3), (2, 2, 3.0, 2), (0, 0, 3.0, 0)])
+def test_gather_copies(precision, ndim, nbin, ncomp, calpha, targets):
+    # Psi_E / Psi_B z-stencils and the gather filter (Sec. 2, Eq. 6): one step with no particles,
+    # then the copies the particles would have seen.
+    pair = _random_pair(ndim, precision, npart=0, nx=40, ny=10, nz=36, nbin=nbin, ncomp=ncomp, calpha=calpha,
+                        targets=targets)
+    try:
+        expect = pair.o.gather_copies()
+        P.pic_step(pair.h, 1)
+        T = pair.T
+        outs = [np.zeros(pair.o.shape, dtype=T) for _ in range(6)]
+        P.pic_debug_gather_copies(pair.h, P.PIC_HOST, outs)
+        for c in range(6):
+            assert rel_l2(outs[c], expect[c]) <= TOL[precision], c
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_yee_vacuum(precision, ndim):
+    # field-only steps (no particles, J = 0)
+    pair = _random_pair(ndim, precision, npart=0, nx=24, ny=8, nz=40)
+    try:
+        pair.step(10)
+        _compare(pair, TOL[precision] * (10 if precision == 0 else 1), particles=False)
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_current_deposit(precision, ndim, scheme):
+    # Esirkepov current of one step from zero fields (pure drift), filtered
+    pair = _random_pair(ndim, precision, scheme=scheme, npart=6000, nx=20, ny=10, nz=36, field_scale=0.0)
+    try:
+        pair.step(1)
+        T = pair.T
+        outs = [np.zeros(pair.o.shape, dtype=T) for _ in range(3)]
+        P.pic_debug_current(pair.h, P.PIC_HOST, outs)
+        for c, n in enumerate(("jx", "jy", "jz")):
+            assert rel_l2(outs[c], pair.o.f[n]) <= TOL[precision], n
+    finally:
+        pair.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# whole-step parity
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("nx,nz", [(40, 72), (16, 16), (7, 33)])
+def test_step_2d(precision, scheme, nx, nz):
+    pair = _random_pair(2, precision, scheme=scheme, nx=nx, nz=nz, npart=min(20000, nx * nz * 8))
+    try:
+        pair.step(1)
+        _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_step_3d(precision, scheme):
+    pair = _random_pair(3, precision, scheme=scheme, nx=20, ny=12, nz=28, npart=15000, sigma=1.0)
+    try:
+        pair.step(1)
+        _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+def test_multi_step_fp64():
+    # several steps in FP64 stay within the per-step bar (errors grow only by roundoff)
+    pair = _random_pair(2, 1, nx=32, nz=48, npart=12000)
+    try:
+        for _ in range(5):
+            pair.step(1)
+        _compare(pair, 1e-10)
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_edge_particles(precision, ndim):
+    # particles on faces, nodes, next to the wrap on either side, moving backwards
+    nx, ny, nz = 12, 6, 16
+    cfg = make_cfg(ndim=ndim, nx=nx, ny=ny, nz=nz, dt=0.5, precision=precision)
+    part = synth.edge_particles(ndim, nx, ny if ndim == 3 else 1, nz)
+    fields = synth.random_fields((nz, ny if ndim == 3 else 1, nx), seed=3, scale=0.05)
+    pair = Pair(cfg, psi=_coeffs(0, 0.5), fields=fields, part=part)
+    try:
+        for _ in range(3):
+            pair.step(1)
+            _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_empty_and_single(precision):
+    cfg = make_cfg(nx=16, nz=16, precision=precision)
+    pair = Pair(cfg, fields=synth.random_fields((16, 1, 16), seed=1))
+    try:
+        pair.step(2)
+        _compare(pair, TOL[precision], particles=False)
+        assert P.pic_num_particles(pair.h) == 0
+    finally:
+        pair.close()
+    part = synth.random_particles(2, 16, 1, 16, 1, seed=9)
+    pair = Pair(cfg, part=part, fields=synth.random_fields((16, 1, 16), seed=2))
+    try:
+        pair.step(3)
+        _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# beam initialisation and energies
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_beam_init_matches_oracle(precision, ndim):
+    nx, ny, nz, ppc = (20, 1, 36, 4) if ndim == 2 else (10, 8, 12, 8)
+    cfg = make_cfg(ndim=ndim, nx=nx, ny=ny, nz=nz, dt=0.5, precision=precision, ppc=ppc, init_beam=1, seed=11,
+                   sigma_perp=3.0 if ndim == 3 else 0.0)
+    h = P.pic_create(cfg)
+    try:
+        from tests._pic import Pair as _P
+        pair = object.__new__(_P)
+        pair.cfg, pair.h, pair.T = cfg, h, (np.float32 if precision == 0 else np.float64)
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.o = O.Sim(ndim=ndim, nx=nx, ny=ny, nz=nz, dt=0.5)
+        _, p = _P.gpu_state(pair)
+        o = pair.o
+        o.init_beam(ppc=ppc, seed=11, sigma_perp=3.0 if ndim == 3 else 0.0)
+        n = nx * ny * nz * ppc * 2
+        assert len(p["id"]) == n
+        np.testing.assert_array_equal(p["id"], np.arange(n))
+        tol = 1e-14 if precision == 1 else 1e-6
+        assert np.abs(periodic_diff(p["x"], o.part["x"], nx)).max() < tol * 10
+        assert np.abs(periodic_diff(p["z"], o.part["z"], nz)).max() < tol * 10
+        for c in ("ux", "uy", "uz"):
+            assert rel_l2(p[c], o.part[c]) < tol
+        if ndim == 3:
+            assert rel_l2(p["w"], o.part["w"]) < tol
+        else:
+            np.testing.assert_allclose(p["w"], uniform_weight(cfg), rtol=tol)
+    finally:
+        P.pic_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_energies(precision):
+    pair = _random_pair(2, precision, nx=24, nz=40, npart=5000)
+    try:
+        pair.step(2)
+        e = P.pic_energy(pair.h)
+        ref = pair.o.energy()
+        tol = 1e-12 if precision == 1 else 1e-5
+        assert abs(e["w_e"] - ref[0]) <= tol * ref[0]
+        assert abs(e["w_b"] - ref[1]) <= tol * ref[1]
+        assert abs(e["w_perp"] - ref[2]) <= tol * ref[2]
+        assert abs(e["k"] - ref[3]) <= tol * ref[3]
+        assert e["np"] == 5000
+    finally:
+        pair.close()
+
+
+def test_beam_run_fp64_config1_size():
+    # the 2D 64x128, 4 ppc, gamma = 130, alpha = 0.5, Galerkin + Psi beam: 20 FP64 steps vs the oracle
+    cfg = make_cfg(nx=64, nz=128, dt=0.5, precision=1, ppc=4, init_beam=1, seed=1)
+    psi = _coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    P.pic_set_correction_stencil(h, *psi)
+    o = O.Sim(ndim=2, nx=64, nz=128, dt=0.5, psi_e=psi[0], psi_b=psi[1])
+    o.init_beam(ppc=4, seed=1)
+    try:
+        # start the oracle from the GPU's own initial state (identical up to FP64 roundoff)
+        pair = object.__new__(Pair)
+        pair.cfg, pair.h, pair.T, pair.o = cfg, h, np.float64, o
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.npart = 65536
+        _, p0 = pair.gpu_state()
+        o.set_particles(p0["x"], None, p0["z"], p0["ux"], p0["uy"], p0["uz"], p0["w"], p0["q"], pid=p0["id"])
+        for _ in range(4):
+            P.pic_step(h, 5)
+            o.step(5)
+        # fields are tiny and noise-driven; compare with a floor at 1e-6 of the field scale
+        f, p = pair.gpu_state()
+        for n in FIELDS:
+            assert rel_l2(f[n], o.f[n]) < 1e-9, n
+        order = np.argsort(o.pid)
+        assert np.abs(periodic_diff(p["z"], o.part["z"][order], 128)).max() < 1e-10
+        for c in ("ux", "uy", "uz"):
+            assert rel_l2(p[c], o.part[c][order]) < 1e-10
+        e, ref = P.pic_energy(h), o.energy()
+        assert abs(e["w_perp"] - ref[2]) < 1e-8 * ref[2]
+    finally:
+        P.pic_destroy(h)
+
+
+def test_gauss_law_full_size_fp32():
+    # full benchmark size (2D 512x1024, 16 ppc/species, 16.8M particles, FP32): after steps from the
+    # seeded beam, div E - F rho (oracle rho of the GPU particles, oracle filter) stays at roundoff
+    cfg = make_cfg(nx=512, nz=1024, dt=0.5, precision=0, ppc=16, init_beam=1, seed=2, nbin=2, ncomp=1, calpha=2.0,
+                   track_ids=0)
+    psi = _coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    try:
+        P.pic_set_correction_stencil(h, *psi)
+        P.pic_step(h, 3)
+        pair = object.__new__(Pair)
+        pair.cfg, pair.h, pair.T = cfg, h, np.float32
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.o = O.Sim(ndim=2, nx=512, nz=1024, dt=0.5, f_nbin=2, f_ncomp=1, f_alpha=2.0)
+        f, p = pair.gpu_state()
+        assert len(p["x"]) == 512 * 1024 * 32
+        o = pair.o
+        o.set_particles(p["x"], None, p["z"], p["ux"], p["uy"], p["uz"], p["w"], p["q"])
+        o.f.update({n: f[n].reshape(o.shape).copy() for n in FIELDS})
+        g = o.div_e() - o.filter(o.rho())
+        scale = uniform_weight(cfg)  # one macro-particle's charge density
+        assert np.abs(g).max() < 2e-3 * scale
+    finally:
+        P.pic_destroy(h)

@@ -274,14 +274,15 @@ class Sim:
         lib().orc_yee_e(ctypes.byref(self.p), ctypes.byref(F), h)
 
     def deposit(self, x0, z0, x1, z1, vy, qw, y0=None, y1=None):
-        """Esirkepov deposit of one particle into self.f['jx','jy','jz'] (accumulating)."""
+        """Esirkepov deposit of one particle moving from (x0, y0, z0) to (x1, y1, z1), unwrapped grid
+        units, into self.f['jx','jy','jz'] (accumulating)."""
         F = self._fields()
         if self.ndim == 2:
-            lib().orc_deposit_2d(ctypes.byref(self.p), ctypes.byref(F), x0, z0, x1, z1, vy, qw)
+            lib().orc_deposit_2d(ctypes.byref(self.p), ctypes.byref(F), x0, z0, x1 - x0, z1 - z0, vy, qw)
         else:
             r0 = np.array([x0, y0, z0], dtype=np.float64)
-            r1 = np.array([x1, y1, z1], dtype=np.float64)
-            lib().orc_deposit_3d(ctypes.byref(self.p), ctypes.byref(F), _ptr(r0), _ptr(r1), qw)
+            dr = np.array([x1 - x0, y1 - y0, z1 - z0], dtype=np.float64)
+            lib().orc_deposit_3d(ctypes.byref(self.p), ctypes.byref(F), _ptr(r0), _ptr(dr), qw)
 
     def rho(self):
         out = np.zeros(self.shape)

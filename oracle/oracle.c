@@ -405,23 +405,49 @@ void orc_boris_many(const double* q, double dt, double* const E3[3], double* con
  * The weights W satisfy S1(x1)S1(z1) - S1(x0)S1(z0) = Wx + Wz (2D) and the
  * currents follow from discrete continuity,
  *   J_a(node + 1/2 e_a) - J_a(node - 1/2 e_a) = -(q w d_a / (dV dt)) W_a(node),
- * summed from a node left of the footprint where J = 0. x0, x1 are unwrapped
- * positions (grid units) before and after the move.
+ * summed from a node left of the footprint where J = 0.
+ * The move is given as start position r0 (grid units) and displacement dr
+ * (|dr| < 1 cell); shapes are evaluated relative to the start cell
+ * floor(r0), and each shape change dS = S1(n - r0 - dr) - S1(n - r0) is formed
+ * from the displacement: where both arguments lie on the same linear piece of
+ * S1 it equals the slope times -dr exactly, so that a move far below one cell
+ * (the transverse drift of a cold relativistic beam) keeps full relative
+ * precision. Across a kink of S1 the two shape values are subtracted.
  */
-#define FP 6 /* footprint window: enough nodes for |x1 - x0| < 1 */
+#define FP 6 /* footprint window: nodes -2..3 relative to the start cell */
 
-void orc_deposit_2d(const orc_params* p, orc_fields* F, double x0, double z0, double x1, double z1, double vy,
+/* piece of S1 containing a: 0 (a <= -1), 1 (-1 < a <= 0), 2 (0 < a < 1), 3 (a >= 1) */
+static int s1_piece(double a) { return a <= -1.0 ? 0 : a <= 0.0 ? 1 : a < 1.0 ? 2 : 3; }
+
+static double s1_change(double a0, double d) {
+  double a1 = a0 - d;
+  int p = s1_piece(a0);
+  if (p == s1_piece(a1)) {
+    double slope = p == 1 ? 1.0 : p == 2 ? -1.0 : 0.0;
+    return slope * (-d);
+  }
+  return S1(a1) - S1(a0);
+}
+
+/* S0 and dS on the window nodes lo+a, a = 0..FP-1, for one direction */
+static void shape_window(double r0, double dr, int* lo, double S0[FP], double dS[FP]) {
+  double c = floor(r0);
+  double o = r0 - c;
+  *lo = (int)c - 2;
+  for (int a = 0; a < FP; ++a) {
+    double node = a - 2; /* relative to the start cell */
+    S0[a] = S1(node - o);
+    dS[a] = s1_change(node - o, dr);
+  }
+}
+
+void orc_deposit_2d(const orc_params* p, orc_fields* F, double x0, double z0, double ddx, double ddz, double vy,
                     double qw) {
   double dV = p->dx * p->dy * p->dz;
-  int ia = (int)floor(fmin(x0, x1)) - 1;
-  int ka = (int)floor(fmin(z0, z1)) - 1;
+  int ia, ka;
   double S0x[FP], dSx[FP], S0z[FP], dSz[FP];
-  for (int a = 0; a < FP; ++a) {
-    S0x[a] = S1((ia + a) - x0);
-    dSx[a] = S1((ia + a) - x1) - S0x[a];
-    S0z[a] = S1((ka + a) - z0);
-    dSz[a] = S1((ka + a) - z1) - S0z[a];
-  }
+  shape_window(x0, ddx, &ia, S0x, dSx);
+  shape_window(z0, ddz, &ka, S0z, dSz);
   double cx = -qw * p->dx / (dV * p->dt);
   double cz = -qw * p->dz / (dV * p->dt);
   double cy = qw * vy / dV;
@@ -446,19 +472,13 @@ void orc_deposit_2d(const orc_params* p, orc_fields* F, double x0, double z0, do
     }
 }
 
-void orc_deposit_3d(const orc_params* p, orc_fields* F, const double r0[3], const double r1[3], double qw) {
+void orc_deposit_3d(const orc_params* p, orc_fields* F, const double r0[3], const double dr[3], double qw) {
   double dV = p->dx * p->dy * p->dz;
   int n[3] = {p->nx, p->ny, p->nz};
   double d[3] = {p->dx, p->dy, p->dz};
   int lo[3];
   double S0[3][FP], dS[3][FP];
-  for (int ax = 0; ax < 3; ++ax) {
-    lo[ax] = (int)floor(fmin(r0[ax], r1[ax])) - 1;
-    for (int a = 0; a < FP; ++a) {
-      S0[ax][a] = S1((lo[ax] + a) - r0[ax]);
-      dS[ax][a] = S1((lo[ax] + a) - r1[ax]) - S0[ax][a];
-    }
-  }
+  for (int ax = 0; ax < 3; ++ax) shape_window(r0[ax], dr[ax], &lo[ax], S0[ax], dS[ax]);
   double* J[3] = {F->jx, F->jy, F->jz};
   for (int ax = 0; ax < 3; ++ax) {
     int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3; /* the two transverse axes */
@@ -539,18 +559,19 @@ void orc_step(const orc_params* p, orc_fields* F, orc_particles* P) {
     P->ux[m] = u[0];
     P->uy[m] = u[1];
     P->uz[m] = u[2];
-    /* 4. move */
+    /* 4. move: displacement in grid units */
     double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    double x1 = x0 + p->dt * u[0] / gam / p->dx;
-    double y1 = y0 + p->dt * u[1] / gam / p->dy;
-    double z1 = z0 + p->dt * u[2] / gam / p->dz;
+    double ddx = p->dt * u[0] / gam / p->dx;
+    double ddy = p->dt * u[1] / gam / p->dy;
+    double ddz = p->dt * u[2] / gam / p->dz;
+    double x1 = x0 + ddx, y1 = y0 + ddy, z1 = z0 + ddz;
     /* 5. Esirkepov deposition of J^{n+1/2} */
     double qw = P->q[m] * P->w[m];
     if (p->ndim == 2) {
-      orc_deposit_2d(p, F, x0, z0, x1, z1, u[1] / gam, qw);
+      orc_deposit_2d(p, F, x0, z0, ddx, ddz, u[1] / gam, qw);
     } else {
-      double r0[3] = {x0, y0, z0}, r1[3] = {x1, y1, z1};
-      orc_deposit_3d(p, F, r0, r1, qw);
+      double r0[3] = {x0, y0, z0}, dr[3] = {ddx, ddy, ddz};
+      orc_deposit_3d(p, F, r0, dr, qw);
     }
     P->x[m] = wrapf(x1, nn[0]);
     if (p->ndim == 3) P->y[m] = wrapf(y1, nn[1]);

@@ -249,3 +249,24 @@ def test_esirkepov_brute_force_3d():
             J[a] += Jl
     for a, nm in enumerate(("jx", "jy", "jz")):
         np.testing.assert_allclose(sim.f[nm], J[a], atol=1e-14)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_esirkepov_tiny_move_precision(ndim):
+    # A transverse move of 1e-9 cells far from the origin (the drift of a cold gamma = 130 beam is
+    # ~4e-7 cells per step): the current is linear in the displacement, so J / d must match the
+    # small-move limit to FP64 precision, not to 1e-16 / 1e-9.
+    dt, qw = 0.5, 0.8
+    sim = O.Sim(ndim=ndim, nx=300, ny=8, nz=300, dt=dt)
+    x0, y0, z0 = 201.3, 3.6, 123.7
+    d = 1e-9
+    sim.deposit(x0, z0, x0 + d, z0, 0.0, qw, y0=y0, y1=y0)
+    jx = sim.f["jx"]
+    assert abs(jx.sum() - qw * d / dt) < 1e-12 * qw * d / dt
+    # node values: Jx(i+1/2) = (qw/dt) d * S1(z) (S1(y)): the particle's cell column only
+    i, k = 201, 123
+    wz = [1 - 0.7, 0.7]
+    for b in range(2):
+        v = jx[k + b, 3 if ndim == 3 else 0, i] if ndim == 3 else jx[k + b, 0, i]
+        wy = (1 - 0.6) if ndim == 3 else 1.0
+        assert abs(v - qw / dt * d * wz[b] * wy) < 1e-12 * qw / dt * d

@@ -284,6 +284,16 @@ class Sim:
             dr = np.array([x1 - x0, y1 - y0, z1 - z0], dtype=np.float64)
             lib().orc_deposit_3d(ctypes.byref(self.p), ctypes.byref(F), _ptr(r0), _ptr(dr), qw)
 
+    def deposit_move(self, x0, z0, ddx, ddz, vy, qw, y0=0.0, ddy=0.0):
+        """Esirkepov deposit of one particle given its start position and its displacement (grid units)."""
+        F = self._fields()
+        if self.ndim == 2:
+            lib().orc_deposit_2d(ctypes.byref(self.p), ctypes.byref(F), x0, z0, ddx, ddz, vy, qw)
+        else:
+            r0 = np.array([x0, y0, z0], dtype=np.float64)
+            dr = np.array([ddx, ddy, ddz], dtype=np.float64)
+            lib().orc_deposit_3d(ctypes.byref(self.p), ctypes.byref(F), _ptr(r0), _ptr(dr), qw)
+
     def rho(self):
         out = np.zeros(self.shape)
         P = self._particles()

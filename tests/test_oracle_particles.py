@@ -260,7 +260,7 @@ def test_esirkepov_tiny_move_precision(ndim):
     sim = O.Sim(ndim=ndim, nx=300, ny=8, nz=300, dt=dt)
     x0, y0, z0 = 201.3, 3.6, 123.7
     d = 1e-9
-    sim.deposit(x0, z0, x0 + d, z0, 0.0, qw, y0=y0, y1=y0)
+    sim.deposit_move(x0, z0, d, 0.0, 0.0, qw, y0=y0, ddy=0.0)
     jx = sim.f["jx"]
     assert abs(jx.sum() - qw * d / dt) < 1e-12 * qw * d / dt
     # node values: Jx(i+1/2) = (qw/dt) d * S1(z) (S1(y)): the particle's cell column only

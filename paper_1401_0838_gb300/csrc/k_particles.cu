@@ -127,6 +127,48 @@ __device__ __forceinline__ int find_cell(const int* pre, int n, int f) {
   return lo;
 }
 
+// One direction of an Esirkepov move of displacement d (|d| < 1 cell) from offset o in [0,1):
+// the 3-node window (origin a = -1 or 0 relative to the cell), the start shapes S0 and the shape
+// changes dS on it, and the new cell shift and offset. dS is formed from d itself (slope times
+// the move on the linear piece of the spline), not as S(o + d) - S(o), so that moves far below one
+// ulp of the offset (the transverse drift of a cold relativistic beam) keep full relative
+// precision; the three dS always sum to zero (charge conservation).
+template <typename T>
+struct EsirDir {
+  int a, shift;
+  T off;
+  T S0[3], dS[3];
+};
+
+template <typename T>
+__device__ __forceinline__ EsirDir<T> esir_dir(T o, T d) {
+  EsirDir<T> e;
+  const T x1 = o + d;
+  if (x1 < T(0)) {  // into the cell below: window nodes -1, 0, 1
+    e.a = -1;
+    e.S0[0] = T(0); e.S0[1] = T(1) - o; e.S0[2] = o;
+    e.dS[0] = -x1; e.dS[2] = -o; e.dS[1] = -(e.dS[0] + e.dS[2]);
+    e.off = T(1) + x1;
+    e.shift = -1;
+    if (e.off >= T(1)) { e.off = T(0); e.shift = 0; }
+  } else {
+    e.a = 0;
+    e.S0[0] = T(1) - o; e.S0[1] = o; e.S0[2] = T(0);
+    const T am = T(1) - o;  // distance to the upper face
+    const T c = d - am;     // x1 - 1, without the rounding of x1
+    if (x1 >= T(1) && c > T(0)) {  // into the cell above: nodes 0, 1, 2
+      e.dS[0] = -am; e.dS[2] = c; e.dS[1] = -(e.dS[0] + e.dS[2]);
+      e.off = c;
+      e.shift = 1;
+    } else {  // same cell (or onto the upper face within rounding)
+      e.dS[0] = -d; e.dS[1] = d; e.dS[2] = T(0);
+      if (x1 >= T(1)) { e.off = T(0); e.shift = 1; }
+      else { e.off = x1; e.shift = 0; }
+    }
+  }
+  return e;
+}
+
 template <typename T, int NDIM, int SCHEME, bool HAS_W, bool HAS_ID>
 __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
   using S = PushSmem<T, NDIM>;
@@ -258,32 +300,28 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
         T vx = ux * ign, vy = uy * ign, vz = Uz * ign;
         kin += w * (u2 / (gn + T(1)));
 
-        // move (cell-relative)
-        T x1 = ox + r.dtdx * vx;
-        T y1 = NDIM == 3 ? oy + r.dtdy * vy : T(0);
-        T z1 = oz + r.dtdz * vz;
-        if (!(x1 > T(-1) && x1 < T(2) && y1 > T(-1) && y1 < T(2) && z1 > T(-1) && z1 < T(2))) {
+        // move (cell-relative displacement in grid units)
+        T ddx = r.dtdx * vx;
+        T ddy = NDIM == 3 ? r.dtdy * vy : T(0);
+        T ddz = r.dtdz * vz;
+        if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
           flag_error(r.err, ERR_NONFINITE);
-          x1 = ox; y1 = oy; z1 = oz;
+          ddx = ddy = ddz = T(0);
           ux = uy = uz = T(0);
           vx = vy = T(0);
         }
-
-        // Esirkepov: window of 3 nodes per direction starting at min(cell, new cell)
-        const int ax = x1 < T(0) ? -1 : 0;
-        const int ay = y1 < T(0) ? -1 : 0;
-        const int az = z1 < T(0) ? -1 : 0;
+        const EsirDir<T> ex_ = esir_dir(ox, ddx);
+        const EsirDir<T> ez_ = esir_dir(oz, ddz);
+        EsirDir<T> ey_;
+        if (NDIM == 3) ey_ = esir_dir(oy, ddy);
+        else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
+        const int ax = ex_.a, ay = NDIM == 3 ? ey_.a : 0, az = ez_.a;
         T S0x[3], dSx[3], S0y[3], dSy[3], S0z[3], dSz[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          S0x[a] = tri(T(ax + a) - ox);
-          dSx[a] = tri(T(ax + a) - x1) - S0x[a];
-          S0z[a] = tri(T(az + a) - oz);
-          dSz[a] = tri(T(az + a) - z1) - S0z[a];
-          if (NDIM == 3) {
-            S0y[a] = tri(T(ay + a) - oy);
-            dSy[a] = tri(T(ay + a) - y1) - S0y[a];
-          }
+          S0x[a] = ex_.S0[a]; dSx[a] = ex_.dS[a];
+          S0z[a] = ez_.S0[a]; dSz[a] = ez_.dS[a];
+          if (NDIM == 3) { S0y[a] = ey_.S0[a]; dSy[a] = ey_.dS[a]; }
         }
         const T qw = q * w;
         T* sjx = sj;
@@ -357,16 +395,12 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
         }
 
         // new cell and offsets
-        int fx = (int)dev_floor(x1), fy = (int)dev_floor(y1), fz = (int)dev_floor(z1);
-        nox = x1 - T(fx);
-        noy = y1 - T(fy);
-        noz = z1 - T(fz);
-        if (nox >= T(1)) { nox = T(0); fx += 1; }
-        if (noy >= T(1)) { noy = T(0); fy += 1; }
-        if (noz >= T(1)) { noz = T(0); fz += 1; }
-        const int ni = wrapi(gi + fx, r.nx);
-        const int nj = NDIM == 3 ? wrapi(gj + fy, r.ny) : 0;
-        const int nk = wrapi(gk + fz, r.nz);
+        nox = ex_.off;
+        noy = NDIM == 3 ? ey_.off : T(0);
+        noz = ez_.off;
+        const int ni = wrapi(gi + ex_.shift, r.nx);
+        const int nj = NDIM == 3 ? wrapi(gj + ey_.shift, r.ny) : 0;
+        const int nk = wrapi(gk + ez_.shift, r.nz);
         dst = (int)((long long)nk * nxy + (long long)nj * r.nx + ni);
       }
       // 4. rebin: warp-aggregated slot reservation in the destination cell's bin

@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of the stabilised FDTD-Esirkepov PIC step (Godfrey & Vay, arXiv 1401.0838) on GB300.
+
+Workload (one step = one pass of the whole hot path): 2D x-z periodic 512 x 1024 grid,
+16 particles per cell per species (16,777,216 particles), gamma = 130 beam along +z,
+c dt / dz = 0.5, Galerkin gather, Psi_E / Psi_B correction (Sec. 2) and the 3-pass filter
+(2 bilinear + 1 compensation pass, a = 2, per direction) on the current and on the field copies,
+FP32, seeded Philox beam; energies recorded on the device every step. Per step:
+copy stencil -> fused gather/Boris/move/Esirkepov/rebin -> current filter -> Yee (3) -> energy.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path does not shard (one independent replica per GPU, no collective on the data
+path); value = particles of all ranks x K / max-over-ranks time. Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit+filter) and % HBM roofline, FP32 vs FP64"
+UNIT = "particle-steps/s"
+NX, NZ, PPC, ALPHA, GAMMA = 512, 1024, 16, 0.5, 130.0
+FILTER = dict(filter_nbin=2, filter_ncomp=1, filter_comp_alpha=2.0)
+WORKLOAD = ("2D x-z 512x1024 periodic beam, 16 particles/cell/species (16.8M particles), gamma=130, "
+            "c dt/dz=0.5, Galerkin gather, Psi correction + 3-pass binomial/compensation filter, FP32")
+# algorithmic bytes of the fused particle kernel (2D): per particle 2 offsets + 3 momenta read and
+# written (cell index implicit in the per-cell bins); per cell 6 field copies read, 3 currents written
+PUSH_BYTES_PER_PARTICLE = {4: 40, 8: 80}
+PUSH_BYTES_PER_CELL = {4: 36, 8: 72}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def config_dict(n_gpus: int) -> dict:
+    return {"workload": WORKLOAD, "grid": [NX, NZ], "ppc_per_species": PPC, "particles": NX * NZ * PPC * 2,
+            "alpha": ALPHA, "gamma": GAMMA, "scheme": "galerkin",
+            "filter": "2 bilinear + 1 compensation (a=2) per direction on J and on the field copies",
+            "l2": "inputs larger than L2: 671 MB of particle state read + written per step (L2 129 MB)",
+            "parallelism": "replicas" if n_gpus > 1 else "single"}
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed helpers (used with NCCL on GPUs, tested with gloo on CPU)
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def reduce_max(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(ms_local: float, units_local: float, steps: int, device=None) -> dict:
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    ms = reduce_max(ms_local, device)
+    units = reduce_sum(units_local, device)
+    return {"ms": ms, "units": units, "value": units * steps / (ms / 1e3) if ms > 0 else 0.0}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the push kernel from the committed ncu summary, if that summary was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_push_2d_512x1024_fp32.md")
+    src = os.path.join(ROOT, "paper_1401_0838_gb300", "csrc", "k_particles.cu")
+    try:
+        text = open(prof).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    sha, traffic = None, None
+    for line in text.splitlines():
+        if line.startswith("source_sha256:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if sha == digest else None
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def make_handle(P, precision: int, seed: int, stream_ptr):
+    cfg = P.pic_config_default(nx=NX, nz=NZ, dt=ALPHA, gamma=GAMMA, scheme=P.PIC_GALERKIN, precision=precision,
+                               ppc_per_species=PPC, seed=seed, init_beam=1, diag_every=1, **FILTER)
+    h = P.pic_create(cfg)
+    pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, ALPHA)
+    P.pic_set_correction_stencil(h, pe, pb)
+    P.pic_set_stream(h, stream_ptr)
+    return h, cfg
+
+
+def timed_steps(P, torch, h, stream, steps: int, device):
+    """Device time of `steps` whole steps (CUDA events on the launching stream) + per-kernel times."""
+    P.pic_enable_timing(h, True)
+    l0 = P.pic_launch_count(h)
+    barrier(device)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        P.pic_step(h, 1)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(device)
+    ms = e0.elapsed_time(e1)
+    kt = P.pic_kernel_times(h)
+    launches = P.pic_launch_count(h) - l0
+    P.pic_enable_timing(h, False)
+    P.pic_sync(h)
+    return ms, kt, launches
+
+
+def roofline(kt: dict, np_: int, ncell: int, es: int, peak: float, peak_kind: str, traffic=None) -> dict:
+    ms, cnt = kt["push"]
+    per_launch_s = ms / 1e3 / max(cnt, 1)
+    bytes_per_launch = np_ * PUSH_BYTES_PER_PARTICLE[es] + ncell * PUSH_BYTES_PER_CELL[es]
+    achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    return {"kernel": "k_push (fused gather + Boris + move + Esirkepov + rebin)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "launch_ms": round(per_launch_s * 1e3, 4)}
+
+
+def e2e_measure(P, torch, h, cfg, stream, steps: int):
+    """Same metric through the C ABI with host buffers: per step, the full state goes host -> device
+    from pinned memory (pic_set_state), one step runs, and the step's energy sample comes back."""
+    import numpy as np
+    ncell = cfg.nx * cfg.ny * cfg.nz
+    n = P.pic_num_particles(h)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)
+    f = {k: pin((ncell,), torch.float32) for k in ("ex", "ey", "ez", "bx", "by", "bz")}
+    part = {"cell": pin((n,), torch.int32), "species": pin((n,), torch.int32)}
+    for k in ("ox", "oz", "dux", "duy", "duz"):
+        part[k] = pin((n,), torch.float32)
+    s = P.make_state(P.PIC_HOST, f, part)
+    s.np = n
+    P.pic_get_state(h, s)
+    state_in = P.make_state(P.PIC_HOST, f, part)
+    state_in.np = n
+    h2d = 6 * ncell * 4 + n * (4 + 4 + 5 * 4)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        P.pic_set_state(h, state_in)
+        P.pic_step(h, 1)
+        hist = P.pic_energy_history(h, 1)
+        times.append(time.perf_counter() - t0)
+        assert hist and hist[-1]["np"] == n
+    t = statistics.median(times)
+    return {"value": n / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 48,
+            "ms_per_step": round(t * 1e3, 3), "how": "pic_set_state (pinned host) + pic_step(1) + "
+                                                      "pic_energy_history(1), median of steps"}
+
+
+# ------------------------------------------------------------------------------------------------
+# oracle (CPU baseline and reference arm)
+# ------------------------------------------------------------------------------------------------
+SAMPLE_NZ = 64  # the CPU sample is a 512 x 64 slab of the same beam (1/16 of the box)
+
+
+def oracle_sample():
+    import oracle as O
+    st, pe, pb = O.rational_coeffs(O.GALERKIN, ALPHA)
+    sim = O.Sim(ndim=2, nx=NX, nz=SAMPLE_NZ, dt=ALPHA, scheme=O.GALERKIN, psi_e=pe, psi_b=pb,
+                f_nbin=FILTER["filter_nbin"], f_ncomp=FILTER["filter_ncomp"], f_alpha=FILTER["filter_comp_alpha"],
+                f_targets=3)
+    sim.init_beam(ppc=PPC, gamma=GAMMA, seed=2)
+    return sim
+
+
+def oracle_time(steps: int, warmup: int):
+    sim = oracle_sample()
+    for _ in range(warmup):
+        sim.step(1)
+        sim.energy()
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        sim.energy()
+        times.append(time.perf_counter() - t0)
+    return sim.n, times
+
+
+def cpu_baseline(steps: int = 8) -> dict:
+    n, times = oracle_time(steps, 1)
+    t = sum(times) / len(times)
+    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, one thread: {steps} steps of a 512x{SAMPLE_NZ} slab of the same beam "
+                      f"({n} particles, same density, gamma, alpha, correction and filter) + energies each step"}
+
+
+def run_reference(args):
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return
+    steps, warmup = max(args.steps, 1), max(args.warmup, 0)
+    n, times = oracle_time(steps, warmup)
+    total = sum(times)
+    value = n * steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warmup, "ms_per_step": total / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle step (one thread) of a 512x{SAMPLE_NZ} slab of "
+                                       f"the workload ({n} particles) + energies"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1401_0838_gb300 as P
+
+    rank, local, ws = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=device)
+    P.lib()
+    stream = torch.cuda.Stream(device=device)
+    peak, peak_kind = measured_hbm_peak()
+
+    # FP32: the headline
+    h, cfg = make_handle(P, P.PIC_FP32, seed=2 + rank, stream_ptr=stream.cuda_stream)
+    ncell = cfg.nx * cfg.ny * cfg.nz
+    np_ = P.pic_num_particles(h)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            P.pic_step(h, 1)
+    P.pic_sync(h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
+    clk = clocks.stop()
+    hist = P.pic_energy_history(h, 1)
+    assert hist and hist[-1]["np"] == np_, "particle count changed"
+    agg = aggregate(ms, np_, args.steps, device)
+    cells = aggregate(ms, ncell, args.steps, device)
+    launches_all = int(reduce_sum(launches, device))
+    traffic = args.traffic if args.traffic is not None else profiled_traffic()
+    rf = roofline(kt, np_, ncell, 4, peak, peak_kind, traffic=traffic)
+    kernel_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(P, torch, h, cfg, stream, args.e2e_steps)
+        e2e_all = aggregate(e2e["ms_per_step"] * args.e2e_steps, np_, args.e2e_steps, device)
+        e2e["value"] = e2e_all["value"]
+    P.pic_destroy(h)
+
+    # FP64 on the same workload (the metric compares the two precisions)
+    fp64 = None
+    if args.fp64_steps > 0:
+        h64, _ = make_handle(P, P.PIC_FP64, seed=2 + rank, stream_ptr=stream.cuda_stream)
+        for _ in range(2):
+            P.pic_step(h64, 1)
+        P.pic_sync(h64)
+        ms64, kt64, _ = timed_steps(P, torch, h64, stream, args.fp64_steps, device)
+        a64 = aggregate(ms64, np_, args.fp64_steps, device)
+        fp64 = {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms"] / args.fp64_steps,
+                "roofline": roofline(kt64, np_, ncell, 8, peak, peak_kind)}
+        P.pic_destroy(h64)
+
+    line = {"metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": agg["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(ws), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
+            "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
+            "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist.is_initialized():
+        barrier(device)
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

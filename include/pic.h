@@ -83,6 +83,8 @@ typedef struct pic_config {
   int init_beam;            /* 1: pic_create fills the seeded beam; 0: start empty */
   int bin_capacity;         /* particle slots per cell per species; 0: automatic */
   int track_ids;            /* 1: carry a 32-bit id per particle (for tests) */
+  int diag_every;           /* > 0: record the energies on the device every diag_every steps */
+  int diag_capacity;        /* ring size of the energy history; 0: 4096 samples */
 } pic_config;
 
 /* Energies, all FP64 sums over the whole grid / all particles (c = 1, m = 1). */
@@ -180,6 +182,32 @@ int pic_debug_current(pic_handle* h, int where, void* const* out3);
  * the first later sample within one decade of the maximum; if that window has fewer than 5
  * samples, the steepest window of max(5, n/5) samples after the first tenth. Host only. */
 int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_out, int* i0, int* i1);
+
+/* Energies recorded on the device every cfg.diag_every steps (fused into the step: the kinetic
+ * sum and particle count come from the push kernel, the field sums from one reduction launch;
+ * no host synchronisation). Copies out the most recent min(max, recorded, diag_capacity) samples,
+ * oldest first; *count receives that number. Synchronises. */
+int pic_energy_history(pic_handle* h, pic_energy_t* out, int max, int* count);
+
+/* Kernel classes of pic_kernel_times. */
+#define PIC_K_COPIES 0 /* Psi + gather-filter stencil of the field copies */
+#define PIC_K_PUSH 1   /* fused gather + Boris + move + Esirkepov deposition + rebin */
+#define PIC_K_FILTER 2 /* current filter */
+#define PIC_K_YEE 3    /* Yee updates */
+#define PIC_K_DIAG 4   /* energy reductions */
+#define PIC_K_OTHER 5  /* initialisation, import, export */
+#define PIC_NKERNEL 6
+
+/* on = 1: bracket every later kernel launch with CUDA events on the handle's stream and reset the
+ * totals; on = 0: stop. */
+int pic_enable_timing(pic_handle* h, int on);
+
+/* Device milliseconds and launch counts per kernel class since pic_enable_timing(h, 1).
+ * Synchronises. */
+int pic_kernel_times(pic_handle* h, double ms[PIC_NKERNEL], long long launches[PIC_NKERNEL]);
+
+/* Kernel launches made by this handle since it was created. */
+int pic_launch_count(pic_handle* h, long long* n);
 
 /* Frees everything the handle owns. NULL is a no-op. */
 void pic_destroy(pic_handle* h);

@@ -26,7 +26,10 @@ PIC_HOST, PIC_DEVICE = 0, 1
 EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", "pic_set_stream",
            "pic_set_correction_stencil", "pic_step", "pic_sync", "pic_energy", "pic_num_particles",
            "pic_get_state", "pic_set_state", "pic_debug_gather_copies", "pic_debug_current",
-           "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror")
+           "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror", "pic_energy_history",
+           "pic_enable_timing", "pic_kernel_times", "pic_launch_count")
+PIC_NKERNEL = 6
+KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other")
 
 
 class pic_config(ctypes.Structure):
@@ -37,7 +40,8 @@ class pic_config(ctypes.Structure):
                 ("jitter", ctypes.c_double), ("u_th", ctypes.c_double), ("sigma_perp", ctypes.c_double),
                 ("filter_nbin", ctypes.c_int), ("filter_ncomp", ctypes.c_int), ("filter_comp_alpha", ctypes.c_double),
                 ("filter_targets", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("init_beam", ctypes.c_int),
-                ("bin_capacity", ctypes.c_int), ("track_ids", ctypes.c_int)]
+                ("bin_capacity", ctypes.c_int), ("track_ids", ctypes.c_int), ("diag_every", ctypes.c_int),
+                ("diag_capacity", ctypes.c_int)]
 
 
 class pic_energy_t(ctypes.Structure):
@@ -90,6 +94,10 @@ def lib() -> ctypes.CDLL:
         L.pic_destroy.restype = None
         L.pic_last_error.argtypes = [V]
         L.pic_last_error.restype = ctypes.c_char_p
+        L.pic_energy_history.argtypes = [V, P(pic_energy_t), I, P(I)]
+        L.pic_enable_timing.argtypes = [V, I]
+        L.pic_kernel_times.argtypes = [V, DP, P(ctypes.c_longlong)]
+        L.pic_launch_count.argtypes = [V, P(ctypes.c_longlong)]
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -229,3 +237,28 @@ def pic_last_error(h) -> str:
 
 def pic_strerror(code: int) -> str:
     return lib().pic_strerror(code).decode()
+
+
+def pic_energy_history(h, max_samples: int = 4096):
+    buf = (pic_energy_t * max(max_samples, 1))()
+    n = ctypes.c_int()
+    _check(lib().pic_energy_history(h, buf, max_samples, ctypes.byref(n)), h)
+    return [{"w_e": e.w_e, "w_b": e.w_b, "w_perp": e.w_perp, "k": e.k, "total": e.total, "np": e.np}
+            for e in buf[:n.value]]
+
+
+def pic_enable_timing(h, on: bool = True):
+    _check(lib().pic_enable_timing(h, 1 if on else 0), h)
+
+
+def pic_kernel_times(h):
+    ms = (ctypes.c_double * PIC_NKERNEL)()
+    cnt = (ctypes.c_longlong * PIC_NKERNEL)()
+    _check(lib().pic_kernel_times(h, ms, cnt), h)
+    return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(PIC_NKERNEL)}
+
+
+def pic_launch_count(h) -> int:
+    n = ctypes.c_longlong()
+    _check(lib().pic_launch_count(h, ctypes.byref(n)), h)
+    return n.value

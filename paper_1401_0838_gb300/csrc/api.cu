@@ -43,6 +43,22 @@ struct pic_handle {
   // taps (FP64, host) of the copy and current stencils
   double pe[5] = {1, 0, 0, 0, 0}, pb[5] = {1, 0, 0, 0, 0};
   std::vector<double> zt_e, zt_b, xt_g, zt_j, xt_j;
+  // energy history (device ring of 8 doubles per sample: sum E^2, sum B^2, sum perp^2, K, np)
+  double* d_hist = nullptr;
+  int hist_cap = 0;
+  long long nhist = 0;
+  long long nstep = 0;
+  // kernel timing
+  bool timing = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double tms[PIC_NKERNEL] = {};
+  long long tcount[PIC_NKERNEL] = {};
+  long long launches = 0;
   std::string err;
 };
 
@@ -63,6 +79,50 @@ int cuda_fail(pic_handle* h, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                         \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
+
+cudaEvent_t take_event(pic_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Accumulate the elapsed times of every bracketed launch (synchronises the stream).
+cudaError_t collect_times(pic_handle* h) {
+  if (h->pending.empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->tms[p.cls] += ms;
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->pending.clear();
+  return cudaSuccess;
+}
+
+// Launch one kernel of class `cls`, counted, and bracketed by events when timing is on.
+template <class F>
+cudaError_t launch(pic_handle* h, int cls, F&& go) {
+  h->launches++;
+  h->tcount[cls]++;
+  if (!h->timing) return go();
+  if (h->pending.size() > 200000) {
+    cudaError_t e = collect_times(h);
+    if (e != cudaSuccess) return e;
+  }
+  pic_handle::Pending p{take_event(h), take_event(h), cls};
+  cudaEventRecord(p.a, h->stream);
+  cudaError_t e = go();
+  cudaEventRecord(p.b, h->stream);
+  h->pending.push_back(p);
+  return e;
+}
 
 void* dalloc(pic_handle* h, size_t bytes) {
   void* p = nullptr;
@@ -233,20 +293,37 @@ template <typename T>
 int step_once(pic_handle* h) {
   cudaStream_t st = h->stream;
   const size_t fb = (size_t)h->ncell * sizeof(T);
+  const bool rec = h->cfg.diag_every > 0 && (h->nstep + 1) % h->cfg.diag_every == 0;
+  double* slot = rec ? h->d_hist + 8 * (h->nhist % h->hist_cap) : nullptr;
+  if (rec) CK(cudaMemsetAsync(slot, 0, 8 * sizeof(double), st), "zero history slot");
   // 1. field copies seen by the particles: Psi(D_z) and the gather filter
-  CK(launch_sep<T>(sep_args<T>(h, true), st), "copy stencil");
+  SepArgs<T> ca = sep_args<T>(h, true);
+  CK(launch(h, PIC_K_COPIES, [&] { return launch_sep<T>(ca, st); }), "copy stencil");
   // 2-5. gather, Boris, move, Esirkepov, rebin
   for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(h->f[6 + q], 0, fb, st), "zero J");
   RunDev<T> r = make_run<T>(h, h->parity);
-  CK(launch_push<T>(r, h->has_w, h->has_id, st), "push");
+  r.kin = rec ? slot + 3 : nullptr;
+  CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, h->has_w, h->has_id, st); }), "push");
   // 6. current filter
-  if (h->cfg.filter_targets & PIC_FILTER_J) CK(launch_sep<T>(sep_args<T>(h, false), st), "current filter");
+  if (h->cfg.filter_targets & PIC_FILTER_J) {
+    SepArgs<T> ja = sep_args<T>(h, false);
+    CK(launch(h, PIC_K_FILTER, [&] { return launch_sep<T>(ja, st); }), "current filter");
+  }
   // 7. Yee: B half, E full, B half
   const double dt = h->cfg.dt;
-  CK(launch_yee_b<T>(yee_args<T>(h, 0.5 * dt), st), "yee B");
-  CK(launch_yee_e<T>(yee_args<T>(h, dt), st), "yee E");
-  CK(launch_yee_b<T>(yee_args<T>(h, 0.5 * dt), st), "yee B");
+  YeeArgs<T> yb = yee_args<T>(h, 0.5 * dt), ye = yee_args<T>(h, dt);
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_b<T>(yb, st); }), "yee B");
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_e<T>(ye, st); }), "yee E");
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_b<T>(yb, st); }), "yee B");
+  // 8. diagnostics: field energies of the new state into the history slot
+  if (rec) {
+    const T* f6[6];
+    for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
+    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, slot, st); }), "field energy");
+    h->nhist++;
+  }
   h->parity ^= 1;
+  h->nstep++;
   return PIC_OK;
 }
 
@@ -269,7 +346,11 @@ int init_beam(pic_handle* h) {
   int lat[3];
   lattice_dims(c.ndim, c.ppc_per_species, lat);
   RunDev<T> r = make_run<T>(h, h->parity);
-  CK(launch_init_beam<T>(r, c.ppc_per_species, lat, h->u0, h->w0, c.jitter, c.u_th, c.sigma_perp, c.seed, h->stream),
+  CK(launch(h, PIC_K_OTHER,
+            [&] {
+              return launch_init_beam<T>(r, c.ppc_per_species, lat, h->u0, h->w0, c.jitter, c.u_th, c.sigma_perp,
+                                         c.seed, h->stream);
+            }),
      "init beam");
   return PIC_OK;
 }
@@ -346,7 +427,7 @@ int set_state_t(pic_handle* h, const pic_state* s) {
   if (s->id && h->has_id) CK(cudaMemcpyAsync(f.id, s->id, 4 * (size_t)n, k, st), "copy id");
   else f.id = nullptr;
   RunDev<T> r = make_run<T>(h, 0);
-  CK(launch_import<T>(r, f, st), "import");
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_import<T>(r, f, st); }), "import");
   return PIC_OK;
 }
 
@@ -396,7 +477,7 @@ int get_state_t(pic_handle* h, pic_state* s) {
   for (int sp = 0; sp < 2; ++sp) {
     CK(launch_count_prefix(h->cnt[sp][h->parity], h->ncell, h->cap, h->d_offs, h->d_bsum, h->d_total, st),
        "count prefix");
-    CK(launch_export<T>(r, sp, h->d_offs, base, f, st), "export");
+    CK(launch(h, PIC_K_OTHER, [&] { return launch_export<T>(r, sp, h->d_offs, base, f, st); }), "export");
     base += cnts[sp];
   }
   if (s->cell) CK(cudaMemcpyAsync(s->cell, f.cell, 4 * (size_t)n, k, st), "copy cell out");
@@ -419,9 +500,9 @@ int energy_t(pic_handle* h, pic_energy_t* out) {
   CK(cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), st), "zero accumulators");
   const T* f6[6];
   for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-  CK(launch_field_energy<T>(f6, h->ncell, h->d_acc, st), "field energy");
+  CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, h->d_acc, st); }), "field energy");
   RunDev<T> r = make_run<T>(h, h->parity);
-  CK(launch_kinetic<T>(r, h->d_acc + 3, st), "kinetic energy");
+  CK(launch(h, PIC_K_DIAG, [&] { return launch_kinetic<T>(r, h->d_acc + 3, st); }), "kinetic energy");
   double acc[8];
   CK(cudaMemcpyAsync(acc, h->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st), "read energies");
   long long cnts[2];
@@ -490,6 +571,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       !(c.dz > 0) || !(c.dt > 0) || !(c.gamma >= 1.0) || (c.scheme != PIC_GALERKIN && c.scheme != PIC_UNIFORM) ||
       c.shape_order != 1 || (c.precision != PIC_FP32 && c.precision != PIC_FP64) || c.ppc_per_species < 0 ||
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
+      c.diag_every < 0 || c.diag_capacity < 0 ||
       (long long)c.nx * c.ny * c.nz > (1ll << 31) - 1)
     return PIC_E_ARG;
   const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
@@ -535,6 +617,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
   if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
   if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;
+  h->hist_cap = c.diag_capacity > 0 ? c.diag_capacity : 4096;
+  if (ok) ok = (h->d_hist = (double*)dalloc(h, 8 * sizeof(double) * (size_t)h->hist_cap)) != nullptr;
   if (!ok) {
     pic_destroy(h);
     return PIC_E_OOM;
@@ -639,11 +723,75 @@ int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_o
   return growth_fit(t, w, n, gamma_out, i0, i1);
 }
 
+int pic_energy_history(pic_handle* h, pic_energy_t* out, int max, int* count) {
+  if (!h || (!out && max > 0) || max < 0) return PIC_E_ARG;
+  int rc = check_err(h);
+  if (rc) return rc;
+  long long avail = h->nhist < h->hist_cap ? h->nhist : h->hist_cap;
+  long long n = avail < max ? avail : max;
+  std::vector<double> buf(8 * (size_t)(n > 0 ? n : 1));
+  const long long first = (h->nhist - n) % h->hist_cap;  // ring slot of the oldest sample wanted
+  const long long run1 = n < h->hist_cap - first ? n : h->hist_cap - first;
+  if (n > 0) {
+    CK(cudaMemcpy(buf.data(), h->d_hist + 8 * first, 8 * sizeof(double) * run1, cudaMemcpyDeviceToHost),
+       "read history");
+    if (n > run1)
+      CK(cudaMemcpy(buf.data() + 8 * run1, h->d_hist, 8 * sizeof(double) * (n - run1), cudaMemcpyDeviceToHost),
+         "read history");
+  }
+  const pic_config& c = h->cfg;
+  const double dV = c.dx * c.dy * c.dz;
+  for (long long q = 0; q < n; ++q) {
+    const double* v = buf.data() + 8 * q;  // oldest first
+    out[q].w_e = 0.5 * v[0] * dV;
+    out[q].w_b = 0.5 * v[1] * dV;
+    out[q].w_perp = 0.5 * v[2] * dV;
+    out[q].k = v[3];
+    out[q].total = out[q].w_e + out[q].w_b + out[q].k;
+    out[q].np = (long long)v[4];
+  }
+  if (count) *count = (int)n;
+  return PIC_OK;
+}
+
+int pic_enable_timing(pic_handle* h, int on) {
+  if (!h) return PIC_E_ARG;
+  CK(collect_times(h), "collect timings");
+  h->timing = on != 0;
+  if (on)
+    for (int q = 0; q < PIC_NKERNEL; ++q) {
+      h->tms[q] = 0.0;
+      h->tcount[q] = 0;
+    }
+  return PIC_OK;
+}
+
+int pic_kernel_times(pic_handle* h, double ms[PIC_NKERNEL], long long launches[PIC_NKERNEL]) {
+  if (!h) return PIC_E_ARG;
+  CK(collect_times(h), "collect timings");
+  for (int q = 0; q < PIC_NKERNEL; ++q) {
+    if (ms) ms[q] = h->tms[q];
+    if (launches) launches[q] = h->tcount[q];
+  }
+  return PIC_OK;
+}
+
+int pic_launch_count(pic_handle* h, long long* n) {
+  if (!h || !n) return PIC_E_ARG;
+  *n = h->launches;
+  return PIC_OK;
+}
+
 void pic_destroy(pic_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs)
     if (p) cudaFree(p);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }

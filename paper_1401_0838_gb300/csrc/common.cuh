@@ -46,7 +46,8 @@ struct RunDev {
   T* j[3];            // current accumulator
   SpeciesBuf<T> in[2], out[2];
   int* err;
-  double* kin;        // FP64 accumulator for sum w (gamma - 1) of this step (may be nullptr)
+  double* kin;        // FP64 accumulators of this step: [0] sum w (gamma - 1), [1] particle count
+                      // (nullptr: not recorded)
 };
 
 // ---------------------------------------------------------------------------------------------

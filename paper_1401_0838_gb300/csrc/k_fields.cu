@@ -88,8 +88,12 @@ cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
   int LX = CX + 2 * a.hx, LY = CY + 2 * hy, LZ = CZ + 2 * hzmax;
   size_t sm = sizeof(T) * ((size_t)LX * LY * LZ + (size_t)LX * LY * CZ + (a.ndim == 3 ? (size_t)LX * CY * CZ : 0));
   int ntx = (a.nx + CX - 1) / CX, nty = a.ndim == 3 ? (a.ny + CY - 1) / CY : 1, ntz = (a.nz + CZ - 1) / CZ;
-  cudaError_t e = cudaFuncSetAttribute(k_sep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  static size_t attr_bytes = 0;  // largest dynamic shared memory size enabled so far
+  if (sm > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_sep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_bytes = sm;
+  }
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
   k_sep<T><<<grid, SEP_THREADS, sm, st>>>(a, CX, CY, CZ, ntx, nty);
   return cudaGetLastError();

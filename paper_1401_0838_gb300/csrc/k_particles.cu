@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) sj[e] = T(0);
 
   T kin = T(0);  // per-thread partial sum of w (gamma - 1)
+  int npush = 0;  // particles pushed by this thread
   for (int s = 0; s < 2; ++s) {
     const SpeciesBuf<T> pin = r.in[s];
     const SpeciesBuf<T> pout = r.out[s];
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
         T ign = T(1) / gn;
         T vx = ux * ign, vy = uy * ign, vz = Uz * ign;
         kin += w * (u2 / (gn + T(1)));
+        ++npush;
 
         // move (cell-relative displacement in grid units)
         T ddx = r.dtdx * vx;
@@ -444,18 +446,32 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
     atomicAdd(r.j[c] + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
   }
 
-  // 6. kinetic energy of this step: per-thread FP32 partial sums, FP64 across the block
+  // 6. kinetic energy and particle count of this step: per-thread partial sums in the working
+  // precision, FP64 across the block and the grid
   if (r.kin) {
     double kd = (double)kin;
+    int nd = npush;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) kd += __shfl_xor_sync(0xffffffffu, kd, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      kd += __shfl_xor_sync(0xffffffffu, kd, o);
+      nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
     __shared__ double skin[PUSH_THREADS / 32];
-    if (lane == 0) skin[warp] = kd;
+    __shared__ int scnt[PUSH_THREADS / 32];
+    if (lane == 0) {
+      skin[warp] = kd;
+      scnt[warp] = nd;
+    }
     __syncthreads();
     if (tid == 0) {
       double t = 0;
-      for (int w2 = 0; w2 < PUSH_THREADS / 32; ++w2) t += skin[w2];
+      long long c = 0;
+      for (int w2 = 0; w2 < PUSH_THREADS / 32; ++w2) {
+        t += skin[w2];
+        c += scnt[w2];
+      }
       atomicAdd(r.kin, t);
+      atomicAdd(r.kin + 1, (double)c);
     }
   }
 }
@@ -466,8 +482,12 @@ static cudaError_t launch_push_t(const RunDev<T>& r, bool has_w, bool has_id, cu
   const size_t sm = S::bytes();
   const int ntiles = r.ntx * r.nty * r.ntz;
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+    static bool attr_set = false;  // one per kernel instantiation
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
     kern<<<ntiles, PUSH_THREADS, sm, st>>>(r);
     return cudaGetLastError();
   };

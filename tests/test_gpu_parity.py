@@ -260,10 +260,14 @@ def test_beam_run_fp64_config1_size():
         for _ in range(4):
             P.pic_step(h, 5)
             o.step(5)
-        # fields are tiny and noise-driven; compare with a floor at 1e-6 of the field scale
+        # The pair plasma is neutral and co-moving: each species carries a current density
+        # n_s c = omega_p^2 / 2 while the net current is ~1e-6 of that, so the summation order of the
+        # deposit (atomics) moves the net fields by FP64 roundoff of the per-species current. Errors
+        # are therefore normalised by the field change one step of one species' current makes.
         f, p = pair.gpu_state()
+        gross = math.sqrt(64 * 128) * 0.5 * 0.3868 ** 2 / 2
         for n in FIELDS:
-            assert rel_l2(f[n], o.f[n]) < 1e-10, n
+            assert rel_l2(f[n], o.f[n], floor=gross) < 1e-10, (n, rel_l2(f[n], o.f[n], floor=gross))
         order = np.argsort(o.pid)
         assert np.abs(periodic_diff(p["z"], o.part["z"][order], 128)).max() < 1e-10
         for c in ("ux", "uy", "uz"):

@@ -588,7 +588,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   h->has_id = c.track_ids != 0;
   int cap = c.bin_capacity;
   if (cap == 0) cap = c.ppc_per_species * 2 + 8;
-  cap = (cap + 7) / 8 * 8;
+  const int align = (int)(64 / h->es);  // bins start on 64-byte boundaries
+  cap = (cap + align - 1) / align * align;
   h->cap = cap;
   cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
   if (e != cudaSuccess) {

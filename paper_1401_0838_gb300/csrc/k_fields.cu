@@ -3,7 +3,21 @@
 #include "common.cuh"
 #include "launch.h"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace picgb {
+
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> enabled;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = enabled.find(kernel);
+  if (it != enabled.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) enabled[kernel] = bytes;
+  return e;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Separable periodic stencil. One CTA computes a CX x CY x CZ output tile of one component:
@@ -88,12 +102,8 @@ cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
   int LX = CX + 2 * a.hx, LY = CY + 2 * hy, LZ = CZ + 2 * hzmax;
   size_t sm = sizeof(T) * ((size_t)LX * LY * LZ + (size_t)LX * LY * CZ + (a.ndim == 3 ? (size_t)LX * CY * CZ : 0));
   int ntx = (a.nx + CX - 1) / CX, nty = a.ndim == 3 ? (a.ny + CY - 1) / CY : 1, ntz = (a.nz + CZ - 1) / CZ;
-  static size_t attr_bytes = 0;  // largest dynamic shared memory size enabled so far
-  if (sm > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_sep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr_bytes = sm;
-  }
+  cudaError_t e = ensure_dynamic_smem((const void*)k_sep<T>, sm);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
   k_sep<T><<<grid, SEP_THREADS, sm, st>>>(a, CX, CY, CZ, ntx, nty);
   return cudaGetLastError();

@@ -169,6 +169,72 @@ __device__ __forceinline__ EsirDir<T> esir_dir(T o, T d) {
   return e;
 }
 
+// Layout of one particle's current contributions: index i -> (component, node offset in the
+// 3-node window). 2D: 6 Jx (b*2+a), 6 Jz (6+a*2+b), 9 Jy (12+b*3+a). 3D: 18 Jx ((c*3+b)*2+a),
+// 18 Jy (18+(c*3+a)*2+b), 18 Jz (36+(b*3+a)*2+c); a, b, c are the x, y, z node offsets.
+template <int NDIM>
+struct DepLayout;
+template <>
+struct DepLayout<2> {
+  static constexpr int NV = 21;
+  static __device__ __forceinline__ void at(int i, int& comp, int& a, int& b, int& c) {
+    b = 0;
+    if (i < 6) { comp = 0; c = i >> 1; a = i & 1; }
+    else if (i < 12) { comp = 2; a = (i - 6) >> 1; c = (i - 6) & 1; }
+    else { comp = 1; c = (i - 12) / 3; a = (i - 12) % 3; }
+  }
+};
+template <>
+struct DepLayout<3> {
+  static constexpr int NV = 54;
+  static __device__ __forceinline__ void at(int i, int& comp, int& a, int& b, int& c) {
+    if (i < 18) { comp = 0; a = i & 1; b = (i >> 1) % 3; c = (i >> 1) / 3; }
+    else if (i < 36) { const int m = i - 18; comp = 1; b = m & 1; a = (m >> 1) % 3; c = (m >> 1) / 3; }
+    else { const int m = i - 36; comp = 2; c = m & 1; a = (m >> 1) % 3; b = (m >> 1) / 3; }
+  }
+};
+
+// Add the NV contributions of every valid lane into shared memory. Lanes are grouped by window
+// origin `key`; per group and per round of 32 values, a butterfly transpose-reduction leaves in
+// lane l the group's sum of value l, which that lane adds with one shared-memory atomic (the 32
+// lanes of a round touch distinct addresses).
+template <typename T, int NDIM>
+__device__ __forceinline__ void deposit_warp(T* sj, const T (&dv)[DepLayout<NDIM>::NV], int key, bool valid,
+                                             int lane) {
+  using S = PushSmem<T, NDIM>;
+  constexpr int NV = DepLayout<NDIM>::NV;
+  constexpr int ROUNDS = (NV + 31) / 32;
+  unsigned pending = __ballot_sync(0xffffffffu, valid);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    const int k = __shfl_sync(0xffffffffu, key, src);
+    const bool mine = valid && key == k;
+    pending &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+    for (int rd = 0; rd < ROUNDS; ++rd) {
+      T x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = (mine && rd * 32 + i < NV) ? dv[rd * 32 + i] : T(0);
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const bool up = (lane & sh) != 0;
+#pragma unroll
+        for (int j = 0; j < sh; ++j) {
+          const T send = up ? x[j] : x[j + sh];
+          const T keep = up ? x[j + sh] : x[j];
+          x[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+        }
+      }
+      const int i = rd * 32 + lane;
+      if (i < NV && x[0] != T(0)) {
+        int comp, a, b, c;
+        DepLayout<NDIM>::at(i, comp, a, b, c);
+        atomicAdd(sj + comp * S::JN + k + (c * S::JY + b) * S::JX + a, x[0]);
+      }
+    }
+  }
+}
+
 template <typename T, int NDIM, int SCHEME, bool HAS_W, bool HAS_ID>
 __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
   using S = PushSmem<T, NDIM>;
@@ -259,6 +325,9 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
       int dst = -1 - lane;  // unique per lane when invalid
       T nox = 0, noy = 0, noz = 0, ux = 0, uy = 0, uz = 0, w = 0;
       unsigned pid = 0;
+      constexpr int NV = DepLayout<NDIM>::NV;
+      T dv[NV];
+      int wkey = -1;
       if (valid) {
         const int cl = find_cell(spre, NCL, f);
         const int j = f - spre[cl];
@@ -326,73 +395,63 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
           if (NDIM == 3) { S0y[a] = ey_.S0[a]; dSy[a] = ey_.dS[a]; }
         }
         const T qw = q * w;
-        T* sjx = sj;
-        T* sjy = sj + S::JN;
-        T* sjz = sj + 2 * S::JN;
+        // per-particle current contributions v[i] to the smem tile at offset dep_off<NDIM>(i)
+        // from the window origin (bx, by, bz)
         const int bx = lx + ax + 1, by = NDIM == 3 ? ly + ay + 1 : 0, bz = lz + az + 1;
+        wkey = (bz * S::JY + by) * S::JX + bx;
         if (NDIM == 2) {
           const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
 #pragma unroll
-          for (int b = 0; b < 3; ++b) {
+          for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b): running sum over a
             T fz = S0z[b] + T(0.5) * dSz[b];
             T a0 = dSx[0] * fz, a1 = a0 + dSx[1] * fz;
-            T* row = sjx + (bz + b) * S::JX + bx;
-            atomicAdd(row, cx * a0);
-            atomicAdd(row + 1, cx * a1);
+            dv[b * 2 + 0] = cx * a0;
+            dv[b * 2 + 1] = cx * a1;
           }
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
+          for (int a = 0; a < 3; ++a) {  // Jz(a, b+1/2): running sum over b
             T fx = S0x[a] + T(0.5) * dSx[a];
             T a0 = dSz[0] * fx, a1 = a0 + dSz[1] * fx;
-            T* col = sjz + bz * S::JX + bx + a;
-            atomicAdd(col, cz * a0);
-            atomicAdd(col + S::JX, cz * a1);
+            dv[6 + a * 2 + 0] = cz * a0;
+            dv[6 + a * 2 + 1] = cz * a1;
           }
 #pragma unroll
           for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              T wy = S0x[a] * S0z[b] + T(0.5) * dSx[a] * S0z[b] + T(0.5) * S0x[a] * dSz[b] +
-                     dSx[a] * dSz[b] * T(1.0 / 3.0);
-              atomicAdd(sjy + (bz + b) * S::JX + bx + a, cy * wy);
-            }
+            for (int a = 0; a < 3; ++a)  // Jy(a, b): out-of-plane weight
+              dv[12 + b * 3 + a] = cy * (S0x[a] * S0z[b] + T(0.5) * dSx[a] * S0z[b] + T(0.5) * S0x[a] * dSz[b] +
+                                         dSx[a] * dSz[b] * T(1.0 / 3.0));
         } else {
           const T cx = qw * r.jfx, cy = qw * r.jfy, cz = qw * r.jfz;
-          // Jx(a+1/2, b, c)
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
+            for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b, c)
               T tr = S0y[b] * S0z[c] + T(0.5) * dSy[b] * S0z[c] + T(0.5) * S0y[b] * dSz[c] +
                      dSy[b] * dSz[c] * T(1.0 / 3.0);
               T a0 = dSx[0] * tr, a1 = a0 + dSx[1] * tr;
-              T* p = sjx + ((bz + c) * S::JY + by + b) * S::JX + bx;
-              atomicAdd(p, cx * a0);
-              atomicAdd(p + 1, cx * a1);
+              dv[(c * 3 + b) * 2 + 0] = cx * a0;
+              dv[(c * 3 + b) * 2 + 1] = cx * a1;
             }
-          // Jy(a, b+1/2, c)
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < 3; ++a) {  // Jy(a, b+1/2, c)
               T tr = S0x[a] * S0z[c] + T(0.5) * dSx[a] * S0z[c] + T(0.5) * S0x[a] * dSz[c] +
                      dSx[a] * dSz[c] * T(1.0 / 3.0);
               T a0 = dSy[0] * tr, a1 = a0 + dSy[1] * tr;
-              T* p = sjy + ((bz + c) * S::JY + by) * S::JX + bx + a;
-              atomicAdd(p, cy * a0);
-              atomicAdd(p + S::JX, cy * a1);
+              dv[18 + (c * 3 + a) * 2 + 0] = cy * a0;
+              dv[18 + (c * 3 + a) * 2 + 1] = cy * a1;
             }
-          // Jz(a, b, c+1/2)
 #pragma unroll
           for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < 3; ++a) {  // Jz(a, b, c+1/2)
               T tr = S0x[a] * S0y[b] + T(0.5) * dSx[a] * S0y[b] + T(0.5) * S0x[a] * dSy[b] +
                      dSx[a] * dSy[b] * T(1.0 / 3.0);
               T a0 = dSz[0] * tr, a1 = a0 + dSz[1] * tr;
-              T* p = sjz + (bz * S::JY + by + b) * S::JX + bx + a;
-              atomicAdd(p, cz * a0);
-              atomicAdd(p + S::JX * S::JY, cz * a1);
+              dv[36 + (b * 3 + a) * 2 + 0] = cz * a0;
+              dv[36 + (b * 3 + a) * 2 + 1] = cz * a1;
             }
         }
 
@@ -405,6 +464,10 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
         const int nk = wrapi(gk + ez_.shift, r.nz);
         dst = (int)((long long)nk * nxy + (long long)nj * r.nx + ni);
       }
+      // deposit: lanes that share a window origin sum their contributions by a warp transpose-
+      // reduction, then every lane adds one distinct value to shared memory (no atomic conflicts)
+      deposit_warp<T, NDIM>(sj, dv, wkey, valid, lane);
+
       // 4. rebin: warp-aggregated slot reservation in the destination cell's bin
       const unsigned peers = __match_any_sync(0xffffffffu, dst);
       const int leader = __ffs(peers) - 1;
@@ -481,13 +544,9 @@ static cudaError_t launch_push_t(const RunDev<T>& r, bool has_w, bool has_id, cu
   using S = PushSmem<T, NDIM>;
   const size_t sm = S::bytes();
   const int ntiles = r.ntx * r.nty * r.ntz;
-  auto go = [&](auto kern) -> cudaError_t {
-    static bool attr_set = false;  // one per kernel instantiation
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
+  auto go = [&](void (*kern)(RunDev<T>)) -> cudaError_t {
+    cudaError_t e = ensure_dynamic_smem((const void*)kern, sm);
+    if (e != cudaSuccess) return e;
     kern<<<ntiles, PUSH_THREADS, sm, st>>>(r);
     return cudaGetLastError();
   };

@@ -42,6 +42,9 @@ struct YeeArgs {
 
 void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);
 
+// Raise a kernel's dynamic shared memory limit to `bytes` (once per kernel and size).
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 template <typename T>
 cudaError_t launch_push(const RunDev<T>& r, bool has_w, bool has_id, cudaStream_t st);
 template <typename T>

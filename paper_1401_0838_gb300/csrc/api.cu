@@ -303,7 +303,7 @@ int step_once(pic_handle* h) {
   for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(h->f[6 + q], 0, fb, st), "zero J");
   RunDev<T> r = make_run<T>(h, h->parity);
   r.kin = rec ? slot + 3 : nullptr;
-  CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, h->has_w, h->has_id, st); }), "push");
+  CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
   // 6. current filter
   if (h->cfg.filter_targets & PIC_FILTER_J) {
     SepArgs<T> ja = sep_args<T>(h, false);

@@ -33,7 +33,7 @@ struct PushSmem {
   // current tile: nodes [X0-1, X0+TX+1]
   static constexpr int JX = TX + 3, JY = (NDIM == 3 ? TY + 3 : 1), JZ = TZ + 3, JN = JX * JY * JZ;
   static constexpr size_t bytes() {
-    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (NCL + 1 + PUSH_THREADS / 32 + 1);
+    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (2 * NCL);
   }
 };
 
@@ -117,16 +117,6 @@ __device__ __forceinline__ T gather_comp(const T* __restrict__ sgc, int c, int l
   return acc;
 }
 
-// Largest c in [0, n) with pre[c] <= f (pre is a nondecreasing exclusive prefix, pre[0] = 0).
-__device__ __forceinline__ int find_cell(const int* pre, int n, int f) {
-  int lo = 0, hi = n;  // invariant pre[lo] <= f < pre[hi] (pre[n] = total > f)
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (pre[mid] <= f) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // One direction of an Esirkepov move of displacement d (|d| < 1 cell) from offset o in [0,1):
 // the 3-node window (origin a = -1 or 0 relative to the cell), the start shapes S0 and the shape
 // changes dS on it, and the new cell shift and offset. dS is formed from d itself (slope times
@@ -194,69 +184,62 @@ struct DepLayout<3> {
   }
 };
 
-// Add the NV contributions of every valid lane into shared memory. Lanes are grouped by window
-// origin `key`; per group and per round of 32 values, a butterfly transpose-reduction leaves in
-// lane l the group's sum of value l, which that lane adds with one shared-memory atomic (the 32
-// lanes of a round touch distinct addresses).
-template <typename T, int NDIM>
-__device__ __forceinline__ void deposit_warp(T* sj, const T (&dv)[DepLayout<NDIM>::NV], int key, bool valid,
-                                             int lane) {
-  using S = PushSmem<T, NDIM>;
-  constexpr int NV = DepLayout<NDIM>::NV;
-  constexpr int ROUNDS = (NV + 31) / 32;
-  unsigned pending = __ballot_sync(0xffffffffu, valid);
-  while (pending) {
-    const int src = __ffs(pending) - 1;
-    const int k = __shfl_sync(0xffffffffu, key, src);
-    const bool mine = valid && key == k;
-    pending &= ~__ballot_sync(0xffffffffu, mine);
-#pragma unroll
-    for (int rd = 0; rd < ROUNDS; ++rd) {
-      T x[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = (mine && rd * 32 + i < NV) ? dv[rd * 32 + i] : T(0);
-#pragma unroll
-      for (int sh = 16; sh >= 1; sh >>= 1) {
-        const bool up = (lane & sh) != 0;
-#pragma unroll
-        for (int j = 0; j < sh; ++j) {
-          const T send = up ? x[j] : x[j + sh];
-          const T keep = up ? x[j + sh] : x[j];
-          x[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
-        }
-      }
-      const int i = rd * 32 + lane;
-      if (i < NV && x[0] != T(0)) {
-        int comp, a, b, c;
-        DepLayout<NDIM>::at(i, comp, a, b, c);
-        atomicAdd(sj + comp * S::JN + k + (c * S::JY + b) * S::JX + a, x[0]);
-      }
-    }
-  }
+// Vector loads of 4 consecutive slots (16-byte aligned: bins start on 64-byte boundaries and
+// packs start at multiples of 4 slots).
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void load4(const unsigned* p, unsigned (&o)[4]) {
+  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 
-template <typename T, int NDIM, int SCHEME, bool HAS_W, bool HAS_ID>
+// Work assignment of the push kernel: a warp takes CPW = 32/LPC cells of its tile at a time,
+// LPC lanes per cell. The cell's particles are split into packs of 4 consecutive slots of one
+// species (electron packs first); lane l of the cell takes packs l, l + LPC, ... . Each lane sums
+// the Esirkepov contributions of its particles in registers (all particles whose 3-node window
+// starts at their own cell, which is every particle that does not step back across a cell face);
+// at the end one segmented butterfly transpose-reduction over the cell's LPC lanes leaves
+// PER = NVP/LPC of the cell's NVP (padded) sums in each lane, added to shared memory with distinct
+// addresses. Particles that step back (window origin -1 in some direction) add their
+// contributions to shared memory directly.
+template <int NDIM, int LPC>
+struct PushPlan {
+  static constexpr int NV = DepLayout<NDIM>::NV;
+  static constexpr int PER = (NV + LPC - 1) / LPC;
+  static constexpr int NVP = PER * LPC;
+  static constexpr int CPW = 32 / LPC;
+};
+
+template <typename T, int NDIM, int SCHEME, int LPC>
 __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
   using S = PushSmem<T, NDIM>;
-  constexpr int TX = S::TX, TY = S::TY, TZ = S::TZ, NCL = S::NCL;
-  constexpr int PER = NCL / PUSH_THREADS;
-  static_assert(NCL % PUSH_THREADS == 0, "cells per tile must be a multiple of the block size");
+  using PL = PushPlan<NDIM, LPC>;
+  constexpr int TX = S::TX, TY = S::TY, NCL = S::NCL;
+  constexpr int NV = PL::NV, PER = PL::PER, NVP = PL::NVP, CPW = PL::CPW;
+  constexpr int NWARP = PUSH_THREADS / 32;
+  static_assert(NCL % CPW == 0, "cells per tile must be a multiple of the cells per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);
   T* sj = sg + 6 * S::GN;
-  int* spre = reinterpret_cast<int*>(sj + 3 * S::JN);
-  int* swarp = spre + NCL + 1;
+  int* sn = reinterpret_cast<int*>(sj + 3 * S::JN);  // [species][cell] particle counts
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
   const int tix = tile % r.ntx;
   const int tiy = (tile / r.ntx) % r.nty;
   const int tiz = tile / (r.ntx * r.nty);
-  const int X0 = tix * TX, Y0 = tiy * TY, Z0 = tiz * TZ;
-  const int wx = min(TX, r.nx - X0), wy = min(TY, r.ny - Y0), wz = min(TZ, r.nz - Z0);
+  const int X0 = tix * S::TX, Y0 = tiy * S::TY, Z0 = tiz * S::TZ;
+  const int wx = min(S::TX, r.nx - X0), wy = min(S::TY, r.ny - Y0), wz = min(S::TZ, r.nz - Z0);
   const long long nxy = (long long)r.nx * r.ny;
 
-  // 1. field copies of the tile and its halo into shared memory (periodic wrap)
+  // 1. field copies of the tile and its halo into shared memory (periodic wrap); zero the current
   for (int e = tid; e < 6 * S::GN; e += PUSH_THREADS) {
     int c = e / S::GN, rem = e - c * S::GN;
     int lz = rem / (S::GX * S::GY);
@@ -268,234 +251,244 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
     sg[e] = __ldg(r.g[c] + (long long)gz * nxy + (long long)gy * r.nx + gx);
   }
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) sj[e] = T(0);
-
-  T kin = T(0);  // per-thread partial sum of w (gamma - 1)
-  int npush = 0;  // particles pushed by this thread
-  for (int s = 0; s < 2; ++s) {
-    const SpeciesBuf<T> pin = r.in[s];
-    const SpeciesBuf<T> pout = r.out[s];
-    const T q = s == 0 ? T(-1) : T(1);
-    // 2. particle counts of the tile's cells -> exclusive prefix (cells x-fastest in the tile)
-    int loc[PER];
-    int mysum = 0;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      int cl = tid * PER + u;
-      int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
-      int n = 0;
-      if (lx < wx && ly < wy && lz < wz) {
-        long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
-        n = pin.cnt[cell];
-        n = n > r.cap ? r.cap : n;  // an overflow was flagged when it happened
-        pin.cnt[cell] = 0;          // this count array is the next step's output
-      }
-      loc[u] = mysum;
-      mysum += n;
+  // 2. particle counts of the tile's cells; the input counts are zeroed (they are the next step's
+  // output counts)
+  for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    int n0 = 0, n1 = 0;
+    if (lx < wx && ly < wy && lz < wz) {
+      const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
+      n0 = min(r.in[0].cnt[cell], r.cap);  // an overflow was flagged when it happened
+      n1 = min(r.in[1].cnt[cell], r.cap);
+      r.in[0].cnt[cell] = 0;
+      r.in[1].cnt[cell] = 0;
     }
-    int incl = mysum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) swarp[warp] = incl;
-    __syncthreads();
-    if (tid == 0) {
-      int acc = 0;
-      for (int w = 0; w < PUSH_THREADS / 32; ++w) {
-        int v = swarp[w];
-        swarp[w] = acc;
-        acc += v;
-      }
-      spre[NCL] = acc;
-    }
-    __syncthreads();
-    {
-      int base = swarp[warp] + incl - mysum;
-#pragma unroll
-      for (int u = 0; u < PER; ++u) spre[tid * PER + u] = base + loc[u];
-    }
-    __syncthreads();
-    const int N = spre[NCL];
-
-    // 3. particles of the tile, flattened over its cells
-    for (int fb = 0; fb < N; fb += PUSH_THREADS) {
-      const int f = fb + tid;
-      const bool valid = f < N;
-      int dst = -1 - lane;  // unique per lane when invalid
-      T nox = 0, noy = 0, noz = 0, ux = 0, uy = 0, uz = 0, w = 0;
-      unsigned pid = 0;
-      constexpr int NV = DepLayout<NDIM>::NV;
-      T dv[NV];
-      int wkey = -1;
-      if (valid) {
-        const int cl = find_cell(spre, NCL, f);
-        const int j = f - spre[cl];
-        const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
-        const int gi = X0 + lx, gj = Y0 + ly, gk = Z0 + lz;
-        const long long slot = ((long long)gk * nxy + (long long)gj * r.nx + gi) * r.cap + j;
-        T ox = __ldg(pin.ox + slot);
-        T oy = NDIM == 3 ? __ldg(pin.oy + slot) : T(0);
-        T oz = __ldg(pin.oz + slot);
-        ux = __ldg(pin.dux + slot);
-        uy = __ldg(pin.duy + slot);
-        uz = __ldg(pin.duz + slot);
-        w = HAS_W ? __ldg(pin.w + slot) : r.wconst;
-        if (HAS_ID) pid = __ldg(pin.id + slot);
-
-        // gather
-        const DirW<T> dwx = dir_weights(ox), dwy = dir_weights(oy), dwz = dir_weights(oz);
-        T F[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) F[c] = gather_comp<T, NDIM, SCHEME>(sg + c * S::GN, c, lx, ly, lz, dwx, dwy, dwz);
-
-        // relativistic Boris, momenta relative to the drift u0 z_hat
-        const T h = q * r.hq;
-        T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
-        T Mz = r.u0 + mz;
-        T ig = T(1) / dev_sqrt(T(1) + mx * mx + my * my + Mz * Mz);
-        T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
-        T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
-        T sx = sf * tx, sy = sf * ty, sz = sf * tz;
-        T px = mx + (my * tz - Mz * ty);
-        T py = my + (Mz * tx - mx * tz);
-        T pz = Mz + (mx * ty - my * tx);
-        ux = mx + (py * sz - pz * sy) + h * F[0];
-        uy = my + (pz * sx - px * sz) + h * F[1];
-        uz = mz + (px * sy - py * sx) + h * F[2];
-        T Uz = r.u0 + uz;
-        T u2 = ux * ux + uy * uy + Uz * Uz;
-        T gn = dev_sqrt(T(1) + u2);
-        T ign = T(1) / gn;
-        T vx = ux * ign, vy = uy * ign, vz = Uz * ign;
-        kin += w * (u2 / (gn + T(1)));
-        ++npush;
-
-        // move (cell-relative displacement in grid units)
-        T ddx = r.dtdx * vx;
-        T ddy = NDIM == 3 ? r.dtdy * vy : T(0);
-        T ddz = r.dtdz * vz;
-        if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
-          flag_error(r.err, ERR_NONFINITE);
-          ddx = ddy = ddz = T(0);
-          ux = uy = uz = T(0);
-          vx = vy = T(0);
-        }
-        const EsirDir<T> ex_ = esir_dir(ox, ddx);
-        const EsirDir<T> ez_ = esir_dir(oz, ddz);
-        EsirDir<T> ey_;
-        if (NDIM == 3) ey_ = esir_dir(oy, ddy);
-        else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
-        const int ax = ex_.a, ay = NDIM == 3 ? ey_.a : 0, az = ez_.a;
-        T S0x[3], dSx[3], S0y[3], dSy[3], S0z[3], dSz[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          S0x[a] = ex_.S0[a]; dSx[a] = ex_.dS[a];
-          S0z[a] = ez_.S0[a]; dSz[a] = ez_.dS[a];
-          if (NDIM == 3) { S0y[a] = ey_.S0[a]; dSy[a] = ey_.dS[a]; }
-        }
-        const T qw = q * w;
-        // per-particle current contributions v[i] to the smem tile at offset dep_off<NDIM>(i)
-        // from the window origin (bx, by, bz)
-        const int bx = lx + ax + 1, by = NDIM == 3 ? ly + ay + 1 : 0, bz = lz + az + 1;
-        wkey = (bz * S::JY + by) * S::JX + bx;
-        if (NDIM == 2) {
-          const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b): running sum over a
-            T fz = S0z[b] + T(0.5) * dSz[b];
-            T a0 = dSx[0] * fz, a1 = a0 + dSx[1] * fz;
-            dv[b * 2 + 0] = cx * a0;
-            dv[b * 2 + 1] = cx * a1;
-          }
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {  // Jz(a, b+1/2): running sum over b
-            T fx = S0x[a] + T(0.5) * dSx[a];
-            T a0 = dSz[0] * fx, a1 = a0 + dSz[1] * fx;
-            dv[6 + a * 2 + 0] = cz * a0;
-            dv[6 + a * 2 + 1] = cz * a1;
-          }
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a)  // Jy(a, b): out-of-plane weight
-              dv[12 + b * 3 + a] = cy * (S0x[a] * S0z[b] + T(0.5) * dSx[a] * S0z[b] + T(0.5) * S0x[a] * dSz[b] +
-                                         dSx[a] * dSz[b] * T(1.0 / 3.0));
-        } else {
-          const T cx = qw * r.jfx, cy = qw * r.jfy, cz = qw * r.jfz;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b, c)
-              T tr = S0y[b] * S0z[c] + T(0.5) * dSy[b] * S0z[c] + T(0.5) * S0y[b] * dSz[c] +
-                     dSy[b] * dSz[c] * T(1.0 / 3.0);
-              T a0 = dSx[0] * tr, a1 = a0 + dSx[1] * tr;
-              dv[(c * 3 + b) * 2 + 0] = cx * a0;
-              dv[(c * 3 + b) * 2 + 1] = cx * a1;
-            }
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {  // Jy(a, b+1/2, c)
-              T tr = S0x[a] * S0z[c] + T(0.5) * dSx[a] * S0z[c] + T(0.5) * S0x[a] * dSz[c] +
-                     dSx[a] * dSz[c] * T(1.0 / 3.0);
-              T a0 = dSy[0] * tr, a1 = a0 + dSy[1] * tr;
-              dv[18 + (c * 3 + a) * 2 + 0] = cy * a0;
-              dv[18 + (c * 3 + a) * 2 + 1] = cy * a1;
-            }
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {  // Jz(a, b, c+1/2)
-              T tr = S0x[a] * S0y[b] + T(0.5) * dSx[a] * S0y[b] + T(0.5) * S0x[a] * dSy[b] +
-                     dSx[a] * dSy[b] * T(1.0 / 3.0);
-              T a0 = dSz[0] * tr, a1 = a0 + dSz[1] * tr;
-              dv[36 + (b * 3 + a) * 2 + 0] = cz * a0;
-              dv[36 + (b * 3 + a) * 2 + 1] = cz * a1;
-            }
-        }
-
-        // new cell and offsets
-        nox = ex_.off;
-        noy = NDIM == 3 ? ey_.off : T(0);
-        noz = ez_.off;
-        const int ni = wrapi(gi + ex_.shift, r.nx);
-        const int nj = NDIM == 3 ? wrapi(gj + ey_.shift, r.ny) : 0;
-        const int nk = wrapi(gk + ez_.shift, r.nz);
-        dst = (int)((long long)nk * nxy + (long long)nj * r.nx + ni);
-      }
-      // deposit: lanes that share a window origin sum their contributions by a warp transpose-
-      // reduction, then every lane adds one distinct value to shared memory (no atomic conflicts)
-      deposit_warp<T, NDIM>(sj, dv, wkey, valid, lane);
-
-      // 4. rebin: warp-aggregated slot reservation in the destination cell's bin
-      const unsigned peers = __match_any_sync(0xffffffffu, dst);
-      const int leader = __ffs(peers) - 1;
-      const int rank = __popc(peers & ((1u << lane) - 1u));
-      int base = 0;
-      if (valid && lane == leader) base = atomicAdd(pout.cnt + dst, __popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (valid) {
-        const int j = base + rank;
-        if (j < r.cap) {
-          const long long o = (long long)dst * r.cap + j;
-          pout.ox[o] = nox;
-          if (NDIM == 3) pout.oy[o] = noy;
-          pout.oz[o] = noz;
-          pout.dux[o] = ux;
-          pout.duy[o] = uy;
-          pout.duz[o] = uz;
-          if (HAS_W) pout.w[o] = w;
-          if (HAS_ID) pout.id[o] = pid;
-        } else {
-          flag_error(r.err, ERR_OVERFLOW);
-        }
-      }
-    }
-    __syncthreads();  // spre / swarp are reused by the next species
+    sn[cl] = n0;
+    sn[NCL + cl] = n1;
   }
+  __syncthreads();
 
-  // 5. flush the tile's current to global memory
+  const bool has_w = r.in[0].w != nullptr;
+  const bool has_id = r.in[0].id != nullptr;
+  T kin = T(0);
+  int npush = 0;
+  const int sl = lane % LPC;  // lane within its cell group
+
+  for (int grp = warp; grp < NCL / CPW; grp += NWARP) {
+    const int cl = grp * CPW + lane / LPC;
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    const int gi = X0 + lx, gj = Y0 + ly, gk = Z0 + lz;
+    const long long cell = (long long)gk * nxy + (long long)gj * r.nx + gi;
+    const int n0 = sn[cl], n1 = sn[NCL + cl];
+    const int nq0 = (n0 + 3) >> 2, nq = nq0 + ((n1 + 3) >> 2);
+    const int iters = __reduce_max_sync(0xffffffffu, (nq + LPC - 1) / LPC);
+    const int okey = ((lz + 1) * S::JY + (NDIM == 3 ? ly + 1 : 0)) * S::JX + lx + 1;  // cell-origin window
+    T acc[NVP];
+#pragma unroll
+    for (int i = 0; i < NVP; ++i) acc[i] = T(0);
+
+    for (int it = 0; it < iters; ++it) {
+      const int q = sl + it * LPC;
+      const bool has = q < nq;
+      const int s = (has && q >= nq0) ? 1 : 0;
+      const int q4 = 4 * (s ? q - nq0 : q);
+      const int cnt = has ? min(4, (s ? n1 : n0) - q4) : 0;
+      const SpeciesBuf<T> pin = s ? r.in[1] : r.in[0];
+      const SpeciesBuf<T> pout = s ? r.out[1] : r.out[0];
+      const T qs = s ? T(1) : T(-1);
+      T ox[4], oy[4], oz[4], px[4], py[4], pz[4], pw[4];
+      unsigned pid[4];
+      if (has) {
+        const long long slot0 = cell * r.cap + q4;
+        load4(pin.ox + slot0, ox);
+        if (NDIM == 3) load4(pin.oy + slot0, oy);
+        load4(pin.oz + slot0, oz);
+        load4(pin.dux + slot0, px);
+        load4(pin.duy + slot0, py);
+        load4(pin.duz + slot0, pz);
+        if (has_w) load4(pin.w + slot0, pw);
+        if (has_id) load4(pin.id + slot0, pid);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const bool valid = jj < cnt;
+        int dkey = -1 - lane;  // unique per lane when there is no particle
+        T nox = T(0), noy = T(0), noz = T(0), ux = T(0), uy = T(0), uz = T(0);
+        const T w = has_w ? pw[jj] : r.wconst;
+        if (valid) {
+          const T o_x = ox[jj], o_y = NDIM == 3 ? oy[jj] : T(0), o_z = oz[jj];
+          ux = px[jj];
+          uy = py[jj];
+          uz = pz[jj];
+          // gather
+          const DirW<T> dwx = dir_weights(o_x), dwy = dir_weights(o_y), dwz = dir_weights(o_z);
+          T F[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            F[c] = gather_comp<T, NDIM, SCHEME>(sg + c * S::GN, c, lx, ly, lz, dwx, dwy, dwz);
+          // relativistic Boris, momenta relative to the drift u0 z_hat
+          const T h = qs * r.hq;
+          const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
+          const T Mz = r.u0 + mz;
+          const T ig = T(1) / dev_sqrt(T(1) + mx * mx + my * my + Mz * Mz);
+          const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
+          const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+          const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
+          const T qx = mx + (my * tz - Mz * ty);
+          const T qy = my + (Mz * tx - mx * tz);
+          const T qz = Mz + (mx * ty - my * tx);
+          ux = mx + (qy * sz - qz * sy) + h * F[0];
+          uy = my + (qz * sx - qx * sz) + h * F[1];
+          uz = mz + (qx * sy - qy * sx) + h * F[2];
+          const T Uz = r.u0 + uz;
+          const T u2 = ux * ux + uy * uy + Uz * Uz;
+          const T gn = dev_sqrt(T(1) + u2);
+          const T ign = T(1) / gn;
+          T vx = ux * ign, vy = uy * ign;
+          const T vz = Uz * ign;
+          kin += w * (u2 / (gn + T(1)));
+          ++npush;
+          // move (cell-relative displacement in grid units)
+          T ddx = r.dtdx * vx, ddy = NDIM == 3 ? r.dtdy * vy : T(0), ddz = r.dtdz * vz;
+          if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
+            flag_error(r.err, ERR_NONFINITE);
+            ddx = ddy = ddz = T(0);
+            ux = uy = uz = T(0);
+            vy = T(0);
+          }
+          const EsirDir<T> ex_ = esir_dir(o_x, ddx);
+          const EsirDir<T> ez_ = esir_dir(o_z, ddz);
+          EsirDir<T> ey_;
+          if (NDIM == 3) ey_ = esir_dir(o_y, ddy);
+          else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
+          // Esirkepov contributions, summed in registers when the window starts at the own cell
+          const bool own = (ex_.a | ez_.a | (NDIM == 3 ? ey_.a : 0)) == 0;
+          const int wkey = own ? okey
+                               : ((lz + ez_.a + 1) * S::JY + (NDIM == 3 ? ly + ey_.a + 1 : 0)) * S::JX + lx + ex_.a + 1;
+          const T qw = qs * w;
+          auto emit = [&](int i, T v) {
+            if (own) {
+              acc[i] += v;
+            } else {
+              int comp, a, b, c;
+              DepLayout<NDIM>::at(i, comp, a, b, c);
+              atomicAdd(sj + comp * S::JN + wkey + (c * S::JY + b) * S::JX + a, v);
+            }
+          };
+          if (NDIM == 2) {
+            const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b): running sum over a
+              const T fz = ez_.S0[b] + T(0.5) * ez_.dS[b];
+              const T a0 = ex_.dS[0] * fz, a1 = a0 + ex_.dS[1] * fz;
+              emit(b * 2 + 0, cx * a0);
+              emit(b * 2 + 1, cx * a1);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {  // Jz(a, b+1/2): running sum over b
+              const T fx = ex_.S0[a] + T(0.5) * ex_.dS[a];
+              const T a0 = ez_.dS[0] * fx, a1 = a0 + ez_.dS[1] * fx;
+              emit(6 + a * 2 + 0, cz * a0);
+              emit(6 + a * 2 + 1, cz * a1);
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int a = 0; a < 3; ++a)  // Jy(a, b): out-of-plane weight
+                emit(12 + b * 3 + a, cy * (ex_.S0[a] * ez_.S0[b] + T(0.5) * ex_.dS[a] * ez_.S0[b] +
+                                           T(0.5) * ex_.S0[a] * ez_.dS[b] + ex_.dS[a] * ez_.dS[b] * T(1.0 / 3.0)));
+          } else {
+            const T cx = qw * r.jfx, cy = qw * r.jfy, cz = qw * r.jfz;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b, c)
+                const T tr = ey_.S0[b] * ez_.S0[c] + T(0.5) * ey_.dS[b] * ez_.S0[c] + T(0.5) * ey_.S0[b] * ez_.dS[c] +
+                             ey_.dS[b] * ez_.dS[c] * T(1.0 / 3.0);
+                const T a0 = ex_.dS[0] * tr, a1 = a0 + ex_.dS[1] * tr;
+                emit((c * 3 + b) * 2 + 0, cx * a0);
+                emit((c * 3 + b) * 2 + 1, cx * a1);
+              }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {  // Jy(a, b+1/2, c)
+                const T tr = ex_.S0[a] * ez_.S0[c] + T(0.5) * ex_.dS[a] * ez_.S0[c] + T(0.5) * ex_.S0[a] * ez_.dS[c] +
+                             ex_.dS[a] * ez_.dS[c] * T(1.0 / 3.0);
+                const T a0 = ey_.dS[0] * tr, a1 = a0 + ey_.dS[1] * tr;
+                emit(18 + (c * 3 + a) * 2 + 0, cy * a0);
+                emit(18 + (c * 3 + a) * 2 + 1, cy * a1);
+              }
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {  // Jz(a, b, c+1/2)
+                const T tr = ex_.S0[a] * ey_.S0[b] + T(0.5) * ex_.dS[a] * ey_.S0[b] + T(0.5) * ex_.S0[a] * ey_.dS[b] +
+                             ex_.dS[a] * ey_.dS[b] * T(1.0 / 3.0);
+                const T a0 = ez_.dS[0] * tr, a1 = a0 + ez_.dS[1] * tr;
+                emit(36 + (b * 3 + a) * 2 + 0, cz * a0);
+                emit(36 + (b * 3 + a) * 2 + 1, cz * a1);
+              }
+          }
+          // new cell and offsets
+          nox = ex_.off;
+          noy = NDIM == 3 ? ey_.off : T(0);
+          noz = ez_.off;
+          const int ni = wrapi(gi + ex_.shift, r.nx);
+          const int nj = NDIM == 3 ? wrapi(gj + ey_.shift, r.ny) : 0;
+          const int nk = wrapi(gk + ez_.shift, r.nz);
+          dkey = (int)((long long)nk * nxy + (long long)nj * r.nx + ni) * 2 + s;
+        }
+        // rebin: lanes with the same destination (cell, species) reserve consecutive slots with one
+        // atomic, then write their particles there
+        const unsigned peers = __match_any_sync(0xffffffffu, dkey);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int base = 0;
+        if (valid && lane == leader) base = atomicAdd(pout.cnt + (dkey >> 1), __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) {
+          const int j = base + rank;
+          if (j < r.cap) {
+            const long long o = (long long)(dkey >> 1) * r.cap + j;
+            pout.ox[o] = nox;
+            if (NDIM == 3) pout.oy[o] = noy;
+            pout.oz[o] = noz;
+            pout.dux[o] = ux;
+            pout.duy[o] = uy;
+            pout.duz[o] = uz;
+            if (has_w) pout.w[o] = w;
+            if (has_id) pout.id[o] = pid[jj];
+          } else {
+            flag_error(r.err, ERR_OVERFLOW);
+          }
+        }
+      }
+    }
+    // 3. segmented transpose-reduction of the cell's register sums over its LPC lanes
+#pragma unroll
+    for (int sh = LPC / 2; sh >= 1; sh >>= 1) {
+      const bool up = (lane & sh) != 0;
+#pragma unroll
+      for (int j = 0; j < PER * sh; ++j) {
+        const T send = up ? acc[j] : acc[j + PER * sh];
+        const T keep = up ? acc[j + PER * sh] : acc[j];
+        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+      const int i = sl * PER + m;
+      if (i < NV && acc[m] != T(0)) {
+        int comp, a, b, c;
+        DepLayout<NDIM>::at(i, comp, a, b, c);
+        atomicAdd(sj + comp * S::JN + okey + (c * S::JY + b) * S::JX + a, acc[m]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. flush the tile's current to global memory
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) {
     T v = sj[e];
     if (v == T(0)) continue;
@@ -509,7 +502,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
     atomicAdd(r.j[c] + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
   }
 
-  // 6. kinetic energy and particle count of this step: per-thread partial sums in the working
+  // 5. kinetic energy and particle count of this step: per-thread partial sums in the working
   // precision, FP64 across the block and the grid
   if (r.kin) {
     double kd = (double)kin;
@@ -519,8 +512,8 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
       kd += __shfl_xor_sync(0xffffffffu, kd, o);
       nd += __shfl_xor_sync(0xffffffffu, nd, o);
     }
-    __shared__ double skin[PUSH_THREADS / 32];
-    __shared__ int scnt[PUSH_THREADS / 32];
+    __shared__ double skin[NWARP];
+    __shared__ int scnt[NWARP];
     if (lane == 0) {
       skin[warp] = kd;
       scnt[warp] = nd;
@@ -529,7 +522,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
     if (tid == 0) {
       double t = 0;
       long long c = 0;
-      for (int w2 = 0; w2 < PUSH_THREADS / 32; ++w2) {
+      for (int w2 = 0; w2 < NWARP; ++w2) {
         t += skin[w2];
         c += scnt[w2];
       }
@@ -539,8 +532,16 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
   }
 }
 
+// Lanes per cell from the expected particles per cell (both species): packs of 4 per lane.
+static int lanes_per_cell(int ndim, int ppc_total) {
+  const int packs = (ppc_total + 3) / 4 + 1;  // two species round up separately
+  if (packs <= 4) return 4;
+  if (packs <= 8) return 8;
+  return 16;
+}
+
 template <typename T, int NDIM, int SCHEME>
-static cudaError_t launch_push_t(const RunDev<T>& r, bool has_w, bool has_id, cudaStream_t st) {
+static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
   using S = PushSmem<T, NDIM>;
   const size_t sm = S::bytes();
   const int ntiles = r.ntx * r.nty * r.ntz;
@@ -550,20 +551,20 @@ static cudaError_t launch_push_t(const RunDev<T>& r, bool has_w, bool has_id, cu
     kern<<<ntiles, PUSH_THREADS, sm, st>>>(r);
     return cudaGetLastError();
   };
-  if (has_w && has_id) return go(k_push<T, NDIM, SCHEME, true, true>);
-  if (has_w) return go(k_push<T, NDIM, SCHEME, true, false>);
-  if (has_id) return go(k_push<T, NDIM, SCHEME, false, true>);
-  return go(k_push<T, NDIM, SCHEME, false, false>);
+  if (lpc == 4) return go(k_push<T, NDIM, SCHEME, 4>);
+  if (lpc == 8) return go(k_push<T, NDIM, SCHEME, 8>);
+  return go(k_push<T, NDIM, SCHEME, 16>);
 }
 
 template <typename T>
-cudaError_t launch_push(const RunDev<T>& r, bool has_w, bool has_id, cudaStream_t st) {
+cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st) {
+  const int lpc = lanes_per_cell(r.ndim, ppc_total);
   if (r.ndim == 2)
-    return r.scheme == 0 ? launch_push_t<T, 2, 0>(r, has_w, has_id, st) : launch_push_t<T, 2, 1>(r, has_w, has_id, st);
-  return r.scheme == 0 ? launch_push_t<T, 3, 0>(r, has_w, has_id, st) : launch_push_t<T, 3, 1>(r, has_w, has_id, st);
+    return r.scheme == 0 ? launch_push_t<T, 2, 0>(r, lpc, st) : launch_push_t<T, 2, 1>(r, lpc, st);
+  return r.scheme == 0 ? launch_push_t<T, 3, 0>(r, lpc, st) : launch_push_t<T, 3, 1>(r, lpc, st);
 }
-template cudaError_t launch_push<float>(const RunDev<float>&, bool, bool, cudaStream_t);
-template cudaError_t launch_push<double>(const RunDev<double>&, bool, bool, cudaStream_t);
+template cudaError_t launch_push<float>(const RunDev<float>&, int, cudaStream_t);
+template cudaError_t launch_push<double>(const RunDev<double>&, int, cudaStream_t);
 
 void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) {
   if (ndim == 2) {

@@ -45,8 +45,9 @@ void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);
 // Raise a kernel's dynamic shared memory limit to `bytes` (once per kernel and size).
 cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
 
+// ppc_total: expected particles per cell (both species), used to pick the lanes per cell.
 template <typename T>
-cudaError_t launch_push(const RunDev<T>& r, bool has_w, bool has_id, cudaStream_t st);
+cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st);
 template <typename T>
 cudaError_t launch_init_beam(const RunDev<T>& r, int ppc, const int lat[3], double u0, double w0, double jitter,
                              double u_th, double sigma_perp, unsigned long long seed, cudaStream_t st);

@@ -200,6 +200,194 @@ __device__ __forceinline__ void load4(const unsigned* p, unsigned (&o)[4]) {
   o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 
+// FP32 uses the hardware reciprocal square root and fast division (relative error ~1e-7, inside
+// the 1e-5 per-step bar); FP64 keeps IEEE division and square root.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+
+// Galerkin gather (order 0 along each half-staggered direction, order 1 elsewhere): the nodes are
+// the same for every particle of a cell, so they are read once per lane and each component is an
+// affine or bilinear function of the cell offsets. Node (a, b, c) of a component is its value at
+// offsets (a, b, c) from the cell's own node in the shared-memory tile.
+template <typename T, int NDIM>
+struct GalCache;
+
+template <typename T>
+struct GalCache<T, 2> {
+  // Ex: x half -> S0; z -> S1. Ey: S1 x, S1 z. Ez: S1 x; z half -> S0. Bx: S1 x; S0 z.
+  // By: S0 x, S0 z. Bz: S0 x; S1 z.
+  T ex0, ex1, ey00, ey10, ey01, ey11, ez0, ez1, bx0, bx1, by0, bz0, bz1;
+  __device__ __forceinline__ void load(const T* sg, int lx, int ly, int lz) {
+    using S = PushSmem<T, 2>;
+    const int p = (lz + 1) * S::GX + lx + 1;
+    const T* e = sg;
+    ex0 = e[p]; ex1 = e[p + S::GX] - ex0;
+    e = sg + S::GN;
+    ey00 = e[p]; ey10 = e[p + 1] - ey00; ey01 = e[p + S::GX] - ey00; ey11 = e[p + S::GX + 1] - e[p + S::GX] - ey10;
+    e = sg + 2 * S::GN;
+    ez0 = e[p]; ez1 = e[p + 1] - ez0;
+    e = sg + 3 * S::GN;
+    bx0 = e[p]; bx1 = e[p + 1] - bx0;
+    by0 = sg[4 * S::GN + p];
+    e = sg + 5 * S::GN;
+    bz0 = e[p]; bz1 = e[p + S::GX] - bz0;
+  }
+  __device__ __forceinline__ void interp(T ox, T, T oz, T (&F)[6]) const {
+    F[0] = ex0 + oz * ex1;
+    F[1] = ey00 + ox * ey10 + oz * (ey01 + ox * ey11);
+    F[2] = ez0 + ox * ez1;
+    F[3] = bx0 + ox * bx1;
+    F[4] = by0;
+    F[5] = bz0 + oz * bz1;
+  }
+};
+
+template <typename T>
+struct GalCache<T, 3> {
+  // Ex: S0 x, bilinear (y, z). Ey: S0 y, bilinear (x, z). Ez: S0 z, bilinear (x, y).
+  // Bx: S0 y, z, linear x. By: S0 x, z, linear y. Bz: S0 x, y, linear z.
+  T e[3][4], b[3][2];
+  __device__ __forceinline__ void bil(const T* f, int p, int s1, int s2, T (&o)[4]) {
+    o[0] = f[p];
+    o[1] = f[p + s1] - o[0];
+    o[2] = f[p + s2] - o[0];
+    o[3] = f[p + s1 + s2] - f[p + s2] - o[1];
+  }
+  __device__ __forceinline__ void load(const T* sg, int lx, int ly, int lz) {
+    using S = PushSmem<T, 3>;
+    const int p = ((lz + 1) * S::GY + ly + 1) * S::GX + lx + 1;
+    const int sx = 1, sy = S::GX, sz = S::GX * S::GY;
+    bil(sg, p, sy, sz, e[0]);
+    bil(sg + S::GN, p, sx, sz, e[1]);
+    bil(sg + 2 * S::GN, p, sx, sy, e[2]);
+    b[0][0] = sg[3 * S::GN + p]; b[0][1] = sg[3 * S::GN + p + sx] - b[0][0];
+    b[1][0] = sg[4 * S::GN + p]; b[1][1] = sg[4 * S::GN + p + sy] - b[1][0];
+    b[2][0] = sg[5 * S::GN + p]; b[2][1] = sg[5 * S::GN + p + sz] - b[2][0];
+  }
+  __device__ __forceinline__ void interp(T ox, T oy, T oz, T (&F)[6]) const {
+    F[0] = e[0][0] + oy * e[0][1] + oz * (e[0][2] + oy * e[0][3]);
+    F[1] = e[1][0] + ox * e[1][1] + oz * (e[1][2] + ox * e[1][3]);
+    F[2] = e[2][0] + ox * e[2][1] + oy * (e[2][2] + ox * e[2][3]);
+    F[3] = b[0][0] + ox * b[0][1];
+    F[4] = b[1][0] + oy * b[1][1];
+    F[5] = b[2][0] + oz * b[2][1];
+  }
+};
+
+// Esirkepov contributions of one particle, written as sums into the 3-node window of its own
+// cell (layout of DepLayout). With f = S0 + dS/2 per direction, the 2D out-of-plane weight
+// S0x S0z + dSx S0z/2 + S0x dSz/2 + dSx dSz/3 equals fx fz + dSx dSz / 12, and the running sums
+// of the in-plane weights at the two half-nodes are dS[0] and -dS[2] times the transverse factor.
+template <typename T, int NVP>
+__device__ __forceinline__ void deposit2(T (&acc)[NVP], const EsirDir<T>& X, const EsirDir<T>& Z, T cx, T cy, T cz) {
+  T fx[3], fz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fx[a] = X.S0[a] + T(0.5) * X.dS[a];
+    fz[a] = Z.S0[a] + T(0.5) * Z.dS[a];
+  }
+  const T gx0 = cx * X.dS[0], gx1 = -cx * X.dS[2];
+  const T gz0 = cz * Z.dS[0], gz1 = -cz * Z.dS[2];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    acc[b * 2 + 0] += gx0 * fz[b];
+    acc[b * 2 + 1] += gx1 * fz[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc[6 + a * 2 + 0] += gz0 * fx[a];
+    acc[6 + a * 2 + 1] += gz1 * fx[a];
+  }
+  T hx[3], kx[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hx[a] = cy * fx[a];
+    kx[a] = cy * X.dS[a] * T(1.0 / 12.0);
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[12 + b * 3 + a] += hx[a] * fz[b] + kx[a] * Z.dS[b];
+}
+
+// Same contributions added to shared memory at the window origin (wx, wz) (tile indices).
+template <typename T, int NDIM>
+__device__ __noinline__ void deposit2_smem(T* sj, int wx, int wz, EsirDir<T> X, EsirDir<T> Z, T cx, T cy, T cz) {
+  using S = PushSmem<T, NDIM>;
+  T v[DepLayout<2>::NV];
+#pragma unroll
+  for (int i = 0; i < DepLayout<2>::NV; ++i) v[i] = T(0);
+  deposit2<T, DepLayout<2>::NV>(v, X, Z, cx, cy, cz);
+  const int key = wz * S::JX + wx;
+#pragma unroll
+  for (int i = 0; i < DepLayout<2>::NV; ++i) {
+    int comp, a, b, c;
+    DepLayout<2>::at(i, comp, a, b, c);
+    atomicAdd(sj + comp * S::JN + key + c * S::JX + a, v[i]);
+  }
+}
+
+// 3D: W_a = dS_a T(b1, b2) with T = f f + dS dS / 12 over the two transverse directions.
+template <typename T, int NVP>
+__device__ __forceinline__ void deposit3(T (&acc)[NVP], const EsirDir<T>& X, const EsirDir<T>& Y, const EsirDir<T>& Z,
+                                         T cx, T cy, T cz) {
+  T fx[3], fy[3], fz[3], kx[3], ky[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fx[a] = X.S0[a] + T(0.5) * X.dS[a];
+    fy[a] = Y.S0[a] + T(0.5) * Y.dS[a];
+    fz[a] = Z.S0[a] + T(0.5) * Z.dS[a];
+    kx[a] = X.dS[a] * T(1.0 / 12.0);
+    ky[a] = Y.dS[a] * T(1.0 / 12.0);
+  }
+  const T gx0 = cx * X.dS[0], gx1 = -cx * X.dS[2];
+  const T gy0 = cy * Y.dS[0], gy1 = -cy * Y.dS[2];
+  const T gz0 = cz * Z.dS[0], gz1 = -cz * Z.dS[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b, c)
+      const T t = fy[b] * fz[c] + ky[b] * Z.dS[c];
+      acc[(c * 3 + b) * 2 + 0] += gx0 * t;
+      acc[(c * 3 + b) * 2 + 1] += gx1 * t;
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // Jy(a, b+1/2, c)
+      const T t = fx[a] * fz[c] + kx[a] * Z.dS[c];
+      acc[18 + (c * 3 + a) * 2 + 0] += gy0 * t;
+      acc[18 + (c * 3 + a) * 2 + 1] += gy1 * t;
+    }
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // Jz(a, b, c+1/2)
+      const T t = fx[a] * fy[b] + kx[a] * Y.dS[b];
+      acc[36 + (b * 3 + a) * 2 + 0] += gz0 * t;
+      acc[36 + (b * 3 + a) * 2 + 1] += gz1 * t;
+    }
+}
+
+template <typename T, int NDIM>
+__device__ __noinline__ void deposit3_smem(T* sj, int wx, int wy, int wz, EsirDir<T> X, EsirDir<T> Y, EsirDir<T> Z,
+                                           T cx, T cy, T cz) {
+  using S = PushSmem<T, NDIM>;
+  T v[DepLayout<3>::NV];
+#pragma unroll
+  for (int i = 0; i < DepLayout<3>::NV; ++i) v[i] = T(0);
+  deposit3<T, DepLayout<3>::NV>(v, X, Y, Z, cx, cy, cz);
+  const int key = (wz * S::JY + wy) * S::JX + wx;
+#pragma unroll
+  for (int i = 0; i < DepLayout<3>::NV; ++i) {
+    int comp, a, b, c;
+    DepLayout<3>::at(i, comp, a, b, c);
+    atomicAdd(sj + comp * S::JN + key + (c * S::JY + b) * S::JX + a, v[i]);
+  }
+}
+
 // Work assignment of the push kernel: a warp takes CPW = 32/LPC cells of its tile at a time,
 // LPC lanes per cell. The cell's particles are split into packs of 4 consecutive slots of one
 // species (electron packs first); lane l of the cell takes packs l, l + LPC, ... . Each lane sums
@@ -217,8 +405,14 @@ struct PushPlan {
   static constexpr int CPW = 32 / LPC;
 };
 
+// Resident blocks per SM the push kernel is compiled for (register budget): FP32 2D fits two.
+template <typename T, int NDIM>
+struct PushMinBlocks {
+  static constexpr int value = (sizeof(T) == 4 && NDIM == 2) ? 2 : 1;
+};
+
 template <typename T, int NDIM, int SCHEME, int LPC>
-__global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
+__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k_push(RunDev<T> r) {
   using S = PushSmem<T, NDIM>;
   using PL = PushPlan<NDIM, LPC>;
   constexpr int TX = S::TX, TY = S::TY, NCL = S::NCL;
@@ -286,6 +480,9 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
     T acc[NVP];
 #pragma unroll
     for (int i = 0; i < NVP; ++i) acc[i] = T(0);
+    // Galerkin: every particle of the cell interpolates the same nodes, so the lane reads them once
+    GalCache<T, NDIM> gc;
+    if (SCHEME == 0 && iters > 0) gc.load(sg, lx, ly, lz);
 
     for (int it = 0; it < iters; ++it) {
       const int q = sl + it * LPC;
@@ -321,18 +518,22 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
           uy = py[jj];
           uz = pz[jj];
           // gather
-          const DirW<T> dwx = dir_weights(o_x), dwy = dir_weights(o_y), dwz = dir_weights(o_z);
           T F[6];
+          if (SCHEME == 0) {
+            gc.interp(o_x, o_y, o_z, F);
+          } else {
+            const DirW<T> dwx = dir_weights(o_x), dwy = dir_weights(o_y), dwz = dir_weights(o_z);
 #pragma unroll
-          for (int c = 0; c < 6; ++c)
-            F[c] = gather_comp<T, NDIM, SCHEME>(sg + c * S::GN, c, lx, ly, lz, dwx, dwy, dwz);
+            for (int c = 0; c < 6; ++c)
+              F[c] = gather_comp<T, NDIM, SCHEME>(sg + c * S::GN, c, lx, ly, lz, dwx, dwy, dwz);
+          }
           // relativistic Boris, momenta relative to the drift u0 z_hat
           const T h = qs * r.hq;
           const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
           const T Mz = r.u0 + mz;
-          const T ig = T(1) / dev_sqrt(T(1) + mx * mx + my * my + Mz * Mz);
+          const T ig = rsqrt_t(T(1) + mx * mx + my * my + Mz * Mz);
           const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
-          const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+          const T sf = div_t(T(2), T(1) + tx * tx + ty * ty + tz * tz);
           const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
           const T qx = mx + (my * tz - Mz * ty);
           const T qy = my + (Mz * tx - mx * tz);
@@ -342,11 +543,10 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
           uz = mz + (qx * sy - qy * sx) + h * F[2];
           const T Uz = r.u0 + uz;
           const T u2 = ux * ux + uy * uy + Uz * Uz;
-          const T gn = dev_sqrt(T(1) + u2);
-          const T ign = T(1) / gn;
+          const T ign = rsqrt_t(T(1) + u2);
           T vx = ux * ign, vy = uy * ign;
           const T vz = Uz * ign;
-          kin += w * (u2 / (gn + T(1)));
+          kin += w * div_t(u2, dev_sqrt(T(1) + u2) + T(1));
           ++npush;
           // move (cell-relative displacement in grid units)
           T ddx = r.dtdx * vx, ddy = NDIM == 3 ? r.dtdy * vy : T(0), ddz = r.dtdz * vz;
@@ -361,74 +561,18 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
           EsirDir<T> ey_;
           if (NDIM == 3) ey_ = esir_dir(o_y, ddy);
           else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
-          // Esirkepov contributions, summed in registers when the window starts at the own cell
-          const bool own = (ex_.a | ez_.a | (NDIM == 3 ? ey_.a : 0)) == 0;
-          const int wkey = own ? okey
-                               : ((lz + ez_.a + 1) * S::JY + (NDIM == 3 ? ly + ey_.a + 1 : 0)) * S::JX + lx + ex_.a + 1;
+          // Esirkepov deposit: summed in registers when the 3-node window starts at the own cell
+          // (every particle that does not step back across a face), else straight to shared memory
           const T qw = qs * w;
-          auto emit = [&](int i, T v) {
-            if (own) {
-              acc[i] += v;
-            } else {
-              int comp, a, b, c;
-              DepLayout<NDIM>::at(i, comp, a, b, c);
-              atomicAdd(sj + comp * S::JN + wkey + (c * S::JY + b) * S::JX + a, v);
-            }
-          };
+          const bool own = (ex_.a | ez_.a | (NDIM == 3 ? ey_.a : 0)) == 0;
           if (NDIM == 2) {
             const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b): running sum over a
-              const T fz = ez_.S0[b] + T(0.5) * ez_.dS[b];
-              const T a0 = ex_.dS[0] * fz, a1 = a0 + ex_.dS[1] * fz;
-              emit(b * 2 + 0, cx * a0);
-              emit(b * 2 + 1, cx * a1);
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {  // Jz(a, b+1/2): running sum over b
-              const T fx = ex_.S0[a] + T(0.5) * ex_.dS[a];
-              const T a0 = ez_.dS[0] * fx, a1 = a0 + ez_.dS[1] * fx;
-              emit(6 + a * 2 + 0, cz * a0);
-              emit(6 + a * 2 + 1, cz * a1);
-            }
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-              for (int a = 0; a < 3; ++a)  // Jy(a, b): out-of-plane weight
-                emit(12 + b * 3 + a, cy * (ex_.S0[a] * ez_.S0[b] + T(0.5) * ex_.dS[a] * ez_.S0[b] +
-                                           T(0.5) * ex_.S0[a] * ez_.dS[b] + ex_.dS[a] * ez_.dS[b] * T(1.0 / 3.0)));
+            if (own) deposit2<T, NVP>(acc, ex_, ez_, cx, cy, cz);
+            else deposit2_smem<T, NDIM>(sj, lx + ex_.a + 1, lz + ez_.a + 1, ex_, ez_, cx, cy, cz);
           } else {
             const T cx = qw * r.jfx, cy = qw * r.jfy, cz = qw * r.jfz;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-              for (int b = 0; b < 3; ++b) {  // Jx(a+1/2, b, c)
-                const T tr = ey_.S0[b] * ez_.S0[c] + T(0.5) * ey_.dS[b] * ez_.S0[c] + T(0.5) * ey_.S0[b] * ez_.dS[c] +
-                             ey_.dS[b] * ez_.dS[c] * T(1.0 / 3.0);
-                const T a0 = ex_.dS[0] * tr, a1 = a0 + ex_.dS[1] * tr;
-                emit((c * 3 + b) * 2 + 0, cx * a0);
-                emit((c * 3 + b) * 2 + 1, cx * a1);
-              }
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {  // Jy(a, b+1/2, c)
-                const T tr = ex_.S0[a] * ez_.S0[c] + T(0.5) * ex_.dS[a] * ez_.S0[c] + T(0.5) * ex_.S0[a] * ez_.dS[c] +
-                             ex_.dS[a] * ez_.dS[c] * T(1.0 / 3.0);
-                const T a0 = ey_.dS[0] * tr, a1 = a0 + ey_.dS[1] * tr;
-                emit(18 + (c * 3 + a) * 2 + 0, cy * a0);
-                emit(18 + (c * 3 + a) * 2 + 1, cy * a1);
-              }
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {  // Jz(a, b, c+1/2)
-                const T tr = ex_.S0[a] * ey_.S0[b] + T(0.5) * ex_.dS[a] * ey_.S0[b] + T(0.5) * ex_.S0[a] * ey_.dS[b] +
-                             ex_.dS[a] * ey_.dS[b] * T(1.0 / 3.0);
-                const T a0 = ez_.dS[0] * tr, a1 = a0 + ez_.dS[1] * tr;
-                emit(36 + (b * 3 + a) * 2 + 0, cz * a0);
-                emit(36 + (b * 3 + a) * 2 + 1, cz * a1);
-              }
+            if (own) deposit3<T, NVP>(acc, ex_, ey_, ez_, cx, cy, cz);
+            else deposit3_smem<T, NDIM>(sj, lx + ex_.a + 1, ly + ey_.a + 1, lz + ez_.a + 1, ex_, ey_, ez_, cx, cy, cz);
           }
           // new cell and offsets
           nox = ex_.off;
@@ -534,7 +678,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push(RunDev<T> r) {
 
 // Lanes per cell from the expected particles per cell (both species): packs of 4 per lane.
 static int lanes_per_cell(int ndim, int ppc_total) {
-  const int packs = (ppc_total + 3) / 4 + 1;  // two species round up separately
+  const int packs = 2 * ((ppc_total / 2 + 3) / 4);  // packs of 4 per species
   if (packs <= 4) return 4;
   if (packs <= 8) return 8;
   return 16;

@@ -24,6 +24,50 @@ struct PTile<3> {
 
 constexpr int PUSH_THREADS = 256;
 
+// cp.async (16-byte, L2 only) staging of particle packs into shared memory.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void copy4_async(float* dst, const float* src) { cp_async16(dst, src); }
+__device__ __forceinline__ void copy4_async(double* dst, const double* src) {
+  cp_async16(dst, src);
+  cp_async16(dst + 2, src + 2);
+}
+__device__ __forceinline__ void copy4_async(unsigned* dst, const unsigned* src) { cp_async16(dst, src); }
+template <typename V>
+__device__ __forceinline__ void read4(const V* p, V (&o)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o[i] = p[i];
+}
+__device__ __forceinline__ void read4(const float* p, float (&o)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void read4(const unsigned* p, unsigned (&o)[4]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(p);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+
+// Per-warp double-buffered stage: [stage][array][lane][4] for the 7 real arrays (ox oy oz dux
+// duy duz w), then [stage][lane][4] ids.
+template <typename T>
+struct PushStage {
+  static constexpr __host__ __device__ size_t per_warp_elems() {
+    return 2 * 7 * 32 * 4 + (2 * 32 * 4 * sizeof(unsigned) + sizeof(T) - 1) / sizeof(T);
+  }
+  static __device__ __forceinline__ T* at(T* base, int stage, int arr, int lane) {
+    return base + ((stage * 7 + arr) * 32 + lane) * 4;
+  }
+  static __device__ __forceinline__ unsigned* id_at(T* base, int stage, int lane) {
+    return reinterpret_cast<unsigned*>(base + 2 * 7 * 32 * 4) + (stage * 32 + lane) * 4;
+  }
+};
+
+
 template <typename T, int NDIM>
 struct PushSmem {
   static constexpr int TX = PTile<NDIM>::TX, TY = PTile<NDIM>::TY, TZ = PTile<NDIM>::TZ;
@@ -33,7 +77,8 @@ struct PushSmem {
   // current tile: nodes [X0-1, X0+TX+1]
   static constexpr int JX = TX + 3, JY = (NDIM == 3 ? TY + 3 : 1), JZ = TZ + 3, JN = JX * JY * JZ;
   static constexpr size_t bytes() {
-    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (2 * NCL);
+    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (2 * NCL) + 16 +
+           sizeof(T) * PushStage<T>::per_warp_elems() * (PUSH_THREADS / 32);
   }
 };
 
@@ -468,43 +513,95 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   int npush = 0;
   const int sl = lane % LPC;  // lane within its cell group
 
-  for (int grp = warp; grp < NCL / CPW; grp += NWARP) {
-    const int cl = grp * CPW + lane / LPC;
+  // Items of this warp: (cell group, pack round). The packs of the next item are copied into the
+  // warp's shared-memory stage with cp.async while the current item is computed.
+  constexpr int NGRP = NCL / CPW;
+  // per-warp stages start on a 16-byte boundary after the counts (cp.async destinations)
+  const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(sn + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
+  T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * PushStage<T>::per_warp_elems();
+  auto group_iters = [&](int g) -> int {
+    const int c = g * CPW + lane / LPC;
+    const int nq = ((sn[c] + 3) >> 2) + ((sn[NCL + c] + 3) >> 2);
+    return __reduce_max_sync(0xffffffffu, (nq + LPC - 1) / LPC);
+  };
+  auto issue = [&](int g, int it, int stage) {
+    const int c = g * CPW + lane / LPC;
+    const int n0 = sn[c], n1 = sn[NCL + c];
+    const int nq0 = (n0 + 3) >> 2, nq = nq0 + ((n1 + 3) >> 2);
+    const int q = sl + it * LPC;
+    if (q >= nq) return;
+    const int s = q >= nq0 ? 1 : 0;
+    const int q4 = 4 * (s ? q - nq0 : q);
+    const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+    const long long slot0 = ((long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx) * r.cap + q4;
+    const SpeciesBuf<T> pin = s ? r.in[1] : r.in[0];
+    const T* src[7] = {pin.ox, pin.oy, pin.oz, pin.dux, pin.duy, pin.duz, pin.w};
+#pragma unroll
+    for (int arr = 0; arr < 7; ++arr) {
+      if (arr == 1 && NDIM == 2) continue;
+      if (arr == 6 && !has_w) continue;
+      copy4_async(PushStage<T>::at(stg, stage, arr, lane), src[arr] + slot0);
+    }
+    if (has_id) copy4_async(PushStage<T>::id_at(stg, stage, lane), pin.id + slot0);
+  };
+
+  int g = warp, it = 0;
+  int giters = g < NGRP ? group_iters(g) : 0;
+  while (g < NGRP && giters == 0) {
+    g += NWARP;
+    giters = g < NGRP ? group_iters(g) : 0;
+  }
+  int stage = 0;
+  if (g < NGRP) issue(g, 0, 0);
+  cp_async_commit();
+  T acc[NVP];
+  GalCache<T, NDIM> gc;
+  while (g < NGRP) {
+    // prefetch the next item
+    int ng = g, nit = it + 1, niters = giters;
+    if (nit >= giters) {
+      nit = 0;
+      do {
+        ng += NWARP;
+        niters = ng < NGRP ? group_iters(ng) : 0;
+      } while (ng < NGRP && niters == 0);
+    }
+    if (ng < NGRP) issue(ng, nit, stage ^ 1);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncwarp();
+
+    const int cl = g * CPW + lane / LPC;
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
     const int gi = X0 + lx, gj = Y0 + ly, gk = Z0 + lz;
-    const long long cell = (long long)gk * nxy + (long long)gj * r.nx + gi;
     const int n0 = sn[cl], n1 = sn[NCL + cl];
     const int nq0 = (n0 + 3) >> 2, nq = nq0 + ((n1 + 3) >> 2);
-    const int iters = __reduce_max_sync(0xffffffffu, (nq + LPC - 1) / LPC);
     const int okey = ((lz + 1) * S::JY + (NDIM == 3 ? ly + 1 : 0)) * S::JX + lx + 1;  // cell-origin window
-    T acc[NVP];
+    if (it == 0) {
 #pragma unroll
-    for (int i = 0; i < NVP; ++i) acc[i] = T(0);
-    // Galerkin: every particle of the cell interpolates the same nodes, so the lane reads them once
-    GalCache<T, NDIM> gc;
-    if (SCHEME == 0 && iters > 0) gc.load(sg, lx, ly, lz);
-
-    for (int it = 0; it < iters; ++it) {
+      for (int i = 0; i < NVP; ++i) acc[i] = T(0);
+      // Galerkin: every particle of the cell interpolates the same nodes; read them once per lane
+      if (SCHEME == 0) gc.load(sg, lx, ly, lz);
+    }
+    {
       const int q = sl + it * LPC;
       const bool has = q < nq;
       const int s = (has && q >= nq0) ? 1 : 0;
       const int q4 = 4 * (s ? q - nq0 : q);
       const int cnt = has ? min(4, (s ? n1 : n0) - q4) : 0;
-      const SpeciesBuf<T> pin = s ? r.in[1] : r.in[0];
       const SpeciesBuf<T> pout = s ? r.out[1] : r.out[0];
       const T qs = s ? T(1) : T(-1);
       T ox[4], oy[4], oz[4], px[4], py[4], pz[4], pw[4];
       unsigned pid[4];
       if (has) {
-        const long long slot0 = cell * r.cap + q4;
-        load4(pin.ox + slot0, ox);
-        if (NDIM == 3) load4(pin.oy + slot0, oy);
-        load4(pin.oz + slot0, oz);
-        load4(pin.dux + slot0, px);
-        load4(pin.duy + slot0, py);
-        load4(pin.duz + slot0, pz);
-        if (has_w) load4(pin.w + slot0, pw);
-        if (has_id) load4(pin.id + slot0, pid);
+        read4(PushStage<T>::at(stg, stage, 0, lane), ox);
+        if (NDIM == 3) read4(PushStage<T>::at(stg, stage, 1, lane), oy);
+        read4(PushStage<T>::at(stg, stage, 2, lane), oz);
+        read4(PushStage<T>::at(stg, stage, 3, lane), px);
+        read4(PushStage<T>::at(stg, stage, 4, lane), py);
+        read4(PushStage<T>::at(stg, stage, 5, lane), pz);
+        if (has_w) read4(PushStage<T>::at(stg, stage, 6, lane), pw);
+        if (has_id) read4(PushStage<T>::id_at(stg, stage, lane), pid);
       }
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
@@ -609,27 +706,35 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
         }
       }
     }
-    // 3. segmented transpose-reduction of the cell's register sums over its LPC lanes
+    if (it == giters - 1) {
+      // 3. segmented transpose-reduction of the cell's register sums over its LPC lanes
 #pragma unroll
-    for (int sh = LPC / 2; sh >= 1; sh >>= 1) {
-      const bool up = (lane & sh) != 0;
+      for (int sh = LPC / 2; sh >= 1; sh >>= 1) {
+        const bool up = (lane & sh) != 0;
 #pragma unroll
-      for (int j = 0; j < PER * sh; ++j) {
-        const T send = up ? acc[j] : acc[j + PER * sh];
-        const T keep = up ? acc[j + PER * sh] : acc[j];
-        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+        for (int j = 0; j < PER * sh; ++j) {
+          const T send = up ? acc[j] : acc[j + PER * sh];
+          const T keep = up ? acc[j + PER * sh] : acc[j];
+          acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < PER; ++m) {
+        const int i = sl * PER + m;
+        if (i < NV && acc[m] != T(0)) {
+          int comp, a, b, c;
+          DepLayout<NDIM>::at(i, comp, a, b, c);
+          atomicAdd(sj + comp * S::JN + okey + (c * S::JY + b) * S::JX + a, acc[m]);
+        }
       }
     }
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-      const int i = sl * PER + m;
-      if (i < NV && acc[m] != T(0)) {
-        int comp, a, b, c;
-        DepLayout<NDIM>::at(i, comp, a, b, c);
-        atomicAdd(sj + comp * S::JN + okey + (c * S::JY + b) * S::JX + a, acc[m]);
-      }
-    }
+    __syncwarp();  // the stage just read is refilled by the next iteration's prefetch
+    g = ng;
+    it = nit;
+    giters = niters;
+    stage ^= 1;
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // 4. flush the tile's current to global memory

@@ -33,6 +33,9 @@ struct pic_handle {
   int* cnt[2][2] = {};
   int parity = 0;
   int* d_err = nullptr;
+  void* lv[10] = {};        // leaver list: key, ox, oy, oz, dux, duy, duz, w, id
+  int* d_lv_count = nullptr;  // two counters, one per step parity
+  long long lv_cap = 0;
   double* d_acc = nullptr;  // 8 doubles of reduction scratch
   long long* d_offs = nullptr;
   long long* d_bsum = nullptr;
@@ -217,6 +220,17 @@ RunDev<T> make_run(pic_handle* h, int parity) {
       sb.cnt = h->cnt[s][b];
       if (io == 0) r.in[s] = sb; else r.out[s] = sb;
     }
+  r.lv.key = (int*)h->lv[0];
+  r.lv.ox = (T*)h->lv[1];
+  r.lv.oy = (T*)h->lv[2];
+  r.lv.oz = (T*)h->lv[3];
+  r.lv.dux = (T*)h->lv[4];
+  r.lv.duy = (T*)h->lv[5];
+  r.lv.duz = (T*)h->lv[6];
+  r.lv.w = (T*)h->lv[7];
+  r.lv.id = (unsigned*)h->lv[8];
+  r.lv_count = h->d_lv_count + parity;
+  r.lv_cap = h->lv_cap;
   r.err = h->d_err;
   r.kin = nullptr;
   return r;
@@ -304,6 +318,7 @@ int step_once(pic_handle* h) {
   RunDev<T> r = make_run<T>(h, h->parity);
   r.kin = rec ? slot + 3 : nullptr;
   CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
+  CK(launch(h, PIC_K_PUSH, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }), "migrate");
   // 6. current filter
   if (h->cfg.filter_targets & PIC_FILTER_J) {
     SepArgs<T> ja = sep_args<T>(h, false);
@@ -402,9 +417,10 @@ int set_state_t(pic_handle* h, const pic_state* s) {
   const long long n = s->np;
   if (n == -1) return PIC_OK;  // fields only: particles untouched
   if (n < 0) return fail(h, PIC_E_ARG, "negative particle count");
-  // particles: clear bins, stage, bin
+  // particles: clear bins and leaver counters, stage, bin
   for (int sp = 0; sp < 2; ++sp)
     for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
+  CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "clear leaver counters");
   h->parity = 0;
   if (n == 0) return PIC_OK;
   if (!s->cell || !s->species || !s->ox || !s->oz || !s->dux || !s->duy || !s->duz ||
@@ -572,7 +588,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       c.shape_order != 1 || (c.precision != PIC_FP32 && c.precision != PIC_FP64) || c.ppc_per_species < 0 ||
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
       c.diag_every < 0 || c.diag_capacity < 0 ||
-      (long long)c.nx * c.ny * c.nz > (1ll << 31) - 1)
+      (long long)c.nx * c.ny * c.nz > (1ll << 30) - 1)
     return PIC_E_ARG;
   const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
   if (c.dt >= 1.0 / sqrt(inv)) return PIC_E_CFL;
@@ -614,6 +630,16 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       if (ok) ok = (h->cnt[s][b] = (int*)dalloc(h, sizeof(int) * h->ncell)) != nullptr;
     }
   if (ok) ok = (h->d_err = (int*)dalloc(h, 16)) != nullptr;
+  // leaver list: particles that leave their tile in one step
+  h->lv_cap = (long long)(2 * slots / 8);
+  if (h->lv_cap < 65536) h->lv_cap = 65536;
+  for (int a = 0; a < 9 && ok; ++a) {
+    if (a == 2 && c.ndim == 2) continue;
+    if (a == 7 && !h->has_w) continue;
+    if (a == 8 && !h->has_id) continue;
+    ok = (h->lv[a] = dalloc(h, (size_t)h->lv_cap * (a == 0 || a == 8 ? 4 : h->es))) != nullptr;
+  }
+  if (ok) ok = (h->d_lv_count = (int*)dalloc(h, 2 * sizeof(int))) != nullptr;
   if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
   if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
   if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
@@ -628,6 +654,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   for (int s = 0; s < 2; ++s)
     for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->cnt[s][b], 0, sizeof(int) * h->ncell, h->stream);
   cudaMemsetAsync(h->d_err, 0, 16, h->stream);
+  cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), h->stream);
   rebuild_taps(h);
   int rc = PIC_OK;
   if (c.init_beam && c.ppc_per_species > 0)

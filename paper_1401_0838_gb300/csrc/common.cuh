@@ -28,6 +28,15 @@ struct SpeciesBuf {
   int* cnt;            // particles per cell
 };
 
+// Particles that left their tile in a push (appended by the push kernel, inserted into their
+// destination bins by the migrate kernel). key = destination cell * 2 + species.
+template <typename T>
+struct LeaverList {
+  int* key;
+  T *ox, *oy, *oz, *dux, *duy, *duz, *w;
+  unsigned* id;
+};
+
 // Everything a kernel needs about one simulation (passed by value as a kernel parameter).
 template <typename T>
 struct RunDev {
@@ -45,6 +54,9 @@ struct RunDev {
   T* g[6];            // field copies seen by the particles (Ex Ey Ez Bx By Bz)
   T* j[3];            // current accumulator
   SpeciesBuf<T> in[2], out[2];
+  LeaverList<T> lv;
+  int* lv_count;       // leavers appended in this step
+  long long lv_cap;    // capacity of the leaver list
   int* err;
   double* kin;        // FP64 accumulators of this step: [0] sum w (gamma - 1), [1] particle count
                       // (nullptr: not recorded)

@@ -77,7 +77,7 @@ struct PushSmem {
   // current tile: nodes [X0-1, X0+TX+1]
   static constexpr int JX = TX + 3, JY = (NDIM == 3 ? TY + 3 : 1), JZ = TZ + 3, JN = JX * JY * JZ;
   static constexpr size_t bytes() {
-    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (2 * NCL) + 16 +
+    return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (4 * NCL) + 16 +
            sizeof(T) * PushStage<T>::per_warp_elems() * (PUSH_THREADS / 32);
   }
 };
@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);
   T* sj = sg + 6 * S::GN;
-  int* sn = reinterpret_cast<int*>(sj + 3 * S::JN);  // [species][cell] particle counts
+  int* sn = reinterpret_cast<int*>(sj + 3 * S::JN);  // [species][cell] particle counts (input)
+  int* scnt = sn + 2 * NCL;                          // [species][cell] output counts of this tile
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
@@ -504,6 +505,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
     }
     sn[cl] = n0;
     sn[NCL + cl] = n1;
+    scnt[cl] = 0;
+    scnt[NCL + cl] = 0;
   }
   __syncthreads();
 
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   // warp's shared-memory stage with cp.async while the current item is computed.
   constexpr int NGRP = NCL / CPW;
   // per-warp stages start on a 16-byte boundary after the counts (cp.async destinations)
-  const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(sn + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
+  const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(scnt + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
   T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * PushStage<T>::per_warp_elems();
   auto group_iters = [&](int g) -> int {
     const int c = g * CPW + lane / LPC;
@@ -607,6 +610,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
       for (int jj = 0; jj < 4; ++jj) {
         const bool valid = jj < cnt;
         int dkey = -1 - lane;  // unique per lane when there is no particle
+        bool leave = false;
         T nox = T(0), noy = T(0), noz = T(0), ux = T(0), uy = T(0), uz = T(0);
         const T w = has_w ? pw[jj] : r.wconst;
         if (valid) {
@@ -675,23 +679,41 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
           nox = ex_.off;
           noy = NDIM == 3 ? ey_.off : T(0);
           noz = ez_.off;
-          const int ni = wrapi(gi + ex_.shift, r.nx);
-          const int nj = NDIM == 3 ? wrapi(gj + ey_.shift, r.ny) : 0;
-          const int nk = wrapi(gk + ez_.shift, r.nz);
-          dkey = (int)((long long)nk * nxy + (long long)nj * r.nx + ni) * 2 + s;
+          const int nlx = lx + ex_.shift, nly = NDIM == 3 ? ly + ey_.shift : 0, nlz = lz + ez_.shift;
+          if (nlx >= 0 && nlx < wx && nly >= 0 && nly < wy && nlz >= 0 && nlz < wz) {
+            dkey = ((nlz * TY + nly) * TX + nlx) * 2 + s;  // stays in this tile
+          } else {
+            leave = true;  // global destination, as cell * 2 + species
+            const int ni = wrapi(gi + ex_.shift, r.nx);
+            const int nj = NDIM == 3 ? wrapi(gj + ey_.shift, r.ny) : 0;
+            const int nk = wrapi(gk + ez_.shift, r.nz);
+            dkey = (int)((long long)nk * nxy + (long long)nj * r.nx + ni) * 2 + s;
+          }
         }
-        // rebin: lanes with the same destination (cell, species) reserve consecutive slots with one
-        // atomic, then write their particles there
-        const unsigned peers = __match_any_sync(0xffffffffu, dkey);
+        // rebin. Destination in this tile: lanes with the same (cell, species) reserve consecutive
+        // slots with one shared-memory atomic on the tile's output counts. Destination in another
+        // tile: the particle is appended to the leaver list (one global atomic per warp), which
+        // k_migrate inserts after this kernel.
+        const bool stay = valid && !leave;
+        const unsigned peers = __match_any_sync(0xffffffffu, stay ? dkey : -1 - lane);
         const int leader = __ffs(peers) - 1;
         const int rank = __popc(peers & ((1u << lane) - 1u));
         int base = 0;
-        if (valid && lane == leader) base = atomicAdd(pout.cnt + (dkey >> 1), __popc(peers));
+        if (stay && lane == leader) base = atomicAdd(scnt + (dkey & 1) * NCL + (dkey >> 1), __popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (valid) {
+        const unsigned lmask = __ballot_sync(0xffffffffu, valid && leave);
+        int lbase = 0;
+        if (lmask) {
+          const int lleader = __ffs(lmask) - 1;
+          if (lane == lleader) lbase = atomicAdd(r.lv_count, __popc(lmask));
+          lbase = __shfl_sync(0xffffffffu, lbase, lleader);
+        }
+        if (stay) {
           const int j = base + rank;
           if (j < r.cap) {
-            const long long o = (long long)(dkey >> 1) * r.cap + j;
+            const int dl = dkey >> 1;
+            const int dx = dl % TX, dy = (dl / TX) % TY, dz = dl / (TX * TY);
+            const long long o = ((long long)(Z0 + dz) * nxy + (long long)(Y0 + dy) * r.nx + X0 + dx) * r.cap + j;
             pout.ox[o] = nox;
             if (NDIM == 3) pout.oy[o] = noy;
             pout.oz[o] = noz;
@@ -700,6 +722,21 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
             pout.duz[o] = uz;
             if (has_w) pout.w[o] = w;
             if (has_id) pout.id[o] = pid[jj];
+          } else {
+            flag_error(r.err, ERR_OVERFLOW);
+          }
+        } else if (valid) {
+          const long long o = lbase + __popc(lmask & ((1u << lane) - 1u));
+          if (o < r.lv_cap) {
+            r.lv.key[o] = dkey;
+            r.lv.ox[o] = nox;
+            if (NDIM == 3) r.lv.oy[o] = noy;
+            r.lv.oz[o] = noz;
+            r.lv.dux[o] = ux;
+            r.lv.duy[o] = uy;
+            r.lv.duz[o] = uz;
+            if (has_w) r.lv.w[o] = w;
+            if (has_id) r.lv.id[o] = pid[jj];
           } else {
             flag_error(r.err, ERR_OVERFLOW);
           }
@@ -737,7 +774,17 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   cp_async_wait_all();
   __syncthreads();
 
-  // 4. flush the tile's current to global memory
+  // 4. output counts of the tile's cells (leavers from other tiles are added by k_migrate)
+  for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
+      r.out[0].cnt[cell] = scnt[cl];
+      r.out[1].cnt[cell] = scnt[NCL + cl];
+    }
+  }
+
+  // 5. flush the tile's current to global memory
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) {
     T v = sj[e];
     if (v == T(0)) continue;
@@ -751,7 +798,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
     atomicAdd(r.j[c] + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
   }
 
-  // 5. kinetic energy and particle count of this step: per-thread partial sums in the working
+  // 6. kinetic energy and particle count of this step: per-thread partial sums in the working
   // precision, FP64 across the block and the grid
   if (r.kin) {
     double kd = (double)kin;
@@ -826,6 +873,45 @@ void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) 
     *ntz = (nz + PTile<3>::TZ - 1) / PTile<3>::TZ;
   }
 }
+
+// ---------------------------------------------------------------------------------------------
+// Migrate: insert the particles that left their tile in this step (leaver list of the push
+// kernel) into their destination bins, then zero the other parity's list counter for the next
+// step's push.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_migrate(RunDev<T> r, int* other_count) {
+  const long long n = min((long long)*r.lv_count, r.lv_cap);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int key = r.lv.key[i];
+    const int s = key & 1;
+    const long long cell = key >> 1;
+    const SpeciesBuf<T> b = s ? r.out[1] : r.out[0];
+    const int j = atomicAdd(b.cnt + cell, 1);
+    if (j >= r.cap) {
+      flag_error(r.err, ERR_OVERFLOW);
+      continue;
+    }
+    const long long o = cell * r.cap + j;
+    b.ox[o] = r.lv.ox[i];
+    if (r.ndim == 3) b.oy[o] = r.lv.oy[i];
+    b.oz[o] = r.lv.oz[i];
+    b.dux[o] = r.lv.dux[i];
+    b.duy[o] = r.lv.duy[i];
+    b.duz[o] = r.lv.duz[i];
+    if (b.w) b.w[o] = r.lv.w[i];
+    if (b.id) b.id[o] = r.lv.id[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *other_count = 0;
+}
+
+template <typename T>
+cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st) {
+  k_migrate<T><<<152 * 4, 256, 0, st>>>(r, other_count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_migrate<float>(const RunDev<float>&, int*, cudaStream_t);
+template cudaError_t launch_migrate<double>(const RunDev<double>&, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Insert one particle into its cell bin (used by init and import).

@@ -49,6 +49,8 @@ cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
 template <typename T>
 cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st);
 template <typename T>
+cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st);
+template <typename T>
 cudaError_t launch_init_beam(const RunDev<T>& r, int ppc, const int lat[3], double u0, double w0, double jitter,
                              double u_th, double sigma_perp, unsigned long long seed, cudaStream_t st);
 template <typename T>

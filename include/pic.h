@@ -194,9 +194,10 @@ int pic_energy_history(pic_handle* h, pic_energy_t* out, int max, int* count);
 #define PIC_K_PUSH 1   /* fused gather + Boris + move + Esirkepov deposition + rebin */
 #define PIC_K_FILTER 2 /* current filter */
 #define PIC_K_YEE 3    /* Yee updates */
-#define PIC_K_DIAG 4   /* energy reductions */
-#define PIC_K_OTHER 5  /* initialisation, import, export */
-#define PIC_NKERNEL 6
+#define PIC_K_DIAG 4    /* energy reductions */
+#define PIC_K_OTHER 5   /* initialisation, import, export */
+#define PIC_K_MIGRATE 6 /* insertion of the particles that left their tile into their new bins */
+#define PIC_NKERNEL 7
 
 /* on = 1: bracket every later kernel launch with CUDA events on the handle's stream and reset the
  * totals; on = 0: stop. */

@@ -28,8 +28,8 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_get_state", "pic_set_state", "pic_debug_gather_copies", "pic_debug_current",
            "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror", "pic_energy_history",
            "pic_enable_timing", "pic_kernel_times", "pic_launch_count")
-PIC_NKERNEL = 6
-KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other")
+PIC_NKERNEL = 7
+KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
 
 
 class pic_config(ctypes.Structure):

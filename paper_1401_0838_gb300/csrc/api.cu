@@ -318,7 +318,8 @@ int step_once(pic_handle* h) {
   RunDev<T> r = make_run<T>(h, h->parity);
   r.kin = rec ? slot + 3 : nullptr;
   CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
-  CK(launch(h, PIC_K_PUSH, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }), "migrate");
+  CK(launch(h, PIC_K_MIGRATE, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }),
+     "migrate");
   // 6. current filter
   if (h->cfg.filter_targets & PIC_FILTER_J) {
     SepArgs<T> ja = sep_args<T>(h, false);

@@ -594,30 +594,23 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
       const int cnt = has ? min(4, (s ? n1 : n0) - q4) : 0;
       const SpeciesBuf<T> pout = s ? r.out[1] : r.out[0];
       const T qs = s ? T(1) : T(-1);
-      T ox[4], oy[4], oz[4], px[4], py[4], pz[4], pw[4];
-      unsigned pid[4];
-      if (has) {
-        read4(PushStage<T>::at(stg, stage, 0, lane), ox);
-        if (NDIM == 3) read4(PushStage<T>::at(stg, stage, 1, lane), oy);
-        read4(PushStage<T>::at(stg, stage, 2, lane), oz);
-        read4(PushStage<T>::at(stg, stage, 3, lane), px);
-        read4(PushStage<T>::at(stg, stage, 4, lane), py);
-        read4(PushStage<T>::at(stg, stage, 5, lane), pz);
-        if (has_w) read4(PushStage<T>::at(stg, stage, 6, lane), pw);
-        if (has_id) read4(PushStage<T>::id_at(stg, stage, lane), pid);
-      }
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
+      const T* st_x = PushStage<T>::at(stg, stage, 0, lane);
+      const unsigned* st_id = PushStage<T>::id_at(stg, stage, lane);
+#pragma unroll 1
+      for (int rnd = 0; rnd < 4; ++rnd) {
+        // pack element of this round, rotated by lane / 8 so the 32 lanes' shared-memory reads of
+        // one array fall in distinct banks
+        const int jj = (rnd + (lane >> 3)) & 3;
         const bool valid = jj < cnt;
         int dkey = -1 - lane;  // unique per lane when there is no particle
         bool leave = false;
         T nox = T(0), noy = T(0), noz = T(0), ux = T(0), uy = T(0), uz = T(0);
-        const T w = has_w ? pw[jj] : r.wconst;
+        const T w = (has_w && valid) ? st_x[6 * 32 * 4 + jj] : r.wconst;
         if (valid) {
-          const T o_x = ox[jj], o_y = NDIM == 3 ? oy[jj] : T(0), o_z = oz[jj];
-          ux = px[jj];
-          uy = py[jj];
-          uz = pz[jj];
+          const T o_x = st_x[jj], o_y = NDIM == 3 ? st_x[1 * 32 * 4 + jj] : T(0), o_z = st_x[2 * 32 * 4 + jj];
+          ux = st_x[3 * 32 * 4 + jj];
+          uy = st_x[4 * 32 * 4 + jj];
+          uz = st_x[5 * 32 * 4 + jj];
           // gather
           T F[6];
           if (SCHEME == 0) {
@@ -647,7 +640,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
           const T ign = rsqrt_t(T(1) + u2);
           T vx = ux * ign, vy = uy * ign;
           const T vz = Uz * ign;
-          kin += w * div_t(u2, dev_sqrt(T(1) + u2) + T(1));
+          kin += w * div_t(u2, (T(1) + u2) * ign + T(1));  // gamma - 1 = u^2 / (gamma + 1)
           ++npush;
           // move (cell-relative displacement in grid units)
           T ddx = r.dtdx * vx, ddy = NDIM == 3 ? r.dtdy * vy : T(0), ddz = r.dtdz * vz;
@@ -721,7 +714,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
             pout.duy[o] = uy;
             pout.duz[o] = uz;
             if (has_w) pout.w[o] = w;
-            if (has_id) pout.id[o] = pid[jj];
+            if (has_id) pout.id[o] = st_id[jj];
           } else {
             flag_error(r.err, ERR_OVERFLOW);
           }
@@ -736,7 +729,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
             r.lv.duy[o] = uy;
             r.lv.duz[o] = uz;
             if (has_w) r.lv.w[o] = w;
-            if (has_id) r.lv.id[o] = pid[jj];
+            if (has_id) r.lv.id[o] = st_id[jj];
           } else {
             flag_error(r.err, ERR_OVERFLOW);
           }

@@ -27,7 +27,7 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_set_correction_stencil", "pic_step", "pic_sync", "pic_energy", "pic_num_particles",
            "pic_get_state", "pic_set_state", "pic_debug_gather_copies", "pic_debug_current",
            "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror", "pic_energy_history",
-           "pic_enable_timing", "pic_kernel_times", "pic_launch_count")
+           "pic_enable_timing", "pic_kernel_times", "pic_launch_count", "pic_field_energy_noalloc")
 PIC_NKERNEL = 7
 KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
 
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.pic_enable_timing.argtypes = [V, I]
         L.pic_kernel_times.argtypes = [V, DP, P(ctypes.c_longlong)]
         L.pic_launch_count.argtypes = [V, P(ctypes.c_longlong)]
+        L.pic_field_energy_noalloc.argtypes = [P(V), ctypes.c_longlong, I, D, DP, V]
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -262,3 +263,11 @@ def pic_launch_count(h) -> int:
     n = ctypes.c_longlong()
     _check(lib().pic_launch_count(h, ctypes.byref(n)), h)
     return n.value
+
+
+def pic_field_energy_noalloc(fields, ncell: int, precision: int, dv: float, stream_ptr=None):
+    """W_E, W_B, W_perp of six device arrays, computed without allocating (see include/pic.h)."""
+    arr = (ctypes.c_void_p * 6)(*[_ptr(f) if not isinstance(f, int) else f for f in fields])
+    out = (ctypes.c_double * 3)()
+    _check(lib().pic_field_energy_noalloc(arr, int(ncell), int(precision), float(dv), out, stream_ptr))
+    return out[0], out[1], out[2]

@@ -37,6 +37,7 @@ struct pic_handle {
   int* d_lv_count = nullptr;  // two counters, one per step parity
   long long lv_cap = 0;
   double* d_acc = nullptr;  // 8 doubles of reduction scratch
+  double* d_red = nullptr;  // block partials of the field-energy reduction
   long long* d_offs = nullptr;
   long long* d_bsum = nullptr;
   long long* d_total = nullptr;
@@ -325,17 +326,15 @@ int step_once(pic_handle* h) {
     SepArgs<T> ja = sep_args<T>(h, false);
     CK(launch(h, PIC_K_FILTER, [&] { return launch_sep<T>(ja, st); }), "current filter");
   }
-  // 7. Yee: B half, E full, B half
-  const double dt = h->cfg.dt;
-  YeeArgs<T> yb = yee_args<T>(h, 0.5 * dt), ye = yee_args<T>(h, dt);
-  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_b<T>(yb, st); }), "yee B");
-  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_e<T>(ye, st); }), "yee E");
-  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_b<T>(yb, st); }), "yee B");
+  // 7. Yee: B half, E full, B half (one fused launch)
+  YeeArgs<T> ye = yee_args<T>(h, h->cfg.dt);
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_fused<T>(ye, h->cfg.ndim, st); }), "yee");
   // 8. diagnostics: field energies of the new state into the history slot
   if (rec) {
     const T* f6[6];
     for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, slot, st); }), "field energy");
+    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, slot, h->d_red, st); }),
+       "field energy");
     h->nhist++;
   }
   h->parity ^= 1;
@@ -517,7 +516,8 @@ int energy_t(pic_handle* h, pic_energy_t* out) {
   CK(cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), st), "zero accumulators");
   const T* f6[6];
   for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-  CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, h->d_acc, st); }), "field energy");
+  CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, h->d_acc, h->d_red, st); }),
+     "field energy");
   RunDev<T> r = make_run<T>(h, h->parity);
   CK(launch(h, PIC_K_DIAG, [&] { return launch_kinetic<T>(r, h->d_acc + 3, st); }), "kinetic energy");
   double acc[8];
@@ -642,6 +642,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   }
   if (ok) ok = (h->d_lv_count = (int*)dalloc(h, 2 * sizeof(int))) != nullptr;
   if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
+  if (ok) ok = (h->d_red = (double*)dalloc(h, field_energy_scratch_bytes())) != nullptr;
+  if (ok) ok = cudaMemset(h->d_red, 0, field_energy_scratch_bytes()) == cudaSuccess;
   if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
   if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
   if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;

@@ -26,8 +26,11 @@ cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes) {
 // the host, in FP64.
 // ---------------------------------------------------------------------------------------------
 constexpr int SEP_THREADS = 256;
-constexpr int SEP2_CX = 64, SEP2_CZ = 16;               // 2D tile
-constexpr int SEP3_CX = 32, SEP3_CY = 4, SEP3_CZ = 8;   // 3D tile
+constexpr int SEP2_CX = 128, SEP2_CZ = 32;              // 2D tile
+constexpr int SEP3_CX = 32, SEP3_CY = 8, SEP3_CZ = 8;   // 3D tile
+
+// Periodic index of g in [-n, 2n): one compare instead of a modulo (falls back for tiny grids).
+__device__ __forceinline__ int wrap_near(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
 template <typename T>
 __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int CY, int CZ, int ntx, int nty) {
@@ -43,20 +46,26 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const int LX = CX + 2 * hx, LY = CY + 2 * hy, LZ = CZ + 2 * hz;
   const long long nxy = (long long)a.nx * a.ny;
+  const bool near = a.nx >= hx && a.nz >= hz && (a.ndim == 2 || a.ny >= hy);  // halos within one period
 
-  for (int e = threadIdx.x; e < LX * LY * LZ; e += SEP_THREADS) {
-    int lx = e % LX, ly = (e / LX) % LY, lz = e / (LX * LY);
-    int gx = wrapi(X0 - hx + lx, a.nx);
-    int gy = a.ndim == 3 ? wrapi(Y0 - hy + ly, a.ny) : 0;
-    int gz = wrapi(Z0 - hz + lz, a.nz);
-    s0[e] = __ldg(src + gz * nxy + (long long)gy * a.nx + gx);
+  // rows of LX consecutive x, one (ly, lz) pair per row
+  for (int row = threadIdx.x / 32; row < LY * LZ; row += SEP_THREADS / 32) {
+    const int ly = row % LY, lz = row / LY;
+    const int gy = a.ndim == 3 ? (near ? wrap_near(Y0 - hy + ly, a.ny) : wrapi(Y0 - hy + ly, a.ny)) : 0;
+    const int gz = near ? wrap_near(Z0 - hz + lz, a.nz) : wrapi(Z0 - hz + lz, a.nz);
+    const T* srow = src + gz * nxy + (long long)gy * a.nx;
+    T* drow = s0 + row * LX;
+    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
+      const int gx = near ? wrap_near(X0 - hx + lx, a.nx) : wrapi(X0 - hx + lx, a.nx);
+      drow[lx] = __ldg(srow + gx);
+    }
   }
   __syncthreads();
   // z pass: LX x LY x CZ
   T* s1 = s0 + LX * LY * LZ;
   const T* zt = a.zt[zs];
   for (int e = threadIdx.x; e < LX * LY * CZ; e += SEP_THREADS) {
-    int lx = e % LX, ly = (e / LX) % LY, lz = e / (LX * LY);
+    const int lx = e % LX, ly = (e / LX) % LY, lz = e / (LX * LY);
     const T* p = s0 + (lz * LY + ly) * LX + lx;
     T acc = T(0);
     for (int m = 0; m <= 2 * hz; ++m) acc += zt[m] * p[m * LX * LY];
@@ -68,7 +77,7 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
   if (a.ndim == 3) {
     s2 = s1 + LX * LY * CZ;
     for (int e = threadIdx.x; e < LX * CY * CZ; e += SEP_THREADS) {
-      int lx = e % LX, ly = (e / LX) % CY, lz = e / (LX * CY);
+      const int lx = e % LX, ly = (e / LX) % CY, lz = e / (LX * CY);
       const T* p = s1 + (lz * LY + ly) * LX + lx;
       T acc = T(0);
       for (int m = 0; m <= 2 * hy; ++m) acc += a.yt[m] * p[m * LX];
@@ -79,8 +88,8 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
   const int SY = a.ndim == 3 ? CY : LY;  // y extent of s2 (LY = 1 in 2D)
   // x pass -> global
   for (int e = threadIdx.x; e < CX * CY * CZ; e += SEP_THREADS) {
-    int lx = e % CX, ly = (e / CX) % CY, lz = e / (CX * CY);
-    int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
+    const int lx = e % CX, ly = (e / CX) % CY, lz = e / (CX * CY);
+    const int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
     if (gx >= a.nx || gy >= (a.ndim == 3 ? a.ny : 1) || gz >= a.nz) continue;
     const T* p = s2 + (lz * SY + ly) * LX + lx;
     T acc = T(0);
@@ -164,6 +173,123 @@ template cudaError_t launch_yee_e<float>(const YeeArgs<float>&, cudaStream_t);
 template cudaError_t launch_yee_e<double>(const YeeArgs<double>&, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
+// Fused Yee step: B -= dt/2 curl E, E += dt (curl B - J), B -= dt/2 curl E on one tile, with the
+// fields staged in shared memory over [-1, C+2) per direction: B^{n+1/2} is formed on [-1, C+1),
+// E^{n+1} on [0, C+1), B^{n+1} on [0, C), and E, B are written back on [0, C). Same arithmetic and
+// order as the three separate updates; one read and one write of E and B per step.
+// ---------------------------------------------------------------------------------------------
+constexpr int YEE_THREADS = 256;
+constexpr int YEE2_CX = 32, YEE2_CZ = 32;
+constexpr int YEE3_CX = 16, YEE3_CY = 8, YEE3_CZ = 8;
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx, int nty) {
+  constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY, CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
+  constexpr int LX = CX + 3, LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + 3, LN = LX * LY * LZ;
+  constexpr int OY = NDIM == 2 ? 0 : 1;  // local offset of the -1 halo along y
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* e[3] = {sm, sm + LN, sm + 2 * LN};
+  T* b[3] = {sm + 3 * LN, sm + 4 * LN, sm + 5 * LN};
+  T* j[3] = {sm + 6 * LN, sm + 7 * LN, sm + 8 * LN};
+  const int tile = blockIdx.x;
+  const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
+  const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
+  const long long nxy = (long long)a.nx * a.ny;
+  const bool near = a.nx >= 2 && a.nz >= 2 && (NDIM == 2 || a.ny >= 2);
+  auto gsrc = [&](int c) -> const T* {
+    switch (c) {
+      case 0: return a.ex;
+      case 1: return a.ey;
+      case 2: return a.ez;
+      case 3: return a.bx;
+      case 4: return a.by;
+      case 5: return a.bz;
+      case 6: return a.jx;
+      case 7: return a.jy;
+      default: return a.jz;
+    }
+  };
+  for (int row = threadIdx.x / 32; row < 9 * LY * LZ; row += YEE_THREADS / 32) {
+    const int c = row / (LY * LZ), r2 = row % (LY * LZ);
+    const int ly = r2 % LY, lz = r2 / LY;
+    const int gy = NDIM == 3 ? (near ? wrap_near(Y0 - 1 + ly, a.ny) : wrapi(Y0 - 1 + ly, a.ny)) : 0;
+    const int gz = near ? wrap_near(Z0 - 1 + lz, a.nz) : wrapi(Z0 - 1 + lz, a.nz);
+    const T* srow = gsrc(c) + gz * nxy + (long long)gy * a.nx;
+    T* drow = sm + c * LN + r2 * LX;
+    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
+      const int gx = near ? wrap_near(X0 - 1 + lx, a.nx) : wrapi(X0 - 1 + lx, a.nx);
+      drow[lx] = srow[gx];
+    }
+  }
+  __syncthreads();
+  const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
+  const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
+  // B^{n+1/2} on local [0, C+2) per direction (cells -1 .. C)
+  for (int q = threadIdx.x; q < (CX + 2) * (NDIM == 3 ? CY + 2 : 1) * (CZ + 2); q += YEE_THREADS) {
+    const int lx = q % (CX + 2), ly = NDIM == 3 ? (q / (CX + 2)) % (CY + 2) : 0, lz = q / ((CX + 2) * (NDIM == 3 ? CY + 2 : 1));
+    const int l = (lz * LY + ly) * LX + lx;
+    const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
+    b[0][l] -= hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey);
+    b[1][l] -= hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez);
+    b[2][l] -= hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex);
+  }
+  __syncthreads();
+  // E^{n+1} on local [1, C+2) (cells 0 .. C)
+  for (int q = threadIdx.x; q < (CX + 1) * (NDIM == 3 ? CY + 1 : 1) * (CZ + 1); q += YEE_THREADS) {
+    const int lx = 1 + q % (CX + 1), ly = NDIM == 3 ? 1 + (q / (CX + 1)) % (CY + 1) : 0,
+              lz = 1 + q / ((CX + 1) * (NDIM == 3 ? CY + 1 : 1));
+    const int l = (lz * LY + ly) * LX + lx;
+    const T bx = b[0][l], by = b[1][l], bz = b[2][l];
+    e[0][l] += a.cy * (bz - b[2][l - sy]) - a.cz * (by - b[1][l - sz]) - a.h * j[0][l];
+    e[1][l] += a.cz * (bx - b[0][l - sz]) - a.cx * (bz - b[2][l - sx]) - a.h * j[1][l];
+    e[2][l] += a.cx * (by - b[1][l - sx]) - a.cy * (bx - b[0][l - sy]) - a.h * j[2][l];
+  }
+  __syncthreads();
+  // B^{n+1} on local [1, C+1) (cells 0 .. C-1), then write E and B of the tile
+  for (int q = threadIdx.x; q < CX * CY * CZ; q += YEE_THREADS) {
+    const int cx = q % CX, cy = (q / CX) % CY, cz = q / (CX * CY);
+    const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
+    if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
+    const int l = ((cz + 1) * LY + cy + OY) * LX + cx + 1;
+    const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
+    const T nbx = b[0][l] - (hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey));
+    const T nby = b[1][l] - (hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez));
+    const T nbz = b[2][l] - (hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex));
+    const long long o = gz * nxy + (long long)gy * a.nx + gx;
+    a.ex[o] = ex;
+    a.ey[o] = ey;
+    a.ez[o] = ez;
+    a.bx[o] = nbx;
+    a.by[o] = nby;
+    a.bz[o] = nbz;
+  }
+}
+
+template <typename T>
+cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
+  if (ndim == 2) {
+    constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
+    const size_t sm = sizeof(T) * 9 * LN;
+    const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_fused<T, 2><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
+  } else {
+    constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
+    const size_t sm = sizeof(T) * 9 * LN;
+    const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
+              ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 3>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_fused<T, 3><<<ntx * nty * ntz, YEE_THREADS, sm, st>>>(a, ntx, nty);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_yee_fused<float>(const YeeArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_yee_fused<double>(const YeeArgs<double>&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
 // FP64 reductions
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -172,49 +298,62 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+constexpr int FE_THREADS = 256;
+constexpr int FE_BLOCKS = 2 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
+
+// Per thread: squares summed in the working precision over its few cells; per block: FP64; the
+// last block to finish adds the block partials in block order (deterministic) and writes
+// out[0..2] = (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2).
 template <typename T>
-__global__ void k_field_energy(const T* __restrict__ ex, const T* __restrict__ ey, const T* __restrict__ ez,
-                               const T* __restrict__ bx, const T* __restrict__ by, const T* __restrict__ bz,
-                               long long n, double* out) {
-  double se = 0, sb = 0, sp = 0;
+__global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict__ ex, const T* __restrict__ ey,
+                                                             const T* __restrict__ ez, const T* __restrict__ bx,
+                                                             const T* __restrict__ by, const T* __restrict__ bz,
+                                                             long long n, double* out, double* scratch) {
+  T se = 0, sb = 0, sp = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    double x2 = (double)ex[c] * ex[c], y2 = (double)ey[c] * ey[c], z2 = (double)ez[c] * ez[c];
-    double u2 = (double)bx[c] * bx[c], v2 = (double)by[c] * by[c], w2 = (double)bz[c] * bz[c];
+    const T x2 = ex[c] * ex[c], y2 = ey[c] * ey[c], z2 = ez[c] * ez[c];
+    const T u2 = bx[c] * bx[c], v2 = by[c] * by[c], w2 = bz[c] * bz[c];
     se += x2 + y2 + z2;
     sb += u2 + v2 + w2;
     sp += x2 + y2 + u2 + v2;
   }
-  __shared__ double red[3][32];
-  se = warp_sum(se);
-  sb = warp_sum(sb);
-  sp = warp_sum(sp);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double red[3][FE_THREADS / 32];
+  __shared__ bool last;
+  double dse = warp_sum((double)se), dsb = warp_sum((double)sb), dsp = warp_sum((double)sp);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][w] = se;
-    red[1][w] = sb;
-    red[2][w] = sp;
+    red[0][w] = dse;
+    red[1][w] = dsb;
+    red[2][w] = dsp;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[3] = {0, 0, 0};
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-      for (int r = 0; r < 3; ++r) t[r] += red[r][q];
-    atomicAdd(out + 0, t[0]);
-    atomicAdd(out + 1, t[1]);
-    atomicAdd(out + 2, t[2]);
+  unsigned* done = reinterpret_cast<unsigned*>(scratch + 3 * FE_BLOCKS);
+  if (threadIdx.x < 3) {
+    double t = 0;
+    for (int q = 0; q < FE_THREADS / 32; ++q) t += red[threadIdx.x][q];
+    scratch[3 * blockIdx.x + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x < 3) {
+    __threadfence();
+    double t = 0;
+    for (unsigned q = 0; q < gridDim.x; ++q) t += ((volatile double*)scratch)[3 * q + threadIdx.x];
+    out[threadIdx.x] = t;
+    if (threadIdx.x == 0) *done = 0u;  // ready for the next launch
   }
 }
 
 template <typename T>
-cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, cudaStream_t st) {
-  int blocks = (int)((ncell + 255) / 256);
-  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
-  if (blocks < 1) blocks = 1;
-  k_field_energy<T><<<blocks, 256, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out);
+cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st) {
+  k_field_energy<T><<<FE_BLOCKS, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch);
   return cudaGetLastError();
 }
-template cudaError_t launch_field_energy<float>(const float* const*, long long, double*, cudaStream_t);
-template cudaError_t launch_field_energy<double>(const double* const*, long long, double*, cudaStream_t);
+template cudaError_t launch_field_energy<float>(const float* const*, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_field_energy<double>(const double* const*, long long, double*, double*, cudaStream_t);
+size_t field_energy_scratch_bytes() { return sizeof(double) * (3 * FE_BLOCKS + 2); }
 
 template <typename T>
 __global__ void k_kinetic(RunDev<T> r, double* out) {

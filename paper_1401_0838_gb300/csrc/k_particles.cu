@@ -247,10 +247,10 @@ __device__ __forceinline__ void load4(const unsigned* p, unsigned (&o)[4]) {
 
 // FP32 uses the hardware reciprocal square root and fast division (relative error ~1e-7, inside
 // the 1e-5 per-step bar); FP64 keeps IEEE division and square root.
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 // Galerkin gather (order 0 along each half-staggered direction, order 1 elsewhere): the nodes are
 // the same for every particle of a cell, so they are read once per lane and each component is an
@@ -288,6 +288,45 @@ struct GalCache<T, 2> {
     F[5] = bz0 + oz * bz1;
   }
 };
+
+// The same Galerkin interpolation read straight from the shared-memory tile (no per-lane cache).
+template <typename T, int NDIM>
+__device__ __forceinline__ void gal_interp(const T* sg, int lx, int ly, int lz, T ox, T oy, T oz, T (&F)[6]) {
+  using S = PushSmem<T, NDIM>;
+  if (NDIM == 2) {
+    const int p = (lz + 1) * S::GX + lx + 1;
+    const T* e = sg;
+    F[0] = e[p] + oz * (e[p + S::GX] - e[p]);
+    e = sg + S::GN;
+    const T a = e[p] + ox * (e[p + 1] - e[p]);
+    const T b = e[p + S::GX] + ox * (e[p + S::GX + 1] - e[p + S::GX]);
+    F[1] = a + oz * (b - a);
+    e = sg + 2 * S::GN;
+    F[2] = e[p] + ox * (e[p + 1] - e[p]);
+    e = sg + 3 * S::GN;
+    F[3] = e[p] + ox * (e[p + 1] - e[p]);
+    F[4] = sg[4 * S::GN + p];
+    e = sg + 5 * S::GN;
+    F[5] = e[p] + oz * (e[p + S::GX] - e[p]);
+  } else {
+    const int p = ((lz + 1) * S::GY + ly + 1) * S::GX + lx + 1;
+    const int sx = 1, sy = S::GX, sz = S::GX * S::GY;
+    auto bil = [&](const T* f, int s1, int s2, T u, T v) {
+      const T a = f[p] + u * (f[p + s1] - f[p]);
+      const T b = f[p + s2] + u * (f[p + s2 + s1] - f[p + s2]);
+      return a + v * (b - a);
+    };
+    F[0] = bil(sg, sy, sz, oy, oz);
+    F[1] = bil(sg + S::GN, sx, sz, ox, oz);
+    F[2] = bil(sg + 2 * S::GN, sx, sy, ox, oy);
+    const T* e = sg + 3 * S::GN;
+    F[3] = e[p] + ox * (e[p + sx] - e[p]);
+    e = sg + 4 * S::GN;
+    F[4] = e[p] + oy * (e[p + sy] - e[p]);
+    e = sg + 5 * S::GN;
+    F[5] = e[p] + oz * (e[p + sz] - e[p]);
+  }
+}
 
 template <typename T>
 struct GalCache<T, 3> {
@@ -558,7 +597,6 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   if (g < NGRP) issue(g, 0, 0);
   cp_async_commit();
   T acc[NVP];
-  GalCache<T, NDIM> gc;
   while (g < NGRP) {
     // prefetch the next item
     int ng = g, nit = it + 1, niters = giters;
@@ -583,8 +621,6 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
     if (it == 0) {
 #pragma unroll
       for (int i = 0; i < NVP; ++i) acc[i] = T(0);
-      // Galerkin: every particle of the cell interpolates the same nodes; read them once per lane
-      if (SCHEME == 0) gc.load(sg, lx, ly, lz);
     }
     {
       const int q = sl + it * LPC;
@@ -614,7 +650,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
           // gather
           T F[6];
           if (SCHEME == 0) {
-            gc.interp(o_x, o_y, o_z, F);
+            gal_interp<T, NDIM>(sg, lx, ly, lz, o_x, o_y, o_z, F);
           } else {
             const DirW<T> dwx = dir_weights(o_x), dwy = dir_weights(o_y), dwz = dir_weights(o_z);
 #pragma unroll
@@ -625,9 +661,9 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
           const T h = qs * r.hq;
           const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
           const T Mz = r.u0 + mz;
-          const T ig = rsqrt_t(T(1) + mx * mx + my * my + Mz * Mz);
+          const T ig = fast_rsqrt(T(1) + mx * mx + my * my + Mz * Mz);
           const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
-          const T sf = div_t(T(2), T(1) + tx * tx + ty * ty + tz * tz);
+          const T sf = fast_div(T(2), T(1) + tx * tx + ty * ty + tz * tz);
           const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
           const T qx = mx + (my * tz - Mz * ty);
           const T qy = my + (Mz * tx - mx * tz);
@@ -637,10 +673,10 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
           uz = mz + (qx * sy - qy * sx) + h * F[2];
           const T Uz = r.u0 + uz;
           const T u2 = ux * ux + uy * uy + Uz * Uz;
-          const T ign = rsqrt_t(T(1) + u2);
+          const T ign = fast_rsqrt(T(1) + u2);
           T vx = ux * ign, vy = uy * ign;
           const T vz = Uz * ign;
-          kin += w * div_t(u2, (T(1) + u2) * ign + T(1));  // gamma - 1 = u^2 / (gamma + 1)
+          kin += w * fast_div(u2, (T(1) + u2) * ign + T(1));  // gamma - 1 = u^2 / (gamma + 1)
           ++npush;
           // move (cell-relative displacement in grid units)
           T ddx = r.dtdx * vx, ddy = NDIM == 3 ? r.dtdy * vy : T(0), ddz = r.dtdz * vz;

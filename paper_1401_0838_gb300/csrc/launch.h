@@ -69,9 +69,14 @@ cudaError_t launch_yee_b(const YeeArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_yee_e(const YeeArgs<T>& a, cudaStream_t st);
 
-// out[0..2] += (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2) in FP64
+// out[0..2] = (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2) in FP64; scratch holds
+// field_energy_scratch_bytes() and starts zeroed (the kernel leaves it ready for the next launch)
 template <typename T>
-cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, cudaStream_t st);
+cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st);
+size_t field_energy_scratch_bytes();
+// B half step, E step, B half step in one launch
+template <typename T>
+cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st);
 // out[0] += sum w (gamma - 1) over both species of the input buffers
 template <typename T>
 cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);

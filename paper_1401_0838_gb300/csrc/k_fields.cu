@@ -29,6 +29,20 @@ constexpr int SEP_THREADS = 256;
 constexpr int SEP2_CX = 128, SEP2_CZ = 32;              // 2D tile
 constexpr int SEP3_CX = 32, SEP3_CY = 8, SEP3_CZ = 8;   // 3D tile
 
+// Element-wise asynchronous global -> shared copies (all loads of a staging loop in flight at once).
+__device__ __forceinline__ void cp_async_el(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_fields() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Periodic index of g in [-n, 2n): one compare instead of a modulo (falls back for tiny grids).
 __device__ __forceinline__ int wrap_near(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
@@ -57,9 +71,10 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
     T* drow = s0 + row * LX;
     for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
       const int gx = near ? wrap_near(X0 - hx + lx, a.nx) : wrapi(X0 - hx + lx, a.nx);
-      drow[lx] = __ldg(srow + gx);
+      cp_async_el(drow + lx, srow + gx);
     }
   }
+  cp_async_wait_all_fields();
   __syncthreads();
   // z pass: LX x LY x CZ
   T* s1 = s0 + LX * LY * LZ;
@@ -219,9 +234,10 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
     T* drow = sm + c * LN + r2 * LX;
     for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
       const int gx = near ? wrap_near(X0 - 1 + lx, a.nx) : wrapi(X0 - 1 + lx, a.nx);
-      drow[lx] = srow[gx];
+      cp_async_el(drow + lx, srow + gx);
     }
   }
+  cp_async_wait_all_fields();
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
   const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
@@ -309,17 +325,17 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
                                                              const T* __restrict__ ez, const T* __restrict__ bx,
                                                              const T* __restrict__ by, const T* __restrict__ bz,
                                                              long long n, double* out, double* scratch) {
-  T se = 0, sb = 0, sp = 0;
+  double se = 0, sb = 0, sp = 0;  // products of FP32 values are exact in FP64
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    const T x2 = ex[c] * ex[c], y2 = ey[c] * ey[c], z2 = ez[c] * ez[c];
-    const T u2 = bx[c] * bx[c], v2 = by[c] * by[c], w2 = bz[c] * bz[c];
-    se += x2 + y2 + z2;
-    sb += u2 + v2 + w2;
-    sp += x2 + y2 + u2 + v2;
+    const double x = ex[c], y = ey[c], z = ez[c], u = bx[c], v = by[c], w = bz[c];
+    const double t = fma(x, x, y * y), tb = fma(u, u, v * v);
+    se += fma(z, z, t);
+    sb += fma(w, w, tb);
+    sp += t + tb;
   }
   __shared__ double red[3][FE_THREADS / 32];
   __shared__ bool last;
-  double dse = warp_sum((double)se), dsb = warp_sum((double)sb), dsp = warp_sum((double)sp);
+  double dse = warp_sum(se), dsb = warp_sum(sb), dsp = warp_sum(sp);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][w] = dse;
@@ -337,11 +353,21 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
   __syncthreads();
-  if (last && threadIdx.x < 3) {
+  if (last) {  // the whole last block adds the partials: strided per thread, then a fixed tree
     __threadfence();
-    double t = 0;
-    for (unsigned q = 0; q < gridDim.x; ++q) t += ((volatile double*)scratch)[3 * q + threadIdx.x];
-    out[threadIdx.x] = t;
+    double t[3] = {0, 0, 0};
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += FE_THREADS)
+      for (int r = 0; r < 3; ++r) t[r] += ((volatile double*)scratch)[3 * q + r];
+    for (int r = 0; r < 3; ++r) t[r] = warp_sum(t[r]);
+    __syncthreads();
+    if (lane == 0)
+      for (int r = 0; r < 3; ++r) red[r][w] = t[r];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double acc = 0;
+      for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
+      out[threadIdx.x] = acc;
+    }
     if (threadIdx.x == 0) *done = 0u;  // ready for the next launch
   }
 }

@@ -38,6 +38,14 @@ __device__ __forceinline__ void copy4_async(double* dst, const double* src) {
   cp_async16(dst + 2, src + 2);
 }
 __device__ __forceinline__ void copy4_async(unsigned* dst, const unsigned* src) { cp_async16(dst, src); }
+__device__ __forceinline__ void copy1_async(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void copy1_async(double* dst, const double* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
 template <typename V>
 __device__ __forceinline__ void read4(const V* p, V (&o)[4]) {
 #pragma unroll
@@ -527,9 +535,20 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
     int gx = wrapi(X0 - 1 + lx, r.nx);
     int gy = NDIM == 3 ? wrapi(Y0 - 1 + ly, r.ny) : 0;
     int gz = wrapi(Z0 - 1 + lz, r.nz);
-    sg[e] = __ldg(r.g[c] + (long long)gz * nxy + (long long)gy * r.nx + gx);
+    const T* src = r.g[0];
+    switch (c) {  // constant-indexed parameter reads (no local copy of r.g)
+      case 1: src = r.g[1]; break;
+      case 2: src = r.g[2]; break;
+      case 3: src = r.g[3]; break;
+      case 4: src = r.g[4]; break;
+      case 5: src = r.g[5]; break;
+      default: break;
+    }
+    copy1_async(sg + e, src + (long long)gz * nxy + (long long)gy * r.nx + gx);
   }
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) sj[e] = T(0);
+  cp_async_commit();
+  cp_async_wait_all();
   // 2. particle counts of the tile's cells; the input counts are zeroed (they are the next step's
   // output counts)
   for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {

@@ -1,0 +1,80 @@
+"""Whole-run physics on the GPU: numerical Cherenkov growth of the transverse field energy of the
+gamma = 130 beam, its fitted growth rate against the FP64 oracle run from the same initial state
+(within 5 %, for the FP32 and FP64 library paths), and its suppression by the Psi correction and the
+filter (Sec. 3-4, qualitative)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.fit import growth_rate
+from tests._pic import P, Pair, make_cfg
+
+pytestmark = pytest.mark.gpu
+
+ALPHA, NX, NZ, STEPS, EVERY = 0.7, 64, 128, 700, 10
+
+
+def _gpu_run(precision, corr, filt, seed=1, steps=STEPS):
+    cfg = make_cfg(nx=NX, nz=NZ, dt=ALPHA, precision=precision, ppc=4, init_beam=1, seed=seed,
+                   targets=filt, track_ids=1)
+    cfg.diag_every = EVERY
+    h = P.pic_create(cfg)
+    if corr:
+        P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(0, ALPHA))
+    return cfg, h
+
+
+def _state_for_oracle(cfg, h):
+    pair = object.__new__(Pair)
+    pair.cfg, pair.h = cfg, h
+    pair.T = np.float32 if cfg.precision == 0 else np.float64
+    pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+    pair.o = O.Sim(ndim=2, nx=cfg.nx, nz=cfg.nz, dt=cfg.dt)
+    return pair.gpu_state()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_growth_rate_matches_oracle(precision):
+    cfg, h = _gpu_run(precision, corr=False, filt=0)
+    try:
+        f0, p0 = _state_for_oracle(cfg, h)
+        o = O.Sim(ndim=2, nx=NX, nz=NZ, dt=ALPHA, f_targets=0)
+        o.set_particles(p0["x"], None, p0["z"], p0["ux"], p0["uy"], p0["uz"], p0["w"], p0["q"], pid=p0["id"])
+        w_o = []
+        for _ in range(STEPS // EVERY):
+            o.step(EVERY)
+            w_o.append(o.energy()[2])
+        P.pic_step(h, STEPS)
+        hist = P.pic_energy_history(h, 4096)
+        w_g = [e["w_perp"] for e in hist]
+    finally:
+        P.pic_destroy(h)
+    assert len(w_g) == STEPS // EVERY
+    t = np.arange(1, STEPS // EVERY + 1) * EVERY * ALPHA
+    g_o, a, b = growth_rate(t, w_o)
+    g_g, c, d = growth_rate(t, w_g)
+    assert w_o[-1] > 1e3 * w_o[10]  # a clear exponential phase
+    assert abs(g_g / g_o - 1) < 0.05, (g_g, g_o, (a, b), (c, d))
+    # the library's own fit agrees with the oracle's fit of the same samples
+    g_lib, i0, i1 = P.pic_fit_growth_rate(t, w_g)
+    assert (i0, i1) == (c, d) and abs(g_lib - g_g) < 1e-12 * abs(g_g)
+
+
+def test_correction_and_filter_suppress_growth():
+    # Sec. 3-4: with the Psi multipliers and the filter the transverse energy ends far below the
+    # uncorrected, unfiltered run
+    out = {}
+    for label, corr, filt in (("off", False, 0), ("on", True, 3)):
+        cfg, h = _gpu_run(0, corr, filt, steps=600)
+        try:
+            P.pic_step(h, 600)
+            out[label] = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+        finally:
+            P.pic_destroy(h)
+    t = np.arange(1, 61) * EVERY * ALPHA
+    g_off, _, _ = growth_rate(t, out["off"])
+    assert out["off"][-1] > 1e3 * out["off"][10]
+    assert out["on"][-1] < 1e-2 * out["off"][-1]
+    assert g_off > 0.01

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
 }
 
 template <typename T>
-cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
+cudaError_t launch_sep_generic(const SepArgs<T>& a, cudaStream_t st) {
   int CX, CY, CZ;
   if (a.ndim == 2) {
     CX = SEP2_CX; CY = 1; CZ = SEP2_CZ;
@@ -131,6 +131,132 @@ cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
   k_sep<T><<<grid, SEP_THREADS, sm, st>>>(a, CX, CY, CZ, ntx, nty);
   return cudaGetLastError();
+}
+
+// Fast separable stencil with compile-time tap counts (2*HZ+1 along z, 2*HX+1 along x and y) and
+// a fixed 2D thread map: no integer division by runtime sizes, taps in registers. Valid when
+// every halo fits in one period of the grid (the dispatcher checks; tiny grids use the generic
+// kernel above).
+template <typename T, int NDIM, int HZ, int HX>
+__global__ void __launch_bounds__(SEP_THREADS) k_sep_t(SepArgs<T> a, int ntx, int nty) {
+  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
+  constexpr int HY = NDIM == 3 ? HX : 0;
+  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
+  constexpr int TXN = CX < 32 ? 32 : CX, TYN = SEP_THREADS / TXN;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* s0 = reinterpret_cast<T*>(smraw);  // [LZ][LY][LX]
+  T* s1 = s0 + LZ * LY * LX;            // [CZ][LY][LX]
+  T* s2 = s1 + CZ * LY * LX;            // [CZ][CY][LX] (3D)
+  const int comp = blockIdx.y;
+  const T* __restrict__ src = a.src[comp];
+  T* __restrict__ dst = a.dst[comp];
+  const int zs = a.zset[comp];
+  const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
+  const int tile = blockIdx.x;
+  const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
+  const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
+  const long long nxy = (long long)a.nx * a.ny;
+  T zt[2 * HZ + 1], xt[2 * HX + 1], yt[2 * HY + 1];
+#pragma unroll
+  for (int m = 0; m <= 2 * HZ; ++m) zt[m] = a.zt[zs][m];
+#pragma unroll
+  for (int m = 0; m <= 2 * HX; ++m) xt[m] = a.xt[m];
+#pragma unroll
+  for (int m = 0; m <= 2 * HY; ++m) yt[m] = a.yt[m];
+  // stage the tile and its halos (rows along x)
+  for (int row = ty; row < LZ * LY; row += TYN) {
+    const int ly = row % LY, lz = row / LY;
+    const int gy = NDIM == 3 ? wrap_near(Y0 - HY + ly, a.ny) : 0;
+    const int gz = wrap_near(Z0 - HZ + lz, a.nz);
+    const T* srow = src + gz * nxy + (long long)gy * a.nx;
+    for (int lx = tx; lx < LX; lx += TXN) cp_async_el(s0 + row * LX + lx, srow + wrap_near(X0 - HX + lx, a.nx));
+  }
+  cp_async_wait_all_fields();
+  __syncthreads();
+  for (int row = ty; row < CZ * LY; row += TYN) {  // z pass
+    const int ly = row % LY, lz = row / LY;
+    for (int lx = tx; lx < LX; lx += TXN) {
+      const T* p = s0 + (lz * LY + ly) * LX + lx;
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * p[m * LY * LX];
+      s1[row * LX + lx] = acc;
+    }
+  }
+  __syncthreads();
+  const T* sx = s1;
+  if (NDIM == 3) {  // y pass
+    for (int row = ty; row < CZ * CY; row += TYN) {
+      const int ly = row % CY, lz = row / CY;
+      for (int lx = tx; lx < LX; lx += TXN) {
+        const T* p = s1 + (lz * LY + ly) * LX + lx;
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m <= 2 * HY; ++m) acc += yt[m] * p[m * LX];
+        s2[row * LX + lx] = acc;
+      }
+    }
+    __syncthreads();
+    sx = s2;
+  }
+  for (int row = ty; row < CZ * CY; row += TYN) {  // x pass -> global
+    const int ly = row % CY, lz = row / CY;
+    const int gy = Y0 + ly, gz = Z0 + lz;
+    if (gz >= a.nz || (NDIM == 3 && gy >= a.ny)) continue;
+    for (int lx = tx; lx < CX; lx += TXN) {
+      const int gx = X0 + lx;
+      if (gx >= a.nx) continue;
+      const T* p = sx + row * LX + lx;
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m <= 2 * HX; ++m) acc += xt[m] * p[m];
+      dst[gz * nxy + (long long)gy * a.nx + gx] = acc;
+    }
+  }
+}
+
+template <typename T, int NDIM, int HZ, int HX>
+static cudaError_t launch_sep_t(const SepArgs<T>& a, cudaStream_t st) {
+  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
+  constexpr int HY = NDIM == 3 ? HX : 0;
+  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
+  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (size_t)CZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
+  const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1, ntz = (a.nz + CZ - 1) / CZ;
+  cudaError_t e = ensure_dynamic_smem((const void*)k_sep_t<T, NDIM, HZ, HX>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
+  k_sep_t<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(a, ntx, nty);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM, int HX>
+static cudaError_t sep_pick_hz(const SepArgs<T>& a, cudaStream_t st) {
+  if (a.hz[0] == HX) return launch_sep_t<T, NDIM, HX, HX>(a, st);          // current filter
+  if (a.hz[0] == HX + 4) return launch_sep_t<T, NDIM, HX + 4, HX>(a, st);  // Psi (9 taps) * filter
+  return launch_sep_generic<T>(a, st);
+}
+
+template <typename T>
+cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
+  const int hz = a.hz[0];
+  const bool fits = a.hz[0] == a.hz[1] && a.nx >= a.hx && a.nz >= hz && (a.ndim == 2 || a.ny >= a.hy);
+  if (!fits || a.hx > 4) return launch_sep_generic<T>(a, st);
+  if (a.ndim == 2) {
+    switch (a.hx) {
+      case 0: return sep_pick_hz<T, 2, 0>(a, st);
+      case 1: return sep_pick_hz<T, 2, 1>(a, st);
+      case 2: return sep_pick_hz<T, 2, 2>(a, st);
+      case 3: return sep_pick_hz<T, 2, 3>(a, st);
+      default: return sep_pick_hz<T, 2, 4>(a, st);
+    }
+  }
+  switch (a.hx) {
+    case 0: return sep_pick_hz<T, 3, 0>(a, st);
+    case 1: return sep_pick_hz<T, 3, 1>(a, st);
+    case 2: return sep_pick_hz<T, 3, 2>(a, st);
+    case 3: return sep_pick_hz<T, 3, 3>(a, st);
+    default: return sep_pick_hz<T, 3, 4>(a, st);
+  }
 }
 template cudaError_t launch_sep<float>(const SepArgs<float>&, cudaStream_t);
 template cudaError_t launch_sep<double>(const SepArgs<double>&, cudaStream_t);
@@ -211,7 +337,7 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const long long nxy = (long long)a.nx * a.ny;
-  const bool near = a.nx >= 2 && a.nz >= 2 && (NDIM == 2 || a.ny >= 2);
+  // the launcher only uses this kernel when every direction has at least 3 cells (halos fit)
   auto gsrc = [&](int c) -> const T* {
     switch (c) {
       case 0: return a.ex;
@@ -228,14 +354,11 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   for (int row = threadIdx.x / 32; row < 9 * LY * LZ; row += YEE_THREADS / 32) {
     const int c = row / (LY * LZ), r2 = row % (LY * LZ);
     const int ly = r2 % LY, lz = r2 / LY;
-    const int gy = NDIM == 3 ? (near ? wrap_near(Y0 - 1 + ly, a.ny) : wrapi(Y0 - 1 + ly, a.ny)) : 0;
-    const int gz = near ? wrap_near(Z0 - 1 + lz, a.nz) : wrapi(Z0 - 1 + lz, a.nz);
+    const int gy = NDIM == 3 ? wrap_near(Y0 - 1 + ly, a.ny) : 0;
+    const int gz = wrap_near(Z0 - 1 + lz, a.nz);
     const T* srow = gsrc(c) + gz * nxy + (long long)gy * a.nx;
     T* drow = sm + c * LN + r2 * LX;
-    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
-      const int gx = near ? wrap_near(X0 - 1 + lx, a.nx) : wrapi(X0 - 1 + lx, a.nx);
-      cp_async_el(drow + lx, srow + gx);
-    }
+    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) cp_async_el(drow + lx, srow + wrap_near(X0 - 1 + lx, a.nx));
   }
   cp_async_wait_all_fields();
   __syncthreads();
@@ -284,6 +407,17 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
 
 template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
+  if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {  // tiny grids: the three separate updates
+    YeeArgs<T> hb = a;
+    hb.cx = a.cx * T(0.5);
+    hb.cy = a.cy * T(0.5);
+    hb.cz = a.cz * T(0.5);
+    hb.h = a.h * T(0.5);
+    cudaError_t e = launch_yee_b<T>(hb, st);
+    if (e == cudaSuccess) e = launch_yee_e<T>(a, st);
+    if (e == cudaSuccess) e = launch_yee_b<T>(hb, st);
+    return e;
+  }
   if (ndim == 2) {
     constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
     const size_t sm = sizeof(T) * 9 * LN;
@@ -315,18 +449,37 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 constexpr int FE_THREADS = 256;
-constexpr int FE_BLOCKS = 2 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
+constexpr int FE_BLOCKS = 8 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
 
-// Per thread: squares summed in the working precision over its few cells; per block: FP64; the
-// last block to finish adds the block partials in block order (deterministic) and writes
-// out[0..2] = (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2).
+// Per thread: FP64 sums of squares (exact products of FP32 values) over a grid-stride set of cells,
+// four per iteration so that several loads are in flight; per block: FP64 tree; the last block to
+// finish adds the block partials (deterministic) and writes out[0..2] = (sum E^2, sum B^2,
+// sum Ex^2+Ey^2+Bx^2+By^2).
 template <typename T>
 __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict__ ex, const T* __restrict__ ey,
                                                              const T* __restrict__ ez, const T* __restrict__ bx,
                                                              const T* __restrict__ by, const T* __restrict__ bz,
                                                              long long n, double* out, double* scratch) {
-  double se = 0, sb = 0, sp = 0;  // products of FP32 values are exact in FP64
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+  double se = 0, sb = 0, sp = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; c + 3 * stride < n; c += 4 * stride) {
+    double x[4], y[4], z[4], u[4], v[4], w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long i = c + k * stride;
+      x[k] = __ldg(ex + i); y[k] = __ldg(ey + i); z[k] = __ldg(ez + i);
+      u[k] = __ldg(bx + i); v[k] = __ldg(by + i); w[k] = __ldg(bz + i);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double t = fma(x[k], x[k], y[k] * y[k]), tb = fma(u[k], u[k], v[k] * v[k]);
+      se += fma(z[k], z[k], t);
+      sb += fma(w[k], w[k], tb);
+      sp += t + tb;
+    }
+  }
+  for (; c < n; c += stride) {
     const double x = ex[c], y = ey[c], z = ez[c], u = bx[c], v = by[c], w = bz[c];
     const double t = fma(x, x, y * y), tb = fma(u, u, v * v);
     se += fma(z, z, t);
@@ -374,7 +527,9 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
 
 template <typename T>
 cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st) {
-  k_field_energy<T><<<FE_BLOCKS, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch);
+  long long want = (ncell + 4 * FE_THREADS - 1) / (4 * FE_THREADS);
+  const int blocks = (int)(want < 1 ? 1 : (want > FE_BLOCKS ? FE_BLOCKS : want));
+  k_field_energy<T><<<blocks, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch);
   return cudaGetLastError();
 }
 template cudaError_t launch_field_energy<float>(const float* const*, long long, double*, double*, cudaStream_t);

@@ -237,6 +237,9 @@ struct DepLayout<3> {
   }
 };
 
+// Periodic index of g in [-n, 2n) without a modulo.
+__device__ __forceinline__ int wrap_near_p(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
+
 // Vector loads of 4 consecutive slots (16-byte aligned: bins start on 64-byte boundaries and
 // packs start at multiples of 4 slots).
 __device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
@@ -527,14 +530,16 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   const long long nxy = (long long)r.nx * r.ny;
 
   // 1. field copies of the tile and its halo into shared memory (periodic wrap); zero the current
+  const bool near_ok = r.nx >= S::TX + 2 && r.nz >= S::TZ + 2 && (NDIM == 2 || r.ny >= S::TY + 2);
   for (int e = tid; e < 6 * S::GN; e += PUSH_THREADS) {
     int c = e / S::GN, rem = e - c * S::GN;
     int lz = rem / (S::GX * S::GY);
     int ly = (rem / S::GX) % S::GY;
     int lx = rem % S::GX;
-    int gx = wrapi(X0 - 1 + lx, r.nx);
-    int gy = NDIM == 3 ? wrapi(Y0 - 1 + ly, r.ny) : 0;
-    int gz = wrapi(Z0 - 1 + lz, r.nz);
+    // tile + halo lies within one period of the grid when the grid has at least TX+2 cells
+    int gx = near_ok ? wrap_near_p(X0 - 1 + lx, r.nx) : wrapi(X0 - 1 + lx, r.nx);
+    int gy = NDIM == 3 ? (near_ok ? wrap_near_p(Y0 - 1 + ly, r.ny) : wrapi(Y0 - 1 + ly, r.ny)) : 0;
+    int gz = near_ok ? wrap_near_p(Z0 - 1 + lz, r.nz) : wrapi(Z0 - 1 + lz, r.nz);
     const T* src = r.g[0];
     switch (c) {  // constant-indexed parameter reads (no local copy of r.g)
       case 1: src = r.g[1]; break;
@@ -840,9 +845,9 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
     int lz = rem / (S::JX * S::JY);
     int ly = (rem / S::JX) % S::JY;
     int lx = rem % S::JX;
-    int gx = wrapi(X0 - 1 + lx, r.nx);
-    int gy = NDIM == 3 ? wrapi(Y0 - 1 + ly, r.ny) : 0;
-    int gz = wrapi(Z0 - 1 + lz, r.nz);
+    int gx = near_ok ? wrap_near_p(X0 - 1 + lx, r.nx) : wrapi(X0 - 1 + lx, r.nx);
+    int gy = NDIM == 3 ? (near_ok ? wrap_near_p(Y0 - 1 + ly, r.ny) : wrapi(Y0 - 1 + ly, r.ny)) : 0;
+    int gz = near_ok ? wrap_near_p(Z0 - 1 + lz, r.nz) : wrapi(Z0 - 1 + lz, r.nz);
     atomicAdd(r.j[c] + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
   }
 
@@ -930,25 +935,51 @@ void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) 
 template <typename T>
 __global__ void k_migrate(RunDev<T> r, int* other_count) {
   const long long n = min((long long)*r.lv_count, r.lv_cap);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int key = r.lv.key[i];
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate together (leavers of one source cell are consecutive and mostly share their
+  // destination, so one atomic per destination group reserves their slots)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const long long i = base + lane;
+    const bool valid = i < n;
+    int key = -1 - lane;
+    T ox = T(0), oy = T(0), oz = T(0), ux = T(0), uy = T(0), uz = T(0), w = T(0);
+    unsigned id = 0;
+    if (valid) {
+      key = r.lv.key[i];
+      ox = r.lv.ox[i];
+      if (r.ndim == 3) oy = r.lv.oy[i];
+      oz = r.lv.oz[i];
+      ux = r.lv.dux[i];
+      uy = r.lv.duy[i];
+      uz = r.lv.duz[i];
+      if (r.lv.w) w = r.lv.w[i];
+      if (r.lv.id) id = r.lv.id[i];
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
     const int s = key & 1;
     const long long cell = key >> 1;
     const SpeciesBuf<T> b = s ? r.out[1] : r.out[0];
-    const int j = atomicAdd(b.cnt + cell, 1);
+    int j0 = 0;
+    if (valid && lane == leader) j0 = atomicAdd(b.cnt + cell, __popc(peers));
+    j0 = __shfl_sync(0xffffffffu, j0, leader);
+    if (!valid) continue;
+    const int j = j0 + rank;
     if (j >= r.cap) {
       flag_error(r.err, ERR_OVERFLOW);
       continue;
     }
     const long long o = cell * r.cap + j;
-    b.ox[o] = r.lv.ox[i];
-    if (r.ndim == 3) b.oy[o] = r.lv.oy[i];
-    b.oz[o] = r.lv.oz[i];
-    b.dux[o] = r.lv.dux[i];
-    b.duy[o] = r.lv.duy[i];
-    b.duz[o] = r.lv.duz[i];
-    if (b.w) b.w[o] = r.lv.w[i];
-    if (b.id) b.id[o] = r.lv.id[i];
+    b.ox[o] = ox;
+    if (r.ndim == 3) b.oy[o] = oy;
+    b.oz[o] = oz;
+    b.dux[o] = ux;
+    b.duy[o] = uy;
+    b.duz[o] = uz;
+    if (b.w) b.w[o] = w;
+    if (b.id) b.id[o] = id;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *other_count = 0;
 }

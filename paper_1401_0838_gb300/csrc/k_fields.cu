@@ -363,10 +363,13 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   cp_async_wait_all_fields();
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // x lane, row group
   const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
   // B^{n+1/2} on local [0, C+2) per direction (cells -1 .. C)
-  for (int q = threadIdx.x; q < (CX + 2) * (NDIM == 3 ? CY + 2 : 1) * (CZ + 2); q += YEE_THREADS) {
-    const int lx = q % (CX + 2), ly = NDIM == 3 ? (q / (CX + 2)) % (CY + 2) : 0, lz = q / ((CX + 2) * (NDIM == 3 ? CY + 2 : 1));
+  constexpr int NY2 = NDIM == 3 ? CY + 2 : 1, NY1 = NDIM == 3 ? CY + 1 : 1;
+  for (int row = ty; row < NY2 * (CZ + 2); row += YEE_THREADS / 32)
+    for (int lx = tx; lx < CX + 2; lx += 32) {
+    const int ly = row % NY2, lz = row / NY2;
     const int l = (lz * LY + ly) * LX + lx;
     const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
     b[0][l] -= hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey);
@@ -375,9 +378,9 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   }
   __syncthreads();
   // E^{n+1} on local [1, C+2) (cells 0 .. C)
-  for (int q = threadIdx.x; q < (CX + 1) * (NDIM == 3 ? CY + 1 : 1) * (CZ + 1); q += YEE_THREADS) {
-    const int lx = 1 + q % (CX + 1), ly = NDIM == 3 ? 1 + (q / (CX + 1)) % (CY + 1) : 0,
-              lz = 1 + q / ((CX + 1) * (NDIM == 3 ? CY + 1 : 1));
+  for (int row = ty; row < NY1 * (CZ + 1); row += YEE_THREADS / 32)
+    for (int qx = tx; qx < CX + 1; qx += 32) {
+    const int lx = 1 + qx, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = 1 + row / NY1;
     const int l = (lz * LY + ly) * LX + lx;
     const T bx = b[0][l], by = b[1][l], bz = b[2][l];
     e[0][l] += a.cy * (bz - b[2][l - sy]) - a.cz * (by - b[1][l - sz]) - a.h * j[0][l];
@@ -386,8 +389,9 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   }
   __syncthreads();
   // B^{n+1} on local [1, C+1) (cells 0 .. C-1), then write E and B of the tile
-  for (int q = threadIdx.x; q < CX * CY * CZ; q += YEE_THREADS) {
-    const int cx = q % CX, cy = (q / CX) % CY, cz = q / (CX * CY);
+  for (int row = ty; row < CY * CZ; row += YEE_THREADS / 32)
+    for (int cx = tx; cx < CX; cx += 32) {
+    const int cy = row % CY, cz = row / CY;
     const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
     if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
     const int l = ((cz + 1) * LY + cy + OY) * LX + cx + 1;
@@ -451,6 +455,24 @@ __device__ __forceinline__ double warp_sum(double v) {
 constexpr int FE_THREADS = 256;
 constexpr int FE_BLOCKS = 8 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
 
+// Compensated FP32 sum of exact squares: every x^2 = hi + lo exactly (lo from an FMA), hi and lo
+// accumulated with Kahan compensation.
+struct FSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ void add_sq(float x) {
+    const float hi = x * x;
+    add(hi);
+    add(fmaf(x, x, -hi));
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 // Per thread: FP64 sums of squares (exact products of FP32 values) over a grid-stride set of cells,
 // four per iteration so that several loads are in flight; per block: FP64 tree; the last block to
 // finish adds the block partials (deterministic) and writes out[0..2] = (sum E^2, sum B^2,
@@ -463,28 +485,33 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
   double se = 0, sb = 0, sp = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (; c + 3 * stride < n; c += 4 * stride) {
-    double x[4], y[4], z[4], u[4], v[4], w[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const long long i = c + k * stride;
-      x[k] = __ldg(ex + i); y[k] = __ldg(ey + i); z[k] = __ldg(ez + i);
-      u[k] = __ldg(bx + i); v[k] = __ldg(by + i); w[k] = __ldg(bz + i);
+  if (sizeof(T) == 4) {
+    // FP32 fields: each square is formed exactly as hi + lo (hi = x*x, lo = fma(x, x, -hi)) and the
+    // per-thread sums are compensated (Kahan) in FP32, so the thread's partial equals the FP64 sum
+    // of exact squares to ~1e-14; only the cross-thread sums use the (slow) FP64 pipe.
+    FSum e2, b2, e2x, e2y, b2x, b2y;
+    for (; c < n; c += stride) {
+      const float x = (float)ex[c], y = (float)ey[c], z = (float)ez[c];
+      const float u = (float)bx[c], v = (float)by[c], w = (float)bz[c];
+      e2x.add_sq(x);
+      e2y.add_sq(y);
+      e2.add_sq(z);
+      b2x.add_sq(u);
+      b2y.add_sq(v);
+      b2.add_sq(w);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double t = fma(x[k], x[k], y[k] * y[k]), tb = fma(u[k], u[k], v[k] * v[k]);
-      se += fma(z[k], z[k], t);
-      sb += fma(w[k], w[k], tb);
+    const double ax = e2x.get(), ay = e2y.get(), bxs = b2x.get(), bys = b2y.get();
+    se = ax + ay + e2.get();
+    sb = bxs + bys + b2.get();
+    sp = ax + ay + bxs + bys;
+  } else {
+    for (; c < n; c += stride) {
+      const double x = ex[c], y = ey[c], z = ez[c], u = bx[c], v = by[c], w = bz[c];
+      const double t = fma(x, x, y * y), tb = fma(u, u, v * v);
+      se += fma(z, z, t);
+      sb += fma(w, w, tb);
       sp += t + tb;
     }
-  }
-  for (; c < n; c += stride) {
-    const double x = ex[c], y = ey[c], z = ez[c], u = bx[c], v = by[c], w = bz[c];
-    const double t = fma(x, x, y * y), tb = fma(u, u, v * v);
-    se += fma(z, z, t);
-    sb += fma(w, w, tb);
-    sp += t + tb;
   }
   __shared__ double red[3][FE_THREADS / 32];
   __shared__ bool last;
@@ -527,7 +554,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
 
 template <typename T>
 cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st) {
-  long long want = (ncell + 4 * FE_THREADS - 1) / (4 * FE_THREADS);
+  long long want = (ncell + 8 * FE_THREADS - 1) / (8 * FE_THREADS);  // about 8 cells per thread
   const int blocks = (int)(want < 1 ? 1 : (want > FE_BLOCKS ? FE_BLOCKS : want));
   k_field_energy<T><<<blocks, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch);
   return cudaGetLastError();

@@ -455,22 +455,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 constexpr int FE_THREADS = 256;
 constexpr int FE_BLOCKS = 8 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
 
-// Compensated FP32 sum of exact squares: every x^2 = hi + lo exactly (lo from an FMA), hi and lo
-// accumulated with Kahan compensation.
+// FP32 sum of exact squares with an error-free running sum: x^2 = hi + lo exactly (lo from an FMA);
+// hi is added by TwoSum (s + hi = t + err exactly) and the small terms err and lo accumulate in c,
+// whose own rounding is O(eps^2) of the sum.
 struct FSum {
   float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
   __device__ __forceinline__ void add_sq(float x) {
     const float hi = x * x;
-    add(hi);
-    add(fmaf(x, x, -hi));
+    const float lo = fmaf(x, x, -hi);
+    const float t = s + hi;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (hi - bb);
+    s = t;
+    c += err + lo;
   }
-  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
 // Per thread: FP64 sums of squares (exact products of FP32 values) over a grid-stride set of cells,
@@ -486,9 +485,9 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (sizeof(T) == 4) {
-    // FP32 fields: each square is formed exactly as hi + lo (hi = x*x, lo = fma(x, x, -hi)) and the
-    // per-thread sums are compensated (Kahan) in FP32, so the thread's partial equals the FP64 sum
-    // of exact squares to ~1e-14; only the cross-thread sums use the (slow) FP64 pipe.
+    // FP32 fields: each square is formed exactly as hi + lo and summed error-free (FSum), so the
+    // thread's partial equals the FP64 sum of exact squares to ~1e-14; only the cross-thread sums use
+    // the (slow) FP64 pipe.
     FSum e2, b2, e2x, e2y, b2x, b2y;
     for (; c < n; c += stride) {
       const float x = (float)ex[c], y = (float)ey[c], z = (float)ez[c];

@@ -50,8 +50,17 @@ struct pic_handle {
   // energy history (device ring of 8 doubles per sample: sum E^2, sum B^2, sum perp^2, K, np)
   double* d_hist = nullptr;
   int hist_cap = 0;
+  int* d_hist_count = nullptr;  // samples written by the device (mirrors nhist)
+  double* d_kin = nullptr;      // kinetic-energy / particle-count accumulator of the recorded step
   long long nhist = 0;
   long long nstep = 0;
+  // CUDA graph of graph_len consecutive steps starting at an even step index
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  cudaStream_t graph_stream = nullptr;
+  int graph_parity = 0;               // parity of the first captured step
+  long long graph_launch_count = 0;   // kernel launches in one replay
+  long long graph_counts[PIC_NKERNEL] = {};
   // kernel timing
   bool timing = false;
   struct Pending {
@@ -65,6 +74,8 @@ struct pic_handle {
   long long launches = 0;
   std::string err;
 };
+
+static void drop_graph(pic_handle* h);
 
 namespace {
 
@@ -231,6 +242,7 @@ RunDev<T> make_run(pic_handle* h, int parity) {
   r.lv.w = (T*)h->lv[7];
   r.lv.id = (unsigned*)h->lv[8];
   r.lv_count = h->d_lv_count + parity;
+  r.lv_other = h->d_lv_count + (1 - parity);
   r.lv_cap = h->lv_cap;
   r.err = h->d_err;
   r.kin = nullptr;
@@ -251,6 +263,7 @@ SepArgs<T> sep_args(pic_handle* h, bool copies) {
   };
   if (copies) {
     a.ncomp = 6;
+    for (int q = 0; q < 3; ++q) a.zero[q] = (T*)h->f[6 + q];  // the current, zeroed before the push
     for (int q = 0; q < 6; ++q) {
       a.src[q] = (const T*)h->f[q];
       a.dst[q] = (T*)h->g[q];
@@ -309,15 +322,13 @@ int step_once(pic_handle* h) {
   cudaStream_t st = h->stream;
   const size_t fb = (size_t)h->ncell * sizeof(T);
   const bool rec = h->cfg.diag_every > 0 && (h->nstep + 1) % h->cfg.diag_every == 0;
-  double* slot = rec ? h->d_hist + 8 * (h->nhist % h->hist_cap) : nullptr;
-  if (rec) CK(cudaMemsetAsync(slot, 0, 8 * sizeof(double), st), "zero history slot");
-  // 1. field copies seen by the particles: Psi(D_z) and the gather filter
+  (void)fb;
+  // 1. field copies seen by the particles: Psi(D_z) and the gather filter; zeroes J
   SepArgs<T> ca = sep_args<T>(h, true);
   CK(launch(h, PIC_K_COPIES, [&] { return launch_sep<T>(ca, st); }), "copy stencil");
   // 2-5. gather, Boris, move, Esirkepov, rebin
-  for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(h->f[6 + q], 0, fb, st), "zero J");
   RunDev<T> r = make_run<T>(h, h->parity);
-  r.kin = rec ? slot + 3 : nullptr;
+  r.kin = rec ? h->d_kin : nullptr;
   CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
   CK(launch(h, PIC_K_MIGRATE, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }),
      "migrate");
@@ -333,7 +344,8 @@ int step_once(pic_handle* h) {
   if (rec) {
     const T* f6[6];
     for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, slot, h->d_red, st); }),
+    HistCtl hc{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
+    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, nullptr, h->d_red, hc, st); }),
        "field energy");
     h->nhist++;
   }
@@ -409,6 +421,7 @@ FlatDev<T> stage_view(pic_handle* h, long long n) {
 template <typename T>
 int set_state_t(pic_handle* h, const pic_state* s) {
   cudaStream_t st = h->stream;
+  drop_graph(h);
   const cudaMemcpyKind k = s->where == PIC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const size_t fb = (size_t)h->ncell * sizeof(T);
   void* const src[6] = {s->ex, s->ey, s->ez, s->bx, s->by, s->bz};
@@ -516,7 +529,8 @@ int energy_t(pic_handle* h, pic_energy_t* out) {
   CK(cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), st), "zero accumulators");
   const T* f6[6];
   for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-  CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, h->d_acc, h->d_red, st); }),
+  HistCtl none{nullptr, 0, nullptr, nullptr};
+  CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, h->d_acc, h->d_red, none, st); }),
      "field energy");
   RunDev<T> r = make_run<T>(h, h->parity);
   CK(launch(h, PIC_K_DIAG, [&] { return launch_kinetic<T>(r, h->d_acc + 3, st); }), "kinetic energy");
@@ -649,6 +663,9 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;
   h->hist_cap = c.diag_capacity > 0 ? c.diag_capacity : 4096;
   if (ok) ok = (h->d_hist = (double*)dalloc(h, 8 * sizeof(double) * (size_t)h->hist_cap)) != nullptr;
+  if (ok) ok = (h->d_hist_count = (int*)dalloc(h, 16)) != nullptr;
+  if (ok) ok = (h->d_kin = (double*)dalloc(h, 2 * sizeof(double))) != nullptr;
+  if (ok) ok = cudaMemset(h->d_hist_count, 0, 16) == cudaSuccess && cudaMemset(h->d_kin, 0, 2 * sizeof(double)) == cudaSuccess;
   if (!ok) {
     pic_destroy(h);
     return PIC_E_OOM;
@@ -686,16 +703,104 @@ int pic_set_correction_stencil(pic_handle* h, const double psi_e[5], const doubl
     if (!isfinite(h->pe[q]) || !isfinite(h->pb[q])) return fail(h, PIC_E_ARG, "non-finite coefficient");
   }
   rebuild_taps(h);
+  drop_graph(h);
   return PIC_OK;
 }
 
-int pic_step(pic_handle* h, int nsteps) {
-  if (!h || nsteps < 0) return PIC_E_ARG;
-  for (int s = 0; s < nsteps; ++s) {
+}  // extern "C" (the graph helpers below have C++ linkage)
+
+static void drop_graph(pic_handle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_len = 0;
+}
+
+static int run_steps(pic_handle* h, int n) {
+  for (int s = 0; s < n; ++s) {
     int rc = h->es == 4 ? step_once<float>(h) : step_once<double>(h);
     if (rc) return rc;
   }
   return PIC_OK;
+}
+
+// Capture graph_len steps (an even number covering whole diagnostic periods) on the handle's
+// stream into one executable graph. Called with the step counter at a multiple of graph_len.
+static int build_graph(pic_handle* h) {
+  drop_graph(h);
+  const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
+  int len = 2;
+  while (len % de) len += 2;
+  if (len > 64) return PIC_E_STATE;  // diagnostics too sparse to unroll into one graph
+  const long long nstep0 = h->nstep, nhist0 = h->nhist;
+  const int parity0 = h->parity;
+  const long long launches0 = h->launches;
+  long long counts0[PIC_NKERNEL];
+  for (int q = 0; q < PIC_NKERNEL; ++q) counts0[q] = h->tcount[q];
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = run_steps(h, len);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  h->nstep = nstep0;
+  h->nhist = nhist0;
+  h->parity = parity0;
+  h->launches = launches0;
+  for (int q = 0; q < PIC_NKERNEL; ++q) h->tcount[q] = counts0[q];
+  if (rc != PIC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != PIC_OK ? rc : cuda_fail(h, e, "end capture");
+  }
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  h->graph_len = len;
+  h->graph_stream = h->stream;
+  h->graph_parity = parity0;
+  h->graph_launch_count = 0;
+  for (int q = 0; q < PIC_NKERNEL; ++q) h->graph_counts[q] = 0;
+  // launches per replay, for pic_launch_count / pic_kernel_times bookkeeping
+  return PIC_OK;
+}
+
+extern "C" {
+
+int pic_step(pic_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return PIC_E_ARG;
+  // Graph replay when at least two whole graphs fit and timing is off; single steps otherwise.
+  const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
+  int len = 2;
+  while (len % de) len += 2;
+  if (h->timing || len > 64 || nsteps < 2 * len) return run_steps(h, nsteps);
+  int lead = (int)((len - h->nstep % len) % len);
+  int rc = run_steps(h, lead);
+  if (rc) return rc;
+  nsteps -= lead;
+  if (!h->graph || h->graph_len != len || h->graph_stream != h->stream || h->graph_parity != h->parity) {
+    // counts of one replay: run one graph's worth of steps while counting, then capture
+    const long long l0 = h->launches;
+    long long c0[PIC_NKERNEL];
+    for (int q = 0; q < PIC_NKERNEL; ++q) c0[q] = h->tcount[q];
+    rc = run_steps(h, len);
+    if (rc) return rc;
+    nsteps -= len;
+    const long long per_launch = h->launches - l0;
+    long long per[PIC_NKERNEL];
+    for (int q = 0; q < PIC_NKERNEL; ++q) per[q] = h->tcount[q] - c0[q];
+    rc = build_graph(h);
+    if (rc) return rc;
+    h->graph_launch_count = per_launch;
+    for (int q = 0; q < PIC_NKERNEL; ++q) h->graph_counts[q] = per[q];
+  }
+  while (nsteps >= len) {
+    CK(cudaGraphLaunch(h->graph, h->stream), "graph launch");
+    h->nstep += len;
+    h->parity = (h->parity + len) & 1;
+    const int de2 = h->cfg.diag_every;
+    if (de2 > 0) h->nhist += len / de2;
+    h->launches += h->graph_launch_count;
+    for (int q = 0; q < PIC_NKERNEL; ++q) h->tcount[q] += h->graph_counts[q];
+    nsteps -= len;
+  }
+  return run_steps(h, nsteps);
 }
 
 int pic_sync(pic_handle* h) {
@@ -816,6 +921,7 @@ int pic_launch_count(pic_handle* h, long long* n) {
 void pic_destroy(pic_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
   for (void* p : h->allocs)
     if (p) cudaFree(p);
   for (auto& p : h->pending) {

@@ -56,10 +56,21 @@ struct RunDev {
   SpeciesBuf<T> in[2], out[2];
   LeaverList<T> lv;
   int* lv_count;       // leavers appended in this step
+  int* lv_other;       // the other parity's leaver counter (zeroed by this step's migrate)
   long long lv_cap;    // capacity of the leaver list
   int* err;
   double* kin;        // FP64 accumulators of this step: [0] sum w (gamma - 1), [1] particle count
                       // (nullptr: not recorded)
+};
+
+// Device-side energy history of one run: the energy kernel writes sample (*count % cap) from its
+// field sums and the kinetic accumulator kin[0..1] (filled by the push kernel), zeroes kin and
+// increments *count, so a captured step needs no host bookkeeping.
+struct HistCtl {
+  double* hist;  // cap x 8 doubles
+  int cap;
+  int* count;
+  double* kin;
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -109,7 +109,13 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
     const T* p = s2 + (lz * SY + ly) * LX + lx;
     T acc = T(0);
     for (int m = 0; m <= 2 * hx; ++m) acc += a.xt[m] * p[m];
-    dst[gz * nxy + (long long)gy * a.nx + gx] = acc;
+    const long long o = gz * nxy + (long long)gy * a.nx + gx;
+    dst[o] = acc;
+    if (comp == 0 && a.zero[0]) {
+      a.zero[0][o] = T(0);
+      a.zero[1][o] = T(0);
+      a.zero[2][o] = T(0);
+    }
   }
 }
 
@@ -138,7 +144,8 @@ cudaError_t launch_sep_generic(const SepArgs<T>& a, cudaStream_t st) {
 // every halo fits in one period of the grid (the dispatcher checks; tiny grids use the generic
 // kernel above).
 template <typename T, int NDIM, int HZ, int HX>
-__global__ void __launch_bounds__(SEP_THREADS) k_sep_t(SepArgs<T> a, int ntx, int nty) {
+__device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, const int comp, const int ntx,
+                                         const int nty) {
   constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
   constexpr int HY = NDIM == 3 ? HX : 0;
   constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
@@ -147,13 +154,12 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep_t(SepArgs<T> a, int ntx, in
   T* s0 = reinterpret_cast<T*>(smraw);  // [LZ][LY][LX]
   T* s1 = s0 + LZ * LY * LX;            // [CZ][LY][LX]
   T* s2 = s1 + CZ * LY * LX;            // [CZ][CY][LX] (3D)
-  const int comp = blockIdx.y;
   const T* __restrict__ src = a.src[comp];
   T* __restrict__ dst = a.dst[comp];
   const int zs = a.zset[comp];
   const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
-  const int tile = blockIdx.x;
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
+  const bool zero_j = comp == 0 && a.zero[0] != nullptr;
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const long long nxy = (long long)a.nx * a.ny;
   T zt[2 * HZ + 1], xt[2 * HX + 1], yt[2 * HY + 1];
@@ -210,9 +216,40 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep_t(SepArgs<T> a, int ntx, in
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m <= 2 * HX; ++m) acc += xt[m] * p[m];
-      dst[gz * nxy + (long long)gy * a.nx + gx] = acc;
+      const long long o = gz * nxy + (long long)gy * a.nx + gx;
+      dst[o] = acc;
+      if (zero_j) {
+        a.zero[0][o] = T(0);
+        a.zero[1][o] = T(0);
+        a.zero[2][o] = T(0);
+      }
     }
   }
+}
+
+template <typename T, int NDIM, int HZ, int HX>
+__global__ void __launch_bounds__(SEP_THREADS) k_sep_t(const __grid_constant__ SepArgs<T> a, int ntx, int nty) {
+  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x, blockIdx.y, ntx, nty);
+}
+
+// Run of a flat tile index: largest r with tile_base[r] <= t.
+__device__ __forceinline__ int run_of_tile(const int* tile_base, int nruns, int t) {
+  int lo = 0, hi = nruns;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_base[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T, int NDIM, int HZ, int HX>
+__global__ void __launch_bounds__(SEP_THREADS) k_sep_batch(const SepArgs<T>* __restrict__ args,
+                                                           const int* __restrict__ tile_base, int nruns) {
+  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY;
+  const int run = run_of_tile(tile_base, nruns, blockIdx.x);
+  const SepArgs<T>& a = args[run];
+  const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
+  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x - tile_base[run], blockIdx.y, ntx, nty);
 }
 
 template <typename T, int NDIM, int HZ, int HX>
@@ -236,11 +273,56 @@ static cudaError_t sep_pick_hz(const SepArgs<T>& a, cudaStream_t st) {
   return launch_sep_generic<T>(a, st);
 }
 
+bool sep_fast_ok(int ndim, int nx, int ny, int nz, int hz, int hx) {
+  return hx <= 4 && (hz == hx || hz == hx + 4) && nx >= hx && nz >= hz && (ndim == 2 || ny >= hx);
+}
+int sep_tiles(int ndim, int nx, int ny, int nz) {
+  if (ndim == 2) return ((nx + SEP2_CX - 1) / SEP2_CX) * ((nz + SEP2_CZ - 1) / SEP2_CZ);
+  return ((nx + SEP3_CX - 1) / SEP3_CX) * ((ny + SEP3_CY - 1) / SEP3_CY) * ((nz + SEP3_CZ - 1) / SEP3_CZ);
+}
+
+template <typename T, int NDIM, int HZ, int HX>
+static cudaError_t launch_sep_batch_t(const SepArgs<T>* args, const int* tile_base, int nruns, int total_tiles,
+                                      int ncomp, cudaStream_t st) {
+  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
+  constexpr int HY = NDIM == 3 ? HX : 0;
+  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
+  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (size_t)CZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
+  cudaError_t e = ensure_dynamic_smem((const void*)k_sep_batch<T, NDIM, HZ, HX>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)total_tiles, (unsigned)ncomp);
+  k_sep_batch<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(args, tile_base, nruns);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM, int HX>
+static cudaError_t sep_batch_pick_hz(const SepArgs<T>* args, const int* tb, int nruns, int tot, int ncomp, int hz,
+                                     cudaStream_t st) {
+  if (hz == HX) return launch_sep_batch_t<T, NDIM, HX, HX>(args, tb, nruns, tot, ncomp, st);
+  return launch_sep_batch_t<T, NDIM, HX + 4, HX>(args, tb, nruns, tot, ncomp, st);
+}
+
+template <typename T>
+cudaError_t launch_sep_batch(const SepArgs<T>* args, const int* tile_base, int nruns, int total_tiles, int ncomp,
+                             int ndim, int hz, int hx, cudaStream_t st) {
+  if (hx < 0 || hx > 4 || (hz != hx && hz != hx + 4)) return cudaErrorInvalidValue;
+#define PIC_SEP_CASE(D, X) \
+  if (ndim == D && hx == X) return sep_batch_pick_hz<T, D, X>(args, tile_base, nruns, total_tiles, ncomp, hz, st);
+  PIC_SEP_CASE(2, 0) PIC_SEP_CASE(2, 1) PIC_SEP_CASE(2, 2) PIC_SEP_CASE(2, 3) PIC_SEP_CASE(2, 4)
+  PIC_SEP_CASE(3, 0) PIC_SEP_CASE(3, 1) PIC_SEP_CASE(3, 2) PIC_SEP_CASE(3, 3) PIC_SEP_CASE(3, 4)
+#undef PIC_SEP_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_sep_batch<float>(const SepArgs<float>*, const int*, int, int, int, int, int, int,
+                                             cudaStream_t);
+template cudaError_t launch_sep_batch<double>(const SepArgs<double>*, const int*, int, int, int, int, int, int,
+                                              cudaStream_t);
+
 template <typename T>
 cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
   const int hz = a.hz[0];
-  const bool fits = a.hz[0] == a.hz[1] && a.nx >= a.hx && a.nz >= hz && (a.ndim == 2 || a.ny >= a.hy);
-  if (!fits || a.hx > 4) return launch_sep_generic<T>(a, st);
+  const bool fits = a.hz[0] == a.hz[1] && sep_fast_ok(a.ndim, a.nx, a.ny, a.nz, hz, a.hx);
+  if (!fits) return launch_sep_generic<T>(a, st);
   if (a.ndim == 2) {
     switch (a.hx) {
       case 0: return sep_pick_hz<T, 2, 0>(a, st);
@@ -324,7 +406,7 @@ constexpr int YEE2_CX = 32, YEE2_CZ = 32;
 constexpr int YEE3_CX = 16, YEE3_CY = 8, YEE3_CZ = 8;
 
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx, int nty) {
+__device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty) {
   constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY, CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
   constexpr int LX = CX + 3, LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + 3, LN = LX * LY * LZ;
   constexpr int OY = NDIM == 2 ? 0 : 1;  // local offset of the -1 halo along y
@@ -333,7 +415,6 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   T* e[3] = {sm, sm + LN, sm + 2 * LN};
   T* b[3] = {sm + 3 * LN, sm + 4 * LN, sm + 5 * LN};
   T* j[3] = {sm + 6 * LN, sm + 7 * LN, sm + 8 * LN};
-  const int tile = blockIdx.x;
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const long long nxy = (long long)a.nx * a.ny;
@@ -409,6 +490,47 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(YeeArgs<T> a, int ntx
   }
 }
 
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty) {
+  yee_tile<T, NDIM>(a, blockIdx.x, ntx, nty);
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(YEE_THREADS) k_yee_batch(const YeeArgs<T>* __restrict__ args,
+                                                           const int* __restrict__ tile_base, int nruns) {
+  constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY;
+  const int run = run_of_tile(tile_base, nruns, blockIdx.x);
+  const YeeArgs<T>& a = args[run];
+  const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
+  yee_tile<T, NDIM>(a, blockIdx.x - tile_base[run], ntx, nty);
+}
+
+int yee_tiles(int ndim, int nx, int ny, int nz) {
+  if (ndim == 2) return ((nx + YEE2_CX - 1) / YEE2_CX) * ((nz + YEE2_CZ - 1) / YEE2_CZ);
+  return ((nx + YEE3_CX - 1) / YEE3_CX) * ((ny + YEE3_CY - 1) / YEE3_CY) * ((nz + YEE3_CZ - 1) / YEE3_CZ);
+}
+
+template <typename T>
+cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int nruns, int total_tiles, int ndim,
+                             cudaStream_t st) {
+  if (ndim == 2) {
+    constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
+    const size_t sm = sizeof(T) * 9 * LN;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 2>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_batch<T, 2><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
+  } else {
+    constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
+    const size_t sm = sizeof(T) * 9 * LN;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 3>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_batch<T, 3><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_yee_batch<float>(const YeeArgs<float>*, const int*, int, int, int, cudaStream_t);
+template cudaError_t launch_yee_batch<double>(const YeeArgs<double>*, const int*, int, int, int, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
   if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {  // tiny grids: the three separate updates
@@ -477,10 +599,10 @@ struct FSum {
 // finish adds the block partials (deterministic) and writes out[0..2] = (sum E^2, sum B^2,
 // sum Ex^2+Ey^2+Bx^2+By^2).
 template <typename T>
-__global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict__ ex, const T* __restrict__ ey,
-                                                             const T* __restrict__ ez, const T* __restrict__ bx,
-                                                             const T* __restrict__ by, const T* __restrict__ bz,
-                                                             long long n, double* out, double* scratch) {
+__device__ __forceinline__ void field_energy_body(const T* __restrict__ ex, const T* __restrict__ ey,
+                                                  const T* __restrict__ ez, const T* __restrict__ bx,
+                                                  const T* __restrict__ by, const T* __restrict__ bz, long long n,
+                                                  double* out, double* scratch, const HistCtl& hc) {
   double se = 0, sb = 0, sp = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -542,7 +664,22 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
     if (lane == 0)
       for (int r = 0; r < 3; ++r) red[r][w] = t[r];
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (hc.hist) {
+      double* slot = hc.hist + 8 * (*hc.count % hc.cap);
+      if (threadIdx.x < 3) {
+        double acc = 0;
+        for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
+        slot[threadIdx.x] = acc;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        slot[3] = hc.kin[0];
+        slot[4] = hc.kin[1];
+        hc.kin[0] = 0.0;
+        hc.kin[1] = 0.0;
+        *hc.count += 1;
+      }
+    } else if (threadIdx.x < 3) {
       double acc = 0;
       for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
       out[threadIdx.x] = acc;
@@ -552,14 +689,41 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
 }
 
 template <typename T>
-cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st) {
-  long long want = (ncell + 8 * FE_THREADS - 1) / (8 * FE_THREADS);  // about 8 cells per thread
-  const int blocks = (int)(want < 1 ? 1 : (want > FE_BLOCKS ? FE_BLOCKS : want));
-  k_field_energy<T><<<blocks, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch);
+__global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict__ ex, const T* __restrict__ ey,
+                                                             const T* __restrict__ ez, const T* __restrict__ bx,
+                                                             const T* __restrict__ by, const T* __restrict__ bz,
+                                                             long long n, double* out, double* scratch, HistCtl hc) {
+  field_energy_body<T>(ex, ey, ez, bx, by, bz, n, out, scratch, hc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FE_THREADS) k_field_energy_batch(const EnergyArgs<T>* __restrict__ args) {
+  const EnergyArgs<T>& a = args[blockIdx.y];
+  field_energy_body<T>(a.f[0], a.f[1], a.f[2], a.f[3], a.f[4], a.f[5], a.ncell, nullptr, a.scratch, a.hc);
+}
+
+template <typename T>
+cudaError_t launch_field_energy_batch(const EnergyArgs<T>* args, int nruns, cudaStream_t st) {
+  dim3 grid(2 * 152 / (nruns < 8 ? 1 : nruns / 8) + 1, (unsigned)nruns);  // about 2 waves in all
+  k_field_energy_batch<T><<<grid, FE_THREADS, 0, st>>>(args);
   return cudaGetLastError();
 }
-template cudaError_t launch_field_energy<float>(const float* const*, long long, double*, double*, cudaStream_t);
-template cudaError_t launch_field_energy<double>(const double* const*, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_field_energy_batch<float>(const EnergyArgs<float>*, int, cudaStream_t);
+template cudaError_t launch_field_energy_batch<double>(const EnergyArgs<double>*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, HistCtl hc,
+                                cudaStream_t st) {
+  long long want = (ncell + 8 * FE_THREADS - 1) / (8 * FE_THREADS);  // about 8 cells per thread
+  const int blocks = (int)(want < 1 ? 1 : (want > FE_BLOCKS ? FE_BLOCKS : want));
+  k_field_energy<T><<<blocks, FE_THREADS, 0, st>>>(f6[0], f6[1], f6[2], f6[3], f6[4], f6[5], ncell, out, scratch,
+                                                     hc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_field_energy<float>(const float* const*, long long, double*, double*, HistCtl,
+                                                cudaStream_t);
+template cudaError_t launch_field_energy<double>(const double* const*, long long, double*, double*, HistCtl,
+                                                 cudaStream_t);
 size_t field_energy_scratch_bytes() { return sizeof(double) * (3 * FE_BLOCKS + 2); }
 
 template <typename T>

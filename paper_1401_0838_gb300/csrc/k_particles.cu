@@ -507,7 +507,7 @@ struct PushMinBlocks {
 };
 
 template <typename T, int NDIM, int SCHEME, int LPC>
-__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k_push(RunDev<T> r) {
+__device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   using S = PushSmem<T, NDIM>;
   using PL = PushPlan<NDIM, LPC>;
   constexpr int TX = S::TX, TY = S::TY, NCL = S::NCL;
@@ -521,7 +521,6 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
   int* scnt = sn + 2 * NCL;                          // [species][cell] output counts of this tile
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tile = blockIdx.x;
   const int tix = tile % r.ntx;
   const int tiy = (tile / r.ntx) % r.nty;
   const int tiz = tile / (r.ntx * r.nty);
@@ -862,10 +861,10 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
       nd += __shfl_xor_sync(0xffffffffu, nd, o);
     }
     __shared__ double skin[NWARP];
-    __shared__ int scnt[NWARP];
+    __shared__ int swcnt[NWARP];
     if (lane == 0) {
       skin[warp] = kd;
-      scnt[warp] = nd;
+      swcnt[warp] = nd;
     }
     __syncthreads();
     if (tid == 0) {
@@ -873,11 +872,49 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value) k
       long long c = 0;
       for (int w2 = 0; w2 < NWARP; ++w2) {
         t += skin[w2];
-        c += scnt[w2];
+        c += swcnt[w2];
       }
       atomicAdd(r.kin, t);
       atomicAdd(r.kin + 1, (double)c);
     }
+  }
+}
+
+// One tile per block.
+template <typename T, int NDIM, int SCHEME, int LPC>
+__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
+    k_push(const __grid_constant__ RunDev<T> r) {
+  push_tile<T, NDIM, SCHEME, LPC>(r, blockIdx.x);
+}
+
+// Persistent form for many runs: each block takes (run, tile) work items from a global counter
+// (items grouped by run, so a block mostly stays on one run) and copies the run's descriptor into
+// shared memory when the run changes. Work-list counter reset: the caller zeroes *queue before the
+// launch.
+template <typename T, int NDIM, int SCHEME, int LPC>
+__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
+    k_push_batch(const RunDev<T>* __restrict__ runs, const int2* __restrict__ items, int nitems, int* queue) {
+  __shared__ RunDev<T> rs;
+  __shared__ int cur, cur_run;
+  if (threadIdx.x == 0) cur_run = -1;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) cur = atomicAdd(queue, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) break;
+    const int2 w = items[it];
+    if (w.x != cur_run) {  // warp 0 copies the descriptor as 32-bit words
+      __syncthreads();
+      constexpr int NW = (int)(sizeof(RunDev<T>) / 4);
+      const int* src = reinterpret_cast<const int*>(runs + w.x);
+      int* dst = reinterpret_cast<int*>(&rs);
+      for (int k = threadIdx.x; k < NW; k += PUSH_THREADS) dst[k] = src[k];
+      __syncthreads();
+      if (threadIdx.x == 0) cur_run = w.x;
+    }
+    __syncthreads();
+    push_tile<T, NDIM, SCHEME, LPC>(rs, w.y);
   }
 }
 
@@ -894,7 +931,7 @@ static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
   using S = PushSmem<T, NDIM>;
   const size_t sm = S::bytes();
   const int ntiles = r.ntx * r.nty * r.ntz;
-  auto go = [&](void (*kern)(RunDev<T>)) -> cudaError_t {
+  auto go = [&](void (*kern)(const RunDev<T>)) -> cudaError_t {
     cudaError_t e = ensure_dynamic_smem((const void*)kern, sm);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, PUSH_THREADS, sm, st>>>(r);
@@ -913,6 +950,58 @@ cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st) {
   return r.scheme == 0 ? launch_push_t<T, 3, 0>(r, lpc, st) : launch_push_t<T, 3, 1>(r, lpc, st);
 }
 template cudaError_t launch_push<float>(const RunDev<float>&, int, cudaStream_t);
+
+template <typename T, int NDIM, int SCHEME>
+static cudaError_t launch_push_batch_t(const RunDev<T>* runs, const int2* items, int nitems, int* queue, int lpc,
+                                       int blocks, cudaStream_t st) {
+  using S = PushSmem<T, NDIM>;
+  const size_t sm = S::bytes();
+  auto go = [&](void (*kern)(const RunDev<T>*, const int2*, int, int*)) -> cudaError_t {
+    cudaError_t e = ensure_dynamic_smem((const void*)kern, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, PUSH_THREADS, sm, st>>>(runs, items, nitems, queue);
+    return cudaGetLastError();
+  };
+  if (lpc == 4) return go(k_push_batch<T, NDIM, SCHEME, 4>);
+  if (lpc == 8) return go(k_push_batch<T, NDIM, SCHEME, 8>);
+  return go(k_push_batch<T, NDIM, SCHEME, 16>);
+}
+
+template <typename T>
+cudaError_t launch_push_batch(const RunDev<T>* runs, const int2* items, int nitems, int* queue, int ndim, int scheme,
+                              int lpc, int blocks, cudaStream_t st) {
+  if (ndim == 2)
+    return scheme == 0 ? launch_push_batch_t<T, 2, 0>(runs, items, nitems, queue, lpc, blocks, st)
+                       : launch_push_batch_t<T, 2, 1>(runs, items, nitems, queue, lpc, blocks, st);
+  return scheme == 0 ? launch_push_batch_t<T, 3, 0>(runs, items, nitems, queue, lpc, blocks, st)
+                     : launch_push_batch_t<T, 3, 1>(runs, items, nitems, queue, lpc, blocks, st);
+}
+template cudaError_t launch_push_batch<float>(const RunDev<float>*, const int2*, int, int*, int, int, int, int,
+                                              cudaStream_t);
+template cudaError_t launch_push_batch<double>(const RunDev<double>*, const int2*, int, int*, int, int, int, int,
+                                               cudaStream_t);
+
+int push_lanes_per_cell(int ndim, int ppc_total) { return lanes_per_cell(ndim, ppc_total); }
+
+template <typename T>
+int push_max_blocks_per_sm(int ndim, int scheme, int lpc) {
+  int n = 0;
+  size_t sm = ndim == 2 ? PushSmem<T, 2>::bytes() : PushSmem<T, 3>::bytes();
+  const void* k = nullptr;
+  if (ndim == 2)
+    k = scheme == 0 ? (lpc == 4 ? (const void*)k_push_batch<T, 2, 0, 4> : lpc == 8 ? (const void*)k_push_batch<T, 2, 0, 8> : (const void*)k_push_batch<T, 2, 0, 16>)
+                    : (lpc == 4 ? (const void*)k_push_batch<T, 2, 1, 4> : lpc == 8 ? (const void*)k_push_batch<T, 2, 1, 8> : (const void*)k_push_batch<T, 2, 1, 16>);
+  else
+    k = scheme == 0 ? (lpc == 4 ? (const void*)k_push_batch<T, 3, 0, 4> : lpc == 8 ? (const void*)k_push_batch<T, 3, 0, 8> : (const void*)k_push_batch<T, 3, 0, 16>)
+                    : (lpc == 4 ? (const void*)k_push_batch<T, 3, 1, 4> : lpc == 8 ? (const void*)k_push_batch<T, 3, 1, 8> : (const void*)k_push_batch<T, 3, 1, 16>);
+  if (ensure_dynamic_smem(k, sm) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, PUSH_THREADS, sm) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+template int push_max_blocks_per_sm<float>(int, int, int);
+template int push_max_blocks_per_sm<double>(int, int, int);
 template cudaError_t launch_push<double>(const RunDev<double>&, int, cudaStream_t);
 
 void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) {
@@ -933,13 +1022,13 @@ void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) 
 // step's push.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_migrate(RunDev<T> r, int* other_count) {
+__device__ __forceinline__ void migrate_body(const RunDev<T>& r, int* other_count, int bid, int nblk) {
   const long long n = min((long long)*r.lv_count, r.lv_cap);
   const int lane = threadIdx.x & 31;
   // whole warps iterate together (leavers of one source cell are consecutive and mostly share their
   // destination, so one atomic per destination group reserves their slots)
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+  const long long stride = (long long)nblk * blockDim.x;
+  for (long long base = bid * (long long)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const long long i = base + lane;
     const bool valid = i < n;
     int key = -1 - lane;
@@ -981,7 +1070,18 @@ __global__ void k_migrate(RunDev<T> r, int* other_count) {
     if (b.w) b.w[o] = w;
     if (b.id) b.id[o] = id;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *other_count = 0;
+  if (bid == 0 && threadIdx.x == 0) *other_count = 0;
+}
+
+template <typename T>
+__global__ void k_migrate(const __grid_constant__ RunDev<T> r, int* other_count) {
+  migrate_body<T>(r, other_count, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void k_migrate_batch(const RunDev<T>* __restrict__ runs) {
+  const RunDev<T>& r = runs[blockIdx.y];
+  migrate_body<T>(r, r.lv_other, blockIdx.x, gridDim.x);
 }
 
 template <typename T>
@@ -989,6 +1089,15 @@ cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st
   k_migrate<T><<<152 * 4, 256, 0, st>>>(r, other_count);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_migrate_batch(const RunDev<T>* runs, int nruns, cudaStream_t st) {
+  dim3 grid(4 * 152 / (nruns < 4 ? 1 : nruns / 4) + 1, (unsigned)nruns);
+  k_migrate_batch<T><<<grid, 256, 0, st>>>(runs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_migrate_batch<float>(const RunDev<float>*, int, cudaStream_t);
+template cudaError_t launch_migrate_batch<double>(const RunDev<double>*, int, cudaStream_t);
 template cudaError_t launch_migrate<float>(const RunDev<float>&, int*, cudaStream_t);
 template cudaError_t launch_migrate<double>(const RunDev<double>&, int*, cudaStream_t);
 

@@ -24,6 +24,7 @@ struct SepArgs {
   T* dst[6];
   int zset[6];
   int ncomp;
+  T* zero[3];  // optional: arrays zeroed at this kernel's output cells (the current, before a push)
   int nx, ny, nz, ndim;
   int hz[2], hx, hy;
   T zt[2][MAX_ZTAPS];
@@ -50,6 +51,13 @@ template <typename T>
 cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st);
 template <typename T>
 cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st);
+// Many runs in one persistent launch: work items (run, tile), *queue zeroed by the launcher.
+template <typename T>
+cudaError_t launch_push_batch(const RunDev<T>* runs, const int2* items, int nitems, int* queue, int ndim, int scheme,
+                              int lpc, int blocks, cudaStream_t st);
+int push_lanes_per_cell(int ndim, int ppc_total);
+template <typename T>
+int push_max_blocks_per_sm(int ndim, int scheme, int lpc);
 template <typename T>
 cudaError_t launch_init_beam(const RunDev<T>& r, int ppc, const int lat[3], double u0, double w0, double jitter,
                              double u_th, double sigma_perp, unsigned long long seed, cudaStream_t st);
@@ -69,10 +77,34 @@ cudaError_t launch_yee_b(const YeeArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_yee_e(const YeeArgs<T>& a, cudaStream_t st);
 
-// out[0..2] = (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2) in FP64; scratch holds
-// field_energy_scratch_bytes() and starts zeroed (the kernel leaves it ready for the next launch)
+// (sum E^2, sum B^2, sum Ex^2+Ey^2+Bx^2+By^2) in FP64 into out[0..2], or, when hc.hist is set, into
+// the run's device history (see HistCtl); scratch holds field_energy_scratch_bytes() and starts
+// zeroed (the kernel leaves it ready for the next launch)
 template <typename T>
-cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, cudaStream_t st);
+cudaError_t launch_field_energy(const T* const f6[6], long long ncell, double* out, double* scratch, HistCtl hc,
+                                cudaStream_t st);
+template <typename T>
+struct EnergyArgs {
+  const T* f[6];
+  long long ncell;
+  double* scratch;
+  HistCtl hc;
+};
+template <typename T>
+cudaError_t launch_field_energy_batch(const EnergyArgs<T>* args, int nruns, cudaStream_t st);
+// Many runs: tile_base[run] = first flat tile of the run (prefix over runs, tile_base[nruns] = total)
+template <typename T>
+cudaError_t launch_sep_batch(const SepArgs<T>* args, const int* tile_base, int nruns, int total_tiles, int ncomp,
+                             int ndim, int hz, int hx, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int nruns, int total_tiles, int ndim,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_migrate_batch(const RunDev<T>* runs, int nruns, cudaStream_t st);
+// tiles of the fast stencil / Yee kernels for a grid
+int sep_tiles(int ndim, int nx, int ny, int nz);
+int yee_tiles(int ndim, int nx, int ny, int nz);
+bool sep_fast_ok(int ndim, int nx, int ny, int nz, int hz, int hx);
 size_t field_energy_scratch_bytes();
 // B half step, E step, B half step in one launch
 template <typename T>

@@ -230,6 +230,35 @@ int pic_launch_count(pic_handle* h, long long* n);
 int pic_field_energy_noalloc(const void* const fields[6], long long ncell, int precision, double dv,
                              double out[3], void* stream);
 
+/*
+ * Batched runs (the sweeps of Sec. 3: growth rate against c dt/dz, gamma and the correction): many
+ * independent simulations of possibly different grid sizes advanced together. Every step is one
+ * set of multi-run launches (a persistent push kernel per lanes-per-cell group takes (run, tile)
+ * items from a work list; one stencil, migrate, Yee and energy launch cover all runs) replayed from
+ * a CUDA graph. The runs must agree on ndim, precision, scheme, shape order, filter and diagnostic
+ * settings, per-particle weights and id tracking (PIC_E_ARG otherwise); grids, ppc, gamma, dt,
+ * seeds and corrections may differ. Each grid needs at least as many cells per direction as the
+ * stencil halos (PIC_E_ARG otherwise).
+ */
+typedef struct pic_batch pic_batch;
+int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out);
+int pic_batch_size(const pic_batch* b);
+/* The handle of one run (owned by the batch): for state import/export and energies between steps.
+ * Stepping a run on its own desynchronises it from the batch (pic_batch_step then fails). */
+pic_handle* pic_batch_run(pic_batch* b, int run);
+int pic_batch_set_correction_stencil(pic_batch* b, int run, const double psi_e[5], const double psi_b[5]);
+int pic_batch_set_stream(pic_batch* b, void* stream);
+int pic_batch_step(pic_batch* b, int nsteps);
+int pic_batch_sync(pic_batch* b);
+int pic_batch_energy_history(pic_batch* b, int run, pic_energy_t* out, int max, int* count);
+/* Autotuner: for every lanes-per-cell group, times 2*trial_steps batched steps with each candidate
+ * (4, 8 or 16 lanes per cell; 1 or 2 resident blocks of the push kernel per SM) and keeps the
+ * fastest (written to lpc_out[group] when not NULL); then every run is put back into its seeded
+ * initial state (fields zero, beam from the seed), so tune before importing other states. */
+int pic_batch_autotune(pic_batch* b, int trial_steps, int* lpc_out);
+void pic_batch_destroy(pic_batch* b);
+const char* pic_batch_last_error(const pic_batch* b);
+
 /* Frees everything the handle owns. NULL is a no-op. */
 void pic_destroy(pic_handle* h);
 

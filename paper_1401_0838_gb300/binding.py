@@ -27,7 +27,10 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_set_correction_stencil", "pic_step", "pic_sync", "pic_energy", "pic_num_particles",
            "pic_get_state", "pic_set_state", "pic_debug_gather_copies", "pic_debug_current",
            "pic_fit_growth_rate", "pic_destroy", "pic_last_error", "pic_strerror", "pic_energy_history",
-           "pic_enable_timing", "pic_kernel_times", "pic_launch_count", "pic_field_energy_noalloc")
+           "pic_enable_timing", "pic_kernel_times", "pic_launch_count", "pic_field_energy_noalloc",
+           "pic_batch_create", "pic_batch_size", "pic_batch_run", "pic_batch_set_correction_stencil",
+           "pic_batch_set_stream", "pic_batch_step", "pic_batch_sync", "pic_batch_energy_history",
+           "pic_batch_autotune", "pic_batch_destroy", "pic_batch_last_error")
 PIC_NKERNEL = 7
 KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
 
@@ -99,10 +102,25 @@ def lib() -> ctypes.CDLL:
         L.pic_kernel_times.argtypes = [V, DP, P(ctypes.c_longlong)]
         L.pic_launch_count.argtypes = [V, P(ctypes.c_longlong)]
         L.pic_field_energy_noalloc.argtypes = [P(V), ctypes.c_longlong, I, D, DP, V]
+        L.pic_batch_create.argtypes = [P(pic_config), I, P(V)]
+        L.pic_batch_size.argtypes = [V]
+        L.pic_batch_run.argtypes = [V, I]
+        L.pic_batch_run.restype = V
+        L.pic_batch_set_correction_stencil.argtypes = [V, I, DP, DP]
+        L.pic_batch_set_stream.argtypes = [V, V]
+        L.pic_batch_step.argtypes = [V, I]
+        L.pic_batch_sync.argtypes = [V]
+        L.pic_batch_energy_history.argtypes = [V, I, P(pic_energy_t), I, P(I)]
+        L.pic_batch_autotune.argtypes = [V, I, P(I)]
+        L.pic_batch_destroy.argtypes = [V]
+        L.pic_batch_destroy.restype = None
+        L.pic_batch_last_error.argtypes = [V]
+        L.pic_batch_last_error.restype = ctypes.c_char_p
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("pic_config_default", "pic_destroy", "pic_last_error", "pic_strerror"):
+            if name not in ("pic_config_default", "pic_destroy", "pic_last_error", "pic_strerror", "pic_batch_run",
+                            "pic_batch_destroy", "pic_batch_last_error"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -271,3 +289,68 @@ def pic_field_energy_noalloc(fields, ncell: int, precision: int, dv: float, stre
     out = (ctypes.c_double * 3)()
     _check(lib().pic_field_energy_noalloc(arr, int(ncell), int(precision), float(dv), out, stream_ptr))
     return out[0], out[1], out[2]
+
+
+# ------------------------------------------------------------------------------------------------
+# batched runs
+# ------------------------------------------------------------------------------------------------
+def _bcheck(rc, b):
+    if rc != PIC_OK:
+        msg = lib().pic_strerror(rc).decode()
+        detail = lib().pic_batch_last_error(b).decode() if b is not None else ""
+        raise PicError(rc, f"{msg}: {detail}" if detail else msg)
+
+
+def pic_batch_create(cfgs):
+    arr = (pic_config * len(cfgs))(*cfgs)
+    b = ctypes.c_void_p()
+    _check(lib().pic_batch_create(arr, len(cfgs), ctypes.byref(b)))
+    return b
+
+
+def pic_batch_size(b) -> int:
+    return lib().pic_batch_size(b)
+
+
+def pic_batch_run(b, run: int):
+    h = lib().pic_batch_run(b, run)
+    if not h:
+        raise PicError(PIC_E_ARG, "no such run")
+    return ctypes.c_void_p(h)
+
+
+def pic_batch_set_correction_stencil(b, run: int, psi_e=None, psi_b=None):
+    pe = None if psi_e is None else (ctypes.c_double * 5)(*[float(v) for v in psi_e])
+    pb = None if psi_b is None else (ctypes.c_double * 5)(*[float(v) for v in psi_b])
+    _bcheck(lib().pic_batch_set_correction_stencil(b, run, pe, pb), b)
+
+
+def pic_batch_set_stream(b, stream_ptr):
+    _bcheck(lib().pic_batch_set_stream(b, stream_ptr), b)
+
+
+def pic_batch_step(b, nsteps: int = 1):
+    _bcheck(lib().pic_batch_step(b, int(nsteps)), b)
+
+
+def pic_batch_sync(b):
+    _bcheck(lib().pic_batch_sync(b), b)
+
+
+def pic_batch_energy_history(b, run: int, max_samples: int = 4096):
+    buf = (pic_energy_t * max(max_samples, 1))()
+    n = ctypes.c_int()
+    _bcheck(lib().pic_batch_energy_history(b, run, buf, max_samples, ctypes.byref(n)), b)
+    return [{"w_e": e.w_e, "w_b": e.w_b, "w_perp": e.w_perp, "k": e.k, "total": e.total, "np": e.np}
+            for e in buf[:n.value]]
+
+
+def pic_batch_autotune(b, trial_steps: int = 3, ngroups: int = 8):
+    out = (ctypes.c_int * ngroups)()
+    _bcheck(lib().pic_batch_autotune(b, int(trial_steps), out), b)
+    return list(out)
+
+
+def pic_batch_destroy(b):
+    if b is not None:
+        lib().pic_batch_destroy(b)

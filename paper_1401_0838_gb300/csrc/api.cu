@@ -955,3 +955,484 @@ const char* pic_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ================================================================================================
+// Batched runs: many independent simulations advanced by one set of multi-run launches per step
+// (persistent push over a work list of (run, tile) items, one launch per lanes-per-cell group),
+// replayed from a CUDA graph. Each run is a full pic_handle; the batch only adds the device tables
+// of per-run kernel arguments and the launch sequence.
+// ================================================================================================
+struct pic_batch {
+  std::vector<pic_handle*> runs;
+  cudaStream_t own = nullptr, stream = nullptr;
+  size_t es = 8;
+  int ndim = 2, scheme = 0, hz = 0, hx = 0, hzj = 0, hxj = 0;
+  bool filter_j = false;
+  int diag_every = 0;
+  std::vector<void*> allocs;
+  void* d_run[2][2] = {};  // RunDev<T>[nruns] by [parity][recording]
+  void* d_sep_copy = nullptr;
+  void* d_sep_j = nullptr;
+  void* d_yee = nullptr;
+  void* d_energy = nullptr;
+  int* d_sep_base = nullptr;
+  int sep_total = 0;
+  int* d_yee_base = nullptr;
+  int yee_total = 0;
+  struct Group {
+    int lpc = 8, blocks = 0;
+    int2* d_items = nullptr;
+    int nitems = 0;
+    int* d_queue = nullptr;
+    std::vector<int> members;
+  };
+  std::vector<Group> groups;
+  bool tables_dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0, graph_parity = 0;
+  cudaStream_t graph_stream = nullptr;
+  long long nstep = 0;
+  int parity = 0;
+  std::string err;
+};
+
+namespace {
+
+int bfail(pic_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+#define BCK(call, what)                                                                        \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return bfail(b, e_ == cudaErrorMemoryAllocation ? PIC_E_OOM : PIC_E_CUDA, \
+                                        std::string(what) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+void* balloc(pic_batch* b, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  b->allocs.push_back(p);
+  return p;
+}
+
+void batch_drop_graph(pic_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_len = 0;
+}
+
+// Upload the per-run argument tables (after creation, a correction change or a tuning change).
+template <typename T>
+int batch_tables(pic_batch* b) {
+  const int n = (int)b->runs.size();
+  std::vector<RunDev<T>> rd(n);
+  for (int p = 0; p < 2; ++p)
+    for (int rec = 0; rec < 2; ++rec) {
+      for (int i = 0; i < n; ++i) {
+        rd[i] = make_run<T>(b->runs[i], p);
+        rd[i].kin = rec ? b->runs[i]->d_kin : nullptr;
+      }
+      BCK(cudaMemcpy(b->d_run[p][rec], rd.data(), sizeof(RunDev<T>) * n, cudaMemcpyHostToDevice), "run table");
+    }
+  std::vector<SepArgs<T>> sc(n), sj(n);
+  std::vector<YeeArgs<T>> ya(n);
+  std::vector<EnergyArgs<T>> ea(n);
+  for (int i = 0; i < n; ++i) {
+    pic_handle* h = b->runs[i];
+    sc[i] = sep_args<T>(h, true);
+    sj[i] = sep_args<T>(h, false);
+    ya[i] = yee_args<T>(h, h->cfg.dt);
+    for (int q = 0; q < 6; ++q) ea[i].f[q] = (const T*)h->f[q];
+    ea[i].ncell = h->ncell;
+    ea[i].scratch = h->d_red;
+    ea[i].hc = HistCtl{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
+  }
+  BCK(cudaMemcpy(b->d_sep_copy, sc.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "copy table");
+  BCK(cudaMemcpy(b->d_sep_j, sj.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "filter table");
+  BCK(cudaMemcpy(b->d_yee, ya.data(), sizeof(YeeArgs<T>) * n, cudaMemcpyHostToDevice), "yee table");
+  BCK(cudaMemcpy(b->d_energy, ea.data(), sizeof(EnergyArgs<T>) * n, cudaMemcpyHostToDevice), "energy table");
+  b->tables_dirty = false;
+  return PIC_OK;
+}
+
+template <typename T>
+int batch_step_once(pic_batch* b) {
+  cudaStream_t st = b->stream;
+  const int n = (int)b->runs.size();
+  pic_handle* h0 = b->runs[0];
+  const bool rec = b->diag_every > 0 && (h0->nstep + 1) % b->diag_every == 0;
+  const RunDev<T>* runs = (const RunDev<T>*)b->d_run[b->parity][rec ? 1 : 0];
+  BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_copy, b->d_sep_base, n, b->sep_total, 6, b->ndim, b->hz, b->hx,
+                          st),
+      "batched copy stencil");
+  for (auto& g : b->groups)
+    BCK(launch_push_batch<T>(runs, g.d_items, g.nitems, g.d_queue, b->ndim, b->scheme, g.lpc, g.blocks, st),
+        "batched push");
+  BCK(launch_migrate_batch<T>(runs, n, st), "batched migrate");
+  if (b->filter_j)
+    BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_j, b->d_sep_base, n, b->sep_total, 3, b->ndim, b->hzj, b->hxj,
+                            st),
+        "batched current filter");
+  BCK(launch_yee_batch<T>((const YeeArgs<T>*)b->d_yee, b->d_yee_base, n, b->yee_total, b->ndim, st), "batched yee");
+  if (rec) BCK(launch_field_energy_batch<T>((const EnergyArgs<T>*)b->d_energy, n, st), "batched energy");
+  for (pic_handle* h : b->runs) {
+    h->parity ^= 1;
+    h->nstep++;
+    if (rec) h->nhist++;
+  }
+  b->parity ^= 1;
+  b->nstep++;
+  return PIC_OK;
+}
+
+int batch_run_steps(pic_batch* b, int k) {
+  for (int s = 0; s < k; ++s) {
+    int rc = b->es == 4 ? batch_step_once<float>(b) : batch_step_once<double>(b);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int batch_graph_len(const pic_batch* b) {
+  const int de = b->diag_every > 0 ? b->diag_every : 1;
+  int len = 2;
+  while (len % de) len += 2;
+  return len;
+}
+
+int batch_build_graph(pic_batch* b) {
+  batch_drop_graph(b);
+  const int len = batch_graph_len(b);
+  const long long nstep0 = b->nstep;
+  const int parity0 = b->parity;
+  std::vector<long long> ns(b->runs.size()), nh(b->runs.size());
+  std::vector<int> pa(b->runs.size());
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    ns[i] = b->runs[i]->nstep;
+    nh[i] = b->runs[i]->nhist;
+    pa[i] = b->runs[i]->parity;
+  }
+  BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = batch_run_steps(b, len);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->nstep = nstep0;
+  b->parity = parity0;
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    b->runs[i]->nstep = ns[i];
+    b->runs[i]->nhist = nh[i];
+    b->runs[i]->parity = pa[i];
+  }
+  if (rc != PIC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != PIC_OK ? rc : bfail(b, PIC_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, PIC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->graph_len = len;
+  b->graph_parity = parity0;
+  b->graph_stream = b->stream;
+  return PIC_OK;
+}
+
+// Work items (run, tile) of every group, runs in creation order.
+int batch_items(pic_batch* b) {
+  for (auto& g : b->groups) {
+    std::vector<int2> items;
+    for (int i : g.members) {
+      pic_handle* h = b->runs[i];
+      const int nt = h->ntx * h->nty * h->ntz;
+      for (int t = 0; t < nt; ++t) items.push_back(make_int2(i, t));
+    }
+    g.nitems = (int)items.size();
+    if (!g.d_items) {
+      g.d_items = (int2*)balloc(b, sizeof(int2) * items.size());
+      g.d_queue = (int*)balloc(b, 16);
+      if (!g.d_items || !g.d_queue) return bfail(b, PIC_E_OOM, "work list allocation");
+    }
+    BCK(cudaMemcpy(g.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "work list");
+  }
+  return PIC_OK;
+}
+
+int batch_max_blocks(pic_batch* b, int lpc) {
+  return b->es == 4 ? push_max_blocks_per_sm<float>(b->ndim, b->scheme, lpc)
+                    : push_max_blocks_per_sm<double>(b->ndim, b->scheme, lpc);
+}
+
+int batch_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  return n > 0 ? n : 152;
+}
+
+// Back to the seeded initial state (fields, bins, counters, history), same as after pic_create.
+template <typename T>
+int reseed(pic_handle* h) {
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * h->es;
+  for (int q = 0; q < 9; ++q) CK(cudaMemsetAsync(h->f[q], 0, fb, st), "reseed fields");
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(h->cnt[s][k], 0, sizeof(int) * h->ncell, st), "reseed counts");
+  CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "reseed leavers");
+  CK(cudaMemsetAsync(h->d_hist_count, 0, 16, st), "reseed history");
+  CK(cudaMemsetAsync(h->d_kin, 0, 2 * sizeof(double), st), "reseed kinetic");
+  h->parity = 0;
+  h->nstep = 0;
+  h->nhist = 0;
+  drop_graph(h);
+  if (h->cfg.init_beam && h->cfg.ppc_per_species > 0) return init_beam<T>(h);
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
+  if (!cfgs || nruns < 1 || !out) return PIC_E_ARG;
+  *out = nullptr;
+  const pic_config& c0 = cfgs[0];
+  for (int i = 1; i < nruns; ++i) {
+    const pic_config& c = cfgs[i];
+    if (c.ndim != c0.ndim || c.precision != c0.precision || c.scheme != c0.scheme || c.shape_order != c0.shape_order ||
+        c.filter_nbin != c0.filter_nbin || c.filter_ncomp != c0.filter_ncomp ||
+        c.filter_comp_alpha != c0.filter_comp_alpha || c.filter_targets != c0.filter_targets ||
+        c.diag_every != c0.diag_every || (c.sigma_perp > 0) != (c0.sigma_perp > 0) ||
+        (c.track_ids != 0) != (c0.track_ids != 0))
+      return PIC_E_ARG;  // these must agree across the runs of one batch
+  }
+  pic_batch* b = new pic_batch();
+  b->es = c0.precision == PIC_FP32 ? 4 : 8;
+  b->ndim = c0.ndim;
+  b->scheme = c0.scheme;
+  b->diag_every = c0.diag_every;
+  b->filter_j = (c0.filter_targets & PIC_FILTER_J) != 0;
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return PIC_E_CUDA;
+  }
+  b->stream = b->own;
+  int rc = PIC_OK;
+  for (int i = 0; i < nruns && rc == PIC_OK; ++i) {
+    pic_handle* h = nullptr;
+    rc = pic_create(&cfgs[i], &h);
+    if (rc == PIC_OK) {
+      b->runs.push_back(h);
+      h->stream = b->stream;
+    }
+  }
+  if (rc != PIC_OK) {
+    pic_batch_destroy(b);
+    return rc;
+  }
+  pic_handle* h0 = b->runs[0];
+  b->hz = (int)(h0->zt_e.size() / 2);
+  b->hx = (int)(h0->xt_g.size() / 2);
+  b->hzj = (int)(h0->zt_j.size() / 2);
+  b->hxj = (int)(h0->xt_j.size() / 2);
+  std::vector<int> sep_base{0}, yee_base{0};
+  for (pic_handle* h : b->runs) {
+    const pic_config& c = h->cfg;
+    if (!sep_fast_ok(c.ndim, c.nx, c.ny, c.nz, b->hz, b->hx) ||
+        (b->filter_j && !sep_fast_ok(c.ndim, c.nx, c.ny, c.nz, b->hzj, b->hxj)) || c.nx < 3 || c.nz < 3 ||
+        (c.ndim == 3 && c.ny < 3)) {
+      pic_batch_destroy(b);
+      return PIC_E_ARG;  // grids too small for the batched stencil kernels
+    }
+    sep_base.push_back(sep_base.back() + sep_tiles(c.ndim, c.nx, c.ny, c.nz));
+    yee_base.push_back(yee_base.back() + yee_tiles(c.ndim, c.nx, c.ny, c.nz));
+  }
+  b->sep_total = sep_base.back();
+  b->yee_total = yee_base.back();
+  size_t rd = b->es == 4 ? sizeof(RunDev<float>) : sizeof(RunDev<double>);
+  size_t sa = b->es == 4 ? sizeof(SepArgs<float>) : sizeof(SepArgs<double>);
+  size_t ya = b->es == 4 ? sizeof(YeeArgs<float>) : sizeof(YeeArgs<double>);
+  size_t ea = b->es == 4 ? sizeof(EnergyArgs<float>) : sizeof(EnergyArgs<double>);
+  bool ok = true;
+  for (int p = 0; p < 2 && ok; ++p)
+    for (int r = 0; r < 2 && ok; ++r) ok = (b->d_run[p][r] = balloc(b, rd * nruns)) != nullptr;
+  if (ok) ok = (b->d_sep_copy = balloc(b, sa * nruns)) && (b->d_sep_j = balloc(b, sa * nruns)) &&
+               (b->d_yee = balloc(b, ya * nruns)) && (b->d_energy = balloc(b, ea * nruns)) &&
+               (b->d_sep_base = (int*)balloc(b, sizeof(int) * (nruns + 1))) &&
+               (b->d_yee_base = (int*)balloc(b, sizeof(int) * (nruns + 1)));
+  if (!ok) {
+    pic_batch_destroy(b);
+    return PIC_E_OOM;
+  }
+  cudaMemcpy(b->d_sep_base, sep_base.data(), sizeof(int) * (nruns + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_yee_base, yee_base.data(), sizeof(int) * (nruns + 1), cudaMemcpyHostToDevice);
+  // push groups by the default lanes per cell; two resident blocks per SM where they fit
+  const int sms = batch_sm_count();
+  for (int i = 0; i < nruns; ++i) {
+    const int lpc = push_lanes_per_cell(b->ndim, 2 * b->runs[i]->cfg.ppc_per_species);
+    pic_batch::Group* g = nullptr;
+    for (auto& gg : b->groups)
+      if (gg.lpc == lpc) g = &gg;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->lpc = lpc;
+      const int mb = batch_max_blocks(b, lpc);
+      g->blocks = sms * (mb < 2 ? mb : 2);
+    }
+    g->members.push_back(i);
+  }
+  rc = batch_items(b);
+  if (rc == PIC_OK) rc = b->es == 4 ? batch_tables<float>(b) : batch_tables<double>(b);
+  if (rc == PIC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = PIC_E_CUDA;
+  if (rc != PIC_OK) {
+    pic_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return PIC_OK;
+}
+
+pic_handle* pic_batch_run(pic_batch* b, int run) {
+  if (!b || run < 0 || run >= (int)b->runs.size()) return nullptr;
+  return b->runs[run];
+}
+
+int pic_batch_size(const pic_batch* b) { return b ? (int)b->runs.size() : 0; }
+
+int pic_batch_set_correction_stencil(pic_batch* b, int run, const double psi_e[5], const double psi_b[5]) {
+  if (!b || run < 0 || run >= (int)b->runs.size()) return PIC_E_ARG;
+  int rc = pic_set_correction_stencil(b->runs[run], psi_e, psi_b);
+  if (rc) return bfail(b, rc, pic_last_error(b->runs[run]));
+  if ((int)(b->runs[run]->zt_e.size() / 2) != b->hz) return bfail(b, PIC_E_STATE, "stencil length changed");
+  b->tables_dirty = true;
+  batch_drop_graph(b);
+  return PIC_OK;
+}
+
+int pic_batch_set_stream(pic_batch* b, void* stream) {
+  if (!b) return PIC_E_ARG;
+  b->stream = stream ? (cudaStream_t)stream : b->own;
+  for (pic_handle* h : b->runs) h->stream = b->stream;
+  batch_drop_graph(b);
+  return PIC_OK;
+}
+
+int pic_batch_step(pic_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return PIC_E_ARG;
+  for (pic_handle* h : b->runs)
+    if (h->parity != b->parity) return bfail(b, PIC_E_STATE, "a run was stepped or reset on its own");
+  if (b->tables_dirty) {
+    int rc = b->es == 4 ? batch_tables<float>(b) : batch_tables<double>(b);
+    if (rc) return rc;
+  }
+  const int len = batch_graph_len(b);
+  if (len > 64 || nsteps < 2 * len) return batch_run_steps(b, nsteps);
+  int lead = (int)((len - b->nstep % len) % len);
+  int rc = batch_run_steps(b, lead);
+  if (rc) return rc;
+  nsteps -= lead;
+  if (!b->graph || b->graph_len != len || b->graph_stream != b->stream || b->graph_parity != b->parity) {
+    rc = batch_run_steps(b, len);  // warm the kernel attributes before capturing
+    if (rc) return rc;
+    nsteps -= len;
+    rc = batch_build_graph(b);
+    if (rc) return rc;
+  }
+  while (nsteps >= len) {
+    BCK(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+    for (pic_handle* h : b->runs) {
+      h->nstep += len;
+      if (b->diag_every > 0) h->nhist += len / b->diag_every;
+    }
+    b->nstep += len;
+    nsteps -= len;
+  }
+  return batch_run_steps(b, nsteps);
+}
+
+int pic_batch_sync(pic_batch* b) {
+  if (!b) return PIC_E_ARG;
+  BCK(cudaStreamSynchronize(b->stream), "synchronize");
+  for (pic_handle* h : b->runs) {
+    int rc = check_err(h);
+    if (rc) return bfail(b, rc, pic_last_error(h));
+  }
+  return PIC_OK;
+}
+
+int pic_batch_energy_history(pic_batch* b, int run, pic_energy_t* out, int max, int* count) {
+  if (!b || run < 0 || run >= (int)b->runs.size()) return PIC_E_ARG;
+  return pic_energy_history(b->runs[run], out, max, count);
+}
+
+int pic_batch_autotune(pic_batch* b, int trial_steps, int* lpc_out) {
+  if (!b || trial_steps < 1) return PIC_E_ARG;
+  if (b->tables_dirty) {
+    int rc = b->es == 4 ? batch_tables<float>(b) : batch_tables<double>(b);
+    if (rc) return rc;
+  }
+  const int sms = batch_sm_count();
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0), "event");
+  BCK(cudaEventCreate(&e1), "event");
+  int rc = PIC_OK;
+  for (size_t gi = 0; gi < b->groups.size() && rc == PIC_OK; ++gi) {
+    auto& g = b->groups[gi];
+    float best = 1e30f;
+    int best_lpc = g.lpc, best_blocks = g.blocks;
+    for (int lpc : {4, 8, 16}) {
+      const int mb = batch_max_blocks(b, lpc);
+      for (int bps = 1; bps <= mb && bps <= 2 && rc == PIC_OK; ++bps) {
+        g.lpc = lpc;
+        g.blocks = sms * bps;
+        rc = batch_run_steps(b, 2);  // warm-up of this variant
+        if (rc) break;
+        cudaEventRecord(e0, b->stream);
+        rc = batch_run_steps(b, 2 * trial_steps);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = PIC_E_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == PIC_OK && ms < best) {
+          best = ms;
+          best_lpc = lpc;
+          best_blocks = g.blocks;
+        }
+      }
+    }
+    g.lpc = best_lpc;
+    g.blocks = best_blocks;
+    if (lpc_out) lpc_out[gi] = best_lpc;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  // the trials advanced the runs: back to the seeded initial state
+  for (pic_handle* h : b->runs) {
+    rc = b->es == 4 ? reseed<float>(h) : reseed<double>(h);
+    if (rc) return bfail(b, rc, pic_last_error(h));
+  }
+  b->parity = 0;
+  b->nstep = 0;
+  batch_drop_graph(b);
+  return pic_batch_sync(b);
+}
+
+void pic_batch_destroy(pic_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (pic_handle* h : b->runs) {
+    h->stream = h->own;
+    pic_destroy(h);
+  }
+  for (void* p : b->allocs)
+    if (p) cudaFree(p);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+}
+
+const char* pic_batch_last_error(const pic_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

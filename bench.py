@@ -379,6 +379,99 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------------
+# batched sweep (64 independent 2D runs; not the default workload)
+# ------------------------------------------------------------------------------------------------
+def sweep_configs(P, nruns=64, seed=4):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nruns):
+        nx = int(rng.choice([64, 128, 256]))
+        nz = int(rng.choice([128, 256, 512, 1024]))
+        ppc = int(rng.choice([4, 8, 16]))
+        alpha = float(rng.uniform(0.1, 0.7))
+        gamma = float(rng.choice([10.0, 50.0, 130.0]))
+        corr = bool(rng.integers(0, 2))
+        c = P.pic_config_default(nx=nx, nz=nz, dt=alpha, gamma=gamma, scheme=P.PIC_GALERKIN, precision=P.PIC_FP32,
+                                 ppc_per_species=ppc, seed=100 + i, init_beam=1, diag_every=10, **FILTER)
+        out.append((c, corr))
+    return out
+
+
+def run_sweep(args):
+    import numpy as np
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    runs = sweep_configs(P, args.sweep_runs)
+    cfgs = [c for c, _ in runs]
+    particles = sum(c.nx * c.nz * c.ppc_per_species * 2 for c in cfgs)
+    b = P.pic_batch_create(cfgs)
+    P.pic_batch_set_stream(b, stream.cuda_stream)
+    for i, (c, corr) in enumerate(runs):
+        if corr:
+            P.pic_batch_set_correction_stencil(b, i, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, c.dt))
+    lpcs = P.pic_batch_autotune(b, trial_steps=2)
+    P.pic_batch_step(b, 10)  # warm-up (includes the graph capture)
+    P.pic_batch_sync(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P.pic_batch_step(b, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    P.pic_batch_sync(b)
+    rates = []
+    for i, c in enumerate(cfgs):
+        w = [e["w_perp"] for e in P.pic_batch_energy_history(b, i)]
+        t = np.arange(1, len(w) + 1) * 10 * c.dt
+        try:
+            rates.append(P.pic_fit_growth_rate(t, w)[0])
+        except P.PicError:
+            rates.append(float("nan"))
+    P.pic_batch_destroy(b)
+    # the same runs one after another, each with plain per-step launches
+    seq_steps = max(2, min(args.steps, args.sweep_seq_steps))
+    handles = []
+    for c, corr in runs:
+        h = P.pic_create(c)
+        P.pic_set_stream(h, stream.cuda_stream)
+        if corr:
+            P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, c.dt))
+        P.pic_step(h, 1)
+        handles.append(h)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for h in handles:
+        for _ in range(seq_steps):
+            P.pic_step(h, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    for h in handles:
+        P.pic_destroy(h)
+    vb = particles * args.steps / (ms_b / 1e3)
+    vs = particles * seq_steps / (ms_s / 1e3)
+    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 10,
+            "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched sweep: {len(runs)} independent 2D runs, grids 64-256 x 128-1024 "
+                                   "(seeded mix), 4-16 particles/cell/species, c dt/dz U[0.1,0.7), gamma in "
+                                   "{10,50,130}, correction on/off, FP32, one persistent push launch per "
+                                   "lanes-per-cell group per step, CUDA graph", "runs": len(runs),
+                       "particles": particles},
+            "sequential": {"value": vs, "unit": UNIT, "steps": seq_steps, "ms_per_step": ms_s / seq_steps,
+                           "how": "each run alone, pic_step(1) per step (plain launches), runs one after another"},
+            "speedup_vs_sequential": vb / vs, "autotune_lanes_per_cell": lpcs,
+            "growth_rates": {"min": float(np.nanmin(rates)), "median": float(np.nanmedian(rates)),
+                             "max": float(np.nanmax(rates))}}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,6 +483,9 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")
+    ap.add_argument("--sweep-runs", type=int, default=64)
+    ap.add_argument("--sweep-seq-steps", type=int, default=40)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args(argv)
@@ -397,6 +493,8 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -99,3 +99,22 @@ def test_create_validates_before_touching_the_gpu():
 
 def test_destroy_null_is_noop():
     P.lib().pic_destroy(None)
+
+
+def test_breakdown_windows_agree_with_oracle():
+    # The (4,4) interpolation of the Galerkin multiplier (Yee solver) has a pole inside [0, 1] in
+    # narrow alpha windows (the counterpart of the window Sec. 3 excises for its CK setting). The
+    # library and the oracle, with different solvers, must refuse exactly the same alphas.
+    alphas = np.linspace(0.60, 0.706, 213)
+    lib_bad, orc_bad = [], []
+    for a in alphas:
+        try:
+            P.pic_compute_correction_coeffs(0, a)
+        except P.PicError as e:
+            assert e.code == P.PIC_E_SINGULAR
+            lib_bad.append(a)
+        if O.rational_coeffs(0, a)[0] != 0:
+            orc_bad.append(a)
+    assert lib_bad == orc_bad
+    assert 5 <= len(lib_bad) < 40
+    assert min(lib_bad) > 0.64 and max(lib_bad) < 0.70

@@ -262,7 +262,8 @@ const char* pic_batch_last_error(const pic_batch* b);
 /* Frees everything the handle owns. NULL is a no-op. */
 void pic_destroy(pic_handle* h);
 
-/* Text of the last error on this handle (never NULL). */
+/* Text of the last error on this handle (never NULL); with h = NULL, the reason the calling
+ * thread's last pic_create failed. */
 const char* pic_last_error(const pic_handle* h);
 
 /* Static text for a PIC_E_* code. */

@@ -167,7 +167,9 @@ def pic_compute_correction_coeffs(scheme: int, alpha: float):
 
 def pic_create(cfg: pic_config):
     h = ctypes.c_void_p()
-    _check(lib().pic_create(ctypes.byref(cfg), ctypes.byref(h)))
+    rc = lib().pic_create(ctypes.byref(cfg), ctypes.byref(h))
+    if rc != PIC_OK:
+        raise PicError(rc, f"{lib().pic_strerror(rc).decode()}: {lib().pic_last_error(None).decode()}")
     return h
 
 

@@ -76,6 +76,7 @@ struct pic_handle {
 };
 
 static void drop_graph(pic_handle* h);
+static thread_local std::string g_create_err;  // why the last pic_create / pic_batch_create failed
 
 namespace {
 
@@ -124,6 +125,7 @@ cudaError_t collect_times(pic_handle* h) {
 // Launch one kernel of class `cls`, counted, and bracketed by events when timing is on.
 template <class F>
 cudaError_t launch(pic_handle* h, int cls, F&& go) {
+  (void)cudaGetLastError();  // a failed earlier query must not be reported as this launch's error
   h->launches++;
   h->tcount[cls]++;
   if (!h->timing) return go();
@@ -622,8 +624,10 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   const int align = (int)(64 / h->es);  // bins start on 64-byte boundaries
   cap = (cap + align - 1) / align * align;
   h->cap = cap;
+  (void)cudaGetLastError();
   cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    g_create_err = std::string("stream creation: ") + cudaGetErrorString(e);
     delete h;
     return PIC_E_CUDA;
   }
@@ -667,6 +671,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   if (ok) ok = (h->d_kin = (double*)dalloc(h, 2 * sizeof(double))) != nullptr;
   if (ok) ok = cudaMemset(h->d_hist_count, 0, 16) == cudaSuccess && cudaMemset(h->d_kin, 0, 2 * sizeof(double)) == cudaSuccess;
   if (!ok) {
+    g_create_err = "device allocation failed";
     pic_destroy(h);
     return PIC_E_OOM;
   }
@@ -681,6 +686,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
     rc = c.precision == PIC_FP32 ? init_beam<float>(h) : init_beam<double>(h);
   if (rc == PIC_OK) rc = check_err(h);
   if (rc != PIC_OK) {
+    g_create_err = h->err;
     pic_destroy(h);
     return rc;
   }
@@ -934,7 +940,7 @@ void pic_destroy(pic_handle* h) {
 }
 
 const char* pic_last_error(const pic_handle* h) {
-  if (!h) return "null handle";
+  if (!h) return g_create_err.c_str();  // no handle: the reason the last create failed
   return h->err.c_str();
 }
 

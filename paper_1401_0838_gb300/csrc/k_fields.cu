@@ -43,8 +43,18 @@ __device__ __forceinline__ void cp_async_wait_all_fields() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Periodic index of g in [-n, 2n): one compare instead of a modulo (falls back for tiny grids).
-__device__ __forceinline__ int wrap_near(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
+// Periodic index of any g: one compare and add in the common case g in [-n, 2n); a modulo only when
+// a tile and its halo are wider than the grid (tiles are staged whole, even past the grid's end).
+__device__ __forceinline__ int wrap_near(int g, int n) {
+  if (g < 0) {
+    g += n;
+    if (g < 0) g = wrapi(g, n);
+  } else if (g >= n) {
+    g -= n;
+    if (g >= n) g %= n;
+  }
+  return g;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int CY, int CZ, int ntx, int nty) {
@@ -60,18 +70,16 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int C
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const int LX = CX + 2 * hx, LY = CY + 2 * hy, LZ = CZ + 2 * hz;
   const long long nxy = (long long)a.nx * a.ny;
-  const bool near = a.nx >= hx && a.nz >= hz && (a.ndim == 2 || a.ny >= hy);  // halos within one period
 
   // rows of LX consecutive x, one (ly, lz) pair per row
   for (int row = threadIdx.x / 32; row < LY * LZ; row += SEP_THREADS / 32) {
     const int ly = row % LY, lz = row / LY;
-    const int gy = a.ndim == 3 ? (near ? wrap_near(Y0 - hy + ly, a.ny) : wrapi(Y0 - hy + ly, a.ny)) : 0;
-    const int gz = near ? wrap_near(Z0 - hz + lz, a.nz) : wrapi(Z0 - hz + lz, a.nz);
+    const int gy = a.ndim == 3 ? wrap_near(Y0 - hy + ly, a.ny) : 0;
+    const int gz = wrap_near(Z0 - hz + lz, a.nz);
     const T* srow = src + gz * nxy + (long long)gy * a.nx;
     T* drow = s0 + row * LX;
     for (int lx = threadIdx.x & 31; lx < LX; lx += 32) {
-      const int gx = near ? wrap_near(X0 - hx + lx, a.nx) : wrapi(X0 - hx + lx, a.nx);
-      cp_async_el(drow + lx, srow + gx);
+      cp_async_el(drow + lx, srow + wrap_near(X0 - hx + lx, a.nx));
     }
   }
   cp_async_wait_all_fields();

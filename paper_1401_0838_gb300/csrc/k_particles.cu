@@ -237,7 +237,7 @@ struct DepLayout<3> {
   }
 };
 
-// Periodic index of g in [-n, 2n) without a modulo.
+// Periodic index of g in [-n, 2n) without a modulo (callers guarantee the range: near_ok).
 __device__ __forceinline__ int wrap_near_p(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
 // Vector loads of 4 consecutive slots (16-byte aligned: bins start on 64-byte boundaries and

@@ -259,6 +259,39 @@ int pic_batch_autotune(pic_batch* b, int trial_steps, int* lpc_out);
 void pic_batch_destroy(pic_batch* b);
 const char* pic_batch_last_error(const pic_batch* b);
 
+/*
+ * Adjoint (reverse mode) of the 2D step: the gradient of the final transverse field energy
+ * W_perp(T) = 1/2 sum (Ex^2 + Ey^2 + Bx^2 + By^2) dV (the quantity whose growth Sec. 4 measures)
+ * with respect to the Psi_E / Psi_B polynomial coefficients a_0..a_4 (Sec. 2) and the initial E,
+ * B, from hand-written transposes of every pass of the step: the gather copies Psi(D_z) and the
+ * filter (Sec. 2 last paragraph, Sec. 3 Eq. 6), the gather with the Galerkin or Uniform shapes
+ * (Sec. 2, Eq. 3-4), the Boris push, the move, the Esirkepov deposition and the Yee update.
+ * Derivatives are exact almost everywhere (the linear shapes have kinks).
+ *
+ * pic_adjoint_forward advances the run nsteps from its current state (as pic_step would) and
+ * returns W_perp(T) in *w_perp. On the way it stores the full state (fields, particles by id)
+ * every checkpoint_every steps and at the end, in device memory the handle keeps until
+ * pic_adjoint_release or pic_destroy: (nsteps / checkpoint_every + 2 + checkpoint_every) states of
+ * about N x (8 + 5 x element size) bytes for N particles, plus 6 field arrays each.
+ * 2D runs only (PIC_E_ARG otherwise), and cfg.track_ids = 1 with ids 0 .. N-1, as the seeded beam
+ * and any import without explicit ids have (PIC_E_STATE otherwise).
+ *
+ * pic_adjoint_backward, with the state still the final state of the recorded run (no step, state
+ * or correction change in between; PIC_E_STATE otherwise), writes for L = dw x W_perp(T):
+ * dL/da_n of Psi_E and Psi_B into grad_psi_e[5] / grad_psi_b[5] (host; either may be NULL), and
+ * dL/dE^0, dL/dB^0 into grad_fields[6] (device arrays of the handle's precision and layout, order
+ * Ex Ey Ez Bx By Bz; NULL or NULL entries skip them). Each segment between checkpoints is
+ * recomputed once, so the call costs about one more forward run plus the transposed passes. It
+ * leaves the state at the recorded final state again (the order of the particles inside a cell may
+ * differ) and synchronises the stream. The particle adjoints are carried in the handle's
+ * precision.
+ */
+int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double* w_perp);
+int pic_adjoint_backward(pic_handle* h, double dw, double grad_psi_e[5], double grad_psi_b[5],
+                         void* const grad_fields[6]);
+/* Frees the adjoint's checkpoint and work storage (no-op when there is none; NULL is a no-op). */
+void pic_adjoint_release(pic_handle* h);
+
 /* Frees everything the handle owns. NULL is a no-op. */
 void pic_destroy(pic_handle* h);
 

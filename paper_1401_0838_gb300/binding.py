@@ -30,7 +30,8 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_enable_timing", "pic_kernel_times", "pic_launch_count", "pic_field_energy_noalloc",
            "pic_batch_create", "pic_batch_size", "pic_batch_run", "pic_batch_set_correction_stencil",
            "pic_batch_set_stream", "pic_batch_step", "pic_batch_sync", "pic_batch_energy_history",
-           "pic_batch_autotune", "pic_batch_destroy", "pic_batch_last_error")
+           "pic_batch_autotune", "pic_batch_destroy", "pic_batch_last_error", "pic_adjoint_forward",
+           "pic_adjoint_backward", "pic_adjoint_release")
 PIC_NKERNEL = 7
 KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
 
@@ -116,11 +117,15 @@ def lib() -> ctypes.CDLL:
         L.pic_batch_destroy.restype = None
         L.pic_batch_last_error.argtypes = [V]
         L.pic_batch_last_error.restype = ctypes.c_char_p
+        L.pic_adjoint_forward.argtypes = [V, I, I, DP]
+        L.pic_adjoint_backward.argtypes = [V, D, DP, DP, P(V)]
+        L.pic_adjoint_release.argtypes = [V]
+        L.pic_adjoint_release.restype = None
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("pic_config_default", "pic_destroy", "pic_last_error", "pic_strerror", "pic_batch_run",
-                            "pic_batch_destroy", "pic_batch_last_error"):
+                            "pic_batch_destroy", "pic_batch_last_error", "pic_adjoint_release"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -291,6 +296,32 @@ def pic_field_energy_noalloc(fields, ncell: int, precision: int, dv: float, stre
     out = (ctypes.c_double * 3)()
     _check(lib().pic_field_energy_noalloc(arr, int(ncell), int(precision), float(dv), out, stream_ptr))
     return out[0], out[1], out[2]
+
+
+# ------------------------------------------------------------------------------------------------
+# adjoint
+# ------------------------------------------------------------------------------------------------
+def pic_adjoint_forward(h, nsteps: int, checkpoint_every: int = 10) -> float:
+    """Runs nsteps recording checkpoints; returns W_perp after them."""
+    w = ctypes.c_double()
+    _check(lib().pic_adjoint_forward(h, int(nsteps), int(checkpoint_every), ctypes.byref(w)), h)
+    return w.value
+
+
+def pic_adjoint_backward(h, dw: float = 1.0, grad_fields=None):
+    """Gradient of dw * W_perp(T): returns (dPsi_E coefficients, dPsi_B coefficients) as numpy arrays
+    and writes dE0, dB0 into grad_fields (six device tensors or addresses; None skips)."""
+    ge = (ctypes.c_double * 5)()
+    gb = (ctypes.c_double * 5)()
+    gf = None
+    if grad_fields is not None:
+        gf = (ctypes.c_void_p * 6)(*[f if isinstance(f, int) or f is None else _ptr(f) for f in grad_fields])
+    _check(lib().pic_adjoint_backward(h, float(dw), ge, gb, gf), h)
+    return np.array(ge[:]), np.array(gb[:])
+
+
+def pic_adjoint_release(h):
+    lib().pic_adjoint_release(h)
 
 
 # ------------------------------------------------------------------------------------------------

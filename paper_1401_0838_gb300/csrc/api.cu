@@ -1,6 +1,7 @@
-// C ABI (include/pic.h): handle management, the per-step launch sequence, state import/export
-// and diagnostics. All arithmetic of the step runs in the CUDA kernels of k_fields.cu and
-// k_particles.cu; this file only allocates, marshals and orders launches on one stream.
+// C ABI (include/pic.h): handle management, the per-step launch sequence, state import/export,
+// diagnostics, batched runs and the adjoint's checkpoint / recompute schedule. All arithmetic of
+// the step and of its adjoint runs in the CUDA kernels of k_fields.cu, k_particles.cu and
+// k_adjoint.cu; this file only allocates, marshals and orders launches on one stream.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -72,6 +73,30 @@ struct pic_handle {
   double tms[PIC_NKERNEL] = {};
   long long tcount[PIC_NKERNEL] = {};
   long long launches = 0;
+  // adjoint: checkpoints of the forward run, the recomputed segment's tape, adjoint work arrays
+  struct Flat {
+    void* a[9] = {};  // cell, species, ox, oy, oz, dux, duy, duz, w (id order)
+  };
+  struct Adj {
+    bool ready = false;  // a forward run was recorded and the state has not changed since
+    int nsteps = 0, every = 0, nseg = 0;
+    long long np = 0, final_step = 0, final_hist = 0;
+    int cap_ck = 0, cap_tape = 0;
+    long long cap_np = 0;
+    std::vector<void*> ck_f;    // (nseg + 1) x 6 fields at the checkpoints (the last: final state)
+    std::vector<Flat> ck_p;     // nseg + 1 particle states
+    std::vector<void*> tape_f;  // every x 6: fields at the start of each step of a segment
+    std::vector<Flat> tape_p;   // every: particles at the start of each step of a segment
+    void* lam[6] = {};          // adjoint of E, B
+    void* lj[3] = {};           // adjoint of J
+    void* lg[6] = {};           // adjoint of the gather copies
+    void* y[6] = {};            // filtered lg
+    void* lp[5] = {};           // particle adjoints: ox, oz, ux, uy, uz (id order)
+    double* dots = nullptr;     // 10 coefficient-gradient accumulators
+    unsigned long long* seen = nullptr;
+    std::vector<void*> mem;
+  } adj;
+  bool no_diag = false;  // the adjoint's recomputed steps record no diagnostics
   std::string err;
 };
 
@@ -323,7 +348,7 @@ template <typename T>
 int step_once(pic_handle* h) {
   cudaStream_t st = h->stream;
   const size_t fb = (size_t)h->ncell * sizeof(T);
-  const bool rec = h->cfg.diag_every > 0 && (h->nstep + 1) % h->cfg.diag_every == 0;
+  const bool rec = !h->no_diag && h->cfg.diag_every > 0 && (h->nstep + 1) % h->cfg.diag_every == 0;
   (void)fb;
   // 1. field copies seen by the particles: Psi(D_z) and the gather filter; zeroes J
   SepArgs<T> ca = sep_args<T>(h, true);
@@ -366,6 +391,7 @@ int check_err(pic_handle* h) {
   if (e & ERR_NONFINITE) return fail(h, PIC_E_NONFINITE, "a particle became non-finite or moved more than a cell");
   if (e & ERR_IMPORT) return fail(h, PIC_E_ARG, "imported particle with invalid cell or species");
   if (e & ERR_TIMEOUT) return fail(h, PIC_E_TIMEOUT, "a bounded device wait gave up");
+  if (e & ERR_IDS) return fail(h, PIC_E_STATE, "particle ids are not a permutation of 0 .. N-1");
   return fail(h, PIC_E_CUDA, "unknown device error flag");
 }
 
@@ -710,6 +736,7 @@ int pic_set_correction_stencil(pic_handle* h, const double psi_e[5], const doubl
   }
   rebuild_taps(h);
   drop_graph(h);
+  h->adj.ready = false;
   return PIC_OK;
 }
 
@@ -835,6 +862,7 @@ int pic_get_state(pic_handle* h, pic_state* s) {
 
 int pic_set_state(pic_handle* h, const pic_state* s) {
   if (!h || !s || (s->where != PIC_HOST && s->where != PIC_DEVICE)) return PIC_E_ARG;
+  h->adj.ready = false;
   return h->es == 4 ? set_state_t<float>(h, s) : set_state_t<double>(h, s);
 }
 
@@ -929,6 +957,8 @@ void pic_destroy(pic_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
   for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  for (void* p : h->adj.mem)
     if (p) cudaFree(p);
   for (auto& p : h->pending) {
     cudaEventDestroy(p.a);
@@ -1440,5 +1470,376 @@ void pic_batch_destroy(pic_batch* b) {
 }
 
 const char* pic_batch_last_error(const pic_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"
+
+// ================================================================================================
+// Adjoint of the 2D step with checkpoint and recompute. The forward run stores the full state
+// (fields, particles in id order) every `every` steps. The backward pass walks the segments from
+// the last: it restores the segment's checkpoint, recomputes the segment with the ordinary step
+// while taping the state at the start of each step, then applies the transposed passes of each
+// step in reverse (k_adjoint.cu), carrying the adjoints of E, B and of every particle's position
+// and momentum from step to step.
+// ================================================================================================
+namespace {
+
+void* adj_malloc(pic_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  h->adj.mem.push_back(p);
+  return p;
+}
+
+void adj_release(pic_handle* h) {
+  auto& A = h->adj;
+  cudaStreamSynchronize(h->stream);
+  for (void* p : A.mem)
+    if (p) cudaFree(p);
+  A = pic_handle::Adj();
+}
+
+int adj_flat(pic_handle* h, pic_handle::Flat& f, long long np) {
+  const size_t n = (size_t)np;
+  const size_t sz[9] = {4, 4, h->es, 0, h->es, h->es, h->es, h->es, h->has_w ? h->es : 0};
+  for (int q = 0; q < 9; ++q) {
+    if (!sz[q]) continue;
+    f.a[q] = adj_malloc(h, sz[q] * n);
+    if (!f.a[q]) return PIC_E_OOM;
+    if (cudaMemset(f.a[q], 0, sz[q] * n) != cudaSuccess) return PIC_E_CUDA;  // valid cells until written
+  }
+  return PIC_OK;
+}
+
+// Storage for nck checkpoints, ntape taped steps and np particles (kept when large enough).
+int adj_reserve(pic_handle* h, int nck, int ntape, long long np) {
+  auto& A = h->adj;
+  if (A.cap_ck >= nck && A.cap_tape >= ntape && A.cap_np >= np && A.dots) return PIC_OK;
+  adj_release(h);
+  const size_t fb = (size_t)h->ncell * h->es;
+  A.ck_f.assign((size_t)nck * 6, nullptr);
+  A.ck_p.assign(nck, pic_handle::Flat());
+  A.tape_f.assign((size_t)ntape * 6, nullptr);
+  A.tape_p.assign(ntape, pic_handle::Flat());
+  bool ok = true;
+  for (auto& p : A.ck_f) ok = ok && (p = adj_malloc(h, fb)) != nullptr;
+  for (auto& p : A.tape_f) ok = ok && (p = adj_malloc(h, fb)) != nullptr;
+  for (auto& f : A.ck_p) ok = ok && adj_flat(h, f, np) == PIC_OK;
+  for (auto& f : A.tape_p) ok = ok && adj_flat(h, f, np) == PIC_OK;
+  for (int q = 0; q < 6; ++q) ok = ok && (A.lam[q] = adj_malloc(h, fb)) && (A.lg[q] = adj_malloc(h, fb)) &&
+                                   (A.y[q] = adj_malloc(h, fb));
+  for (int q = 0; q < 3; ++q) ok = ok && (A.lj[q] = adj_malloc(h, fb));
+  for (int q = 0; q < 5; ++q) ok = ok && (A.lp[q] = adj_malloc(h, h->es * (size_t)np));
+  ok = ok && (A.dots = (double*)adj_malloc(h, 16 * sizeof(double)));
+  ok = ok && (A.seen = (unsigned long long*)adj_malloc(h, 8 * (size_t)(np / 64 + 1)));
+  if (!ok) {
+    adj_release(h);
+    return fail(h, PIC_E_OOM, "adjoint storage allocation failed");
+  }
+  A.cap_ck = nck;
+  A.cap_tape = ntape;
+  A.cap_np = np;
+  return PIC_OK;
+}
+
+template <typename T>
+FlatDev<T> flat_view(const pic_handle::Flat& f, long long np) {
+  FlatDev<T> v;
+  v.np = np;
+  v.cell = (int*)f.a[0];
+  v.species = (int*)f.a[1];
+  v.ox = (T*)f.a[2];
+  v.oy = nullptr;
+  v.oz = (T*)f.a[4];
+  v.dux = (T*)f.a[5];
+  v.duy = (T*)f.a[6];
+  v.duz = (T*)f.a[7];
+  v.w = (T*)f.a[8];
+  v.id = nullptr;  // the flat index is the id
+  return v;
+}
+
+// Fields and particles of the current state into (fields[6], flat) in id order.
+template <typename T>
+int adj_save(pic_handle* h, void* const* fields, const pic_handle::Flat& flat, bool check_ids) {
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  for (int q = 0; q < 6; ++q)
+    if (fields) CK(cudaMemcpyAsync(fields[q], h->f[q], fb, cudaMemcpyDeviceToDevice, st), "save fields");
+  unsigned long long* seen = nullptr;
+  if (check_ids) {
+    seen = h->adj.seen;
+    CK(cudaMemsetAsync(seen, 0, 8 * (size_t)(h->adj.np / 64 + 1), st), "clear id bitmap");
+  }
+  RunDev<T> r = make_run<T>(h, h->parity);
+  FlatDev<T> f = flat_view<T>(flat, h->adj.np);
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_tape<T>(r, f, seen, st); }), "tape");
+  return PIC_OK;
+}
+
+// Back to checkpoint j: fields copied in, particles re-binned from the id-ordered arrays.
+template <typename T>
+int adj_restore(pic_handle* h, int j) {
+  auto& A = h->adj;
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  drop_graph(h);
+  for (int q = 0; q < 6; ++q)
+    CK(cudaMemcpyAsync(h->f[q], A.ck_f[(size_t)j * 6 + q], fb, cudaMemcpyDeviceToDevice, st), "restore fields");
+  for (int sp = 0; sp < 2; ++sp)
+    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
+  CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "clear leaver counters");
+  h->parity = 0;
+  RunDev<T> r = make_run<T>(h, 0);
+  FlatDev<T> f = flat_view<T>(A.ck_p[j], A.np);
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_import<T>(r, f, st); }), "restore particles");
+  return PIC_OK;
+}
+
+template <typename T>
+void put_taps(T* dst, const double* src, int n, double scale = 1.0) {
+  for (int i = 0; i < n; ++i) dst[i] = (T)(src[i] * scale);
+}
+
+// Transposed passes of one step, in reverse order, for taped step s of the current segment.
+template <typename T>
+int adj_step(pic_handle* h, int s) {
+  auto& A = h->adj;
+  const pic_config& c = h->cfg;
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  T* lam[6];
+  T* lj[3];
+  for (int q = 0; q < 6; ++q) lam[q] = (T*)A.lam[q];
+  for (int q = 0; q < 3; ++q) lj[q] = (T*)A.lj[q];
+  // Yee^T. Forward: B' = B - dt/2 C_E E; E' = E + dt C_B B' - dt J~; B'' = B' - dt/2 C_E E', and
+  // C_E^T = C_B on the periodic Yee mesh. Reverse: lE -= dt/2 C_B lB; lJ~ = -dt lE;
+  // lB += dt C_E lE; lE -= dt/2 C_B lB.
+  YeeArgs<T> ya;
+  ya.ex = lam[0];
+  ya.ey = lam[1];
+  ya.ez = lam[2];
+  ya.bx = lam[3];
+  ya.by = lam[4];
+  ya.bz = lam[5];
+  ya.jx = lj[0];
+  ya.jy = lj[1];
+  ya.jz = lj[2];
+  ya.nx = c.nx;
+  ya.ny = c.ny;
+  ya.nz = c.nz;
+  ya.h = T(0);
+  auto coef = [&](double hs) {
+    ya.cx = (T)(hs / c.dx);
+    ya.cy = (T)(hs / c.dy);
+    ya.cz = (T)(hs / c.dz);
+  };
+  coef(-0.5 * c.dt);
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_e<T>(ya, st); }), "adjoint yee (e half)");
+  // lJ = F_J^T lJ~ = -dt F_J lE (symmetric filter taps, scaled by -dt)
+  SepArgs<T> ja = sep_args<T>(h, false);
+  for (int q = 0; q < 3; ++q) {
+    ja.src[q] = lam[q];
+    ja.dst[q] = lj[q];
+  }
+  put_taps(ja.zt[0], h->zt_j.data(), (int)h->zt_j.size(), -c.dt);
+  put_taps(ja.zt[1], h->zt_j.data(), (int)h->zt_j.size(), -c.dt);
+  CK(launch(h, PIC_K_FILTER, [&] { return launch_sep<T>(ja, st); }), "adjoint current filter");
+  coef(-c.dt);
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_b<T>(ya, st); }), "adjoint yee (b)");
+  coef(-0.5 * c.dt);
+  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_e<T>(ya, st); }), "adjoint yee (e half)");
+  // gather copies of the taped fields (the forward's own copies, recomputed)
+  SepArgs<T> ca = sep_args<T>(h, true);
+  for (int q = 0; q < 6; ++q) ca.src[q] = (const T*)A.tape_f[(size_t)s * 6 + q];
+  for (int q = 0; q < 3; ++q) ca.zero[q] = nullptr;
+  CK(launch(h, PIC_K_COPIES, [&] { return launch_sep<T>(ca, st); }), "adjoint: copies");
+  // particles
+  for (int q = 0; q < 6; ++q) CK(cudaMemsetAsync(A.lg[q], 0, fb, st), "zero copy adjoint");
+  const pic_handle::Flat& tp = A.tape_p[s];
+  AdjPartArgs<T> pa;
+  pa.n = A.np;
+  pa.nx = c.nx;
+  pa.nz = c.nz;
+  pa.cell = (const int*)tp.a[0];
+  pa.species = (const int*)tp.a[1];
+  pa.ox = (const T*)tp.a[2];
+  pa.oz = (const T*)tp.a[4];
+  pa.dux = (const T*)tp.a[5];
+  pa.duy = (const T*)tp.a[6];
+  pa.duz = (const T*)tp.a[7];
+  pa.w = h->has_w ? (const T*)tp.a[8] : nullptr;
+  for (int q = 0; q < 6; ++q) pa.g[q] = (const T*)h->g[q];
+  for (int q = 0; q < 3; ++q) pa.lj[q] = lj[q];
+  for (int q = 0; q < 6; ++q) pa.lg[q] = (T*)A.lg[q];
+  pa.lox = (T*)A.lp[0];
+  pa.loz = (T*)A.lp[1];
+  pa.lux = (T*)A.lp[2];
+  pa.luy = (T*)A.lp[3];
+  pa.luz = (T*)A.lp[4];
+  const double dV = c.dx * c.dy * c.dz;
+  pa.dtdx = (T)(c.dt / c.dx);
+  pa.dtdz = (T)(c.dt / c.dz);
+  pa.u0 = (T)h->u0;
+  pa.hq = (T)(0.5 * c.dt);
+  pa.wconst = (T)h->w0;
+  pa.jfx = (T)(-c.dx / (dV * c.dt));
+  pa.jfz = (T)(-c.dz / (dV * c.dt));
+  pa.jfy2d = (T)(1.0 / dV);
+  pa.err = h->d_err;
+  CK(launch(h, PIC_K_PUSH, [&] { return launch_adj_particles<T>(pa, c.scheme, st); }), "adjoint: particles");
+  // copies^T = Psi(D_z) F_gather: the filter here, Psi fused with the coefficient gradient
+  const bool fg = (c.filter_targets & PIC_FILTER_GATHER) != 0;
+  if (fg) {
+    SepArgs<T> fa = sep_args<T>(h, true);
+    for (int q = 0; q < 6; ++q) {
+      fa.src[q] = (const T*)A.lg[q];
+      fa.dst[q] = (T*)A.y[q];
+    }
+    for (int q = 0; q < 3; ++q) fa.zero[q] = nullptr;
+    fa.hz[0] = fa.hz[1] = (int)(h->xt_g.size() / 2);
+    put_taps(fa.zt[0], h->xt_g.data(), (int)h->xt_g.size());
+    put_taps(fa.zt[1], h->xt_g.data(), (int)h->xt_g.size());
+    CK(launch(h, PIC_K_COPIES, [&] { return launch_sep<T>(fa, st); }), "adjoint: copy filter");
+  }
+  AdjPsiArgs<T> ps;
+  for (int q = 0; q < 6; ++q) {
+    ps.y[q] = (const T*)(fg ? A.y[q] : A.lg[q]);
+    ps.f[q] = (const T*)A.tape_f[(size_t)s * 6 + q];
+    ps.lf[q] = lam[q];
+  }
+  ps.ncell = h->ncell;
+  ps.nxy = (long long)c.nx * c.ny;
+  ps.nz = c.nz;
+  double te[9], tb[9];
+  psi_stencil(h->pe, te);
+  psi_stencil(h->pb, tb);
+  put_taps(ps.taps[0], te, 9);
+  put_taps(ps.taps[1], tb, 9);
+  for (int n = 0; n < 5; ++n) {
+    double e[5] = {0, 0, 0, 0, 0}, t[9];
+    e[n] = 1.0;
+    psi_stencil(e, t);
+    put_taps(ps.dpow[n], t, 9);
+  }
+  ps.dots = A.dots;
+  CK(launch(h, PIC_K_DIAG, [&] { return launch_adj_psi<T>(ps, st); }), "adjoint: psi");
+  return PIC_OK;
+}
+
+template <typename T>
+int adjoint_forward_t(pic_handle* h, int nsteps, int every, double* w_perp) {
+  auto& A = h->adj;
+  A.ready = false;
+  long long cnt[2];
+  int rc = count_particles<T>(h, cnt);
+  if (rc) return rc;
+  rc = check_err(h);
+  if (rc) return rc;
+  const long long np = cnt[0] + cnt[1];
+  const int nseg = nsteps > 0 ? (nsteps + every - 1) / every : 0;
+  rc = adj_reserve(h, nseg + 1, nsteps < every ? (nsteps > 0 ? nsteps : 1) : every, np);
+  if (rc) return rc;
+  A.nsteps = nsteps;
+  A.every = every;
+  A.nseg = nseg;
+  A.np = np;
+  for (int j = 0; j < nseg; ++j) {
+    rc = adj_save<T>(h, &A.ck_f[(size_t)j * 6], A.ck_p[j], j == 0);
+    if (rc) return rc;
+    const int len = nsteps - j * every < every ? nsteps - j * every : every;
+    rc = pic_step(h, len);
+    if (rc) return rc;
+  }
+  rc = adj_save<T>(h, &A.ck_f[(size_t)nseg * 6], A.ck_p[nseg], nseg == 0);
+  if (rc) return rc;
+  pic_energy_t e;
+  rc = energy_t<T>(h, &e);  // synchronises and reads the device error flag (ids, overflow)
+  if (rc) return rc;
+  if (e.np != np) return fail(h, PIC_E_STATE, "particles were lost during the recorded run");
+  *w_perp = e.w_perp;
+  A.final_step = h->nstep;
+  A.final_hist = h->nhist;
+  A.ready = true;
+  return PIC_OK;
+}
+
+template <typename T>
+int adjoint_backward_t(pic_handle* h, double dw, double grad_psi_e[5], double grad_psi_b[5],
+                       void* const grad_fields[6]) {
+  auto& A = h->adj;
+  if (!A.ready || h->nstep != A.final_step)
+    return fail(h, PIC_E_STATE, "no recorded forward run for the current state (pic_adjoint_forward)");
+  const pic_config& c = h->cfg;
+  cudaStream_t st = h->stream;
+  const size_t fb = (size_t)h->ncell * sizeof(T);
+  const double dV = c.dx * c.dy * c.dz;
+  // seed: adjoint of the final fields for dw * W_perp
+  AdjSeedArgs<T> sa;
+  for (int q = 0; q < 6; ++q) {
+    sa.f[q] = (const T*)A.ck_f[(size_t)A.nseg * 6 + q];
+    sa.lam[q] = (T*)A.lam[q];
+  }
+  sa.ncell = h->ncell;
+  sa.scale = (T)(dw * dV);
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_adj_seed<T>(sa, st); }), "adjoint seed");
+  for (int q = 0; q < 5; ++q) CK(cudaMemsetAsync(A.lp[q], 0, h->es * (size_t)A.np, st), "zero particle adjoint");
+  for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(A.lj[q], 0, fb, st), "zero current adjoint");
+  CK(cudaMemsetAsync(A.dots, 0, 16 * sizeof(double), st), "zero coefficient gradient");
+  h->no_diag = true;
+  int rc = PIC_OK;
+  for (int j = A.nseg - 1; j >= 0 && rc == PIC_OK; --j) {
+    const int len = A.nsteps - j * A.every < A.every ? A.nsteps - j * A.every : A.every;
+    rc = adj_restore<T>(h, j);
+    for (int s = 0; s < len && rc == PIC_OK; ++s) {
+      rc = adj_save<T>(h, &A.tape_f[(size_t)s * 6], A.tape_p[s], false);
+      if (rc == PIC_OK && s + 1 < len) rc = step_once<T>(h);
+    }
+    for (int s = len - 1; s >= 0 && rc == PIC_OK; --s) rc = adj_step<T>(h, s);
+  }
+  h->no_diag = false;
+  if (rc) return rc;
+  // back to the final state of the recorded run
+  rc = adj_restore<T>(h, A.nseg);
+  if (rc) return rc;
+  h->nstep = A.final_step;
+  h->nhist = A.final_hist;
+  double dots[16];
+  CK(cudaMemcpyAsync(dots, A.dots, sizeof dots, cudaMemcpyDeviceToHost, st), "read coefficient gradient");
+  if (grad_fields)
+    for (int q = 0; q < 6; ++q)
+      if (grad_fields[q])
+        CK(cudaMemcpyAsync(grad_fields[q], A.lam[q], fb, cudaMemcpyDeviceToDevice, st), "copy field gradient");
+  rc = check_err(h);  // synchronises
+  if (rc) return rc;
+  for (int n = 0; n < 5; ++n) {
+    if (grad_psi_e) grad_psi_e[n] = dots[n];
+    if (grad_psi_b) grad_psi_b[n] = dots[5 + n];
+  }
+  A.ready = true;  // the state is the recorded run's final state again
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double* w_perp) {
+  if (!h || nsteps < 0 || checkpoint_every < 1 || !w_perp) return PIC_E_ARG;
+  if (h->cfg.ndim != 2) return fail(h, PIC_E_ARG, "the adjoint covers 2D runs");
+  if (!h->has_id) return fail(h, PIC_E_STATE, "the adjoint needs particle ids (cfg.track_ids = 1)");
+  return h->es == 4 ? adjoint_forward_t<float>(h, nsteps, checkpoint_every, w_perp)
+                    : adjoint_forward_t<double>(h, nsteps, checkpoint_every, w_perp);
+}
+
+int pic_adjoint_backward(pic_handle* h, double dw, double grad_psi_e[5], double grad_psi_b[5],
+                         void* const grad_fields[6]) {
+  if (!h || !isfinite(dw)) return PIC_E_ARG;
+  return h->es == 4 ? adjoint_backward_t<float>(h, dw, grad_psi_e, grad_psi_b, grad_fields)
+                    : adjoint_backward_t<double>(h, dw, grad_psi_e, grad_psi_b, grad_fields);
+}
+
+void pic_adjoint_release(pic_handle* h) {
+  if (h) adj_release(h);
+}
 
 }  // extern "C"

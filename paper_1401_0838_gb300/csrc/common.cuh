@@ -12,6 +12,7 @@ enum : int {
   ERR_NONFINITE = 2,  // a particle position or momentum became NaN/Inf or moved > 1 cell
   ERR_IMPORT = 4,     // an imported particle had an invalid cell or species
   ERR_TIMEOUT = 8,    // a bounded device wait gave up
+  ERR_IDS = 16,       // particle ids are not a permutation of 0 .. N-1 (adjoint tape)
 };
 
 constexpr int MAX_ZTAPS = 33;  // combined z stencil: Psi (9 taps) convolved with the filter

@@ -113,4 +113,48 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st);
 template <typename T>
 cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);
 
+// ---- adjoint of the 2D step (k_adjoint.cu) ----
+// bins of the current buffers -> flat arrays indexed by particle id (f.np = number of ids);
+// `seen` (optional, one zeroed bit per id) flags repeated ids
+template <typename T>
+cudaError_t launch_tape(const RunDev<T>& r, const FlatDev<T>& f, unsigned long long* seen, cudaStream_t st);
+template <typename T>
+struct AdjSeedArgs {
+  const T* f[6];  // final E, B
+  T* lam[6];      // out: adjoint of the final E, B for L = W_perp scaled (scale = dL/dW_perp * dV)
+  long long ncell;
+  T scale;
+};
+template <typename T>
+cudaError_t launch_adj_seed(const AdjSeedArgs<T>& a, cudaStream_t st);
+template <typename T>
+struct AdjPartArgs {
+  long long n;  // particles (ids 0 .. n-1)
+  int nx, nz;
+  const int* cell;  // start state of the step, id order
+  const int* species;
+  const T *ox, *oz, *dux, *duy, *duz, *w;  // w: NULL = wconst
+  const T* g[6];                           // gather copies of the step's E, B
+  const T* lj[3];                          // adjoint of the unfiltered current J^{n+1/2}
+  T* lg[6];                                // adjoint of the gather copies (accumulated atomically)
+  T *lox, *loz, *lux, *luy, *luz;          // in: adjoint of x^{n+1}, u^{n+1/2}; out: of x^n, u^{n-1/2}
+  T dtdx, dtdz, u0, hq, wconst, jfx, jfz, jfy2d;
+  int* err;  // device error flags (ERR_IDS for an invalid taped particle)
+};
+template <typename T>
+cudaError_t launch_adj_particles(const AdjPartArgs<T>& a, int scheme, cudaStream_t st);
+template <typename T>
+struct AdjPsiArgs {
+  const T* y[6];  // filtered adjoint of the gather copies
+  const T* f[6];  // the step's E, B
+  T* lf[6];       // adjoint of E, B (accumulated)
+  long long ncell, nxy;
+  int nz;
+  T taps[2][9];   // Psi_E, Psi_B z-stencils
+  T dpow[5][9];   // D^n, n = 0..4
+  double* dots;   // [10]: d/d a_n of Psi_E (0..4) and Psi_B (5..9), accumulated
+};
+template <typename T>
+cudaError_t launch_adj_psi(const AdjPsiArgs<T>& a, cudaStream_t st);
+
 }  // namespace picgb

@@ -480,6 +480,82 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Adjoint of the 2D step on 256 x 512, 8 particles/cell/species, gamma 130, 100 steps with a
+    checkpoint every 10: the time of the forward run with checkpoints and of the backward pass
+    against the plain forward run, and the Psi_E gradient against central differences (h = 1e-3)."""
+    import numpy as np
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    nsteps, every, alpha = 100, 10, 0.5
+    pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, alpha)
+
+    def cfg(prec):
+        return P.pic_config_default(nx=256, nz=512, dt=alpha, gamma=130.0, precision=prec, ppc_per_species=8,
+                                    init_beam=1, track_ids=1, seed=5)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def w_after(prec, a_e):
+        h = P.pic_create(cfg(prec))
+        P.pic_set_correction_stencil(h, a_e, pb)
+        P.pic_step(h, nsteps)
+        w = P.pic_energy(h)["w_perp"]
+        P.pic_destroy(h)
+        return w
+
+    res = {}
+    for prec, name in ((P.PIC_FP32, "f32"), (P.PIC_FP64, "f64")):
+        reps = []
+        for _ in range(max(1, args.adjoint_reps)):
+            h = P.pic_create(cfg(prec))
+            P.pic_set_correction_stencil(h, pe, pb)
+            P.pic_sync(h)  # the library's stream is synchronised by every call that returns data
+            w, t_f = timed(lambda: P.pic_adjoint_forward(h, nsteps, every))
+            (ge, gb), t_b = timed(lambda: P.pic_adjoint_backward(h, 1.0))
+            P.pic_destroy(h)
+            h = P.pic_create(cfg(prec))
+            P.pic_set_correction_stencil(h, pe, pb)
+            P.pic_sync(h)
+            _, t_p = timed(lambda: (P.pic_step(h, nsteps), P.pic_sync(h)))
+            P.pic_destroy(h)
+            reps.append((t_f, t_b, t_p))
+        t_f, t_b, t_p = (float(np.median([r[i] for r in reps])) for i in range(3))
+        res[name] = {"w_perp": w, "grad_psi_e": ge.tolist(), "grad_psi_b": gb.tolist(), "ms_forward_checkpointed": t_f,
+                     "ms_backward": t_b, "ms_plain_forward": t_p, "adjoint_over_forward": (t_f + t_b) / t_p}
+    fd = []
+    for n in range(5):
+        d = np.zeros(5)
+        d[n] = 1e-3
+        fd.append((w_after(P.PIC_FP64, pe + d) - w_after(P.PIC_FP64, pe - d)) / 2e-3)
+    fd = np.array(fd)
+    for name in ("f32", "f64"):
+        ge = np.array(res[name]["grad_psi_e"])
+        res[name]["max_rel_err_vs_central_differences"] = float(np.abs(ge - fd).max() / np.abs(fd).max())
+    np_ = 256 * 512 * 8 * 2
+    r32 = res["f32"]
+    value = np_ * nsteps / ((r32["ms_forward_checkpointed"] + r32["ms_backward"]) / 1e3)
+    line = {"metric": "particle-steps/s through forward + adjoint (gradient of W_perp(T))", "value": value,
+            "unit": "particle-steps/s", "n_gpus": 1, "steps": nsteps, "warmup": 0,
+            "ms_per_step": (r32["ms_forward_checkpointed"] + r32["ms_backward"]) / nsteps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint: 2D 256x512, 8 particles/cell/species (2,097,152 particles), gamma 130, "
+                                   "c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), 100 steps, checkpoint "
+                                   "every 10; gradient of W_perp(T) w.r.t. Psi_E, Psi_B and E0/B0",
+                       "central_differences": {"h": 1e-3, "forward": "FP64 library run", "grad_psi_e": fd.tolist()}},
+            "f32": r32, "f64": res["f64"]}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +570,8 @@ def main(argv=None):
     ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")
     ap.add_argument("--sweep-runs", type=int, default=64)
     ap.add_argument("--sweep-seq-steps", type=int, default=40)
+    ap.add_argument("--adjoint", action="store_true", help="time the adjoint (256x512, 100 steps) instead")
+    ap.add_argument("--adjoint-reps", type=int, default=3)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args(argv)
@@ -503,6 +581,8 @@ def main(argv=None):
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.adjoint:
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -12,6 +12,8 @@
 // Reverse order per step: Yee^T (host: the curl kernels with negated coefficients), filter^T = the
 // filter (symmetric taps), then k_adj_particles (this file), then copies^T = filter then Psi(D_z)
 // (symmetric taps), the last fused with the coefficient gradient in k_adj_psi.
+#include <climits>
+
 #include "launch.h"
 
 namespace picgb {
@@ -101,6 +103,7 @@ __device__ __constant__ int kStagZ[6] = {0, 0, 1, 1, 1, 0};
 template <typename T>
 struct Gw {
   int i0, i1;  // node indices (periodic)
+  int fl;      // first node relative to the start cell
   T w0, w1;
   bool two;
 };
@@ -114,6 +117,7 @@ __device__ __forceinline__ Gw<T> gweights(T o, int st, int order, int c0, int n)
     const T fr = xs - T(fl);
     g.i0 = wrapi(c0 + fl, n);
     g.i1 = wrapi(c0 + fl + 1, n);
+    g.fl = fl;
     g.w0 = T(1) - fr;
     g.w1 = fr;
     g.two = true;
@@ -121,6 +125,7 @@ __device__ __forceinline__ Gw<T> gweights(T o, int st, int order, int c0, int n)
     const T xs = st ? o : o + T(0.5);  // the box of the node floor(x - st/2 + 1/2)
     const int fl = xs >= T(1) ? 1 : 0;
     g.i0 = g.i1 = wrapi(c0 + fl, n);
+    g.fl = fl;
     g.w0 = T(1);
     g.w1 = T(0);
     g.two = false;
@@ -174,18 +179,46 @@ __device__ __forceinline__ void atomic_add(T* p, T v) {
   atomicAdd(p, v);
 }
 
+constexpr int ADJ_THREADS = 128;
+
+// Inclusive sum of v over the run of consecutive lanes that hold the same key (the run starts at
+// lane `start`); the last lane of a run ends with the run's total. All 32 lanes take part.
+template <typename T>
+__device__ __forceinline__ T run_sum(T v, int start, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= start) v += t;
+  }
+  return v;
+}
+
 template <typename T, int SCHEME>
-__global__ void __launch_bounds__(128) k_adj_particles(const __grid_constant__ AdjPartArgs<T> a) {
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_constant__ AdjPartArgs<T> a) {
+  // Consecutive ids start close together (the beam keeps its lattice order), so neighbouring lanes
+  // mostly add into the same nodes of the copies' adjoint: each node's contributions are summed over
+  // the run of lanes that share it, and the run's last lane adds the total to global memory.
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
+  const int lane = threadIdx.x & 31;
   const int nx = a.nx, nz = a.nz;
-  const int cell = a.cell[p], s = a.species[p];
-  if (cell < 0 || cell >= nx * nz || (s != 0 && s != 1)) {  // a particle the recomputed step lost
-    flag_error(a.err, ERR_IDS);
-    return;
+  bool active = p < a.n;
+  int cell = 0, s = 0;
+  if (active) {
+    cell = a.cell[p];
+    s = a.species[p];
+    if (cell < 0 || cell >= nx * nz || (s != 0 && s != 1)) {  // a particle the recomputed step lost
+      flag_error(a.err, ERR_IDS);
+      active = false;
+      cell = 0;
+      s = 0;
+    }
   }
   const int ci = cell % nx, ck = cell / nx;
-  const T ox = a.ox[p], oz = a.oz[p];
+  T lF[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T ox = T(0), oz = T(0);
+  if (active) {
+  ox = a.ox[p];
+  oz = a.oz[p];
   const T ux0 = a.dux[p], uy0 = a.duy[p], uz0 = a.duz[p];
   const T w = a.w ? a.w[p] : a.wconst;
   const T qs = s ? T(1) : T(-1);
@@ -352,32 +385,56 @@ __global__ void __launch_bounds__(128) k_adj_particles(const __grid_constant__ A
   a.luy[p] = lmy;
   a.luz[p] = lmz;
 
-  // 6. gather transpose: into the adjoint of the copies, and the weights' dependence on x^n
-  const T lF[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
+  // 6. gather transpose: the weights' dependence on x^n here, the copies' adjoint below
   T lox = lx1 + lox_dep, loz = lz1 + loz_dep;
+  const T lFv[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
+    lF[c] = lFv[c];
     lox += lF[c] * dFx[c];
     loz += lF[c] * dFz[c];
-    T* LG = a.lg[c];
-    const T v = lF[c];
-    atomic_add(LG + (long long)gz[c].i0 * nx + gx[c].i0, v * gz[c].w0 * gx[c].w0);
-    if (gx[c].two) atomic_add(LG + (long long)gz[c].i0 * nx + gx[c].i1, v * gz[c].w0 * gx[c].w1);
-    if (gz[c].two) {
-      atomic_add(LG + (long long)gz[c].i1 * nx + gx[c].i0, v * gz[c].w1 * gx[c].w0);
-      if (gx[c].two) atomic_add(LG + (long long)gz[c].i1 * nx + gx[c].i1, v * gz[c].w1 * gx[c].w1);
-    }
   }
   a.lox[p] = lox;
   a.loz[p] = loz;
+  }  // active
+  // adjoint of the copies: lambda_F times the gather weights, summed over runs of lanes that share
+  // the component's base node (inactive lanes carry zeros under keys of their own)
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int sx = kStagX[c], sz = kStagZ[c];
+    const Gw<T> wx = gweights(ox, sx, SCHEME == 0 ? 1 - sx : 1, ci, nx);
+    const Gw<T> wz = gweights(oz, sz, SCHEME == 0 ? 1 - sz : 1, ck, nz);
+    const int key = active ? wz.i0 * nx + wx.i0 : -1 - lane;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool tail = active && (lane == 31 || next != key);
+    T* LG = a.lg[c];
+    const T v = lF[c];
+    const T s00 = run_sum(v * wz.w0 * wx.w0, start, lane);
+    if (tail) atomic_add(LG + (long long)wz.i0 * nx + wx.i0, s00);
+    if (wx.two) {  // the same for every lane (the order depends on the component only)
+      const T s01 = run_sum(v * wz.w0 * wx.w1, start, lane);
+      if (tail) atomic_add(LG + (long long)wz.i0 * nx + wx.i1, s01);
+    }
+    if (wz.two) {
+      const T s10 = run_sum(v * wz.w1 * wx.w0, start, lane);
+      if (tail) atomic_add(LG + (long long)wz.i1 * nx + wx.i0, s10);
+      if (wx.two) {
+        const T s11 = run_sum(v * wz.w1 * wx.w1, start, lane);
+        if (tail) atomic_add(LG + (long long)wz.i1 * nx + wx.i1, s11);
+      }
+    }
+  }
 }
 
 template <typename T>
 cudaError_t launch_adj_particles(const AdjPartArgs<T>& a, int scheme, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((a.n + 127) / 128);
-  if (scheme == 0) k_adj_particles<T, 0><<<blocks, 128, 0, st>>>(a);
-  else k_adj_particles<T, 1><<<blocks, 128, 0, st>>>(a);
+  const unsigned blocks = (unsigned)((a.n + ADJ_THREADS - 1) / ADJ_THREADS);
+  if (scheme == 0) k_adj_particles<T, 0><<<blocks, ADJ_THREADS, 0, st>>>(a);
+  else k_adj_particles<T, 1><<<blocks, ADJ_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_adj_particles<float>(const AdjPartArgs<float>&, int, cudaStream_t);

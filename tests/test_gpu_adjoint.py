@@ -80,7 +80,7 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         pair, pe, pb = _beam_pair(nx=24, nz=40, seed=7)
         res.append(_gpu_grad(pair.h, pair.cfg, 7, every))
     for r in res[1:]:
-        assert r[0] == res[0][0]
+        assert abs(r[0] - res[0][0]) <= 1e-13 * res[0][0]  # the forward's atomics may reorder sums
         assert np.abs(r[1] - res[0][1]).max() <= 1e-11 * np.abs(res[0][1]).max()
         for q in range(6):
             assert np.abs(r[3][q] - res[0][3][q]).max() <= 1e-11 * max(np.abs(res[0][3][q]).max(), 1e-300)

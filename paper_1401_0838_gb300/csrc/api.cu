@@ -1827,6 +1827,7 @@ int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double*
   if (!h || nsteps < 0 || checkpoint_every < 1 || !w_perp) return PIC_E_ARG;
   if (h->cfg.ndim != 2) return fail(h, PIC_E_ARG, "the adjoint covers 2D runs");
   if (!h->has_id) return fail(h, PIC_E_STATE, "the adjoint needs particle ids (cfg.track_ids = 1)");
+  if (h->ncell >= (1LL << 31)) return fail(h, PIC_E_ARG, "the adjoint covers grids below 2^31 cells");
   return h->es == 4 ? adjoint_forward_t<float>(h, nsteps, checkpoint_every, w_perp)
                     : adjoint_forward_t<double>(h, nsteps, checkpoint_every, w_perp);
 }

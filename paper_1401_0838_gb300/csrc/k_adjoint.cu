@@ -24,41 +24,42 @@ namespace picgb {
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_tape(RunDev<T> r, FlatDev<T> f, unsigned long long* seen) {
-  const long long cell = blockIdx.x * (long long)blockDim.y + threadIdx.y;
+  // one thread per (cell, species, slot); slots at or past the cell's count do nothing
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long per_cell = 2LL * r.cap;
+  const long long cell = e / per_cell;
   if (cell >= r.ncell) return;
-  for (int s = 0; s < 2; ++s) {
-    const SpeciesBuf<T> b = r.in[s];
-    int n = b.cnt[cell];
-    n = n > r.cap ? r.cap : n;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const long long src = cell * r.cap + j;
-      const unsigned id = b.id[src];
-      if ((long long)id >= f.np) {
-        flag_error(r.err, ERR_IDS);
-        continue;
-      }
-      if (seen) {
-        const unsigned long long bit = 1ull << (id & 63u);
-        if (atomicOr(seen + (id >> 6), bit) & bit) flag_error(r.err, ERR_IDS);
-      }
-      f.cell[id] = (int)cell;
-      f.species[id] = s;
-      f.ox[id] = b.ox[src];
-      if (f.oy) f.oy[id] = r.ndim == 3 ? b.oy[src] : T(0);
-      f.oz[id] = b.oz[src];
-      f.dux[id] = b.dux[src];
-      f.duy[id] = b.duy[src];
-      f.duz[id] = b.duz[src];
-      if (f.w) f.w[id] = b.w ? b.w[src] : r.wconst;
-    }
+  const int rem = (int)(e - cell * per_cell);
+  const int s = rem >= r.cap ? 1 : 0;
+  const int j = rem - s * r.cap;
+  const SpeciesBuf<T> b = r.in[s];
+  if (j >= min(b.cnt[cell], r.cap)) return;
+  const long long src = cell * r.cap + j;
+  const unsigned id = b.id[src];
+  if ((long long)id >= f.np) {
+    flag_error(r.err, ERR_IDS);
+    return;
   }
+  if (seen) {
+    const unsigned long long bit = 1ull << (id & 63u);
+    if (atomicOr(seen + (id >> 6), bit) & bit) flag_error(r.err, ERR_IDS);
+  }
+  f.cell[id] = (int)cell;
+  f.species[id] = s;
+  f.ox[id] = b.ox[src];
+  if (f.oy) f.oy[id] = r.ndim == 3 ? b.oy[src] : T(0);
+  f.oz[id] = b.oz[src];
+  f.dux[id] = b.dux[src];
+  f.duy[id] = b.duy[src];
+  f.duz[id] = b.duz[src];
+  if (f.w) f.w[id] = b.w ? b.w[src] : r.wconst;
 }
 
 template <typename T>
 cudaError_t launch_tape(const RunDev<T>& r, const FlatDev<T>& f, unsigned long long* seen, cudaStream_t st) {
-  dim3 blk(32, 8);
-  const long long blocks = (r.ncell + 7) / 8;
-  if (blocks > 0) k_tape<T><<<(unsigned)blocks, blk, 0, st>>>(r, f, seen);
+  const long long n = r.ncell * 2LL * r.cap;
+  const long long blocks = (n + 255) / 256;
+  if (blocks > 0) k_tape<T><<<(unsigned)blocks, 256, 0, st>>>(r, f, seen);
   return cudaGetLastError();
 }
 template cudaError_t launch_tape<float>(const RunDev<float>&, const FlatDev<float>&, unsigned long long*,
@@ -108,15 +109,19 @@ struct Gw {
   bool two;
 };
 
+// Periodic index of i in [-n, 2n).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// nodes[k] = periodic index of start cell + k - 1, k = 0..3
 template <typename T>
-__device__ __forceinline__ Gw<T> gweights(T o, int st, int order, int c0, int n) {
+__device__ __forceinline__ Gw<T> gweights(T o, int st, int order, const int nodes[4]) {
   Gw<T> g;
   if (order == 1) {
     const T xs = st ? o - T(0.5) : o;
     const int fl = xs < T(0) ? -1 : 0;
     const T fr = xs - T(fl);
-    g.i0 = wrapi(c0 + fl, n);
-    g.i1 = wrapi(c0 + fl + 1, n);
+    g.i0 = fl < 0 ? nodes[0] : nodes[1];
+    g.i1 = fl < 0 ? nodes[1] : nodes[2];
     g.fl = fl;
     g.w0 = T(1) - fr;
     g.w1 = fr;
@@ -124,7 +129,7 @@ __device__ __forceinline__ Gw<T> gweights(T o, int st, int order, int c0, int n)
   } else {
     const T xs = st ? o : o + T(0.5);  // the box of the node floor(x - st/2 + 1/2)
     const int fl = xs >= T(1) ? 1 : 0;
-    g.i0 = g.i1 = wrapi(c0 + fl, n);
+    g.i0 = g.i1 = fl ? nodes[2] : nodes[1];
     g.fl = fl;
     g.w0 = T(1);
     g.w1 = T(0);
@@ -213,7 +218,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
       s = 0;
     }
   }
-  const int ci = cell % nx, ck = cell / nx;
+  const int ck = cell / nx, ci = cell - ck * nx;
+  int ix[4], iz[4];  // periodic node indices of the start cell - 1 .. + 2
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ix[q] = wrap1(ci + q - 1, nx);
+    iz[q] = wrap1(ck + q - 1, nz);
+  }
   T lF[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   T ox = T(0), oz = T(0);
   if (active) {
@@ -229,13 +240,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const int sx = kStagX[c], sz = kStagZ[c];
-    gx[c] = gweights(ox, sx, SCHEME == 0 ? 1 - sx : 1, ci, nx);
-    gz[c] = gweights(oz, sz, SCHEME == 0 ? 1 - sz : 1, ck, nz);
-    const T* G = a.g[c];
-    const T g00 = G[(long long)gz[c].i0 * nx + gx[c].i0];
-    const T g01 = G[(long long)gz[c].i0 * nx + gx[c].i1];
-    const T g10 = G[(long long)gz[c].i1 * nx + gx[c].i0];
-    const T g11 = G[(long long)gz[c].i1 * nx + gx[c].i1];
+    gx[c] = gweights(ox, sx, SCHEME == 0 ? 1 - sx : 1, ix);
+    gz[c] = gweights(oz, sz, SCHEME == 0 ? 1 - sz : 1, iz);
+    const T* G0 = a.g[c] + gz[c].i0 * nx;  // 32-bit offsets: the launcher caps the cell count
+    const T* G1 = a.g[c] + gz[c].i1 * nx;
+    const T g00 = G0[gx[c].i0], g01 = G0[gx[c].i1], g10 = G1[gx[c].i0], g11 = G1[gx[c].i1];
     const T zx0 = gz[c].w0 * gx[c].w0, zx1 = gz[c].w0 * gx[c].w1, zx2 = gz[c].w1 * gx[c].w0, zx3 = gz[c].w1 * gx[c].w1;
     F[c] = zx0 * g00 + zx1 * g01 + zx2 * g10 + zx3 * g11;
     dFx[c] = gx[c].two ? gz[c].w0 * (g01 - g00) + gz[c].w1 * (g11 - g10) : T(0);
@@ -247,10 +256,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
   const T mx = ux0 + h * F[0], my = uy0 + h * F[1], mz = uz0 + h * F[2];
   const T Mz = a.u0 + mz;
   const T gm = sqrt(T(1) + mx * mx + my * my + Mz * Mz);
-  const T tx = h * F[3] / gm, ty = h * F[4] / gm, tz = h * F[5] / gm;
+  const T igm = T(1) / gm;
+  const T tx = h * F[3] * igm, ty = h * F[4] * igm, tz = h * F[5] * igm;
   const T tt = tx * tx + ty * ty + tz * tz;
   const T den = T(1) + tt;
-  const T sx = T(2) * tx / den, sy = T(2) * ty / den, sz = T(2) * tz / den;
+  const T iden = T(1) / den;
+  const T sx = T(2) * tx * iden, sy = T(2) * ty * iden, sz = T(2) * tz * iden;
   const T px = mx + (my * tz - Mz * ty), py = my + (Mz * tx - mx * tz), pz = Mz + (mx * ty - my * tx);
   const T ux = mx + (py * sz - pz * sy) + h * F[0];
   const T uy = my + (pz * sx - px * sz) + h * F[1];
@@ -268,12 +279,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
   shape_win(oz, ddz, wz);
   const T qw = qs * w;
   const T cx = qw * a.jfx, cz = qw * a.jfz, cyc = qw * a.jfy2d;
-  int ix[4], iz[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    ix[q] = wrapi(ci + q - 1, nx);
-    iz[q] = wrapi(ck + q - 1, nz);
-  }
   T gS0x[4] = {}, gdSx[4] = {}, gS0z[4] = {}, gdSz[4] = {};
   T Tx[4], Tz[4];
 #pragma unroll
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
   // Jx on the edges i+1/2 of the window nodes -1..1 (the running sum closes to 0 at node 2)
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const T* row = a.lj[0] + (long long)iz[b] * nx;
+    const T* row = a.lj[0] + iz[b] * nx;
     const T l0 = row[ix[0]], l1 = row[ix[1]], l2 = row[ix[2]];
     const T L2 = l2, L1 = l1 + l2, L0 = l0 + l1 + l2;  // suffix sums: dJ/dW over the edges at or right of a
     gdSx[0] += cx * Tz[b] * L0;
@@ -296,33 +301,41 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
   // Jz on the edges k+1/2 of the window nodes -1..1
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const T l0 = a.lj[2][(long long)iz[0] * nx + ix[q]];
-    const T l1 = a.lj[2][(long long)iz[1] * nx + ix[q]];
-    const T l2 = a.lj[2][(long long)iz[2] * nx + ix[q]];
+    const T l0 = a.lj[2][iz[0] * nx + ix[q]];
+    const T l1 = a.lj[2][iz[1] * nx + ix[q]];
+    const T l2 = a.lj[2][iz[2] * nx + ix[q]];
     const T L2 = l2, L1 = l1 + l2, L0 = l0 + l1 + l2;
     gdSz[0] += cz * Tx[q] * L0;
     gdSz[1] += cz * Tx[q] * L1;
     gdSz[2] += cz * Tx[q] * L2;
     gTx[q] += cz * (wz.dS[0] * L0 + wz.dS[1] * L1 + wz.dS[2] * L2);
   }
-  // Jy at the nodes: weight S0x S0z + dSx S0z/2 + S0x dSz/2 + dSx dSz/3, coefficient q w vy / dV
-  T gcy = T(0);
+  // Jy at the nodes, coefficient q w vy / dV, weight S0x S0z + dSx S0z/2 + S0x dSz/2 + dSx dSz/3,
+  // which is Tx Tz + dSx dSz / 12 with T = S0 + dS/2
+  T Aq[4] = {}, Bq[4] = {}, Cb[4] = {}, Db[4] = {};
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const T* row = a.lj[1] + (long long)iz[b] * nx;
+    const T* row = a.lj[1] + iz[b] * nx;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T l = row[ix[q]] * cyc;  // d(lambda . Jy) / d(weight) / vy
-      const T wyq = wx.S0[q] * wz.S0[b] + T(0.5) * wx.dS[q] * wz.S0[b] + T(0.5) * wx.S0[q] * wz.dS[b] +
-                    wx.dS[q] * wz.dS[b] / T(3);
-      gcy += l * wyq;
-      const T lv = l * vy;
-      gS0x[q] += lv * Tz[b];
-      gdSx[q] += lv * (T(0.5) * wz.S0[b] + wz.dS[b] / T(3));
-      gS0z[b] += lv * Tx[q];
-      gdSz[b] += lv * (T(0.5) * wx.S0[q] + wx.dS[q] / T(3));
+      const T l = row[ix[q]];
+      Aq[q] += l * Tz[b];
+      Bq[q] += l * wz.dS[b];
+      Cb[b] += l * Tx[q];
+      Db[b] += l * wx.dS[q];
     }
   }
+  T gcy = T(0);
+  const T lvy = cyc * vy, k12 = T(1.0 / 12.0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    gcy += Tx[q] * Aq[q] + k12 * wx.dS[q] * Bq[q];
+    gS0x[q] += lvy * Aq[q];
+    gdSx[q] += lvy * (T(0.5) * Aq[q] + k12 * Bq[q]);
+    gS0z[q] += lvy * Cb[q];
+    gdSz[q] += lvy * (T(0.5) * Cb[q] + k12 * Db[q]);
+  }
+  gcy *= cyc;
   T lox_dep = T(0), lddx = T(0), loz_dep = T(0), lddz = T(0);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -364,19 +377,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
   T ltx = lpy * Mz - lpz * my, lty = lpz * mx - lpx * Mz, ltz = lpx * my - lpy * mx;  // lp x m
   // s = 2 t / (1 + |t|^2)
   const T ts = tx * lsx + ty * lsy + tz * lsz;
-  const T f2 = T(2) / den, f4 = T(4) * ts / (den * den);
+  const T f2 = T(2) * iden, f4 = T(4) * ts * iden * iden;
   ltx += f2 * lsx - f4 * tx;
   lty += f2 * lsy - f4 * ty;
   ltz += f2 * lsz - f4 * tz;
   // t = h B / gm
-  const T hg = h / gm;
+  const T hg = h * igm;
   lB[0] = hg * ltx;
   lB[1] = hg * lty;
   lB[2] = hg * ltz;
-  const T lgm = -(tx * ltx + ty * lty + tz * ltz) / gm;
-  lmx += lgm * mx / gm;
-  lmy += lgm * my / gm;
-  lmz += lgm * Mz / gm;
+  const T lgm = -(tx * ltx + ty * lty + tz * ltz) * igm * igm;
+  lmx += lgm * mx;
+  lmy += lgm * my;
+  lmz += lgm * Mz;
   // m = u + h E
   lE[0] += h * lmx;
   lE[1] += h * lmy;
@@ -402,8 +415,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const int sx = kStagX[c], sz = kStagZ[c];
-    const Gw<T> wx = gweights(ox, sx, SCHEME == 0 ? 1 - sx : 1, ci, nx);
-    const Gw<T> wz = gweights(oz, sz, SCHEME == 0 ? 1 - sz : 1, ck, nz);
+    const Gw<T> wx = gweights(ox, sx, SCHEME == 0 ? 1 - sx : 1, ix);
+    const Gw<T> wz = gweights(oz, sz, SCHEME == 0 ? 1 - sz : 1, iz);
     const int key = active ? wz.i0 * nx + wx.i0 : -1 - lane;
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const int next = __shfl_down_sync(0xffffffffu, key, 1);
@@ -413,17 +426,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_particles(const __grid_cons
     T* LG = a.lg[c];
     const T v = lF[c];
     const T s00 = run_sum(v * wz.w0 * wx.w0, start, lane);
-    if (tail) atomic_add(LG + (long long)wz.i0 * nx + wx.i0, s00);
+    if (tail) atomic_add(LG + wz.i0 * nx + wx.i0, s00);
     if (wx.two) {  // the same for every lane (the order depends on the component only)
       const T s01 = run_sum(v * wz.w0 * wx.w1, start, lane);
-      if (tail) atomic_add(LG + (long long)wz.i0 * nx + wx.i1, s01);
+      if (tail) atomic_add(LG + wz.i0 * nx + wx.i1, s01);
     }
     if (wz.two) {
       const T s10 = run_sum(v * wz.w1 * wx.w0, start, lane);
-      if (tail) atomic_add(LG + (long long)wz.i1 * nx + wx.i0, s10);
+      if (tail) atomic_add(LG + wz.i1 * nx + wx.i0, s10);
       if (wx.two) {
         const T s11 = run_sum(v * wz.w1 * wx.w1, start, lane);
-        if (tail) atomic_add(LG + (long long)wz.i1 * nx + wx.i1, s11);
+        if (tail) atomic_add(LG + wz.i1 * nx + wx.i1, s11);
       }
     }
   }
@@ -457,7 +470,12 @@ __global__ void __launch_bounds__(256) k_adj_psi(const __grid_constant__ AdjPsiA
     const T* Y = a.y[q];
     T y[9];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) y[m] = Y[(long long)wrapi((int)k + m - 4, a.nz) * a.nxy + base];
+    for (int m = 0; m < 9; ++m) {
+      int kk = (int)k + m - 4;
+      kk = kk < 0 ? kk + a.nz : (kk >= a.nz ? kk - a.nz : kk);
+      if (kk < 0 || kk >= a.nz) kk = wrapi(kk, a.nz);  // grids shorter than 4 cells
+      y[m] = Y[(long long)kk * a.nxy + base];
+    }
     const int zs = q < 2 ? 0 : 1;
     T psi = T(0);
 #pragma unroll

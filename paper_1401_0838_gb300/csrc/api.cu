@@ -93,6 +93,7 @@ struct pic_handle {
     void* y[6] = {};            // filtered lg
     void* lp[5] = {};           // particle adjoints: ox, oz, ux, uy, uz (id order)
     double* dots = nullptr;     // 10 coefficient-gradient accumulators
+    double* partial = nullptr;  // block partial sums of the coefficient gradient
     unsigned long long* seen = nullptr;
     std::vector<void*> mem;
   } adj;
@@ -1530,6 +1531,7 @@ int adj_reserve(pic_handle* h, int nck, int ntape, long long np) {
   for (int q = 0; q < 3; ++q) ok = ok && (A.lj[q] = adj_malloc(h, fb));
   for (int q = 0; q < 5; ++q) ok = ok && (A.lp[q] = adj_malloc(h, h->es * (size_t)np));
   ok = ok && (A.dots = (double*)adj_malloc(h, 16 * sizeof(double)));
+  ok = ok && (A.partial = (double*)adj_malloc(h, adj_psi_partial_doubles() * sizeof(double)));
   ok = ok && (A.seen = (unsigned long long*)adj_malloc(h, 8 * (size_t)(np / 64 + 1)));
   if (!ok) {
     adj_release(h);
@@ -1722,6 +1724,7 @@ int adj_step(pic_handle* h, int s) {
     put_taps(ps.dpow[n], t, 9);
   }
   ps.dots = A.dots;
+  ps.partial = A.partial;
   CK(launch(h, PIC_K_DIAG, [&] { return launch_adj_psi<T>(ps, st); }), "adjoint: psi");
   return PIC_OK;
 }

@@ -23,22 +23,21 @@ namespace picgb {
 // zeroed by the caller) ids that are out of range or repeated raise ERR_IDS.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_tape(RunDev<T> r, FlatDev<T> f, unsigned long long* seen) {
-  // one thread per (cell, species, slot); slots at or past the cell's count do nothing
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long per_cell = 2LL * r.cap;
-  const long long cell = e / per_cell;
+__global__ void __launch_bounds__(256) k_tape(const __grid_constant__ RunDev<T> r, const __grid_constant__ FlatDev<T> f,
+                                              unsigned long long* seen) {
+  // eight lanes per (cell, species) bin, four bins per warp (bins hold about ppc particles)
+  const long long cs = blockIdx.x * 32LL + (threadIdx.x >> 3);
+  const long long cell = cs >> 1;
   if (cell >= r.ncell) return;
-  const int rem = (int)(e - cell * per_cell);
-  const int s = rem >= r.cap ? 1 : 0;
-  const int j = rem - s * r.cap;
-  const SpeciesBuf<T> b = r.in[s];
-  if (j >= min(b.cnt[cell], r.cap)) return;
+  const int s = (int)(cs & 1);
+  const SpeciesBuf<T>& b = s ? r.in[1] : r.in[0];  // constant indices: no local copy of r
+  const int n = min(b.cnt[cell], r.cap);
+  for (int j = threadIdx.x & 7; j < n; j += 8) {
   const long long src = cell * r.cap + j;
   const unsigned id = b.id[src];
   if ((long long)id >= f.np) {
     flag_error(r.err, ERR_IDS);
-    return;
+    continue;
   }
   if (seen) {
     const unsigned long long bit = 1ull << (id & 63u);
@@ -53,12 +52,12 @@ __global__ void k_tape(RunDev<T> r, FlatDev<T> f, unsigned long long* seen) {
   f.duy[id] = b.duy[src];
   f.duz[id] = b.duz[src];
   if (f.w) f.w[id] = b.w ? b.w[src] : r.wconst;
+  }
 }
 
 template <typename T>
 cudaError_t launch_tape(const RunDev<T>& r, const FlatDev<T>& f, unsigned long long* seen, cudaStream_t st) {
-  const long long n = r.ncell * 2LL * r.cap;
-  const long long blocks = (n + 255) / 256;
+  const long long blocks = (2 * r.ncell + 31) / 32;
   if (blocks > 0) k_tape<T><<<(unsigned)blocks, 256, 0, st>>>(r, f, seen);
   return cudaGetLastError();
 }
@@ -460,14 +459,26 @@ template cudaError_t launch_adj_particles<double>(const AdjPartArgs<double>&, in
 // since G_q = Psi_q(D_z) F_filter f_q with Psi_q = sum_n a_n D^n, every operator symmetric.
 // Block partial sums in FP64, one atomic per block and coefficient.
 // ---------------------------------------------------------------------------------------------
+constexpr int PSI_BLOCKS = 304;  // blocks per component (grid-stride), partial sums per block
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_psi(const __grid_constant__ AdjPsiArgs<T> a) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
+  const T* __restrict__ Y = a.y[q];
+  const T* __restrict__ Fq = a.f[q];
+  T* __restrict__ L = a.lf[q];
+  const int zs = q < 2 ? 0 : 1;
+  T taps[9], dp[5][9];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) {
+    taps[m] = a.taps[zs][m];
+#pragma unroll
+    for (int n = 0; n < 5; ++n) dp[n][m] = a.dpow[n][m];
+  }
   double dn[5] = {0, 0, 0, 0, 0};
-  if (c < a.ncell) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
     const long long k = c / a.nxy, base = c - k * a.nxy;
-    const T* Y = a.y[q];
     T y[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
@@ -476,18 +487,17 @@ __global__ void __launch_bounds__(256) k_adj_psi(const __grid_constant__ AdjPsiA
       if (kk < 0 || kk >= a.nz) kk = wrapi(kk, a.nz);  // grids shorter than 4 cells
       y[m] = Y[(long long)kk * a.nxy + base];
     }
-    const int zs = q < 2 ? 0 : 1;
     T psi = T(0);
 #pragma unroll
-    for (int m = 0; m < 9; ++m) psi += a.taps[zs][m] * y[m];
-    a.lf[q][c] += psi;
-    const double f = (double)a.f[q][c];
+    for (int m = 0; m < 9; ++m) psi += taps[m] * y[m];
+    L[c] += psi;
+    const double f = (double)Fq[c];
 #pragma unroll
     for (int n = 0; n < 5; ++n) {
       T v = T(0);
 #pragma unroll
-      for (int m = 0; m < 9; ++m) v += a.dpow[n][m] * y[m];
-      dn[n] = f * (double)v;
+      for (int m = 0; m < 9; ++m) v += dp[n][m] * y[m];
+      dn[n] += f * (double)v;
     }
   }
   __shared__ double red[5][8];
@@ -503,17 +513,35 @@ __global__ void __launch_bounds__(256) k_adj_psi(const __grid_constant__ AdjPsiA
   if (threadIdx.x < 5) {
     double t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
-    atomicAdd(a.dots + (q < 2 ? 0 : 5) + threadIdx.x, t);
+    a.partial[((long long)q * gridDim.x + blockIdx.x) * 5 + threadIdx.x] = t;
   }
+}
+
+// dots[n] += the Psi_E rows (components 0, 1), dots[5 + n] += the Psi_B rows (2..5), in a fixed order
+// One warp per output: lanes stride over the blocks, then a fixed-order shuffle tree.
+__global__ void k_adj_psi_final(const double* __restrict__ partial, int nblocks, double* dots) {
+  const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (t >= 10) return;
+  const int n = t % 5, q0 = t < 5 ? 0 : 2, q1 = t < 5 ? 2 : 6;
+  double s = 0;
+  for (int q = q0; q < q1; ++q)
+    for (int b = lane; b < nblocks; b += 32) s += partial[((long long)q * nblocks + b) * 5 + n];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) dots[t] += s;
 }
 
 template <typename T>
 cudaError_t launch_adj_psi(const AdjPsiArgs<T>& a, cudaStream_t st) {
   if (a.ncell <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((a.ncell + 255) / 256), 6);
+  long long nb = (a.ncell + 255) / 256;
+  nb = nb < PSI_BLOCKS ? nb : PSI_BLOCKS;
+  dim3 grid((unsigned)nb, 6);
   k_adj_psi<T><<<grid, 256, 0, st>>>(a);
+  k_adj_psi_final<<<1, 320, 0, st>>>(a.partial, (int)nb, a.dots);
   return cudaGetLastError();
 }
+size_t adj_psi_partial_doubles() { return (size_t)6 * PSI_BLOCKS * 5; }
 template cudaError_t launch_adj_psi<float>(const AdjPsiArgs<float>&, cudaStream_t);
 template cudaError_t launch_adj_psi<double>(const AdjPsiArgs<double>&, cudaStream_t);
 

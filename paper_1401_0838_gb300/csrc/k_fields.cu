@@ -735,10 +735,10 @@ template cudaError_t launch_field_energy<double>(const double* const*, long long
 size_t field_energy_scratch_bytes() { return sizeof(double) * (3 * FE_BLOCKS + 2); }
 
 template <typename T>
-__global__ void k_kinetic(RunDev<T> r, double* out) {
+__global__ void k_kinetic(const __grid_constant__ RunDev<T> r, double* out) {
   double acc = 0;
   for (int s = 0; s < 2; ++s) {
-    const SpeciesBuf<T> b = r.in[s];
+    const SpeciesBuf<T>& b = s ? r.in[1] : r.in[0];  // constant indices: no local copy of r
     for (long long c = blockIdx.x * (long long)blockDim.y + threadIdx.y; c < r.ncell;
          c += (long long)gridDim.x * blockDim.y) {
       int n = b.cnt[c];

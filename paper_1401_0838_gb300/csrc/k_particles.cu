@@ -1147,7 +1147,7 @@ struct BeamDev {
 __device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
 
 template <typename T>
-__global__ void k_init_beam(RunDev<T> r, BeamDev b, long long npoints) {
+__global__ void k_init_beam(const __grid_constant__ RunDev<T> r, BeamDev b, long long npoints) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= npoints) return;
   const long long nxy = (long long)r.nx * r.ny;
@@ -1185,7 +1185,8 @@ __global__ void k_init_beam(RunDev<T> r, BeamDev b, long long npoints) {
     T ux = (T)(b.u_th * ra * cos(ta));
     T uy = (T)(b.u_th * ra * sin(ta));
     T uz = (T)(b.u_th * rb * cos(tb));
-    insert_particle(r.in[s], r.cap, dcell, tox, toy, toz, ux, uy, uz, (T)w, (unsigned)(p * 2 + s), r.err);
+    insert_particle(s ? r.in[1] : r.in[0], r.cap, dcell, tox, toy, toz, ux, uy, uz, (T)w, (unsigned)(p * 2 + s),
+                    r.err);
   }
 }
 
@@ -1219,7 +1220,7 @@ template cudaError_t launch_init_beam<double>(const RunDev<double>&, int, const 
 // Import: flat particle arrays (device) -> cell bins of the input buffers.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_import(RunDev<T> r, FlatDev<T> f) {
+__global__ void k_import(const __grid_constant__ RunDev<T> r, const __grid_constant__ FlatDev<T> f) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= f.np) return;
   int s = f.species[p];
@@ -1242,7 +1243,7 @@ __global__ void k_import(RunDev<T> r, FlatDev<T> f) {
   long long dcell = (long long)k * nxy + (long long)j * r.nx + i;
   T w = f.w ? f.w[p] : r.wconst;
   unsigned id = f.id ? f.id[p] : (unsigned)p;
-  insert_particle(r.in[s], r.cap, dcell, ox, oy, oz, f.dux[p], f.duy[p], f.duz[p], w, id, r.err);
+  insert_particle(s ? r.in[1] : r.in[0], r.cap, dcell, ox, oy, oz, f.dux[p], f.duy[p], f.duz[p], w, id, r.err);
 }
 
 template <typename T>
@@ -1261,10 +1262,11 @@ template cudaError_t launch_import<double>(const RunDev<double>&, const FlatDev<
 // the (clamped) counts over cells of this species, `base` the species' first flat index.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_export(RunDev<T> r, int s, const long long* __restrict__ offs, long long base, FlatDev<T> f) {
+__global__ void k_export(const __grid_constant__ RunDev<T> r, int s, const long long* __restrict__ offs, long long base,
+                         const __grid_constant__ FlatDev<T> f) {
   long long cell = blockIdx.x * (long long)blockDim.y + threadIdx.y;
   if (cell >= r.ncell) return;
-  const SpeciesBuf<T> b = r.in[s];
+  const SpeciesBuf<T>& b = s ? r.in[1] : r.in[0];  // constant indices: no local copy of r
   int n = b.cnt[cell];
   n = n > r.cap ? r.cap : n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {

@@ -152,9 +152,11 @@ struct AdjPsiArgs {
   int nz;
   T taps[2][9];   // Psi_E, Psi_B z-stencils
   T dpow[5][9];   // D^n, n = 0..4
-  double* dots;   // [10]: d/d a_n of Psi_E (0..4) and Psi_B (5..9), accumulated
+  double* dots;     // [10]: d/d a_n of Psi_E (0..4) and Psi_B (5..9), accumulated
+  double* partial;  // adj_psi_partial_doubles() of block partial sums (scratch)
 };
 template <typename T>
 cudaError_t launch_adj_psi(const AdjPsiArgs<T>& a, cudaStream_t st);
+size_t adj_psi_partial_doubles();
 
 }  // namespace picgb

@@ -226,3 +226,25 @@ def test_adjoint_256x512_100_steps():
     assert fwd < 2e-2
     assert np.abs(ge32 - ge64).max() <= max(3 * fwd, 1e-4) * np.abs(ge64).max()
     assert np.abs(gb32 - gb64).max() <= max(3 * fwd, 1e-4) * np.abs(gb64).max()
+
+
+def test_gradient_step_lowers_late_time_energy():
+    # the use the gradient is for: a small step of the Psi_E coefficients against dW_perp/da lowers
+    # W_perp(T) of the same seeded run (gamma = 130 beam, 40 steps)
+    cfg = P.pic_config_default(nx=64, nz=128, dt=0.5, gamma=130.0, precision=P.PIC_FP64, ppc_per_species=4,
+                               init_beam=1, track_ids=1, seed=21)
+    pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, 0.5)
+    h = P.pic_create(cfg)
+    P.pic_set_correction_stencil(h, pe, pb)
+    w0 = P.pic_adjoint_forward(h, 40, 10)
+    ge, _ = P.pic_adjoint_backward(h, 1.0)
+    P.pic_destroy(h)
+    step = 1e-2 * np.linalg.norm(pe) / np.linalg.norm(ge)
+    h = P.pic_create(cfg)
+    P.pic_set_correction_stencil(h, pe - step * ge, pb)
+    P.pic_step(h, 40)
+    w1 = P.pic_energy(h)["w_perp"]
+    P.pic_destroy(h)
+    predicted = -step * float(ge @ ge)
+    assert w1 < w0
+    assert abs((w1 - w0) - predicted) <= 0.1 * abs(predicted)  # first-order prediction holds

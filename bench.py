@@ -489,7 +489,7 @@ def run_adjoint(args):
 
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
-    nsteps, every, alpha = 100, 10, 0.5
+    nsteps, every, alpha = args.adjoint_steps, 10, 0.5
     pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, alpha)
 
     def cfg(prec):
@@ -532,15 +532,17 @@ def run_adjoint(args):
         t_f, t_b, t_p = (float(np.median([r[i] for r in reps])) for i in range(3))
         res[name] = {"w_perp": w, "grad_psi_e": ge.tolist(), "grad_psi_b": gb.tolist(), "ms_forward_checkpointed": t_f,
                      "ms_backward": t_b, "ms_plain_forward": t_p, "adjoint_over_forward": (t_f + t_b) / t_p}
-    fd = []
-    for n in range(5):
-        d = np.zeros(5)
-        d[n] = 1e-3
-        fd.append((w_after(P.PIC_FP64, pe + d) - w_after(P.PIC_FP64, pe - d)) / 2e-3)
-    fd = np.array(fd)
-    for name in ("f32", "f64"):
-        ge = np.array(res[name]["grad_psi_e"])
-        res[name]["max_rel_err_vs_central_differences"] = float(np.abs(ge - fd).max() / np.abs(fd).max())
+    fd = None
+    if not args.no_fd:
+        fd = []
+        for n in range(5):
+            d = np.zeros(5)
+            d[n] = 1e-3
+            fd.append((w_after(P.PIC_FP64, pe + d) - w_after(P.PIC_FP64, pe - d)) / 2e-3)
+        fd = np.array(fd)
+        for name in ("f32", "f64"):
+            ge = np.array(res[name]["grad_psi_e"])
+            res[name]["max_rel_err_vs_central_differences"] = float(np.abs(ge - fd).max() / np.abs(fd).max())
     np_ = 256 * 512 * 8 * 2
     r32 = res["f32"]
     value = np_ * nsteps / ((r32["ms_forward_checkpointed"] + r32["ms_backward"]) / 1e3)
@@ -549,10 +551,59 @@ def run_adjoint(args):
             "ms_per_step": (r32["ms_forward_checkpointed"] + r32["ms_backward"]) / nsteps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "adjoint: 2D 256x512, 8 particles/cell/species (2,097,152 particles), gamma 130, "
-                                   "c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), 100 steps, checkpoint "
+                                   f"c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), {nsteps} steps, checkpoint "
                                    "every 10; gradient of W_perp(T) w.r.t. Psi_E, Psi_B and E0/B0",
-                       "central_differences": {"h": 1e-3, "forward": "FP64 library run", "grad_psi_e": fd.tolist()}},
+                       "central_differences": None if fd is None else
+                       {"h": 1e-3, "forward": "FP64 library run", "grad_psi_e": fd.tolist()}},
             "f32": r32, "f64": res["f64"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_3d(args):
+    """The 3D workload: 128 x 128 x 512, 8 particles/cell/species (134,217,728 particles), transverse
+    Gaussian weights (sigma 20 cells), gamma 130, c dt/dz 0.5, Galerkin, correction + filter
+    (1, 1, a = 3), FP32. Same timing as the default line; roofline with the 3D bytes per particle."""
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    peak, peak_kind = measured_hbm_peak()
+    cfg = P.pic_config_default(ndim=3, nx=128, ny=128, nz=512, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN,
+                               precision=P.PIC_FP32, ppc_per_species=8, sigma_perp=20.0, seed=3, init_beam=1,
+                               diag_every=1)
+    h = P.pic_create(cfg)
+    P.pic_set_stream(h, stream.cuda_stream)
+    P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, 0.5))
+    ncell = cfg.nx * cfg.ny * cfg.nz
+    np_ = P.pic_num_particles(h)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            P.pic_step(h, 1)
+    P.pic_sync(h)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
+    clk = clocks.stop()
+    hist = P.pic_energy_history(h, 1)
+    assert hist and hist[-1]["np"] == np_, "particle count changed"
+    P.pic_destroy(h)
+    push_ms, push_n = kt["push"]
+    per_launch_s = push_ms / 1e3 / max(push_n, 1)
+    bytes_per_launch = np_ * 56 + ncell * 36  # 3 offsets + 3 momenta + weight each way; gather + J
+    achieved = bytes_per_launch / per_launch_s / 1e9
+    line = {"metric": METRIC, "value": np_ * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "3D 128x128x512, 8 particles/cell/species (134M particles), Gaussian transverse "
+                                   "weights sigma 20 cells, gamma 130, c dt/dz 0.5, Galerkin, correction + filter "
+                                   "(1,1,a=3), FP32", "particles": np_},
+            "roofline": {"kernel": "k_push", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": round(per_launch_s * 1e3, 4)},
+            "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
+            "cell_updates_per_s": ncell * args.steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -572,6 +623,9 @@ def main(argv=None):
     ap.add_argument("--sweep-seq-steps", type=int, default=40)
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint (256x512, 100 steps) instead")
     ap.add_argument("--adjoint-reps", type=int, default=3)
+    ap.add_argument("--adjoint-steps", type=int, default=100)
+    ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
+    ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args(argv)
@@ -583,6 +637,8 @@ def main(argv=None):
         run_sweep(args)
     elif args.adjoint:
         run_adjoint(args)
+    elif args.config3d:
+        run_3d(args)
     else:
         run_ours(args)
 

@@ -301,45 +301,6 @@ struct GalCache<T, 2> {
   }
 };
 
-// The same Galerkin interpolation read straight from the shared-memory tile (no per-lane cache).
-template <typename T, int NDIM>
-__device__ __forceinline__ void gal_interp(const T* sg, int lx, int ly, int lz, T ox, T oy, T oz, T (&F)[6]) {
-  using S = PushSmem<T, NDIM>;
-  if (NDIM == 2) {
-    const int p = (lz + 1) * S::GX + lx + 1;
-    const T* e = sg;
-    F[0] = e[p] + oz * (e[p + S::GX] - e[p]);
-    e = sg + S::GN;
-    const T a = e[p] + ox * (e[p + 1] - e[p]);
-    const T b = e[p + S::GX] + ox * (e[p + S::GX + 1] - e[p + S::GX]);
-    F[1] = a + oz * (b - a);
-    e = sg + 2 * S::GN;
-    F[2] = e[p] + ox * (e[p + 1] - e[p]);
-    e = sg + 3 * S::GN;
-    F[3] = e[p] + ox * (e[p + 1] - e[p]);
-    F[4] = sg[4 * S::GN + p];
-    e = sg + 5 * S::GN;
-    F[5] = e[p] + oz * (e[p + S::GX] - e[p]);
-  } else {
-    const int p = ((lz + 1) * S::GY + ly + 1) * S::GX + lx + 1;
-    const int sx = 1, sy = S::GX, sz = S::GX * S::GY;
-    auto bil = [&](const T* f, int s1, int s2, T u, T v) {
-      const T a = f[p] + u * (f[p + s1] - f[p]);
-      const T b = f[p + s2] + u * (f[p + s2 + s1] - f[p + s2]);
-      return a + v * (b - a);
-    };
-    F[0] = bil(sg, sy, sz, oy, oz);
-    F[1] = bil(sg + S::GN, sx, sz, ox, oz);
-    F[2] = bil(sg + 2 * S::GN, sx, sy, ox, oy);
-    const T* e = sg + 3 * S::GN;
-    F[3] = e[p] + ox * (e[p + sx] - e[p]);
-    e = sg + 4 * S::GN;
-    F[4] = e[p] + oy * (e[p + sy] - e[p]);
-    e = sg + 5 * S::GN;
-    F[5] = e[p] + oz * (e[p + sz] - e[p]);
-  }
-}
-
 template <typename T>
 struct GalCache<T, 3> {
   // Ex: S0 x, bilinear (y, z). Ey: S0 y, bilinear (x, z). Ez: S0 z, bilinear (x, y).
@@ -621,6 +582,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   if (g < NGRP) issue(g, 0, 0);
   cp_async_commit();
   T acc[NVP];
+  GalCache<T, NDIM> gc;  // Galerkin nodes of the lane's cell, loaded once per cell group
   while (g < NGRP) {
     // prefetch the next item
     int ng = g, nit = it + 1, niters = giters;
@@ -643,6 +605,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     const int nq0 = (n0 + 3) >> 2, nq = nq0 + ((n1 + 3) >> 2);
     const int okey = ((lz + 1) * S::JY + (NDIM == 3 ? ly + 1 : 0)) * S::JX + lx + 1;  // cell-origin window
     if (it == 0) {
+      if (SCHEME == 0) gc.load(sg, lx, ly, lz);
 #pragma unroll
       for (int i = 0; i < NVP; ++i) acc[i] = T(0);
     }
@@ -674,7 +637,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           // gather
           T F[6];
           if (SCHEME == 0) {
-            gal_interp<T, NDIM>(sg, lx, ly, lz, o_x, o_y, o_z, F);
+            gc.interp(o_x, o_y, o_z, F);
           } else {
             const DirW<T> dwx = dir_weights(o_x), dwy = dir_weights(o_y), dwz = dir_weights(o_z);
 #pragma unroll

@@ -302,3 +302,33 @@ def test_gauss_law_full_size_fp32():
         assert np.abs(g).max() < 2e-3 * scale
     finally:
         P.pic_destroy(h)
+
+
+def test_gauss_law_full_size_3d_fp32():
+    # the 3D workload at full size (128x128x512, 8 ppc/species, 134M particles, Gaussian transverse
+    # weights, FP32, correction + filter): after steps from the seeded beam, div E - F rho (oracle rho
+    # of the GPU particles, oracle filter) stays at roundoff, and no particle is lost
+    cfg = make_cfg(ndim=3, nx=128, ny=128, nz=512, dt=0.5, precision=0, ppc=8, init_beam=1, seed=3,
+                   sigma_perp=20.0, track_ids=0)
+    psi = _coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    try:
+        P.pic_set_correction_stencil(h, *psi)
+        n0 = P.pic_num_particles(h)
+        assert n0 == 128 * 128 * 512 * 16
+        P.pic_step(h, 2)
+        pair = object.__new__(Pair)
+        pair.cfg, pair.h, pair.T = cfg, h, np.float32
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.o = O.Sim(ndim=3, nx=128, ny=128, nz=512, dt=0.5)
+        f, p = pair.gpu_state()
+        assert len(p["x"]) == n0
+        o = pair.o
+        o.set_particles(p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"], p["w"], p["q"])
+        del p
+        o.f.update({n: f[n].reshape(o.shape).copy() for n in FIELDS})
+        g = o.div_e() - o.filter(o.rho())
+        scale = uniform_weight(cfg)  # one macro-particle's (peak) charge density
+        assert np.abs(g).max() < 2e-3 * scale
+    finally:
+        P.pic_destroy(h)

@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("psi_e", ctypes.c_double * 9), ("psi_b", ctypes.c_double * 9),
                 ("f_nbin", ctypes.c_int), ("f_ncomp", ctypes.c_int), ("f_alpha", ctypes.c_double),
-                ("f_targets", ctypes.c_int)]
+                ("f_targets", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -83,6 +83,8 @@ def _declare(L):
     L.orc_rational_coeffs.restype = ctypes.c_int
     L.orc_rational_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, _DP, _DP]
     L.orc_psi_taps.argtypes = [_DP, _DP]
+    L.orc_bspline.restype = ctypes.c_double
+    L.orc_bspline.argtypes = [ctypes.c_int, ctypes.c_double]
     L.orc_conv_axis.argtypes = [P(Params), _DP, ctypes.c_int, _DP, ctypes.c_int]
     L.orc_filter.argtypes = [P(Params), _DP]
     L.orc_gather_copies.argtypes = [P(Params), P(_Fields), _DP * 6]
@@ -122,6 +124,11 @@ def rational_coeffs(scheme: int, alpha: float):
     pb = np.zeros(5)
     st = lib().orc_rational_coeffs(scheme, alpha, _ptr(pe), _ptr(pb))
     return st, pe, pb
+
+
+def bspline(n: int, t: float) -> float:
+    """Centred cardinal B-spline of order n (0..3) at t (particle shapes, Sec. 3 uses n = 3)."""
+    return lib().orc_bspline(int(n), float(t))
 
 
 def psi_taps(a) -> np.ndarray:
@@ -169,7 +176,8 @@ class Sim:
     """
 
     def __init__(self, ndim=2, nx=16, ny=1, nz=16, dx=1.0, dy=1.0, dz=1.0, dt=0.5, scheme=GALERKIN,
-                 psi_e=None, psi_b=None, f_nbin=1, f_ncomp=1, f_alpha=3.0, f_targets=FILTER_J | FILTER_GATHER):
+                 psi_e=None, psi_b=None, f_nbin=1, f_ncomp=1, f_alpha=3.0, f_targets=FILTER_J | FILTER_GATHER,
+                 order=1):
         if ndim == 2:
             ny, dy = 1, 1.0
         self.p = Params()
@@ -177,6 +185,7 @@ class Sim:
         self.p.dx, self.p.dy, self.p.dz, self.p.dt = dx, dy, dz, dt
         self.p.scheme = scheme
         self.p.f_nbin, self.p.f_ncomp, self.p.f_alpha, self.p.f_targets = f_nbin, f_ncomp, f_alpha, f_targets
+        self.p.order = order
         self.set_correction(psi_e, psi_b)
         self.shape = (nz, ny, nx)
         self.f = {n: np.zeros(self.shape) for n in FIELD_NAMES}

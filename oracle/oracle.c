@@ -51,6 +51,7 @@ typedef struct {
   int f_ncomp;            /* compensation passes per direction, per side */
   double f_alpha;         /* compensation centre weight (3 in the paper's filter) */
   int f_targets;          /* bit 0: filter J; bit 1: filter the gather copies */
+  int order;              /* particle shape order: 1 (linear) or 3 (cubic) */
 } orc_params;
 
 typedef struct {
@@ -304,18 +305,46 @@ static double S1(double d) {
 }
 
 /*
+ * Centred cardinal B-spline of order n (n = 0..3) at t, in cell units: S0 the
+ * box [-1/2, 1/2), S1 the hat, S2 the quadratic and S3 the cubic spline (each
+ * the box convolved with the previous one). Sec. 3 runs with cubic shapes.
+ */
+static double bspline(int n, double t) {
+  double a = fabs(t);
+  switch (n) {
+    case 0:
+      return (t >= -0.5 && t < 0.5) ? 1.0 : 0.0;
+    case 1:
+      return S1(t);
+    case 2:
+      if (a <= 0.5) return 0.75 - a * a;
+      if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+      return 0.0;
+    case 3:
+      if (a <= 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+      if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+      return 0.0;
+    default:
+      return NAN;
+  }
+}
+
+double orc_bspline(int n, double t) { return bspline(n, t); }
+
+/*
  * Interpolate one component at grid-unit position (x[0..2]) with stagger
  * st[axis] (0: nodes at integers, 1: nodes at half-integers) and spline order
- * ord[axis] (1: S1 on the two nearest nodes, 0: S0, the width-1 box, i.e. the
- * one node whose box [node-1/2, node+1/2) holds the position).
- * Galerkin: order 0 along each direction in which the component is half
- * staggered, order 1 along the others (the ratio of Eq. 3 to Eq. 4 is s/sin s,
- * the ratio of the S0 and S1 transforms). Uniform: order 1 everywhere.
+ * ord[axis] (0..3): the ord+1 nodes of this component's lattice nearest the
+ * position, weighted by the B-spline of that order.
+ * Galerkin: one order lower along each direction in which the component is
+ * half staggered, the particle shape order along the others (the ratio of
+ * Eq. 3 to Eq. 4 is s/sin s, the ratio of the transforms of consecutive
+ * B-splines). Uniform: the shape order everywhere.
  */
 static double gather1(const orc_params* p, const double* F, const double x[3], const int st[3], const int ord[3]) {
   int n[3] = {p->nx, p->ny, p->nz};
   int base[3], cnt[3];
-  double wt[3][2];
+  double wt[3][4];
   for (int a = 0; a < 3; ++a) {
     if (a == 1 && p->ndim == 2) {
       base[a] = 0;
@@ -324,17 +353,11 @@ static double gather1(const orc_params* p, const double* F, const double x[3], c
       continue;
     }
     double xs = x[a] - 0.5 * st[a]; /* coordinate in units of this component's node lattice */
-    if (ord[a] == 1) {
-      double fl = floor(xs);
-      base[a] = (int)fl;
-      cnt[a] = 2;
-      wt[a][0] = S1(xs - fl);
-      wt[a][1] = S1(xs - (fl + 1.0));
-    } else {
-      base[a] = (int)floor(xs + 0.5);
-      cnt[a] = 1;
-      wt[a][0] = 1.0;
-    }
+    int o = ord[a];
+    /* first node: floor(xs) - (o-1)/2 for odd orders, floor(xs + 1/2) - o/2 for even ones */
+    base[a] = (o % 2) ? (int)floor(xs) - (o - 1) / 2 : (int)floor(xs + 0.5) - o / 2;
+    cnt[a] = o + 1;
+    for (int q = 0; q < cnt[a]; ++q) wt[a][q] = bspline(o, xs - (double)(base[a] + q));
   }
   double acc = 0.0;
   for (int c = 0; c < cnt[2]; ++c)
@@ -349,12 +372,59 @@ static double gather1(const orc_params* p, const double* F, const double x[3], c
 /* Stagger of Ex, Ey, Ez, Bx, By, Bz along x, y, z. */
 static const int STAG[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
 
+/*
+ * Momentum-conserving scheme (the one Eq. 5 belongs to): a component averaged
+ * from its Yee location to the node (i, j, k), i.e. over the two neighbours
+ * along each direction in which it is half staggered.
+ */
+static double node_average(const orc_params* p, const double* F, int c, int i, int j, int k) {
+  int n[3] = {p->nx, p->ny, p->nz};
+  int lo[3] = {i, j, k};
+  int m[3];
+  for (int a = 0; a < 3; ++a) m[a] = STAG[c][a] ? 2 : 1;
+  double acc = 0.0;
+  for (int dc = 0; dc < m[2]; ++dc)
+    for (int db = 0; db < m[1]; ++db)
+      for (int da = 0; da < m[0]; ++da)
+        acc += F[idx3(p, wrap(lo[0] - da, n[0]), wrap(lo[1] - db, n[1]), wrap(lo[2] - dc, n[2]))];
+  return acc / (double)(m[0] * m[1] * m[2]);
+}
+
+static double gather_momentum(const orc_params* p, const double* F, int c, const double x[3]) {
+  int n[3] = {p->nx, p->ny, p->nz};
+  int o = p->order;
+  int base[3], cnt[3];
+  double wt[3][4];
+  for (int a = 0; a < 3; ++a) {
+    if (a == 1 && p->ndim == 2) {
+      base[a] = 0;
+      cnt[a] = 1;
+      wt[a][0] = 1.0;
+      continue;
+    }
+    base[a] = (int)floor(x[a]) - (o - 1) / 2;
+    cnt[a] = o + 1;
+    for (int q = 0; q < cnt[a]; ++q) wt[a][q] = bspline(o, x[a] - (double)(base[a] + q));
+  }
+  double acc = 0.0;
+  for (int cc = 0; cc < cnt[2]; ++cc)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int a = 0; a < cnt[0]; ++a)
+        acc += wt[0][a] * wt[1][b] * wt[2][cc] *
+               node_average(p, F, c, wrap(base[0] + a, n[0]), wrap(base[1] + b, n[1]), wrap(base[2] + cc, n[2]));
+  return acc;
+}
+
 /* Gather the six components from field arrays G[6] at particle position. */
 void orc_gather_point(const orc_params* p, double* const G[6], double x, double y, double z, double out[6]) {
   double pos[3] = {x, y, z};
   for (int c = 0; c < 6; ++c) {
+    if (p->scheme == ORC_MOMENTUM) {
+      out[c] = gather_momentum(p, G[c], c, pos);
+      continue;
+    }
     int ord[3];
-    for (int a = 0; a < 3; ++a) ord[a] = (p->scheme == ORC_GALERKIN) ? 1 - STAG[c][a] : 1;
+    for (int a = 0; a < 3; ++a) ord[a] = (p->scheme == ORC_GALERKIN) ? p->order - STAG[c][a] : p->order;
     out[c] = gather1(p, G[c], pos, STAG[c], ord);
   }
 }
@@ -429,15 +499,62 @@ static double s1_change(double a0, double d) {
   return S1(a1) - S1(a0);
 }
 
-/* S0 and dS on the window nodes lo+a, a = 0..FP-1, for one direction */
-static void shape_window(double r0, double dr, int* lo, double S0[FP], double dS[FP]) {
+/*
+ * Cubic spline: its polynomial pieces are (-2,-1], (-1,0], (0,1], (1,2); on one
+ * piece P(a0 - d) - P(a0) = -d P'(a0) + d^2/2 P''(a0) - d^3/6 P'''(a0) exactly
+ * (the Taylor series of a cubic ends there), which keeps full relative
+ * precision for small moves; across a knot the two values are subtracted.
+ */
+static int s3_piece(double t) {
+  return t <= -2.0 ? 0 : t <= -1.0 ? 1 : t <= 0.0 ? 2 : t <= 1.0 ? 3 : t < 2.0 ? 4 : 5;
+}
+
+static double s3_change(double a0, double d) {
+  double a1 = a0 - d;
+  int p = s3_piece(a0);
+  if (p != s3_piece(a1)) return bspline(3, a1) - bspline(3, a0);
+  double d1, d2, d3; /* P', P'', P''' at a0 */
+  switch (p) {
+    case 1:
+      d1 = 0.5 * (2.0 + a0) * (2.0 + a0);
+      d2 = 2.0 + a0;
+      d3 = 1.0;
+      break;
+    case 2:
+      d1 = -2.0 * a0 - 1.5 * a0 * a0;
+      d2 = -2.0 - 3.0 * a0;
+      d3 = -3.0;
+      break;
+    case 3:
+      d1 = -2.0 * a0 + 1.5 * a0 * a0;
+      d2 = -2.0 + 3.0 * a0;
+      d3 = 3.0;
+      break;
+    case 4:
+      d1 = -0.5 * (2.0 - a0) * (2.0 - a0);
+      d2 = 2.0 - a0;
+      d3 = -1.0;
+      break;
+    default:
+      return 0.0; /* outside the support on both sides */
+  }
+  return -d * d1 + 0.5 * d * d * d2 - d * d * d * d3 / 6.0;
+}
+
+/* S0 and dS of the particle shape (order 1 or 3) on the window nodes lo+a, a = 0..FP-1, for one direction */
+static void shape_window(int order, double r0, double dr, int* lo, double S0[FP], double dS[FP]) {
   double c = floor(r0);
   double o = r0 - c;
   *lo = (int)c - 2;
   for (int a = 0; a < FP; ++a) {
     double node = a - 2; /* relative to the start cell */
-    S0[a] = S1(node - o);
-    dS[a] = s1_change(node - o, dr);
+    if (order == 3) {
+      S0[a] = bspline(3, node - o);
+      dS[a] = s3_change(node - o, dr);
+    } else {
+      S0[a] = S1(node - o);
+      dS[a] = s1_change(node - o, dr);
+    }
   }
 }
 
@@ -446,8 +563,8 @@ void orc_deposit_2d(const orc_params* p, orc_fields* F, double x0, double z0, do
   double dV = p->dx * p->dy * p->dz;
   int ia, ka;
   double S0x[FP], dSx[FP], S0z[FP], dSz[FP];
-  shape_window(x0, ddx, &ia, S0x, dSx);
-  shape_window(z0, ddz, &ka, S0z, dSz);
+  shape_window(p->order, x0, ddx, &ia, S0x, dSx);
+  shape_window(p->order, z0, ddz, &ka, S0z, dSz);
   double cx = -qw * p->dx / (dV * p->dt);
   double cz = -qw * p->dz / (dV * p->dt);
   double cy = qw * vy / dV;
@@ -478,7 +595,7 @@ void orc_deposit_3d(const orc_params* p, orc_fields* F, const double r0[3], cons
   double d[3] = {p->dx, p->dy, p->dz};
   int lo[3];
   double S0[3][FP], dS[3][FP];
-  for (int ax = 0; ax < 3; ++ax) shape_window(r0[ax], dr[ax], &lo[ax], S0[ax], dS[ax]);
+  for (int ax = 0; ax < 3; ++ax) shape_window(p->order, r0[ax], dr[ax], &lo[ax], S0[ax], dS[ax]);
   double* J[3] = {F->jx, F->jy, F->jz};
   for (int ax = 0; ax < 3; ++ax) {
     int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3; /* the two transverse axes */
@@ -511,17 +628,17 @@ void orc_rho(const orc_params* p, const orc_particles* P, double* rho) {
     double r[3] = {P->x[m], p->ndim == 3 ? P->y[m] : 0.0, P->z[m]};
     int n[3] = {p->nx, p->ny, p->nz};
     int b[3];
-    double wt[3][2];
+    double wt[3][4];
+    const int o = p->order, nn = o + 1; /* the shape's o+1 nodes per direction */
     for (int a = 0; a < 3; ++a) {
       double fl = floor(r[a]);
-      b[a] = (int)fl;
-      wt[a][0] = S1(r[a] - fl);
-      wt[a][1] = S1(r[a] - (fl + 1.0));
+      b[a] = (int)fl - (o - 1) / 2;
+      for (int q = 0; q < nn; ++q) wt[a][q] = bspline(o, r[a] - (double)(b[a] + q));
     }
-    int cy = p->ndim == 3 ? 2 : 1;
-    for (int c = 0; c < 2; ++c)
+    int cy = p->ndim == 3 ? nn : 1;
+    for (int c = 0; c < nn; ++c)
       for (int bb = 0; bb < cy; ++bb)
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < nn; ++a) {
           double wy = p->ndim == 3 ? wt[1][bb] : 1.0;
           rho[idx3(p, wrap(b[0] + a, n[0]), wrap(b[1] + bb, n[1]), wrap(b[2] + c, n[2]))] +=
               P->q[m] * P->w[m] * wt[0][a] * wy * wt[2][c] / dV;

@@ -30,7 +30,7 @@ def make_cfg(ndim=2, nx=40, ny=1, nz=72, dt=0.5, gamma=130.0, scheme=0, precisio
 def oracle_for(cfg, psi_e=None, psi_b=None) -> O.Sim:
     return O.Sim(ndim=cfg.ndim, nx=cfg.nx, ny=cfg.ny, nz=cfg.nz, dx=cfg.dx, dy=cfg.dy, dz=cfg.dz, dt=cfg.dt,
                  scheme=cfg.scheme, psi_e=psi_e, psi_b=psi_b, f_nbin=cfg.filter_nbin, f_ncomp=cfg.filter_ncomp,
-                 f_alpha=cfg.filter_comp_alpha, f_targets=cfg.filter_targets)
+                 f_alpha=cfg.filter_comp_alpha, f_targets=cfg.filter_targets, order=cfg.shape_order)
 
 
 def uniform_weight(cfg):

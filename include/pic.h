@@ -48,7 +48,7 @@ extern "C" {
 
 #define PIC_GALERKIN 0
 #define PIC_UNIFORM 1
-#define PIC_MOMENTUM 2 /* multiplier only (pic_compute_correction_coeffs); no gather yet */
+#define PIC_MOMENTUM 2 /* momentum-conserving gather: fields averaged to the nodes (Eq. 5 multiplier) */
 
 #define PIC_FP32 0
 #define PIC_FP64 1
@@ -68,7 +68,7 @@ typedef struct pic_config {
   double dx, dy, dz, dt;    /* cell sizes and time step (c = 1); dy forced to 1 in 2D */
   double gamma;             /* Lorentz factor of the beam drift along +z */
   int scheme;               /* PIC_GALERKIN or PIC_UNIFORM field gather */
-  int shape_order;          /* 1 (linear particle shapes) */
+  int shape_order;          /* particle shape: 1 (linear) or 3 (cubic B-spline, the Sec. 3 setting) */
   int precision;            /* PIC_FP32 or PIC_FP64 (fields, particles and kernels) */
   int ppc_per_species;      /* lattice points per cell per species of the initial beam */
   double omega_p_dz;        /* total plasma frequency (both species) times dz / c */
@@ -238,7 +238,8 @@ int pic_field_energy_noalloc(const void* const fields[6], long long ncell, int p
  * a CUDA graph. The runs must agree on ndim, precision, scheme, shape order, filter and diagnostic
  * settings, per-particle weights and id tracking (PIC_E_ARG otherwise); grids, ppc, gamma, dt,
  * seeds and corrections may differ. Each grid needs at least as many cells per direction as the
- * stencil halos (PIC_E_ARG otherwise).
+ * stencil halos (PIC_E_ARG otherwise). Batched runs use linear shapes with the Galerkin or Uniform
+ * gather (cubic shapes or the momentum-conserving gather: PIC_E_ARG).
  */
 typedef struct pic_batch pic_batch;
 int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out);
@@ -273,7 +274,8 @@ const char* pic_batch_last_error(const pic_batch* b);
  * every checkpoint_every steps and at the end, in device memory the handle keeps until
  * pic_adjoint_release or pic_destroy: (nsteps / checkpoint_every + 2 + checkpoint_every) states of
  * about N x (8 + 5 x element size) bytes for N particles, plus 6 field arrays each.
- * 2D runs only (PIC_E_ARG otherwise), and cfg.track_ids = 1 with ids 0 .. N-1, as the seeded beam
+ * 2D runs with linear shapes and the Galerkin or Uniform gather only (PIC_E_ARG otherwise), and
+ * cfg.track_ids = 1 with ids 0 .. N-1, as the seeded beam
  * and any import without explicit ids have (PIC_E_STATE otherwise).
  *
  * pic_adjoint_backward, with the state still the final state of the recorded run (no step, state

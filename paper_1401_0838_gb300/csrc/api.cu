@@ -357,7 +357,10 @@ int step_once(pic_handle* h) {
   // 2-5. gather, Boris, move, Esirkepov, rebin
   RunDev<T> r = make_run<T>(h, h->parity);
   r.kin = rec ? h->d_kin : nullptr;
-  CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
+  if (h->cfg.shape_order == 1 && h->cfg.scheme != PIC_MOMENTUM)
+    CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
+  else
+    CK(launch(h, PIC_K_PUSH, [&] { return launch_push_ho<T>(r, h->cfg.shape_order, h->cfg.scheme, st); }), "push");
   CK(launch(h, PIC_K_MIGRATE, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }),
      "migrate");
   // 6. current filter
@@ -628,8 +631,10 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
     c.dy = 1.0;
   }
   if ((c.ndim != 2 && c.ndim != 3) || c.nx < 1 || c.ny < 1 || c.nz < 1 || !(c.dx > 0) || !(c.dy > 0) ||
-      !(c.dz > 0) || !(c.dt > 0) || !(c.gamma >= 1.0) || (c.scheme != PIC_GALERKIN && c.scheme != PIC_UNIFORM) ||
-      c.shape_order != 1 || (c.precision != PIC_FP32 && c.precision != PIC_FP64) || c.ppc_per_species < 0 ||
+      !(c.dz > 0) || !(c.dt > 0) || !(c.gamma >= 1.0) ||
+      (c.scheme != PIC_GALERKIN && c.scheme != PIC_UNIFORM && c.scheme != PIC_MOMENTUM) ||
+      (c.shape_order != 1 && c.shape_order != 3) || (c.precision != PIC_FP32 && c.precision != PIC_FP64) ||
+      c.ppc_per_species < 0 ||
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
       c.diag_every < 0 || c.diag_capacity < 0 ||
       (long long)c.nx * c.ny * c.nz > (1ll << 30) - 1)
@@ -1243,6 +1248,7 @@ int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
         (c.track_ids != 0) != (c0.track_ids != 0))
       return PIC_E_ARG;  // these must agree across the runs of one batch
   }
+  if (c0.shape_order != 1 || c0.scheme == PIC_MOMENTUM) return PIC_E_ARG;  // batched: linear Galerkin / Uniform
   pic_batch* b = new pic_batch();
   b->es = c0.precision == PIC_FP32 ? 4 : 8;
   b->ndim = c0.ndim;
@@ -1829,6 +1835,8 @@ extern "C" {
 int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double* w_perp) {
   if (!h || nsteps < 0 || checkpoint_every < 1 || !w_perp) return PIC_E_ARG;
   if (h->cfg.ndim != 2) return fail(h, PIC_E_ARG, "the adjoint covers 2D runs");
+  if (h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM)
+    return fail(h, PIC_E_ARG, "the adjoint covers linear shapes with the Galerkin or Uniform gather");
   if (!h->has_id) return fail(h, PIC_E_STATE, "the adjoint needs particle ids (cfg.track_ids = 1)");
   if (h->ncell >= (1LL << 31)) return fail(h, PIC_E_ARG, "the adjoint covers grids below 2^31 cells");
   return h->es == 4 ? adjoint_forward_t<float>(h, nsteps, checkpoint_every, w_perp)

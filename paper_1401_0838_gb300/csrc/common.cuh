@@ -45,7 +45,7 @@ struct RunDev {
   long long ncell;
   int ntx, nty, ntz;  // particle tiles per direction
   int cap;            // slots per cell per species
-  int scheme;         // 0 Galerkin, 1 Uniform
+  int scheme;         // 0 Galerkin, 1 Uniform, 2 momentum-conserving
   T dtdx, dtdy, dtdz; // dt / d (grid units per unit velocity)
   T u0;               // drift momentum sqrt(gamma^2 - 1)
   T hq;               // dt / 2 (Boris half-kick for unit charge and mass)

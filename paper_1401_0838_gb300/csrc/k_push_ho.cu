@@ -1,0 +1,511 @@
+// Particle step for cubic shapes (Sec. 3 runs with cubic interpolation) and for the
+// momentum-conserving gather (the scheme Eq. 5 belongs to): gather, Boris push, move, Esirkepov
+// deposition and rebin in one kernel, for any (shape order 1 or 3) x (Galerkin, Uniform,
+// momentum-conserving) combination in 2D and 3D. The linear Galerkin / Uniform step has its own,
+// more specialised kernel (k_particles.cu); this one keeps a plain structure: one CTA per particle
+// tile, the field copies and the tile's current in shared memory, one thread per cell walking the
+// cell's particles, the deposit added with shared-memory atomics.
+//
+// Shapes: centred B-splines S_n (S0 box, S1 hat, S2 quadratic, S3 cubic). Gather along a
+// direction: Uniform uses the particle shape order n at the component's own (staggered) nodes;
+// Galerkin uses order n-1 along each direction in which the component is half staggered; the
+// momentum-conserving scheme averages every component from its Yee location to the nodes and
+// interpolates with S_n there. Deposit: Esirkepov's W from S_n at the old position and the shape
+// change dS, formed from the displacement on each polynomial piece (exact, full relative
+// precision for small moves), the plain difference across a knot.
+#include "common.cuh"
+#include "launch.h"
+
+namespace picgb {
+
+namespace {
+
+constexpr int HO_THREADS = 256;
+
+template <int NDIM>
+struct HoTile;
+template <>
+struct HoTile<2> {
+  static constexpr int TX = 16, TY = 1, TZ = 16;  // the particle tiles of push_tiles()
+};
+template <>
+struct HoTile<3> {
+  static constexpr int TX = 8, TY = 8, TZ = 8;
+};
+
+// Geometry of the shared-memory tiles for shape order ORDER: the field tile holds nodes
+// [-H, T + H) per direction, the current tile nodes [-H, T + H + 1), H = (ORDER + 1) / 2.
+template <int NDIM, int ORDER>
+struct HoGeom {
+  using TL = HoTile<NDIM>;
+  static constexpr int H = (ORDER + 1) / 2;
+  static constexpr int GX = TL::TX + 2 * H, GY = NDIM == 3 ? TL::TY + 2 * H : 1, GZ = TL::TZ + 2 * H;
+  static constexpr int GN = GX * GY * GZ;
+  static constexpr int JX = TL::TX + 2 * H + 1, JY = NDIM == 3 ? TL::TY + 2 * H + 1 : 1, JZ = TL::TZ + 2 * H + 1;
+  static constexpr int JN = JX * JY * JZ;
+  static constexpr int NCL = TL::TX * TL::TY * TL::TZ;
+  static constexpr int NW = ORDER == 3 ? 6 : 4;   // deposit window nodes per direction
+  static constexpr int K0 = ORDER == 3 ? -2 : -1;  // first window node relative to the start cell
+  template <typename T>
+  static constexpr size_t bytes() {
+    return sizeof(T) * (6 * (size_t)GN + 3 * (size_t)JN) + sizeof(int) * 4 * (size_t)NCL;
+  }
+};
+
+// Periodic index of any g.
+__device__ __forceinline__ int wrap_any(int g, int n) {
+  if (g < 0) {
+    g += n;
+    if (g < 0) g = wrapi(g, n);
+  } else if (g >= n) {
+    g -= n;
+    if (g >= n) g %= n;
+  }
+  return g;
+}
+
+// Centred B-splines.
+template <typename T>
+__device__ __forceinline__ T bspl(int n, T t) {
+  const T a = t < T(0) ? -t : t;
+  if (n == 0) return (t >= T(-0.5) && t < T(0.5)) ? T(1) : T(0);
+  if (n == 1) return a < T(1) ? T(1) - a : T(0);
+  if (n == 2) {
+    if (a <= T(0.5)) return T(0.75) - a * a;
+    if (a < T(1.5)) return T(0.5) * (T(1.5) - a) * (T(1.5) - a);
+    return T(0);
+  }
+  if (a <= T(1)) return T(2.0 / 3.0) - a * a + T(0.5) * a * a * a;
+  if (a < T(2)) return (T(2) - a) * (T(2) - a) * (T(2) - a) * T(1.0 / 6.0);
+  return T(0);
+}
+
+// S_n(a0 - d) - S_n(a0) for the particle shape (n = 1 or 3): on one polynomial piece from the
+// displacement (linear: slope times -d; cubic: the terminating Taylor series), else the difference.
+template <typename T>
+__device__ __forceinline__ T shape_change(int n, T a0, T d) {
+  const T a1 = a0 - d;
+  if (n == 1) {
+    const int p0 = (a0 > T(-1)) + (a0 > T(0)) + (a0 >= T(1)), p1 = (a1 > T(-1)) + (a1 > T(0)) + (a1 >= T(1));
+    if (p0 == p1) return p0 == 1 ? -d : (p0 == 2 ? d : T(0));
+    return bspl(1, a1) - bspl(1, a0);
+  }
+  const int p0 = (a0 > T(-2)) + (a0 > T(-1)) + (a0 > T(0)) + (a0 > T(1)) + (a0 >= T(2));
+  const int p1 = (a1 > T(-2)) + (a1 > T(-1)) + (a1 > T(0)) + (a1 > T(1)) + (a1 >= T(2));
+  if (p0 != p1) return bspl(3, a1) - bspl(3, a0);
+  T d1, d2, d3;  // P', P'', P''' of the piece at a0
+  switch (p0) {
+    case 1: d1 = T(0.5) * (T(2) + a0) * (T(2) + a0); d2 = T(2) + a0; d3 = T(1); break;
+    case 2: d1 = -T(2) * a0 - T(1.5) * a0 * a0; d2 = -T(2) - T(3) * a0; d3 = T(-3); break;
+    case 3: d1 = -T(2) * a0 + T(1.5) * a0 * a0; d2 = -T(2) + T(3) * a0; d3 = T(3); break;
+    case 4: d1 = -T(0.5) * (T(2) - a0) * (T(2) - a0); d2 = T(2) - a0; d3 = T(-1); break;
+    default: return T(0);
+  }
+  return -d * (d1 - d * (T(0.5) * d2 - d * d3 * T(1.0 / 6.0)));
+}
+
+// Gather weights along one direction for a position at cell-relative offset o: order `ord`
+// on the integer lattice (st = 0) or the half-integer lattice (st = 1). first = the first node
+// relative to the cell; w[0..ord].
+template <typename T>
+__device__ __forceinline__ void gweights(T o, int st, int ord, int& first, T (&w)[4]) {
+  const T xs = st ? o - T(0.5) : o;  // position in units of the component's node lattice, rel. to the cell
+  if (ord & 1) {
+    const int fl = xs < T(0) ? -1 : 0;
+    first = fl - (ord - 1) / 2;
+  } else {
+    const int fl = xs + T(0.5) >= T(1) ? 1 : (xs + T(0.5) < T(0) ? -1 : 0);
+    first = fl - ord / 2;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = q <= ord ? bspl(ord, xs - T(first + q)) : T(0);
+}
+
+// Stagger of Ex Ey Ez Bx By Bz along x, y, z.
+__device__ __constant__ int c_stag_ho[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+template <typename T, int NDIM, int ORDER, int SCHEME>
+__device__ __forceinline__ T gather_comp(const T* sgc, int c, int lx, int ly, int lz, T ox, T oy, T oz) {
+  using G = HoGeom<NDIM, ORDER>;
+  int fx, fy = 0, fz;
+  T wx[4], wy[4] = {T(1), T(0), T(0), T(0)}, wz[4];
+  int ox_ord, oy_ord = 0, oz_ord;
+  if (SCHEME == 2) {  // momentum-conserving: integer nodes, averaged tile
+    ox_ord = oy_ord = oz_ord = ORDER;
+    gweights(ox, 0, ORDER, fx, wx);
+    if (NDIM == 3) gweights(oy, 0, ORDER, fy, wy);
+    gweights(oz, 0, ORDER, fz, wz);
+  } else {
+    const int sx = c_stag_ho[c][0], sy = c_stag_ho[c][1], sz = c_stag_ho[c][2];
+    ox_ord = SCHEME == 0 ? ORDER - sx : ORDER;
+    oy_ord = SCHEME == 0 ? ORDER - sy : ORDER;
+    oz_ord = SCHEME == 0 ? ORDER - sz : ORDER;
+    gweights(ox, sx, ox_ord, fx, wx);
+    if (NDIM == 3) gweights(oy, sy, oy_ord, fy, wy);
+    gweights(oz, sz, oz_ord, fz, wz);
+  }
+  if (NDIM == 2) oy_ord = 0;
+  T acc = T(0);
+  for (int c3 = 0; c3 <= oz_ord; ++c3) {
+    const int iz = lz + fz + c3 + G::H;
+    for (int c2 = 0; c2 <= oy_ord; ++c2) {
+      const int iy = NDIM == 3 ? ly + fy + c2 + G::H : 0;
+      const T* row = sgc + (iz * G::GY + iy) * G::GX + lx + fx + G::H;
+      const T wyz = wz[c3] * wy[c2];
+      T r = T(0);
+      for (int c1 = 0; c1 <= ox_ord; ++c1) r += wx[c1] * row[c1];
+      acc += wyz * r;
+    }
+  }
+  return acc;
+}
+
+template <typename T, int NDIM, int ORDER, int SCHEME>
+__global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ RunDev<T> r) {
+  using G = HoGeom<NDIM, ORDER>;
+  using TL = HoTile<NDIM>;
+  constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sg = reinterpret_cast<T*>(smem_raw);
+  T* sj = sg + 6 * G::GN;
+  int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);  // [species][cell] input counts
+  int* scnt = sn + 2 * NCL;                          // [species][cell] output counts
+
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int tix = tile % r.ntx, tiy = (tile / r.ntx) % r.nty, tiz = tile / (r.ntx * r.nty);
+  const int X0 = tix * TX, Y0 = tiy * TY, Z0 = tiz * TZ;
+  const int wx = min(TX, r.nx - X0), wy = min(TY, r.ny - Y0), wz = min(TZ, r.nz - Z0);
+  const int nxy = r.nx * r.ny;  // cells < 2^30
+
+  // 1. field copies of the tile and its halo (periodic), current tile zeroed
+  for (int e = tid; e < 6 * G::GN; e += HO_THREADS) {
+    const int c = e / G::GN, rem = e - c * G::GN;
+    const int lz = rem / (G::GX * G::GY), ly = (rem / G::GX) % G::GY, lx = rem % G::GX;
+    const int gx = wrap_any(X0 - H + lx, r.nx);
+    const int gy = NDIM == 3 ? wrap_any(Y0 - H + ly, r.ny) : 0;
+    const int gz = wrap_any(Z0 - H + lz, r.nz);
+    const T* src = r.g[0];
+    switch (c) {  // constant-indexed parameter reads
+      case 1: src = r.g[1]; break;
+      case 2: src = r.g[2]; break;
+      case 3: src = r.g[3]; break;
+      case 4: src = r.g[4]; break;
+      case 5: src = r.g[5]; break;
+      default: break;
+    }
+    sg[e] = src[(long long)gz * nxy + (long long)gy * r.nx + gx];
+  }
+  for (int e = tid; e < 3 * G::JN; e += HO_THREADS) sj[e] = T(0);
+  __syncthreads();
+  if (SCHEME == 2) {
+    // average each component from its Yee location to the nodes along its half-staggered
+    // directions: node i gets (v[i-1] + v[i]) / 2, rows walked from the top so v[i-1] is unchanged
+    for (int axis = 0; axis < 3; ++axis) {
+      if (axis == 1 && NDIM == 2) continue;
+      const int len = axis == 0 ? G::GX : (axis == 1 ? G::GY : G::GZ);
+      const int stride = axis == 0 ? 1 : (axis == 1 ? G::GX : G::GX * G::GY);
+      const int nrows = G::GN / len;
+      for (int e = tid; e < 6 * nrows; e += HO_THREADS) {
+        const int c = e / nrows, row = e - c * nrows;
+        if (!c_stag_ho[c][axis]) continue;
+        int base;  // first element of the row
+        if (axis == 0) base = row * G::GX;
+        else if (axis == 1) base = (row / G::GX) * G::GX * G::GY + row % G::GX;
+        else base = row;
+        T* v = sg + c * G::GN + base;
+        for (int i = len - 1; i >= 1; --i) v[i * stride] = T(0.5) * (v[i * stride] + v[(i - 1) * stride]);
+      }
+      __syncthreads();
+    }
+  }
+  // 2. particle counts of the tile's cells (the input counts become the next step's output counts)
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    int n0 = 0, n1 = 0;
+    if (lx < wx && ly < wy && lz < wz) {
+      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
+      n0 = min(r.in[0].cnt[cell], r.cap);
+      n1 = min(r.in[1].cnt[cell], r.cap);
+      r.in[0].cnt[cell] = 0;
+      r.in[1].cnt[cell] = 0;
+    }
+    sn[cl] = n0;
+    sn[NCL + cl] = n1;
+    scnt[cl] = 0;
+    scnt[NCL + cl] = 0;
+  }
+  __syncthreads();
+
+  const bool has_w = r.in[0].w != nullptr, has_id = r.in[0].id != nullptr;
+  T kin = T(0);
+  int npush = 0;
+  // 3. one thread per cell, the cell's particles in turn
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    const int gi = X0 + lx, gj = Y0 + ly, gk = Z0 + lz;
+    const int cell = (gk * r.ny + gj) * r.nx + gi;
+    for (int s = 0; s < 2; ++s) {
+      const SpeciesBuf<T>& pin = s ? r.in[1] : r.in[0];
+      const SpeciesBuf<T>& pout = s ? r.out[1] : r.out[0];
+      const T qs = s ? T(1) : T(-1);
+      const int n = sn[s * NCL + cl];
+      for (int j = 0; j < n; ++j) {
+        const long long slot = (long long)cell * r.cap + j;
+        const T ox = pin.ox[slot], oy = NDIM == 3 ? pin.oy[slot] : T(0), oz = pin.oz[slot];
+        T ux = pin.dux[slot], uy = pin.duy[slot], uz = pin.duz[slot];
+        const T w = has_w ? pin.w[slot] : r.wconst;
+        const unsigned id = has_id ? pin.id[slot] : 0u;
+        // gather
+        T F[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          F[c] = gather_comp<T, NDIM, ORDER, SCHEME>(sg + c * G::GN, c, lx, ly, lz, ox, oy, oz);
+        // relativistic Boris, momenta relative to the drift u0 z_hat
+        const T h = qs * r.hq;
+        const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
+        const T Mz = r.u0 + mz;
+        const T ig = T(1) / sqrt(T(1) + mx * mx + my * my + Mz * Mz);
+        const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
+        const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+        const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
+        const T qx = mx + (my * tz - Mz * ty);
+        const T qy = my + (Mz * tx - mx * tz);
+        const T qz = Mz + (mx * ty - my * tx);
+        ux = mx + (qy * sz - qz * sy) + h * F[0];
+        uy = my + (qz * sx - qx * sz) + h * F[1];
+        uz = mz + (qx * sy - qy * sx) + h * F[2];
+        const T Uz = r.u0 + uz;
+        const T u2 = ux * ux + uy * uy + Uz * Uz;
+        const T gam = sqrt(T(1) + u2);
+        const T ign = T(1) / gam;
+        kin += w * u2 / (gam + T(1));
+        ++npush;
+        T ddx = r.dtdx * ux * ign, ddy = NDIM == 3 ? r.dtdy * uy * ign : T(0), ddz = r.dtdz * Uz * ign;
+        const T vy = uy * ign;
+        if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
+          flag_error(r.err, ERR_NONFINITE);
+          ddx = ddy = ddz = T(0);
+          ux = uy = uz = T(0);
+        }
+        // Esirkepov on the window nodes K0 .. K0 + NW - 1 of the start cell
+        T S0x[NW], dSx[NW], S0y[NW], dSy[NW], S0z[NW], dSz[NW];
+#pragma unroll
+        for (int a = 0; a < NW; ++a) {
+          const T node = T(K0 + a);
+          S0x[a] = bspl(ORDER, node - ox);
+          dSx[a] = shape_change(ORDER, node - ox, ddx);
+          S0z[a] = bspl(ORDER, node - oz);
+          dSz[a] = shape_change(ORDER, node - oz, ddz);
+          if (NDIM == 3) {
+            S0y[a] = bspl(ORDER, node - oy);
+            dSy[a] = shape_change(ORDER, node - oy, ddy);
+          } else {
+            S0y[a] = T(0);
+            dSy[a] = T(0);
+          }
+        }
+        const T qw = qs * w;
+        // window node a of the start cell is current-tile index (cell + K0 + a) + H
+        const int bx = lx + K0 + H, by = NDIM == 3 ? ly + K0 + H : 0, bz = lz + K0 + H;
+        if (NDIM == 2) {
+          const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
+          T Tx[NW], Tz[NW];
+#pragma unroll
+          for (int a = 0; a < NW; ++a) {
+            Tx[a] = S0x[a] + T(0.5) * dSx[a];
+            Tz[a] = S0z[a] + T(0.5) * dSz[a];
+          }
+          // Jx(i+1/2, k): running sum over the x window
+#pragma unroll
+          for (int b = 0; b < NW; ++b) {
+            T acc = T(0);
+#pragma unroll
+            for (int a = 0; a < NW - 1; ++a) {
+              acc += dSx[a];
+              const T v = cx * acc * Tz[b];
+              if (v != T(0)) atomicAdd(sj + (bz + b) * G::JX + bx + a, v);
+            }
+          }
+          // Jz(i, k+1/2): running sum over the z window
+#pragma unroll
+          for (int a = 0; a < NW; ++a) {
+            T acc = T(0);
+#pragma unroll
+            for (int b = 0; b < NW - 1; ++b) {
+              acc += dSz[b];
+              const T v = cz * acc * Tx[a];
+              if (v != T(0)) atomicAdd(sj + 2 * G::JN + (bz + b) * G::JX + bx + a, v);
+            }
+          }
+          // Jy(i, k): out-of-plane weight Tx Tz + dSx dSz / 12
+#pragma unroll
+          for (int b = 0; b < NW; ++b)
+#pragma unroll
+            for (int a = 0; a < NW; ++a) {
+              const T v = cy * (Tx[a] * Tz[b] + dSx[a] * dSz[b] * T(1.0 / 12.0));
+              if (v != T(0)) atomicAdd(sj + G::JN + (bz + b) * G::JX + bx + a, v);
+            }
+        } else {
+          T Tx[NW], Ty[NW], Tz[NW];
+#pragma unroll
+          for (int a = 0; a < NW; ++a) {
+            Tx[a] = S0x[a] + T(0.5) * dSx[a];
+            Ty[a] = S0y[a] + T(0.5) * dSy[a];
+            Tz[a] = S0z[a] + T(0.5) * dSz[a];
+          }
+          const T cxq = qw * r.jfx, cyq = qw * r.jfy, czq = qw * r.jfz;
+          // J_axis: running sum along the axis of dS times the transverse weight
+          // T1 T2 + dS1 dS2 / 12 over the other two directions
+          for (int t2 = 0; t2 < NW; ++t2)
+            for (int t1 = 0; t1 < NW; ++t1) {
+              const T wx_ = Ty[t1] * Tz[t2] + dSy[t1] * dSz[t2] * T(1.0 / 12.0);  // Jx: (y, z) = (t1, t2)
+              const T wy_ = Tx[t1] * Tz[t2] + dSx[t1] * dSz[t2] * T(1.0 / 12.0);  // Jy: (x, z) = (t1, t2)
+              const T wz_ = Tx[t1] * Ty[t2] + dSx[t1] * dSy[t2] * T(1.0 / 12.0);  // Jz: (x, y) = (t1, t2)
+              T ax_ = T(0), ay_ = T(0), az_ = T(0);
+              for (int a = 0; a < NW - 1; ++a) {
+                ax_ += dSx[a];
+                ay_ += dSy[a];
+                az_ += dSz[a];
+                const T vx = cxq * ax_ * wx_, vyv = cyq * ay_ * wy_, vz = czq * az_ * wz_;
+                if (vx != T(0)) atomicAdd(sj + ((bz + t2) * G::JY + by + t1) * G::JX + bx + a, vx);
+                if (vyv != T(0)) atomicAdd(sj + G::JN + ((bz + t2) * G::JY + by + a) * G::JX + bx + t1, vyv);
+                if (vz != T(0)) atomicAdd(sj + 2 * G::JN + ((bz + a) * G::JY + by + t2) * G::JX + bx + t1, vz);
+              }
+            }
+        }
+        // new cell and offsets
+        auto fold = [](T o, T d, int& sh) -> T {
+          const T t = o + d;
+          sh = t < T(0) ? -1 : (t >= T(1) ? 1 : 0);
+          T no = t - T(sh);
+          if (no >= T(1)) {  // rounding of t - sh
+            no = T(0);
+            sh += 1;
+          }
+          if (no < T(0)) no = T(0);
+          return no;
+        };
+        int shx, shy = 0, shz;
+        const T nox = fold(ox, ddx, shx);
+        const T noy = NDIM == 3 ? fold(oy, ddy, shy) : T(0);
+        const T noz = fold(oz, ddz, shz);
+        const int nlx = lx + shx, nly = ly + shy, nlz = lz + shz;
+        if (nlx >= 0 && nlx < wx && nly >= 0 && nly < wy && nlz >= 0 && nlz < wz) {
+          const int ncl = (nlz * TY + nly) * TX + nlx;
+          const int jj = atomicAdd(scnt + s * NCL + ncl, 1);
+          if (jj < r.cap) {
+            const int dcell = ((Z0 + nlz) * r.ny + Y0 + nly) * r.nx + X0 + nlx;
+            const long long o = (long long)dcell * r.cap + jj;
+            pout.ox[o] = nox;
+            if (NDIM == 3) pout.oy[o] = noy;
+            pout.oz[o] = noz;
+            pout.dux[o] = ux;
+            pout.duy[o] = uy;
+            pout.duz[o] = uz;
+            if (has_w) pout.w[o] = w;
+            if (has_id) pout.id[o] = id;
+          } else {
+            flag_error(r.err, ERR_OVERFLOW);
+          }
+        } else {  // to another tile: the leaver list (inserted by k_migrate)
+          const int ni = wrap_any(gi + shx, r.nx), nj = NDIM == 3 ? wrap_any(gj + shy, r.ny) : 0;
+          const int nk = wrap_any(gk + shz, r.nz);
+          const long long o = atomicAdd(r.lv_count, 1);
+          if (o < r.lv_cap) {
+            r.lv.key[o] = ((nk * r.ny + nj) * r.nx + ni) * 2 + s;
+            r.lv.ox[o] = nox;
+            if (NDIM == 3) r.lv.oy[o] = noy;
+            r.lv.oz[o] = noz;
+            r.lv.dux[o] = ux;
+            r.lv.duy[o] = uy;
+            r.lv.duz[o] = uz;
+            if (has_w) r.lv.w[o] = w;
+            if (has_id) r.lv.id[o] = id;
+          } else {
+            flag_error(r.err, ERR_OVERFLOW);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // 4. output counts of the tile's cells
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
+      r.out[0].cnt[cell] = scnt[cl];
+      r.out[1].cnt[cell] = scnt[NCL + cl];
+    }
+  }
+  // 5. the tile's current into global memory
+  for (int e = tid; e < 3 * G::JN; e += HO_THREADS) {
+    const T v = sj[e];
+    if (v == T(0)) continue;
+    const int c = e / G::JN, rem = e - c * G::JN;
+    const int lz = rem / (G::JX * G::JY), ly = (rem / G::JX) % G::JY, lx = rem % G::JX;
+    const int gx = wrap_any(X0 - H + lx, r.nx);
+    const int gy = NDIM == 3 ? wrap_any(Y0 - H + ly, r.ny) : 0;
+    const int gz = wrap_any(Z0 - H + lz, r.nz);
+    T* dst = c == 0 ? r.j[0] : (c == 1 ? r.j[1] : r.j[2]);
+    atomicAdd(dst + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
+  }
+  // 6. kinetic energy and particle count of the step (FP64 across the block and the grid)
+  if (r.kin) {
+    double kd = (double)kin;
+    int nd = npush;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kd += __shfl_xor_sync(0xffffffffu, kd, o);
+      nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    __shared__ double skin[HO_THREADS / 32];
+    __shared__ int scn[HO_THREADS / 32];
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+      skin[warp] = kd;
+      scn[warp] = nd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      long long c = 0;
+      for (int w2 = 0; w2 < HO_THREADS / 32; ++w2) {
+        t += skin[w2];
+        c += scn[w2];
+      }
+      atomicAdd(r.kin, t);
+      atomicAdd(r.kin + 1, (double)c);
+    }
+  }
+}
+
+template <typename T, int NDIM, int ORDER, int SCHEME>
+cudaError_t launch_ho_t(const RunDev<T>& r, cudaStream_t st) {
+  using G = HoGeom<NDIM, ORDER>;
+  const size_t sm = G::template bytes<T>();
+  cudaError_t e = ensure_dynamic_smem((const void*)k_push_ho<T, NDIM, ORDER, SCHEME>, sm);
+  if (e != cudaSuccess) return e;
+  const int ntiles = r.ntx * r.nty * r.ntz;
+  if (ntiles > 0) k_push_ho<T, NDIM, ORDER, SCHEME><<<ntiles, HO_THREADS, sm, st>>>(r);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM, int ORDER>
+cudaError_t launch_ho_scheme(const RunDev<T>& r, int scheme, cudaStream_t st) {
+  if (scheme == 0) return launch_ho_t<T, NDIM, ORDER, 0>(r, st);
+  if (scheme == 1) return launch_ho_t<T, NDIM, ORDER, 1>(r, st);
+  return launch_ho_t<T, NDIM, ORDER, 2>(r, st);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_push_ho(const RunDev<T>& r, int order, int scheme, cudaStream_t st) {
+  if (r.ndim == 2) return order == 3 ? launch_ho_scheme<T, 2, 3>(r, scheme, st) : launch_ho_scheme<T, 2, 1>(r, scheme, st);
+  return order == 3 ? launch_ho_scheme<T, 3, 3>(r, scheme, st) : launch_ho_scheme<T, 3, 1>(r, scheme, st);
+}
+template cudaError_t launch_push_ho<float>(const RunDev<float>&, int, int, cudaStream_t);
+template cudaError_t launch_push_ho<double>(const RunDev<double>&, int, int, cudaStream_t);
+
+}  // namespace picgb

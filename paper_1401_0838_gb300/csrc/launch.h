@@ -51,6 +51,9 @@ template <typename T>
 cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st);
 template <typename T>
 cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st);
+// Particle step for shape order 3 and/or the momentum-conserving gather (k_push_ho.cu).
+template <typename T>
+cudaError_t launch_push_ho(const RunDev<T>& r, int order, int scheme, cudaStream_t st);
 // Many runs in one persistent launch: work items (run, tile), *queue zeroed by the launcher.
 template <typename T>
 cudaError_t launch_push_batch(const RunDev<T>* runs, const int2* items, int nitems, int* queue, int ndim, int scheme,

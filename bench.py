@@ -41,9 +41,12 @@ PUSH_BYTES_PER_CELL = {4: 36, 8: 72}
 FALLBACK_HBM_GBS = 6800.0
 
 
-def config_dict(n_gpus: int) -> dict:
-    return {"workload": WORKLOAD, "grid": [NX, NZ], "ppc_per_species": PPC, "particles": NX * NZ * PPC * 2,
-            "alpha": ALPHA, "gamma": GAMMA, "scheme": "galerkin",
+def config_dict(n_gpus: int, order: int = 1, scheme: str = "galerkin") -> dict:
+    wl = WORKLOAD
+    if order != 1 or scheme != "galerkin":
+        wl = WORKLOAD.replace("Galerkin gather", f"{scheme} gather, shape order {order}")
+    return {"workload": wl, "grid": [NX, NZ], "ppc_per_species": PPC, "particles": NX * NZ * PPC * 2,
+            "alpha": ALPHA, "gamma": GAMMA, "scheme": scheme, "shape_order": order,
             "filter": "2 bilinear + 1 compensation (a=2) per direction on J and on the field copies",
             "l2": "inputs larger than L2: 671 MB of particle state read + written per step (L2 129 MB)",
             "parallelism": "replicas" if n_gpus > 1 else "single"}
@@ -173,36 +176,45 @@ def measured_hbm_peak():
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def make_handle(P, precision: int, seed: int, stream_ptr):
-    cfg = P.pic_config_default(nx=NX, nz=NZ, dt=ALPHA, gamma=GAMMA, scheme=P.PIC_GALERKIN, precision=precision,
-                               ppc_per_species=PPC, seed=seed, init_beam=1, diag_every=1, **FILTER)
+SCHEMES = {"galerkin": 0, "uniform": 1, "momentum": 2}
+
+
+def make_handle(P, precision: int, seed: int, stream_ptr, order: int = 1, scheme: str = "galerkin"):
+    sc = SCHEMES[scheme]
+    cfg = P.pic_config_default(nx=NX, nz=NZ, dt=ALPHA, gamma=GAMMA, scheme=sc, precision=precision,
+                               ppc_per_species=PPC, seed=seed, init_beam=1, diag_every=1, shape_order=order,
+                               **FILTER)
     h = P.pic_create(cfg)
-    pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, ALPHA)
+    pe, pb = P.pic_compute_correction_coeffs(sc, ALPHA)
     P.pic_set_correction_stencil(h, pe, pb)
     P.pic_set_stream(h, stream_ptr)
     return h, cfg
 
 
 def timed_steps(P, torch, h, stream, steps: int, device):
-    """Device time of `steps` whole steps (CUDA events on the launching stream) + per-kernel times."""
-    P.pic_enable_timing(h, True)
+    """Device time of `steps` whole steps run by one pic_step call (CUDA events on the launching
+    stream; the library replays its captured step graph), then per-kernel times from a second,
+    separately timed pass of `steps` single steps with event-bracketed launches."""
     l0 = P.pic_launch_count(h)
     barrier(device)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        P.pic_step(h, 1)
+    P.pic_step(h, steps)
     e1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
     barrier(device)
     ms = e0.elapsed_time(e1)
-    kt = P.pic_kernel_times(h)
     launches = P.pic_launch_count(h) - l0
-    P.pic_enable_timing(h, False)
     P.pic_sync(h)
+    P.pic_enable_timing(h, True)
+    for _ in range(steps):
+        P.pic_step(h, 1)
+    P.pic_sync(h)
+    kt = P.pic_kernel_times(h)
+    P.pic_enable_timing(h, False)
     return ms, kt, launches
 
 
@@ -324,7 +336,8 @@ def run_ours(args):
     peak, peak_kind = measured_hbm_peak()
 
     # FP32: the headline
-    h, cfg = make_handle(P, P.PIC_FP32, seed=2 + rank, stream_ptr=stream.cuda_stream)
+    h, cfg = make_handle(P, P.PIC_FP32, seed=2 + rank, stream_ptr=stream.cuda_stream, order=args.order,
+                         scheme=args.scheme)
     ncell = cfg.nx * cfg.ny * cfg.nz
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
@@ -340,7 +353,8 @@ def run_ours(args):
     agg = aggregate(ms, np_, args.steps, device)
     cells = aggregate(ms, ncell, args.steps, device)
     launches_all = int(reduce_sum(launches, device))
-    traffic = args.traffic if args.traffic is not None else profiled_traffic()
+    traffic = args.traffic if args.traffic is not None else (
+        profiled_traffic() if args.order == 1 and args.scheme == "galerkin" else None)
     rf = roofline(kt, np_, ncell, 4, peak, peak_kind, traffic=traffic)
     kernel_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]}
 
@@ -354,7 +368,8 @@ def run_ours(args):
     # FP64 on the same workload (the metric compares the two precisions)
     fp64 = None
     if args.fp64_steps > 0:
-        h64, _ = make_handle(P, P.PIC_FP64, seed=2 + rank, stream_ptr=stream.cuda_stream)
+        h64, _ = make_handle(P, P.PIC_FP64, seed=2 + rank, stream_ptr=stream.cuda_stream, order=args.order,
+                             scheme=args.scheme)
         for _ in range(2):
             P.pic_step(h64, 1)
         P.pic_sync(h64)
@@ -367,7 +382,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": agg["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(ws), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
+            "config": config_dict(ws, args.order, args.scheme), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
             "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
             "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -626,6 +641,8 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
+    ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
+    ap.add_argument("--scheme", default="galerkin", choices=("galerkin", "uniform", "momentum"))
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args(argv)

@@ -78,3 +78,32 @@ def test_correction_and_filter_suppress_growth():
     assert out["off"][-1] > 1e3 * out["off"][10]
     assert out["on"][-1] < 1e-2 * out["off"][-1]
     assert g_off > 0.01
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_cubic_shapes_suppress_uniformly(scheme):
+    # Sec. 3's setting: cubic shapes on a 128x128 periodic mesh, gamma = 130, the filter of Eq. 6 (one
+    # bilinear and one compensation pass per direction on J and on the gather copies). With the Psi
+    # correction the fitted growth rate of W_perp drops well below the uncorrected one at small and
+    # large c dt / dz, and stays small at every tested step (with linear shapes the Galerkin run at
+    # 0.7 is barely corrected: the paper's remark that linear interpolation was not uniformly good)
+    steps, every = 2000, 10
+    rates = {}
+    for alpha in (0.3, 0.7):
+        for corr in (False, True):
+            cfg = make_cfg(nx=128, nz=128, dt=alpha, scheme=scheme, precision=0, ppc=4, init_beam=1, seed=7,
+                           track_ids=0, order=3, cap=96)
+            cfg.diag_every = every
+            h = P.pic_create(cfg)
+            try:
+                if corr:
+                    P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(scheme, alpha))
+                P.pic_step(h, steps)
+                w = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+            finally:
+                P.pic_destroy(h)
+            t = np.arange(1, len(w) + 1) * every * alpha
+            rates[(alpha, corr)] = P.pic_fit_growth_rate(t, w)[0]
+    for alpha in (0.3, 0.7):
+        assert rates[(alpha, True)] < 0.5 * rates[(alpha, False)], rates
+        assert rates[(alpha, True)] < 0.01, rates

@@ -622,6 +622,56 @@ def run_3d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gamma_sweep(args):
+    """Growth against c dt/dz at gamma 3 and 130 with the correction and the filter (cubic shapes,
+    128 x 128 mesh, the setting of Sec. 3): the peak fitted growth rate of W_perp per gamma and the
+    ratio of the peaks, against the paper's rough gamma^(-1/2) scaling."""
+    import numpy as np
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    tmax, every = args.gamma_time, 10  # the same physical time c t / dz for every c dt / dz
+    alphas = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7]
+    table = {}
+    t0 = time.perf_counter()
+    for scheme_name, scheme in (("galerkin", 0), ("uniform", 1)):
+        for gamma in (3.0, 130.0):
+            rates = []
+            for alpha in alphas:
+                cfg = P.pic_config_default(nx=128, nz=128, dt=alpha, gamma=gamma, scheme=scheme, precision=P.PIC_FP32,
+                                           ppc_per_species=4, shape_order=3, init_beam=1, seed=11,
+                                           diag_every=every, bin_capacity=96)
+                h = P.pic_create(cfg)
+                P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(scheme, alpha))
+                steps = int(round(tmax / alpha / every)) * every
+                P.pic_step(h, steps)
+                w = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+                P.pic_destroy(h)
+                t = np.arange(1, len(w) + 1) * every * alpha
+                rates.append(float(P.pic_fit_growth_rate(t, w)[0]))
+            table[f"{scheme_name}_gamma{int(gamma)}"] = rates
+    out = {"alphas": alphas, "growth_rates": table, "unit": "1 / (dz/c)", "omega_p_dz": 0.3868}
+    for scheme_name in ("galerkin", "uniform"):
+        p3 = max(table[f"{scheme_name}_gamma3"])
+        p130 = max(table[f"{scheme_name}_gamma130"])
+        out[f"{scheme_name}_peak_ratio_gamma3_over_gamma130"] = p3 / p130
+    out["gamma_minus_half_ratio"] = (130.0 / 3.0) ** 0.5
+    for scheme_name in ("galerkin", "uniform"):
+        out[f"{scheme_name}_ratio_per_alpha"] = [a / b for a, b in zip(table[f"{scheme_name}_gamma3"],
+                                                                        table[f"{scheme_name}_gamma130"])]
+    line = {"metric": "peak growth rate of W_perp against c dt/dz, gamma 3 vs 130 (corrected, filtered)",
+            "value": out["galerkin_peak_ratio_gamma3_over_gamma130"], "unit": "ratio", "n_gpus": 1,
+            "steps": int(round(tmax / alphas[0])), "warmup": 0, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "2D 128x128 beam, 4 particles/cell/species, cubic shapes, Psi correction + "
+                                   f"filter (1,1,a=3), gamma in {{3, 130}}, c dt/dz 0.1..0.7, c t/dz = {tmax} each",
+                       "wall_s":
+                       round(time.perf_counter() - t0, 1)},
+            "sweep": out}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,6 +692,8 @@ def main(argv=None):
     ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
     ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
+    ap.add_argument("--gamma-sweep", action="store_true", help="growth against c dt/dz at gamma 3 and 130 instead")
+    ap.add_argument("--gamma-time", type=float, default=700.0, help="c t / dz of each --gamma-sweep run")
     ap.add_argument("--scheme", default="galerkin", choices=("galerkin", "uniform", "momentum"))
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
@@ -656,6 +708,8 @@ def main(argv=None):
         run_adjoint(args)
     elif args.config3d:
         run_3d(args)
+    elif args.gamma_sweep:
+        run_gamma_sweep(args)
     else:
         run_ours(args)
 

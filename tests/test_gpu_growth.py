@@ -107,3 +107,25 @@ def test_cubic_shapes_suppress_uniformly(scheme):
     for alpha in (0.3, 0.7):
         assert rates[(alpha, True)] < 0.5 * rates[(alpha, False)], rates
         assert rates[(alpha, True)] < 0.01, rates
+
+
+def test_correction_works_less_well_at_gamma_3():
+    # Sec. 3 (Fig. 3): the multipliers are tuned for infinite gamma; at gamma = 3 the corrected run
+    # still grows clearly faster than at gamma = 130 for large c dt / dz (cubic Galerkin, 128x128)
+    alpha, every = 0.6, 10
+    steps = int(round(700 / alpha / every)) * every
+    rates = {}
+    for gamma in (3.0, 130.0):
+        cfg = make_cfg(nx=128, nz=128, dt=alpha, gamma=gamma, scheme=0, precision=0, ppc=4, init_beam=1, seed=11,
+                       track_ids=0, order=3, cap=96)
+        cfg.diag_every = every
+        h = P.pic_create(cfg)
+        try:
+            P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(0, alpha))
+            P.pic_step(h, steps)
+            w = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+        finally:
+            P.pic_destroy(h)
+        t = np.arange(1, len(w) + 1) * every * alpha
+        rates[gamma] = P.pic_fit_growth_rate(t, w)[0]
+    assert rates[3.0] > 1.5 * rates[130.0], rates

@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("psi_e", ctypes.c_double * 9), ("psi_b", ctypes.c_double * 9),
                 ("f_nbin", ctypes.c_int), ("f_ncomp", ctypes.c_int), ("f_alpha", ctypes.c_double),
-                ("f_targets", ctypes.c_int), ("order", ctypes.c_int)]
+                ("f_targets", ctypes.c_int), ("order", ctypes.c_int), ("corr_mode", ctypes.c_int),
+                ("psi_b_coef", ctypes.c_double * 5)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -88,6 +89,7 @@ def _declare(L):
     L.orc_conv_axis.argtypes = [P(Params), _DP, ctypes.c_int, _DP, ctypes.c_int]
     L.orc_filter.argtypes = [P(Params), _DP]
     L.orc_gather_copies.argtypes = [P(Params), P(_Fields), _DP * 6]
+    L.orc_inverse_psi_z.argtypes = [P(Params), _DP]
     L.orc_yee_b.argtypes = [P(Params), P(_Fields), ctypes.c_double]
     L.orc_yee_e.argtypes = [P(Params), P(_Fields), ctypes.c_double]
     L.orc_gather.argtypes = [P(Params), _DP * 6, _DP, _DP, _DP, ctypes.c_long, _DP * 6]
@@ -177,7 +179,7 @@ class Sim:
 
     def __init__(self, ndim=2, nx=16, ny=1, nz=16, dx=1.0, dy=1.0, dz=1.0, dt=0.5, scheme=GALERKIN,
                  psi_e=None, psi_b=None, f_nbin=1, f_ncomp=1, f_alpha=3.0, f_targets=FILTER_J | FILTER_GATHER,
-                 order=1):
+                 order=1, corr_mode=0):
         if ndim == 2:
             ny, dy = 1, 1.0
         self.p = Params()
@@ -186,6 +188,7 @@ class Sim:
         self.p.scheme = scheme
         self.p.f_nbin, self.p.f_ncomp, self.p.f_alpha, self.p.f_targets = f_nbin, f_ncomp, f_alpha, f_targets
         self.p.order = order
+        self.p.corr_mode = corr_mode
         self.set_correction(psi_e, psi_b)
         self.shape = (nz, ny, nx)
         self.f = {n: np.zeros(self.shape) for n in FIELD_NAMES}
@@ -200,6 +203,9 @@ class Sim:
         for m in range(9):
             self.p.psi_e[m] = te[m]
             self.p.psi_b[m] = tb[m]
+        cb = one if psi_b is None else np.asarray(psi_b, dtype=np.float64)
+        for m in range(5):
+            self.p.psi_b_coef[m] = float(cb[m])
 
     @property
     def ndim(self):
@@ -257,6 +263,12 @@ class Sim:
         f = np.ascontiguousarray(f, dtype=np.float64).copy()
         taps = np.ascontiguousarray(taps, dtype=np.float64)
         lib().orc_conv_axis(ctypes.byref(self.p), _ptr(f), axis, _ptr(taps), (len(taps) - 1) // 2)
+        return f
+
+    def inverse_psi_z(self, f):
+        """Psi_B(D_z)^-1 applied to a field (exact circulant inverse along z)."""
+        f = np.ascontiguousarray(f, dtype=np.float64).copy()
+        lib().orc_inverse_psi_z(ctypes.byref(self.p), _ptr(f))
         return f
 
     def filter(self, f):

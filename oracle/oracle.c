@@ -52,6 +52,8 @@ typedef struct {
   double f_alpha;         /* compensation centre weight (3 in the paper's filter) */
   int f_targets;          /* bit 0: filter J; bit 1: filter the gather copies */
   int order;              /* particle shape order: 1 (linear) or 3 (cubic) */
+  int corr_mode;          /* 0: Psi_E on Ex, Ey and Psi_B on the others; 1: Psi_E / Psi_B on Ex, Ey only */
+  double psi_b_coef[5];   /* Psi_B polynomial coefficients (powers of xi), used by corr_mode 1 */
 } orc_params;
 
 typedef struct {
@@ -250,12 +252,59 @@ void orc_filter(const orc_params* p, double* f) {
  * fields themselves are never modified.
  * out[0..5] receive Ex, Ey, Ez, Bx, By, Bz copies.
  */
+/*
+ * Sec. 2: Psi_B applied exactly, by its inverse: on a periodic line of nz
+ * cells the operator Psi_B(D_z) is circulant, with eigenvalue
+ * Psi_B(sin^2(pi m / nz)) on the Fourier mode m, so its inverse divides each
+ * mode by that value. Written as a direct DFT along z (O(nz^2) per line).
+ */
+void orc_inverse_psi_z(const orc_params* p, double* f) {
+  const int nz = p->nz;
+  const long nxy = (long)p->nx * p->ny;
+  const double two_pi = 6.283185307179586476925286766559;
+  double* re = (double*)malloc(sizeof(double) * nz);
+  double* im = (double*)malloc(sizeof(double) * nz);
+  for (long l = 0; l < nxy; ++l) {
+    for (int m = 0; m < nz; ++m) { /* forward transform, then divide by the symbol */
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        double ph = -two_pi * (double)m * (double)k / (double)nz;
+        a += f[k * nxy + l] * cos(ph);
+        b += f[k * nxy + l] * sin(ph);
+      }
+      double sn = sin(0.5 * two_pi * (double)m / (double)nz);
+      double den = poly4(p->psi_b_coef, sn * sn);
+      re[m] = a / den;
+      im[m] = b / den;
+    }
+    for (int k = 0; k < nz; ++k) { /* inverse transform (the result is real) */
+      double a = 0.0;
+      for (int m = 0; m < nz; ++m) {
+        double ph = two_pi * (double)m * (double)k / (double)nz;
+        a += re[m] * cos(ph) - im[m] * sin(ph);
+      }
+      f[k * nxy + l] = a / (double)nz;
+    }
+  }
+  free(re);
+  free(im);
+}
+
 void orc_gather_copies(const orc_params* p, const orc_fields* F, double* out[6]) {
   long ncell = (long)p->nx * p->ny * p->nz;
   const double* src[6] = {F->ex, F->ey, F->ez, F->bx, F->by, F->bz};
   for (int c = 0; c < 6; ++c) {
     memcpy(out[c], src[c], sizeof(double) * ncell);
-    orc_conv_axis(p, out[c], 2, c < 2 ? p->psi_e : p->psi_b, 4);
+    if (p->corr_mode == 1) {
+      /* Sec. 2 / Sec. 3 variant: the rational multiplier Psi_E / Psi_B on the transverse E copies
+         only (Psi_B by exact inversion), none on the other components */
+      if (c < 2) {
+        orc_conv_axis(p, out[c], 2, p->psi_e, 4);
+        orc_inverse_psi_z(p, out[c]);
+      }
+    } else {
+      orc_conv_axis(p, out[c], 2, c < 2 ? p->psi_e : p->psi_b, 4);
+    }
     if (p->f_targets & 2) orc_filter(p, out[c]);
   }
 }

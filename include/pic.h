@@ -85,7 +85,15 @@ typedef struct pic_config {
   int track_ids;            /* 1: carry a 32-bit id per particle (for tests) */
   int diag_every;           /* > 0: record the energies on the device every diag_every steps */
   int diag_capacity;        /* ring size of the energy history; 0: 4096 samples */
+  int correction_mode;      /* PIC_CORR_SPLIT (0): Psi_E on the transverse E copies, Psi_B on the
+                               other copies, as WARP does (Sec. 2); PIC_CORR_RATIONAL (1): the
+                               rational multiplier Psi_E / Psi_B on the transverse E copies only,
+                               Psi_B applied exactly by inverting it along z (Sec. 2; the variant
+                               of Sec. 3 with the multiplier on E only) */
 } pic_config;
+
+#define PIC_CORR_SPLIT 0
+#define PIC_CORR_RATIONAL 1
 
 /* Energies, all FP64 sums over the whole grid / all particles (c = 1, m = 1). */
 typedef struct pic_energy_t {

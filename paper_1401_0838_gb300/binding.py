@@ -21,6 +21,7 @@ PIC_GALERKIN, PIC_UNIFORM, PIC_MOMENTUM = 0, 1, 2
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_FILTER_J, PIC_FILTER_GATHER = 1, 2
 PIC_HOST, PIC_DEVICE = 0, 1
+PIC_CORR_SPLIT, PIC_CORR_RATIONAL = 0, 1
 
 # every symbol the header declares
 EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", "pic_set_stream",
@@ -45,7 +46,7 @@ class pic_config(ctypes.Structure):
                 ("filter_nbin", ctypes.c_int), ("filter_ncomp", ctypes.c_int), ("filter_comp_alpha", ctypes.c_double),
                 ("filter_targets", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("init_beam", ctypes.c_int),
                 ("bin_capacity", ctypes.c_int), ("track_ids", ctypes.c_int), ("diag_every", ctypes.c_int),
-                ("diag_capacity", ctypes.c_int)]
+                ("diag_capacity", ctypes.c_int), ("correction_mode", ctypes.c_int)]
 
 
 class pic_energy_t(ctypes.Structure):

@@ -48,6 +48,10 @@ struct pic_handle {
   // taps (FP64, host) of the copy and current stencils
   double pe[5] = {1, 0, 0, 0, 0}, pb[5] = {1, 0, 0, 0, 0};
   std::vector<double> zt_e, zt_b, xt_g, zt_j, xt_j;
+  // rational correction mode: factors of Psi_B(D_z)^-1 and the complex scratch of the z-solves
+  double inv_lr[4] = {}, inv_li[4] = {}, inv_scale = 1.0;
+  int inv_nf = 0;
+  void* inv_work = nullptr;
   // energy history (device ring of 8 doubles per sample: sum E^2, sum B^2, sum perp^2, K, np)
   double* d_hist = nullptr;
   int hist_cap = 0;
@@ -209,7 +213,13 @@ void rebuild_taps(pic_handle* h) {
   const std::vector<double>& Fj = (c.filter_targets & PIC_FILTER_J) ? F : one;
   double te[9], tb[9];
   psi_stencil(h->pe, te);
-  psi_stencil(h->pb, tb);
+  if (c.correction_mode == PIC_CORR_RATIONAL) {  // Psi_E Psi_B^-1 on E in the FP64 z-line pass
+    const double one[5] = {1, 0, 0, 0, 0};
+    psi_stencil(one, tb);
+    psi_stencil(one, te);
+  } else {
+    psi_stencil(h->pb, tb);
+  }
   h->zt_e = convolve(std::vector<double>(te, te + 9), Fg);
   h->zt_b = convolve(std::vector<double>(tb, tb + 9), Fg);
   h->xt_g = Fg;
@@ -354,6 +364,22 @@ int step_once(pic_handle* h) {
   // 1. field copies seen by the particles: Psi(D_z) and the gather filter; zeroes J
   SepArgs<T> ca = sep_args<T>(h, true);
   CK(launch(h, PIC_K_COPIES, [&] { return launch_sep<T>(ca, st); }), "copy stencil");
+  if (h->cfg.correction_mode == PIC_CORR_RATIONAL) {  // Psi_E / Psi_B on the Ex, Ey copies
+    InvPsiArgs<T> ia;
+    ia.f[0] = (T*)h->g[0];
+    ia.f[1] = (T*)h->g[1];
+    ia.work = (double2*)h->inv_work;
+    ia.nxy = (long long)h->cfg.nx * h->cfg.ny;
+    ia.nz = h->cfg.nz;
+    ia.nf = h->inv_nf;
+    for (int q = 0; q < 4; ++q) {
+      ia.lam_re[q] = h->inv_lr[q];
+      ia.lam_im[q] = h->inv_li[q];
+    }
+    ia.scale = h->inv_scale;
+    psi_stencil(h->pe, ia.pe_taps);
+    CK(launch(h, PIC_K_COPIES, [&] { return launch_inverse_psi_z<T>(ia, st); }), "inverse Psi_B");
+  }
   // 2-5. gather, Boris, move, Esirkepov, rebin
   RunDev<T> r = make_run<T>(h, h->parity);
   r.kin = rec ? h->d_kin : nullptr;
@@ -637,6 +663,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       c.ppc_per_species < 0 ||
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
       c.diag_every < 0 || c.diag_capacity < 0 ||
+      (c.correction_mode != PIC_CORR_SPLIT && c.correction_mode != PIC_CORR_RATIONAL) ||
       (long long)c.nx * c.ny * c.nz > (1ll << 30) - 1)
     return PIC_E_ARG;
   const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
@@ -669,6 +696,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   for (int q = 0; q < 9 && ok; ++q) ok = (h->f[q] = dalloc(h, fb)) != nullptr;
   for (int q = 0; q < 6 && ok; ++q) ok = (h->g[q] = dalloc(h, fb)) != nullptr;
   for (int q = 0; q < 3 && ok; ++q) ok = (h->jf[q] = dalloc(h, fb)) != nullptr;
+  if (ok && c.correction_mode == PIC_CORR_RATIONAL)  // complex scratch of the z-solves, two components
+    ok = (h->inv_work = dalloc(h, 2 * sizeof(double) * 2 * (size_t)h->ncell)) != nullptr;
   const size_t slots = (size_t)h->ncell * cap;
   for (int s = 0; s < 2 && ok; ++s)
     for (int b = 0; b < 2 && ok; ++b) {
@@ -739,6 +768,18 @@ int pic_set_correction_stencil(pic_handle* h, const double psi_e[5], const doubl
     h->pe[q] = psi_e ? psi_e[q] : (q == 0 ? 1.0 : 0.0);
     h->pb[q] = psi_b ? psi_b[q] : (q == 0 ? 1.0 : 0.0);
     if (!isfinite(h->pe[q]) || !isfinite(h->pb[q])) return fail(h, PIC_E_ARG, "non-finite coefficient");
+  }
+  if (h->cfg.correction_mode == PIC_CORR_RATIONAL) {
+    int nf = 0;
+    double lr[4], li[4], sc = 1.0;
+    const int rc = psi_inverse_factors(h->pb, lr, li, &nf, &sc);
+    if (rc) return fail(h, rc, "Psi_B has no inverse (a zero on [0, 1] or identically zero)");
+    for (int q = 0; q < 4; ++q) {
+      h->inv_lr[q] = q < nf ? lr[q] : 0.0;
+      h->inv_li[q] = q < nf ? li[q] : 0.0;
+    }
+    h->inv_nf = nf;
+    h->inv_scale = sc;
   }
   rebuild_taps(h);
   drop_graph(h);
@@ -1248,7 +1289,8 @@ int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
         (c.track_ids != 0) != (c0.track_ids != 0))
       return PIC_E_ARG;  // these must agree across the runs of one batch
   }
-  if (c0.shape_order != 1 || c0.scheme == PIC_MOMENTUM) return PIC_E_ARG;  // batched: linear Galerkin / Uniform
+  if (c0.shape_order != 1 || c0.scheme == PIC_MOMENTUM || c0.correction_mode != PIC_CORR_SPLIT)
+    return PIC_E_ARG;  // batched: linear Galerkin / Uniform with the split correction
   pic_batch* b = new pic_batch();
   b->es = c0.precision == PIC_FP32 ? 4 : 8;
   b->ndim = c0.ndim;
@@ -1835,8 +1877,8 @@ extern "C" {
 int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double* w_perp) {
   if (!h || nsteps < 0 || checkpoint_every < 1 || !w_perp) return PIC_E_ARG;
   if (h->cfg.ndim != 2) return fail(h, PIC_E_ARG, "the adjoint covers 2D runs");
-  if (h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM)
-    return fail(h, PIC_E_ARG, "the adjoint covers linear shapes with the Galerkin or Uniform gather");
+  if (h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM || h->cfg.correction_mode != PIC_CORR_SPLIT)
+    return fail(h, PIC_E_ARG, "the adjoint covers linear shapes, the Galerkin or Uniform gather, the split correction");
   if (!h->has_id) return fail(h, PIC_E_STATE, "the adjoint needs particle ids (cfg.track_ids = 1)");
   if (h->ncell >= (1LL << 31)) return fail(h, PIC_E_ARG, "the adjoint covers grids below 2^31 cells");
   return h->es == 4 ? adjoint_forward_t<float>(h, nsteps, checkpoint_every, w_perp)

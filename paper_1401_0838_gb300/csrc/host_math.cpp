@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -189,6 +190,79 @@ int growth_fit(const double* t_in, const double* w_in, int n_in, double* g, int*
   *g = 0.5 * best;
   if (i0o) *i0o = bi;
   if (i1o) *i1o = bi + m - 1;
+  return PIC_OK;
+}
+
+
+int psi_inverse_factors(const double pb[5], double lam_re[4], double lam_im[4], int* nf, double* scale) {
+  using cd = std::complex<double>;
+  int deg = 4;
+  while (deg > 0 && pb[deg] == 0.0) --deg;
+  if (deg == 0) {
+    if (pb[0] == 0.0) return PIC_E_ARG;
+    *nf = 0;
+    *scale = 1.0 / pb[0];
+    return PIC_OK;
+  }
+  // roots of the monic polynomial by simultaneous (Durand-Kerner) iteration, then Newton polish
+  cd c[5];
+  for (int n = 0; n <= deg; ++n) c[n] = cd(pb[n] / pb[deg], 0.0);
+  auto P = [&](cd x) {
+    cd r = c[deg];
+    for (int n = deg - 1; n >= 0; --n) r = r * x + c[n];
+    return r;
+  };
+  auto dP = [&](cd x) {
+    cd r = double(deg) * c[deg];
+    for (int n = deg - 1; n >= 1; --n) r = r * x + double(n) * c[n];
+    return r;
+  };
+  cd z[4];
+  const cd seed(0.4, 0.9);
+  for (int i = 0; i < deg; ++i) z[i] = std::pow(seed, i) * 2.0;
+  for (int it = 0; it < 500; ++it) {
+    double move = 0.0;
+    for (int i = 0; i < deg; ++i) {
+      cd den(1.0, 0.0);
+      for (int j = 0; j < deg; ++j)
+        if (j != i) den *= (z[i] - z[j]);
+      const cd dz = P(z[i]) / den;
+      z[i] -= dz;
+      move = std::max(move, std::abs(dz));
+    }
+    if (move < 1e-15) break;
+  }
+  for (int i = 0; i < deg; ++i)
+    for (int it = 0; it < 3; ++it) {
+      const cd d = dP(z[i]);
+      if (std::abs(d) > 0) z[i] -= P(z[i]) / d;
+    }
+  // a real root on [0, 1], or Psi_B changing sign there: no inverse
+  for (int i = 0; i < deg; ++i)
+    if (std::abs(z[i].imag()) < 1e-9 * (1.0 + std::abs(z[i])) && z[i].real() >= -1e-12 && z[i].real() <= 1.0 + 1e-12)
+      return PIC_E_SINGULAR;
+  for (int k = 0; k <= 64; ++k) {
+    const double xi = k / 64.0;
+    double v = 0.0, p = 1.0;
+    for (int n = 0; n <= 4; ++n) {
+      v += pb[n] * p;
+      p *= xi;
+    }
+    if (!(v > 0.0) && !(v < 0.0)) return PIC_E_SINGULAR;
+    if (k > 0 && (v > 0.0) != (pb[0] > 0.0)) return PIC_E_SINGULAR;
+  }
+  cd prod(1.0 / pb[deg], 0.0);
+  for (int i = 0; i < deg; ++i) {
+    const cd a = 0.5 - z[i];  // D - r = a - (S + S^-1) / 4
+    const cd root = std::sqrt(4.0 * a * a - 1.0);
+    cd lam = 2.0 * a - root;
+    if (std::abs(lam) >= 1.0) lam = 2.0 * a + root;
+    lam_re[i] = lam.real();
+    lam_im[i] = lam.imag();
+    prod *= 4.0 * lam;
+  }
+  *nf = deg;
+  *scale = prod.real();
   return PIC_OK;
 }
 

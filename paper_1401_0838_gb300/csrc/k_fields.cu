@@ -769,3 +769,98 @@ template cudaError_t launch_kinetic<float>(const RunDev<float>&, double*, cudaSt
 template cudaError_t launch_kinetic<double>(const RunDev<double>&, double*, cudaStream_t);
 
 }  // namespace picgb
+
+namespace picgb {
+
+// ---------------------------------------------------------------------------------------------
+// Psi_E(D_z) Psi_B(D_z)^-1 along z (the exact rational multiplier, Sec. 2): one thread per z-line
+// and component, FP64 (complex) arithmetic; the FP32 copy stencil in front applies the filter only. Each factor 4 lam (1 - lam S)^-1 (1 - lam S^-1)^-1 of the
+// inverse is a causal then an anticausal first-order recursion with the periodic start value
+// sum_m lam^m x_(start - m) / (1 - lam^nz); the factor 4 lam and 1 / b_deg are applied at the end
+// (their product is real).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_inverse_psi_z(InvPsiArgs<T> a) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int comp = blockIdx.y;
+  if (l >= a.nxy) return;
+  T* f = comp == 0 ? a.f[0] : a.f[1];
+  double2* w = a.work + (size_t)comp * a.nz * a.nxy;
+  const long long nxy = a.nxy;
+  const int nz = a.nz;
+  // Psi_E(D_z) (9 taps, periodic) in FP64 into the complex work line
+  for (int k = 0; k < nz; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      int kk = k + m - 4;
+      kk = kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk);
+      if (kk < 0 || kk >= nz) kk = wrapi(kk, nz);  // lines shorter than 4 cells
+      acc += a.pe_taps[m] * (double)f[kk * nxy + l];
+    }
+    w[k * nxy + l] = make_double2(acc, 0.0);
+  }
+  for (int i = 0; i < a.nf; ++i) {
+    const double lr = a.lam_re[i], li = a.lam_im[i];
+    // causal: y_k = x_k + lam y_(k-1), periodic
+    double sr = 0.0, si = 0.0, pr = 1.0, pi = 0.0;
+    for (int m = 0; m < nz; ++m) {
+      const double2 x = w[(m == 0 ? 0 : nz - m) * nxy + l];
+      sr += pr * x.x - pi * x.y;
+      si += pr * x.y + pi * x.x;
+      const double tr = pr * lr - pi * li;
+      pi = pr * li + pi * lr;
+      pr = tr;
+    }
+    // (pr, pi) = lam^nz; start value s / (1 - lam^nz)
+    double dr = 1.0 - pr, di = -pi, dd = dr * dr + di * di;
+    double yr = (sr * dr + si * di) / dd, yi = (si * dr - sr * di) / dd;
+    w[l] = make_double2(yr, yi);
+    for (int k = 1; k < nz; ++k) {
+      const double2 x = w[k * nxy + l];
+      const double nr = x.x + lr * yr - li * yi, ni = x.y + lr * yi + li * yr;
+      yr = nr;
+      yi = ni;
+      w[k * nxy + l] = make_double2(yr, yi);
+    }
+    // anticausal: z_k = y_k + lam z_(k+1), periodic
+    sr = 0.0;
+    si = 0.0;
+    pr = 1.0;
+    pi = 0.0;
+    for (int m = 0; m < nz; ++m) {
+      const double2 x = w[(m == 0 ? nz - 1 : m - 1) * nxy + l];
+      sr += pr * x.x - pi * x.y;
+      si += pr * x.y + pi * x.x;
+      const double tr = pr * lr - pi * li;
+      pi = pr * li + pi * lr;
+      pr = tr;
+    }
+    dr = 1.0 - pr;
+    di = -pi;
+    dd = dr * dr + di * di;
+    yr = (sr * dr + si * di) / dd;
+    yi = (si * dr - sr * di) / dd;
+    w[(nz - 1) * nxy + l] = make_double2(yr, yi);
+    for (int k = nz - 2; k >= 0; --k) {
+      const double2 x = w[k * nxy + l];
+      const double nr = x.x + lr * yr - li * yi, ni = x.y + lr * yi + li * yr;
+      yr = nr;
+      yi = ni;
+      w[k * nxy + l] = make_double2(yr, yi);
+    }
+  }
+  for (int k = 0; k < nz; ++k) f[k * nxy + l] = (T)(a.scale * w[k * nxy + l].x);
+}
+
+template <typename T>
+cudaError_t launch_inverse_psi_z(const InvPsiArgs<T>& a, cudaStream_t st) {
+  if (a.nxy <= 0 || a.nz <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((a.nxy + 63) / 64), 2);
+  k_inverse_psi_z<T><<<grid, 64, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_inverse_psi_z<float>(const InvPsiArgs<float>&, cudaStream_t);
+template cudaError_t launch_inverse_psi_z<double>(const InvPsiArgs<double>&, cudaStream_t);
+
+}  // namespace picgb

@@ -116,6 +116,22 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st);
 template <typename T>
 cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);
 
+// Psi_E(D_z) Psi_B(D_z)^-1 applied in place to the two transverse E copies (k_fields.cu); work:
+// 2 x ncell complex doubles of scratch
+template <typename T>
+struct InvPsiArgs {
+  T* f[2];
+  double2* work;
+  long long nxy;
+  int nz;
+  int nf;  // factors (the degree of Psi_B)
+  double lam_re[4], lam_im[4];
+  double scale;
+  double pe_taps[9];  // Psi_E(D_z), applied first
+};
+template <typename T>
+cudaError_t launch_inverse_psi_z(const InvPsiArgs<T>& a, cudaStream_t st);
+
 // ---- adjoint of the 2D step (k_adjoint.cu) ----
 // bins of the current buffers -> flat arrays indexed by particle id (f.np = number of ids);
 // `seen` (optional, one zeroed bit per id) flags repeated ids

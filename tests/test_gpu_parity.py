@@ -53,15 +53,18 @@ def _compare(pair, tol, fields=True, particles=True, field_floor=0.0):
 
 
 def _random_pair(ndim, precision, scheme=0, nx=40, ny=12, nz=72, npart=20000, seed=0, psi=True, alpha=0.5,
-                 targets=3, nbin=1, ncomp=1, calpha=3.0, sigma=0.0, field_scale=2e-2, order=1):
+                 targets=3, nbin=1, ncomp=1, calpha=3.0, sigma=0.0, field_scale=2e-2, order=1, corr_mode=0,
+                 coeffs=None):
     dt = alpha if ndim == 2 else min(alpha, 0.55)
     cfg = make_cfg(ndim=ndim, nx=nx, ny=ny, nz=nz, dt=dt, scheme=scheme, precision=precision, targets=targets,
-                   nbin=nbin, ncomp=ncomp, calpha=calpha, sigma_perp=sigma, order=order)
+                   nbin=nbin, ncomp=ncomp, calpha=calpha, sigma_perp=sigma, order=order, corr_mode=corr_mode)
     shape = (nz, ny if ndim == 3 else 1, nx)
     fields = synth.random_fields(shape, seed=seed + 100, scale=field_scale, smooth=1)
     part = synth.random_particles(ndim, nx, ny if ndim == 3 else 1, nz, npart, seed=seed + 200,
                                   per_particle_weight=sigma > 0)
-    return Pair(cfg, psi=_coeffs(scheme, alpha) if psi else None, fields=fields, part=part)
+    if coeffs is None and psi:
+        coeffs = _coeffs(scheme, alpha)
+    return Pair(cfg, psi=coeffs, fields=fields, part=part)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -672,6 +672,55 @@ def run_gamma_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_variants(args):
+    """Sec. 3's sensitivity variants of the corrected, filtered run (cubic Galerkin, 128 x 128, gamma
+    130): the fitted growth rate of W_perp at several c dt/dz for the baseline (Psi_E on E, Psi_B on
+    the other copies, filter (1,1,a=3) on J and the copies), (1) no digital filter apart from Psi_B,
+    (2) the rational multiplier Psi_E / Psi_B on E only, (3) no compensation pass, and (0) no
+    correction at all."""
+    import numpy as np
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    every, tmax = 10, args.gamma_time
+    alphas = [0.3, 0.5, 0.6, 0.7]
+    variants = {
+        "baseline": dict(),
+        "no_filter": dict(filter_targets=0),
+        "rational_on_E_only": dict(correction_mode=1),
+        "no_compensation": dict(filter_ncomp=0),
+        "no_correction": dict(_corr=False),
+    }
+    table = {}
+    t0 = time.perf_counter()
+    for name, kw in variants.items():
+        kw = dict(kw)
+        corr = kw.pop("_corr", True)
+        rates = []
+        for alpha in alphas:
+            cfg = P.pic_config_default(nx=128, nz=128, dt=alpha, gamma=130.0, scheme=0, precision=P.PIC_FP32,
+                                       ppc_per_species=4, shape_order=3, init_beam=1, seed=13, diag_every=every,
+                                       bin_capacity=96, **kw)
+            h = P.pic_create(cfg)
+            if corr:
+                P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(0, alpha))
+            steps = int(round(tmax / alpha / every)) * every
+            P.pic_step(h, steps)
+            w = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+            P.pic_destroy(h)
+            t = np.arange(1, len(w) + 1) * every * alpha
+            rates.append(float(P.pic_fit_growth_rate(t, w)[0]))
+        table[name] = rates
+    line = {"metric": "fitted growth rate of W_perp per variant of the correction (Sec. 3)", "value": None,
+            "unit": "1 / (dz/c)", "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"2D 128x128 beam, 4 particles/cell/species, cubic Galerkin, gamma 130, "
+                                   f"c t/dz = {tmax} per run", "alphas": alphas,
+                       "wall_s": round(time.perf_counter() - t0, 1)},
+            "growth_rates": table}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -693,7 +742,9 @@ def main(argv=None):
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
     ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
     ap.add_argument("--gamma-sweep", action="store_true", help="growth against c dt/dz at gamma 3 and 130 instead")
-    ap.add_argument("--gamma-time", type=float, default=700.0, help="c t / dz of each --gamma-sweep run")
+    ap.add_argument("--gamma-time", type=float, default=2000.0,
+                    help="c t / dz of each --gamma-sweep / --variants run")
+    ap.add_argument("--variants", action="store_true", help="growth of the Sec. 3 correction variants instead")
     ap.add_argument("--scheme", default="galerkin", choices=("galerkin", "uniform", "momentum"))
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")
@@ -710,6 +761,8 @@ def main(argv=None):
         run_3d(args)
     elif args.gamma_sweep:
         run_gamma_sweep(args)
+    elif args.variants:
+        run_variants(args)
     else:
         run_ours(args)
 

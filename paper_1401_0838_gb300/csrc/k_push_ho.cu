@@ -2,9 +2,10 @@
 // momentum-conserving gather (the scheme Eq. 5 belongs to): gather, Boris push, move, Esirkepov
 // deposition and rebin in one kernel, for any (shape order 1 or 3) x (Galerkin, Uniform,
 // momentum-conserving) combination in 2D and 3D. The linear Galerkin / Uniform step has its own,
-// more specialised kernel (k_particles.cu); this one keeps a plain structure: one CTA per particle
-// tile, the field copies and the tile's current in shared memory, one thread per cell walking the
-// cell's particles, the deposit added with shared-memory atomics.
+// more specialised kernel (k_particles.cu). Here: one CTA per particle tile with the field copies
+// and the tile's current in shared memory; in 2D one warp per cell (lanes over the cell's
+// particles, the deposit reduced over the warp), in 3D one thread per cell walking the cell's
+// particles with the deposit added by shared-memory atomics.
 //
 // Shapes: centred B-splines S_n (S0 box, S1 hat, S2 quadratic, S3 cubic). Gather along a
 // direction: Uniform uses the particle shape order n at the component's own (staggered) nodes;
@@ -121,62 +122,85 @@ __device__ __forceinline__ void gweights(T o, int st, int ord, int& first, T (&w
   for (int q = 0; q < 4; ++q) w[q] = q <= ord ? bspl(ord, xs - T(first + q)) : T(0);
 }
 
-// Stagger of Ex Ey Ez Bx By Bz along x, y, z.
-__device__ __constant__ int c_stag_ho[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+// Stagger of Ex Ey Ez Bx By Bz along x, y, z (compile-time, so that the gather's orders and loop
+// bounds fold for each unrolled component).
+__host__ __device__ constexpr int stag_ho(int c, int axis) {
+  return axis == 0 ? (c == 0 || c == 4 || c == 5) : (axis == 1 ? (c == 1 || c == 3 || c == 5) : (c == 2 || c == 3 || c == 4));
+}
 
-template <typename T, int NDIM, int ORDER, int SCHEME>
-__device__ __forceinline__ T gather_comp(const T* sgc, int c, int lx, int ly, int lz, T ox, T oy, T oz) {
+template <typename T, int NDIM, int ORDER, int SCHEME, int C>
+__device__ __forceinline__ T gather_comp(const T* sgc, int lx, int ly, int lz, T ox, T oy, T oz) {
   using G = HoGeom<NDIM, ORDER>;
+  // momentum-conserving: integer nodes of the averaged tile; Galerkin: one order lower along the
+  // component's half-staggered directions; Uniform: the shape order at the component's nodes
+  constexpr int SX = SCHEME == 2 ? 0 : stag_ho(C, 0), SY = SCHEME == 2 ? 0 : stag_ho(C, 1);
+  constexpr int SZ = SCHEME == 2 ? 0 : stag_ho(C, 2);
+  constexpr int OX = SCHEME == 0 ? ORDER - SX : ORDER, OZ = SCHEME == 0 ? ORDER - SZ : ORDER;
+  constexpr int OY = NDIM == 3 ? (SCHEME == 0 ? ORDER - SY : ORDER) : 0;
   int fx, fy = 0, fz;
   T wx[4], wy[4] = {T(1), T(0), T(0), T(0)}, wz[4];
-  int ox_ord, oy_ord = 0, oz_ord;
-  if (SCHEME == 2) {  // momentum-conserving: integer nodes, averaged tile
-    ox_ord = oy_ord = oz_ord = ORDER;
-    gweights(ox, 0, ORDER, fx, wx);
-    if (NDIM == 3) gweights(oy, 0, ORDER, fy, wy);
-    gweights(oz, 0, ORDER, fz, wz);
-  } else {
-    const int sx = c_stag_ho[c][0], sy = c_stag_ho[c][1], sz = c_stag_ho[c][2];
-    ox_ord = SCHEME == 0 ? ORDER - sx : ORDER;
-    oy_ord = SCHEME == 0 ? ORDER - sy : ORDER;
-    oz_ord = SCHEME == 0 ? ORDER - sz : ORDER;
-    gweights(ox, sx, ox_ord, fx, wx);
-    if (NDIM == 3) gweights(oy, sy, oy_ord, fy, wy);
-    gweights(oz, sz, oz_ord, fz, wz);
-  }
-  if (NDIM == 2) oy_ord = 0;
+  gweights(ox, SX, OX, fx, wx);
+  if (NDIM == 3) gweights(oy, SY, OY, fy, wy);
+  gweights(oz, SZ, OZ, fz, wz);
   T acc = T(0);
-  for (int c3 = 0; c3 <= oz_ord; ++c3) {
+#pragma unroll
+  for (int c3 = 0; c3 <= OZ; ++c3) {
     const int iz = lz + fz + c3 + G::H;
-    for (int c2 = 0; c2 <= oy_ord; ++c2) {
+#pragma unroll
+    for (int c2 = 0; c2 <= OY; ++c2) {
       const int iy = NDIM == 3 ? ly + fy + c2 + G::H : 0;
       const T* row = sgc + (iz * G::GY + iy) * G::GX + lx + fx + G::H;
-      const T wyz = wz[c3] * wy[c2];
       T r = T(0);
-      for (int c1 = 0; c1 <= ox_ord; ++c1) r += wx[c1] * row[c1];
-      acc += wyz * r;
+#pragma unroll
+      for (int c1 = 0; c1 <= OX; ++c1) r += wx[c1] * row[c1];
+      acc += wz[c3] * wy[c2] * r;
     }
   }
   return acc;
 }
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
-__global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ RunDev<T> r) {
+__device__ __forceinline__ void gather6(const T* sg, int lx, int ly, int lz, T ox, T oy, T oz, T (&F)[6]) {
+  using G = HoGeom<NDIM, ORDER>;
+  F[0] = gather_comp<T, NDIM, ORDER, SCHEME, 0>(sg, lx, ly, lz, ox, oy, oz);
+  F[1] = gather_comp<T, NDIM, ORDER, SCHEME, 1>(sg + G::GN, lx, ly, lz, ox, oy, oz);
+  F[2] = gather_comp<T, NDIM, ORDER, SCHEME, 2>(sg + 2 * G::GN, lx, ly, lz, ox, oy, oz);
+  F[3] = gather_comp<T, NDIM, ORDER, SCHEME, 3>(sg + 3 * G::GN, lx, ly, lz, ox, oy, oz);
+  F[4] = gather_comp<T, NDIM, ORDER, SCHEME, 4>(sg + 4 * G::GN, lx, ly, lz, ox, oy, oz);
+  F[5] = gather_comp<T, NDIM, ORDER, SCHEME, 5>(sg + 5 * G::GN, lx, ly, lz, ox, oy, oz);
+}
+
+// Tile geometry shared by the step's phases.
+struct HoTileRef {
+  int X0, Y0, Z0, wx, wy, wz, nxy;
+};
+
+template <int NDIM>
+__device__ __forceinline__ HoTileRef ho_tile(const int ntx, const int nty, const int nx, const int ny, const int nz) {
+  using TL = HoTile<NDIM>;
+  const int tile = blockIdx.x;
+  const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
+  HoTileRef t;
+  t.X0 = tix * TL::TX;
+  t.Y0 = tiy * TL::TY;
+  t.Z0 = tiz * TL::TZ;
+  t.wx = min(TL::TX, nx - t.X0);
+  t.wy = min(TL::TY, ny - t.Y0);
+  t.wz = min(TL::TZ, nz - t.Z0);
+  t.nxy = nx * ny;  // cells < 2^30
+  return t;
+}
+
+// Phases 1-2: field copies of the tile and halo into shared memory (node-averaged for the
+// momentum scheme), the tile's current zeroed, input counts read (and zeroed), output counts zeroed.
+template <typename T, int NDIM, int ORDER, int SCHEME>
+__device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef& t, T* sg, T* sj, int* sn,
+                                            int* scnt) {
   using G = HoGeom<NDIM, ORDER>;
   using TL = HoTile<NDIM>;
-  constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sg = reinterpret_cast<T*>(smem_raw);
-  T* sj = sg + 6 * G::GN;
-  int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);  // [species][cell] input counts
-  int* scnt = sn + 2 * NCL;                          // [species][cell] output counts
-
-  const int tile = blockIdx.x, tid = threadIdx.x;
-  const int tix = tile % r.ntx, tiy = (tile / r.ntx) % r.nty, tiz = tile / (r.ntx * r.nty);
-  const int X0 = tix * TX, Y0 = tiy * TY, Z0 = tiz * TZ;
-  const int wx = min(TX, r.nx - X0), wy = min(TY, r.ny - Y0), wz = min(TZ, r.nz - Z0);
-  const int nxy = r.nx * r.ny;  // cells < 2^30
-
+  constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, H = G::H;
+  const int tid = threadIdx.x;
+  const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
   // 1. field copies of the tile and its halo (periodic), current tile zeroed
   for (int e = tid; e < 6 * G::GN; e += HO_THREADS) {
     const int c = e / G::GN, rem = e - c * G::GN;
@@ -207,7 +231,7 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
       const int nrows = G::GN / len;
       for (int e = tid; e < 6 * nrows; e += HO_THREADS) {
         const int c = e / nrows, row = e - c * nrows;
-        if (!c_stag_ho[c][axis]) continue;
+        if (!stag_ho(c, axis)) continue;
         int base;  // first element of the row
         if (axis == 0) base = row * G::GX;
         else if (axis == 1) base = (row / G::GX) * G::GX * G::GY + row % G::GX;
@@ -236,6 +260,83 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
   }
   __syncthreads();
 
+}
+
+// Phases 4-6: output counts, the tile's current into global memory, the step's kinetic sums.
+template <typename T, int NDIM, int ORDER>
+__device__ __forceinline__ void ho_epilogue(const RunDev<T>& r, const HoTileRef& t, T* sj, int* scnt, T kin,
+                                            int npush) {
+  using G = HoGeom<NDIM, ORDER>;
+  using TL = HoTile<NDIM>;
+  constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, H = G::H;
+  const int tid = threadIdx.x;
+  const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
+  __syncthreads();
+  // 4. output counts of the tile's cells
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
+      r.out[0].cnt[cell] = scnt[cl];
+      r.out[1].cnt[cell] = scnt[NCL + cl];
+    }
+  }
+  // 5. the tile's current into global memory
+  for (int e = tid; e < 3 * G::JN; e += HO_THREADS) {
+    const T v = sj[e];
+    if (v == T(0)) continue;
+    const int c = e / G::JN, rem = e - c * G::JN;
+    const int lz = rem / (G::JX * G::JY), ly = (rem / G::JX) % G::JY, lx = rem % G::JX;
+    const int gx = wrap_any(X0 - H + lx, r.nx);
+    const int gy = NDIM == 3 ? wrap_any(Y0 - H + ly, r.ny) : 0;
+    const int gz = wrap_any(Z0 - H + lz, r.nz);
+    T* dst = c == 0 ? r.j[0] : (c == 1 ? r.j[1] : r.j[2]);
+    atomicAdd(dst + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
+  }
+  // 6. kinetic energy and particle count of the step (FP64 across the block and the grid)
+  if (r.kin) {
+    double kd = (double)kin;
+    int nd = npush;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kd += __shfl_xor_sync(0xffffffffu, kd, o);
+      nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    __shared__ double skin[HO_THREADS / 32];
+    __shared__ int scn[HO_THREADS / 32];
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+      skin[warp] = kd;
+      scn[warp] = nd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      long long c = 0;
+      for (int w2 = 0; w2 < HO_THREADS / 32; ++w2) {
+        t += skin[w2];
+        c += scn[w2];
+      }
+      atomicAdd(r.kin, t);
+      atomicAdd(r.kin + 1, (double)c);
+    }
+  }
+}
+
+template <typename T, int NDIM, int ORDER, int SCHEME>
+__global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ RunDev<T> r) {
+  using G = HoGeom<NDIM, ORDER>;
+  using TL = HoTile<NDIM>;
+  constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sg = reinterpret_cast<T*>(smem_raw);
+  T* sj = sg + 6 * G::GN;
+  int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);  // [species][cell] input counts
+  int* scnt = sn + 2 * NCL;                          // [species][cell] output counts
+  const int tid = threadIdx.x;
+  const HoTileRef tr = ho_tile<NDIM>(r.ntx, r.nty, r.nx, r.ny, r.nz);
+  const int X0 = tr.X0, Y0 = tr.Y0, Z0 = tr.Z0, wx = tr.wx, wy = tr.wy, wz = tr.wz;
+  ho_prologue<T, NDIM, ORDER, SCHEME>(r, tr, sg, sj, sn, scnt);
   const bool has_w = r.in[0].w != nullptr, has_id = r.in[0].id != nullptr;
   T kin = T(0);
   int npush = 0;
@@ -257,9 +358,7 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
         const unsigned id = has_id ? pin.id[slot] : 0u;
         // gather
         T F[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-          F[c] = gather_comp<T, NDIM, ORDER, SCHEME>(sg + c * G::GN, c, lx, ly, lz, ox, oy, oz);
+        gather6<T, NDIM, ORDER, SCHEME>(sg, lx, ly, lz, ox, oy, oz, F);
         // relativistic Boris, momenta relative to the drift u0 z_hat
         const T h = qs * r.hq;
         const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
@@ -428,65 +527,236 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
       }
     }
   }
-  __syncthreads();
-  // 4. output counts of the tile's cells
-  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
-    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
-    if (lx < wx && ly < wy && lz < wz) {
-      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
-      r.out[0].cnt[cell] = scnt[cl];
-      r.out[1].cnt[cell] = scnt[NCL + cl];
-    }
-  }
-  // 5. the tile's current into global memory
-  for (int e = tid; e < 3 * G::JN; e += HO_THREADS) {
-    const T v = sj[e];
-    if (v == T(0)) continue;
-    const int c = e / G::JN, rem = e - c * G::JN;
-    const int lz = rem / (G::JX * G::JY), ly = (rem / G::JX) % G::JY, lx = rem % G::JX;
-    const int gx = wrap_any(X0 - H + lx, r.nx);
-    const int gy = NDIM == 3 ? wrap_any(Y0 - H + ly, r.ny) : 0;
-    const int gz = wrap_any(Z0 - H + lz, r.nz);
-    T* dst = c == 0 ? r.j[0] : (c == 1 ? r.j[1] : r.j[2]);
-    atomicAdd(dst + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
-  }
-  // 6. kinetic energy and particle count of the step (FP64 across the block and the grid)
-  if (r.kin) {
-    double kd = (double)kin;
-    int nd = npush;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      kd += __shfl_xor_sync(0xffffffffu, kd, o);
-      nd += __shfl_xor_sync(0xffffffffu, nd, o);
-    }
-    __shared__ double skin[HO_THREADS / 32];
-    __shared__ int scn[HO_THREADS / 32];
-    const int lane = tid & 31, warp = tid >> 5;
-    if (lane == 0) {
-      skin[warp] = kd;
-      scn[warp] = nd;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0;
-      long long c = 0;
-      for (int w2 = 0; w2 < HO_THREADS / 32; ++w2) {
-        t += skin[w2];
-        c += scn[w2];
+  ho_epilogue<T, NDIM, ORDER>(r, tr, sj, scnt, kin, npush);
+}
+
+// 2D, one warp per cell: lanes take the cell's particles (consecutive slots, both species), so the
+// loads are coalesced and every lane's Esirkepov window is the cell's window (nodes K0 .. K0+NW-1
+// per direction, which holds any move of less than a cell). The NV window sums are reduced over
+// the warp in chunks of 32 by a butterfly transpose (lane L ends with the warp's total of entry L
+// of the chunk) and added to the tile's current with one shared-memory atomic per lane and chunk.
+template <typename T, int ORDER, int SCHEME>
+__global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant__ RunDev<T> r) {
+  using G = HoGeom<2, ORDER>;
+  constexpr int TX = HoTile<2>::TX, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
+  constexpr int NVX = (NW - 1) * NW, NVZ = NW * (NW - 1), NVY = NW * NW, NV = NVX + NVZ + NVY;
+  constexpr int NCH = (NV + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sg = reinterpret_cast<T*>(smem_raw);
+  T* sj = sg + 6 * G::GN;
+  int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);
+  int* scnt = sn + 2 * NCL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const HoTileRef tr = ho_tile<2>(r.ntx, r.nty, r.nx, r.ny, r.nz);
+  const int X0 = tr.X0, Z0 = tr.Z0, wx = tr.wx, wz = tr.wz;
+  ho_prologue<T, 2, ORDER, SCHEME>(r, tr, sg, sj, sn, scnt);
+  const bool has_w = r.in[0].w != nullptr, has_id = r.in[0].id != nullptr;
+  T kin = T(0);
+  int npush = 0;
+  for (int cl = warp; cl < NCL; cl += HO_THREADS / 32) {
+    const int lx = cl % TX, lz = cl / TX;
+    const int gi = X0 + lx, gk = Z0 + lz;
+    const int cell = gk * r.nx + gi;
+    const int n0 = sn[cl], ntot = n0 + sn[NCL + cl];
+    const int bx = lx + K0 + H, bz = lz + K0 + H;  // current-tile index of window node 0
+    for (int base = 0; base < ntot; base += 32) {
+      const int idx = base + lane;
+      const bool valid = idx < ntot;
+      const int s = idx >= n0 ? 1 : 0;
+      const int j = s ? idx - n0 : idx;
+      const SpeciesBuf<T>& pin = s ? r.in[1] : r.in[0];
+      T ox = T(0.5), oz = T(0.5), ux = T(0), uy = T(0), uz = T(0), w = T(0);
+      unsigned id = 0u;
+      if (valid) {
+        const long long slot = (long long)cell * r.cap + j;
+        ox = pin.ox[slot];
+        oz = pin.oz[slot];
+        ux = pin.dux[slot];
+        uy = pin.duy[slot];
+        uz = pin.duz[slot];
+        w = has_w ? pin.w[slot] : r.wconst;
+        if (has_id) id = pin.id[slot];
       }
-      atomicAdd(r.kin, t);
-      atomicAdd(r.kin + 1, (double)c);
+      const T qs = s ? T(1) : T(-1);
+      // gather and relativistic Boris (momenta relative to the drift u0 z_hat)
+      T F[6];
+      gather6<T, 2, ORDER, SCHEME>(sg, lx, 0, lz, ox, T(0), oz, F);
+      const T h = qs * r.hq;
+      const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
+      const T Mz = r.u0 + mz;
+      const T ig = T(1) / sqrt(T(1) + mx * mx + my * my + Mz * Mz);
+      const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
+      const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+      const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
+      const T qx = mx + (my * tz - Mz * ty);
+      const T qy = my + (Mz * tx - mx * tz);
+      const T qz = Mz + (mx * ty - my * tx);
+      ux = mx + (qy * sz - qz * sy) + h * F[0];
+      uy = my + (qz * sx - qx * sz) + h * F[1];
+      uz = mz + (qx * sy - qy * sx) + h * F[2];
+      const T Uz = r.u0 + uz;
+      const T u2 = ux * ux + uy * uy + Uz * Uz;
+      const T gam = sqrt(T(1) + u2);
+      const T ign = T(1) / gam;
+      if (valid) {
+        kin += w * u2 / (gam + T(1));
+        ++npush;
+      }
+      T ddx = r.dtdx * ux * ign, ddz = r.dtdz * Uz * ign;
+      const T vy = uy * ign;
+      if (valid && !(ddx > T(-1) && ddx < T(1) && ddz > T(-1) && ddz < T(1))) {
+        flag_error(r.err, ERR_NONFINITE);
+        ddx = ddz = T(0);
+        ux = uy = uz = T(0);
+      }
+      if (!valid) ddx = ddz = T(0);
+      // Esirkepov on the cell's window
+      T S0x[NW], dSx[NW], S0z[NW], dSz[NW], Tx[NW], Tz[NW];
+#pragma unroll
+      for (int a = 0; a < NW; ++a) {
+        const T node = T(K0 + a);
+        S0x[a] = bspl(ORDER, node - ox);
+        dSx[a] = shape_change(ORDER, node - ox, ddx);
+        S0z[a] = bspl(ORDER, node - oz);
+        dSz[a] = shape_change(ORDER, node - oz, ddz);
+        Tx[a] = S0x[a] + T(0.5) * dSx[a];
+        Tz[a] = S0z[a] + T(0.5) * dSz[a];
+      }
+      T PX[NW - 1], PZ[NW - 1];  // running sums of dS (the last, over the whole window, is 0)
+      PX[0] = dSx[0];
+      PZ[0] = dSz[0];
+#pragma unroll
+      for (int a = 1; a < NW - 1; ++a) {
+        PX[a] = PX[a - 1] + dSx[a];
+        PZ[a] = PZ[a - 1] + dSz[a];
+      }
+      const T qw = valid ? qs * w : T(0);
+      const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        T v[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int i = ch * 32 + t;
+          if (i < NVX) {  // Jx(a + 1/2, b): i = b (NW - 1) + a
+            v[t] = cx * PX[i % (NW - 1)] * Tz[i / (NW - 1)];
+          } else if (i < NVX + NVZ) {  // Jz(a, b + 1/2): i - NVX = a (NW - 1) + b
+            const int k = i - NVX;
+            v[t] = cz * PZ[k % (NW - 1)] * Tx[k / (NW - 1)];
+          } else if (i < NV) {  // Jy(a, b): i - NVX - NVZ = b NW + a
+            const int k = i - NVX - NVZ;
+            v[t] = cy * (Tx[k % NW] * Tz[k / NW] + dSx[k % NW] * dSz[k / NW] * T(1.0 / 12.0));
+          } else {
+            v[t] = T(0);
+          }
+        }
+#pragma unroll
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+          const bool up = (lane & sh) != 0;
+#pragma unroll
+          for (int q = 0; q < sh; ++q) {
+            const T send = up ? v[q] : v[q + sh];
+            const T keep = up ? v[q + sh] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+          }
+        }
+        const int i = ch * 32 + lane;
+        if (i < NV && v[0] != T(0)) {
+          int comp, a, b;
+          if (i < NVX) {
+            comp = 0;
+            a = i % (NW - 1);
+            b = i / (NW - 1);
+          } else if (i < NVX + NVZ) {
+            comp = 2;
+            a = (i - NVX) / (NW - 1);
+            b = (i - NVX) % (NW - 1);
+          } else {
+            comp = 1;
+            a = (i - NVX - NVZ) % NW;
+            b = (i - NVX - NVZ) / NW;
+          }
+          atomicAdd(sj + comp * G::JN + (bz + b) * G::JX + bx + a, v[0]);
+        }
+      }
+      // new cell and offsets; rebin
+      int shx, shz;
+      T nox = ox + ddx, noz = oz + ddz;
+      shx = nox < T(0) ? -1 : (nox >= T(1) ? 1 : 0);
+      shz = noz < T(0) ? -1 : (noz >= T(1) ? 1 : 0);
+      nox -= T(shx);
+      noz -= T(shz);
+      if (nox >= T(1)) { nox = T(0); shx += 1; }
+      if (noz >= T(1)) { noz = T(0); shz += 1; }
+      if (nox < T(0)) nox = T(0);
+      if (noz < T(0)) noz = T(0);
+      const int nlx = lx + shx, nlz = lz + shz;
+      const bool stay = valid && nlx >= 0 && nlx < wx && nlz >= 0 && nlz < wz;
+      const bool leave = valid && !stay;
+      const int dkey = stay ? ((nlz * TX + nlx) * 2 + s) : -1 - lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, dkey);
+      const int leader = __ffs(peers) - 1;
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      int slot_base = 0;
+      if (stay && lane == leader) slot_base = atomicAdd(scnt + s * NCL + (dkey >> 1), __popc(peers));
+      slot_base = __shfl_sync(0xffffffffu, slot_base, leader);
+      const unsigned lmask = __ballot_sync(0xffffffffu, leave);
+      int lbase = 0;
+      if (lmask) {
+        const int ll = __ffs(lmask) - 1;
+        if (lane == ll) lbase = atomicAdd(r.lv_count, __popc(lmask));
+        lbase = __shfl_sync(0xffffffffu, lbase, ll);
+      }
+      if (stay) {
+        const SpeciesBuf<T>& pout = s ? r.out[1] : r.out[0];
+        const int jj = slot_base + rank;
+        if (jj < r.cap) {
+          const int dcell = (Z0 + nlz) * r.nx + X0 + nlx;
+          const long long o = (long long)dcell * r.cap + jj;
+          pout.ox[o] = nox;
+          pout.oz[o] = noz;
+          pout.dux[o] = ux;
+          pout.duy[o] = uy;
+          pout.duz[o] = uz;
+          if (has_w) pout.w[o] = w;
+          if (has_id) pout.id[o] = id;
+        } else {
+          flag_error(r.err, ERR_OVERFLOW);
+        }
+      } else if (leave) {
+        const long long o = lbase + __popc(lmask & ((1u << lane) - 1u));
+        if (o < r.lv_cap) {
+          const int ni = wrap_any(gi + shx, r.nx), nk = wrap_any(gk + shz, r.nz);
+          r.lv.key[o] = (nk * r.nx + ni) * 2 + s;
+          r.lv.ox[o] = nox;
+          r.lv.oz[o] = noz;
+          r.lv.dux[o] = ux;
+          r.lv.duy[o] = uy;
+          r.lv.duz[o] = uz;
+          if (has_w) r.lv.w[o] = w;
+          if (has_id) r.lv.id[o] = id;
+        } else {
+          flag_error(r.err, ERR_OVERFLOW);
+        }
+      }
     }
   }
+  ho_epilogue<T, 2, ORDER>(r, tr, sj, scnt, kin, npush);
 }
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
 cudaError_t launch_ho_t(const RunDev<T>& r, cudaStream_t st) {
   using G = HoGeom<NDIM, ORDER>;
   const size_t sm = G::template bytes<T>();
+  const int ntiles = r.ntx * r.nty * r.ntz;
+  if (NDIM == 2) {  // one warp per cell
+    cudaError_t e = ensure_dynamic_smem((const void*)k_push_ho_w2<T, ORDER, SCHEME>, sm);
+    if (e != cudaSuccess) return e;
+    if (ntiles > 0) k_push_ho_w2<T, ORDER, SCHEME><<<ntiles, HO_THREADS, sm, st>>>(r);
+    return cudaGetLastError();
+  }
   cudaError_t e = ensure_dynamic_smem((const void*)k_push_ho<T, NDIM, ORDER, SCHEME>, sm);
   if (e != cudaSuccess) return e;
-  const int ntiles = r.ntx * r.nty * r.ntz;
   if (ntiles > 0) k_push_ho<T, NDIM, ORDER, SCHEME><<<ntiles, HO_THREADS, sm, st>>>(r);
   return cudaGetLastError();
 }

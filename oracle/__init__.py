@@ -29,6 +29,7 @@ _lib = None
 
 GALERKIN, UNIFORM, MOMENTUM = 0, 1, 2
 FILTER_J, FILTER_GATHER = 1, 2
+YEE, CK = 0, 1  # field solvers: Yee, Cole-Karkkainen (2D) in the B update
 
 
 def build(force: bool = False) -> str:
@@ -57,7 +58,8 @@ class Params(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("psi_e", ctypes.c_double * 9), ("psi_b", ctypes.c_double * 9),
                 ("f_nbin", ctypes.c_int), ("f_ncomp", ctypes.c_int), ("f_alpha", ctypes.c_double),
                 ("f_targets", ctypes.c_int), ("order", ctypes.c_int), ("corr_mode", ctypes.c_int),
-                ("psi_b_coef", ctypes.c_double * 5)]
+                ("psi_b_coef", ctypes.c_double * 5), ("solver", ctypes.c_int), ("ck_beta_x", ctypes.c_double),
+                ("ck_beta_z", ctypes.c_double)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -179,9 +181,11 @@ class Sim:
 
     def __init__(self, ndim=2, nx=16, ny=1, nz=16, dx=1.0, dy=1.0, dz=1.0, dt=0.5, scheme=GALERKIN,
                  psi_e=None, psi_b=None, f_nbin=1, f_ncomp=1, f_alpha=3.0, f_targets=FILTER_J | FILTER_GATHER,
-                 order=1, corr_mode=0):
+                 order=1, corr_mode=0, solver=YEE, ck_beta=(0.125, 0.125)):
         if ndim == 2:
             ny, dy = 1, 1.0
+        if solver == CK and ndim != 2:
+            raise ValueError("the Cole-Karkkainen solver is defined here for 2D x-z runs only")
         self.p = Params()
         self.p.ndim, self.p.nx, self.p.ny, self.p.nz = ndim, nx, ny, nz
         self.p.dx, self.p.dy, self.p.dz, self.p.dt = dx, dy, dz, dt
@@ -189,6 +193,8 @@ class Sim:
         self.p.f_nbin, self.p.f_ncomp, self.p.f_alpha, self.p.f_targets = f_nbin, f_ncomp, f_alpha, f_targets
         self.p.order = order
         self.p.corr_mode = corr_mode
+        self.p.solver = solver
+        self.p.ck_beta_x, self.p.ck_beta_z = float(ck_beta[0]), float(ck_beta[1])
         self.set_correction(psi_e, psi_b)
         self.shape = (nz, ny, nx)
         self.f = {n: np.zeros(self.shape) for n in FIELD_NAMES}

@@ -54,6 +54,9 @@ typedef struct {
   int order;              /* particle shape order: 1 (linear) or 3 (cubic) */
   int corr_mode;          /* 0: Psi_E on Ex, Ey and Psi_B on the others; 1: Psi_E / Psi_B on Ex, Ey only */
   double psi_b_coef[5];   /* Psi_B polynomial coefficients (powers of xi), used by corr_mode 1 */
+  int solver;             /* 0: Yee; 1: Cole-Karkkainen curl of E in the B update (2D x-z only) */
+  double ck_beta_x;       /* CK: transverse (z) averaging weight of the x differences */
+  double ck_beta_z;       /* CK: transverse (x) averaging weight of the z differences (Fig. 1: 1/8) */
 } orc_params;
 
 typedef struct {
@@ -312,8 +315,54 @@ void orc_gather_copies(const orc_params* p, const orc_fields* F, double* out[6])
 /* ------------------------------------------------------------------------ */
 /* Yee solver (standard staggering, periodic)                                */
 /* ------------------------------------------------------------------------ */
+/* Cole-Karkkainen solver (named in Sec. 2 for Fig. 1, with beta_z = 1/8), 2D x-z reading: the
+   B update uses a curl of E in which the forward difference along z is averaged over the x
+   neighbours i-1, i, i+1 with weights (beta_z, 1 - 2 beta_z, beta_z), and the forward difference
+   along x over the z neighbours with (beta_x, 1 - 2 beta_x, beta_x). The E update stays Yee's, so
+   Gauss's law and the Esirkepov charge conservation are those of Yee. Both are written out literally
+   below: one averaged difference per call. */
+static double ck_dz(const orc_params* p, const double* f, int i, int k) {
+  const int kp = wrap(k + 1, p->nz);
+  double s = 0.0;
+  for (int a = -1; a <= 1; ++a) {
+    const int ia = wrap(i + a, p->nx);
+    const double w = a == 0 ? 1.0 - 2.0 * p->ck_beta_z : p->ck_beta_z;
+    s += w * (f[idx3(p, ia, 0, kp)] - f[idx3(p, ia, 0, k)]);
+  }
+  return s / p->dz;
+}
+
+static double ck_dx(const orc_params* p, const double* f, int i, int k) {
+  const int ip = wrap(i + 1, p->nx);
+  double s = 0.0;
+  for (int b = -1; b <= 1; ++b) {
+    const int kb = wrap(k + b, p->nz);
+    const double w = b == 0 ? 1.0 - 2.0 * p->ck_beta_x : p->ck_beta_x;
+    s += w * (f[idx3(p, ip, 0, kb)] - f[idx3(p, i, 0, kb)]);
+  }
+  return s / p->dx;
+}
+
+/* B -= h curl_CK E (2D: the y differences vanish) */
+static void orc_ck_b(const orc_params* p, orc_fields* F, double h) {
+  for (int k = 0; k < p->nz; ++k)
+    for (int i = 0; i < p->nx; ++i) {
+      const long c = idx3(p, i, 0, k);
+      const double cex = -ck_dz(p, F->ey, i, k);
+      const double cey = ck_dz(p, F->ex, i, k) - ck_dx(p, F->ez, i, k);
+      const double cez = ck_dx(p, F->ey, i, k);
+      F->bx[c] -= h * cex;
+      F->by[c] -= h * cey;
+      F->bz[c] -= h * cez;
+    }
+}
+
 /* B -= h curl E */
 void orc_yee_b(const orc_params* p, orc_fields* F, double h) {
+  if (p->solver == 1) {
+    orc_ck_b(p, F, h);
+    return;
+  }
   for (int k = 0; k < p->nz; ++k)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {

@@ -632,7 +632,10 @@ def run_gamma_sweep(args):
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
     tmax, every = args.gamma_time, 10  # the same physical time c t / dz for every c dt / dz
+    solver = P.PIC_CK if args.solver == "ck" else P.PIC_YEE
     alphas = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7]
+    if solver == P.PIC_CK:  # past Yee's 2D limit 1/sqrt(2); 0.771-0.783 is a Galerkin breakdown window
+        alphas += [0.75, 0.8, 0.85, 0.9, 0.95]
     table = {}
     t0 = time.perf_counter()
     for scheme_name, scheme in (("galerkin", 0), ("uniform", 1)):
@@ -641,7 +644,7 @@ def run_gamma_sweep(args):
             for alpha in alphas:
                 cfg = P.pic_config_default(nx=128, nz=128, dt=alpha, gamma=gamma, scheme=scheme, precision=P.PIC_FP32,
                                            ppc_per_species=4, shape_order=3, init_beam=1, seed=11,
-                                           diag_every=every, bin_capacity=96)
+                                           diag_every=every, bin_capacity=96, field_solver=solver)
                 h = P.pic_create(cfg)
                 P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(scheme, alpha))
                 steps = int(round(tmax / alpha / every)) * every
@@ -665,7 +668,8 @@ def run_gamma_sweep(args):
             "steps": int(round(tmax / alphas[0])), "warmup": 0, "higher_is_better": False, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "2D 128x128 beam, 4 particles/cell/species, cubic shapes, Psi correction + "
-                                   f"filter (1,1,a=3), gamma in {{3, 130}}, c dt/dz 0.1..0.7, c t/dz = {tmax} each",
+                                   f"filter (1,1,a=3), gamma in {{3, 130}}, c dt/dz {alphas[0]}..{alphas[-1]}, "
+                                   f"{args.solver.upper()} solver, c t/dz = {tmax} each",
                        "wall_s":
                        round(time.perf_counter() - t0, 1)},
             "sweep": out}
@@ -684,7 +688,8 @@ def run_variants(args):
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
     every, tmax = 10, args.gamma_time
-    alphas = [0.3, 0.5, 0.6, 0.7]
+    solver = P.PIC_CK if args.solver == "ck" else P.PIC_YEE
+    alphas = [0.3, 0.5, 0.6, 0.7] if solver == P.PIC_YEE else [0.3, 0.5, 0.7, 0.8, 0.9, 0.95]
     variants = {
         "baseline": dict(),
         "no_filter": dict(filter_targets=0),
@@ -701,7 +706,7 @@ def run_variants(args):
         for alpha in alphas:
             cfg = P.pic_config_default(nx=128, nz=128, dt=alpha, gamma=130.0, scheme=0, precision=P.PIC_FP32,
                                        ppc_per_species=4, shape_order=3, init_beam=1, seed=13, diag_every=every,
-                                       bin_capacity=96, **kw)
+                                       bin_capacity=96, field_solver=solver, **kw)
             h = P.pic_create(cfg)
             if corr:
                 P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(0, alpha))
@@ -715,7 +720,7 @@ def run_variants(args):
     line = {"metric": "fitted growth rate of W_perp per variant of the correction (Sec. 3)", "value": None,
             "unit": "1 / (dz/c)", "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"2D 128x128 beam, 4 particles/cell/species, cubic Galerkin, gamma 130, "
-                                   f"c t/dz = {tmax} per run", "alphas": alphas,
+                                   f"{args.solver.upper()} solver, c t/dz = {tmax} per run", "alphas": alphas,
                        "wall_s": round(time.perf_counter() - t0, 1)},
             "growth_rates": table}
     print(json.dumps(line), flush=True)
@@ -745,6 +750,8 @@ def main(argv=None):
     ap.add_argument("--gamma-time", type=float, default=2000.0,
                     help="c t / dz of each --gamma-sweep / --variants run")
     ap.add_argument("--variants", action="store_true", help="growth of the Sec. 3 correction variants instead")
+    ap.add_argument("--solver", default="yee", choices=("yee", "ck"),
+                    help="field solver of --gamma-sweep / --variants (ck: Cole-Karkkainen, c dt/dz up to 0.95)")
     ap.add_argument("--scheme", default="galerkin", choices=("galerkin", "uniform", "momentum"))
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")

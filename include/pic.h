@@ -37,7 +37,7 @@ extern "C" {
 
 #define PIC_OK 0
 #define PIC_E_ARG (-1)        /* invalid argument or configuration */
-#define PIC_E_CFL (-2)        /* dt violates the Yee Courant limit */
+#define PIC_E_CFL (-2)        /* dt violates the Courant limit of the field solver */
 #define PIC_E_SINGULAR (-3)   /* rational interpolation singular / ill-conditioned */
 #define PIC_E_OOM (-4)        /* device or host allocation failed */
 #define PIC_E_CUDA (-5)       /* a CUDA runtime call failed */
@@ -90,10 +90,20 @@ typedef struct pic_config {
                                rational multiplier Psi_E / Psi_B on the transverse E copies only,
                                Psi_B applied exactly by inverting it along z (Sec. 2; the variant
                                of Sec. 3 with the multiplier on E only) */
+  int field_solver;         /* PIC_YEE (0) or PIC_CK (1): the Cole-Karkkainen solver named in Sec. 2
+                               for Fig. 1 (beta_z = 1/8, c dt/dz = 0.9). 2D only. Its B updates use a
+                               curl of E whose forward difference along z is averaged over the x
+                               neighbours with weights (beta_z, 1 - 2 beta_z, beta_z), and along x over
+                               the z neighbours with beta_x; the E update is Yee's. Stable while
+                               dt^2 max(1/dx^2, 1/dz^2, (1-4 beta_x)/dx^2 + (1-4 beta_z)/dz^2) < 1
+                               (c dt < dz at beta = 1/8, dx = dz) */
+  double ck_beta_x, ck_beta_z; /* CK averaging weights in [0, 1/4]; pic_config_default: 1/8 each */
 } pic_config;
 
 #define PIC_CORR_SPLIT 0
 #define PIC_CORR_RATIONAL 1
+#define PIC_YEE 0
+#define PIC_CK 1
 
 /* Energies, all FP64 sums over the whole grid / all particles (c = 1, m = 1). */
 typedef struct pic_energy_t {
@@ -141,8 +151,8 @@ void pic_config_default(pic_config* cfg);
  */
 int pic_compute_correction_coeffs(int scheme, double alpha, double psi_e[5], double psi_b[5]);
 
-/* Validates cfg (PIC_E_ARG, PIC_E_CFL: dt >= 1/sqrt(sum 1/d^2)), allocates device memory,
- * fills the seeded beam (Philox4x32-10, counter = lattice point) when cfg->init_beam, zero fields.
+/* Validates cfg (PIC_E_ARG; PIC_E_CFL: Yee dt >= 1/sqrt(sum 1/d^2), CK the bound stated at
+ * field_solver), allocates device memory, fills the seeded beam (Philox4x32-10, counter = lattice point) when cfg->init_beam, zero fields.
  * The correction starts off (Psi = 1); set it with pic_set_correction_stencil. */
 int pic_create(const pic_config* cfg, pic_handle** out);
 
@@ -244,10 +254,11 @@ int pic_field_energy_noalloc(const void* const fields[6], long long ncell, int p
  * set of multi-run launches (a persistent push kernel per lanes-per-cell group takes (run, tile)
  * items from a work list; one stencil, migrate, Yee and energy launch cover all runs) replayed from
  * a CUDA graph. The runs must agree on ndim, precision, scheme, shape order, filter and diagnostic
- * settings, per-particle weights and id tracking (PIC_E_ARG otherwise); grids, ppc, gamma, dt,
- * seeds and corrections may differ. Each grid needs at least as many cells per direction as the
- * stencil halos (PIC_E_ARG otherwise). Batched runs use linear shapes with the Galerkin or Uniform
- * gather (cubic shapes or the momentum-conserving gather: PIC_E_ARG).
+ * settings, per-particle weights, id tracking, correction mode and field solver (PIC_E_ARG
+ * otherwise); grids, ppc, gamma, dt, seeds and corrections may differ. Each grid needs at least as
+ * many cells per direction as the stencil halos (PIC_E_ARG otherwise). Batched runs use linear
+ * shapes with the Galerkin or Uniform gather, the split correction and the Yee solver (cubic
+ * shapes, the momentum-conserving gather, the rational multiplier or CK: PIC_E_ARG).
  */
 typedef struct pic_batch pic_batch;
 int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out);
@@ -282,7 +293,8 @@ const char* pic_batch_last_error(const pic_batch* b);
  * every checkpoint_every steps and at the end, in device memory the handle keeps until
  * pic_adjoint_release or pic_destroy: (nsteps / checkpoint_every + 2 + checkpoint_every) states of
  * about N x (8 + 5 x element size) bytes for N particles, plus 6 field arrays each.
- * 2D runs with linear shapes and the Galerkin or Uniform gather only (PIC_E_ARG otherwise), and
+ * 2D runs with linear shapes, the Galerkin or Uniform gather, the split correction and the Yee
+ * solver only (PIC_E_ARG otherwise), and
  * cfg.track_ids = 1 with ids 0 .. N-1, as the seeded beam
  * and any import without explicit ids have (PIC_E_STATE otherwise).
  *

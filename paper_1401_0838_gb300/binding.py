@@ -22,6 +22,7 @@ PIC_FP32, PIC_FP64 = 0, 1
 PIC_FILTER_J, PIC_FILTER_GATHER = 1, 2
 PIC_HOST, PIC_DEVICE = 0, 1
 PIC_CORR_SPLIT, PIC_CORR_RATIONAL = 0, 1
+PIC_YEE, PIC_CK = 0, 1  # field solvers: Yee, Cole-Karkkainen (2D)
 
 # every symbol the header declares
 EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", "pic_set_stream",
@@ -46,7 +47,8 @@ class pic_config(ctypes.Structure):
                 ("filter_nbin", ctypes.c_int), ("filter_ncomp", ctypes.c_int), ("filter_comp_alpha", ctypes.c_double),
                 ("filter_targets", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("init_beam", ctypes.c_int),
                 ("bin_capacity", ctypes.c_int), ("track_ids", ctypes.c_int), ("diag_every", ctypes.c_int),
-                ("diag_capacity", ctypes.c_int), ("correction_mode", ctypes.c_int)]
+                ("diag_capacity", ctypes.c_int), ("correction_mode", ctypes.c_int),
+                ("field_solver", ctypes.c_int), ("ck_beta_x", ctypes.c_double), ("ck_beta_z", ctypes.c_double)]
 
 
 class pic_energy_t(ctypes.Structure):

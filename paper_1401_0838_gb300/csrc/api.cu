@@ -352,6 +352,13 @@ YeeArgs<T> yee_args(pic_handle* h, double hstep) {
   a.cy = (T)(hstep / c.dy);
   a.cz = (T)(hstep / c.dz);
   a.h = (T)hstep;
+  if (c.field_solver == PIC_CK) {
+    a.ck = 1;
+    a.wx0 = (T)(1.0 - 2.0 * c.ck_beta_x);
+    a.wx1 = (T)c.ck_beta_x;
+    a.wz0 = (T)(1.0 - 2.0 * c.ck_beta_z);
+    a.wz1 = (T)c.ck_beta_z;
+  }
   return a;
 }
 
@@ -641,6 +648,8 @@ void pic_config_default(pic_config* c) {
   c->init_beam = 1;
   c->bin_capacity = 0;
   c->track_ids = 0;
+  c->field_solver = PIC_YEE;
+  c->ck_beta_x = c->ck_beta_z = 0.125;
 }
 
 int pic_compute_correction_coeffs(int scheme, double alpha, double psi_e[5], double psi_b[5]) {
@@ -664,10 +673,22 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
       c.diag_every < 0 || c.diag_capacity < 0 ||
       (c.correction_mode != PIC_CORR_SPLIT && c.correction_mode != PIC_CORR_RATIONAL) ||
+      (c.field_solver != PIC_YEE && c.field_solver != PIC_CK) ||
+      (c.field_solver == PIC_CK &&
+       (c.ndim != 2 || !(c.ck_beta_x >= 0.0 && c.ck_beta_x <= 0.25) || !(c.ck_beta_z >= 0.0 && c.ck_beta_z <= 0.25))) ||
       (long long)c.nx * c.ny * c.nz > (1ll << 30) - 1)
     return PIC_E_ARG;
-  const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
-  if (c.dt >= 1.0 / sqrt(inv)) return PIC_E_CFL;
+  if (c.field_solver == PIC_CK) {
+    // sin^2(w dt/2) = dt^2 [sz^2 (1 - 4 bz sx^2) / dz^2 + sx^2 (1 - 4 bx sz^2) / dx^2] is bilinear in
+    // (sx^2, sz^2) in [0, 1]^2, so its largest value sits at a corner
+    const double ix = 1.0 / (c.dx * c.dx), iz = 1.0 / (c.dz * c.dz);
+    const double corner = (1.0 - 4.0 * c.ck_beta_x) * ix + (1.0 - 4.0 * c.ck_beta_z) * iz;
+    const double m = fmax(fmax(ix, iz), corner);
+    if (c.dt * c.dt * m >= 1.0) return PIC_E_CFL;
+  } else {
+    const double inv = 1.0 / (c.dx * c.dx) + (c.ndim == 3 ? 1.0 / (c.dy * c.dy) : 0.0) + 1.0 / (c.dz * c.dz);
+    if (c.dt >= 1.0 / sqrt(inv)) return PIC_E_CFL;
+  }
   pic_handle* h = new pic_handle();
   h->cfg = c;
   h->es = c.precision == PIC_FP32 ? 4 : 8;
@@ -1286,11 +1307,13 @@ int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
         c.filter_nbin != c0.filter_nbin || c.filter_ncomp != c0.filter_ncomp ||
         c.filter_comp_alpha != c0.filter_comp_alpha || c.filter_targets != c0.filter_targets ||
         c.diag_every != c0.diag_every || (c.sigma_perp > 0) != (c0.sigma_perp > 0) ||
-        (c.track_ids != 0) != (c0.track_ids != 0))
+        (c.track_ids != 0) != (c0.track_ids != 0) || c.correction_mode != c0.correction_mode ||
+        c.field_solver != c0.field_solver)
       return PIC_E_ARG;  // these must agree across the runs of one batch
   }
-  if (c0.shape_order != 1 || c0.scheme == PIC_MOMENTUM || c0.correction_mode != PIC_CORR_SPLIT)
-    return PIC_E_ARG;  // batched: linear Galerkin / Uniform with the split correction
+  if (c0.shape_order != 1 || c0.scheme == PIC_MOMENTUM || c0.correction_mode != PIC_CORR_SPLIT ||
+      c0.field_solver != PIC_YEE)
+    return PIC_E_ARG;  // batched: linear Galerkin / Uniform with the split correction, Yee solver
   pic_batch* b = new pic_batch();
   b->es = c0.precision == PIC_FP32 ? 4 : 8;
   b->ndim = c0.ndim;
@@ -1877,8 +1900,11 @@ extern "C" {
 int pic_adjoint_forward(pic_handle* h, int nsteps, int checkpoint_every, double* w_perp) {
   if (!h || nsteps < 0 || checkpoint_every < 1 || !w_perp) return PIC_E_ARG;
   if (h->cfg.ndim != 2) return fail(h, PIC_E_ARG, "the adjoint covers 2D runs");
-  if (h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM || h->cfg.correction_mode != PIC_CORR_SPLIT)
-    return fail(h, PIC_E_ARG, "the adjoint covers linear shapes, the Galerkin or Uniform gather, the split correction");
+  if (h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM || h->cfg.correction_mode != PIC_CORR_SPLIT ||
+      h->cfg.field_solver != PIC_YEE)
+    return fail(h, PIC_E_ARG,
+                "the adjoint covers linear shapes, the Galerkin or Uniform gather, the split correction, the Yee "
+                "solver");
   if (!h->has_id) return fail(h, PIC_E_STATE, "the adjoint needs particle ids (cfg.track_ids = 1)");
   if (h->ncell >= (1LL << 31)) return fail(h, PIC_E_ARG, "the adjoint covers grids below 2^31 cells");
   return h->es == 4 ? adjoint_forward_t<float>(h, nsteps, checkpoint_every, w_perp)

@@ -405,18 +405,27 @@ template cudaError_t launch_yee_e<double>(const YeeArgs<double>&, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Fused Yee step: B -= dt/2 curl E, E += dt (curl B - J), B -= dt/2 curl E on one tile, with the
-// fields staged in shared memory over [-1, C+2) per direction: B^{n+1/2} is formed on [-1, C+1),
-// E^{n+1} on [0, C+1), B^{n+1} on [0, C), and E, B are written back on [0, C). Same arithmetic and
+// fields staged in shared memory over [-HL, C+2) per direction: B^{n+1/2} is formed on [-HB, C+1),
+// E^{n+1} on [-HE, C+1), B^{n+1} on [0, C), and E, B are written back on [0, C). Same arithmetic and
 // order as the three separate updates; one read and one write of E and B per step.
+// Yee: HL = 1, HB = 1, HE = 0. Cole-Karkkainen (2D): the B updates average each forward difference
+// over the two transverse neighbours, which widens every stage by one cell: HL = 3, HB = 2, HE = 1.
 // ---------------------------------------------------------------------------------------------
 constexpr int YEE_THREADS = 256;
 constexpr int YEE2_CX = 32, YEE2_CZ = 32;
 constexpr int YEE3_CX = 16, YEE3_CY = 8, YEE3_CZ = 8;
 
-template <typename T, int NDIM>
+template <bool CK>
+struct YeeHalo {
+  static constexpr int HL = CK ? 3 : 1, HB = CK ? 2 : 1, HE = CK ? 1 : 0;
+};
+
+template <typename T, int NDIM, bool CK>
 __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty) {
+  static_assert(!CK || NDIM == 2, "the Cole-Karkkainen curl is built for 2D x-z runs");
+  constexpr int HL = YeeHalo<CK>::HL, HB = YeeHalo<CK>::HB, HE = YeeHalo<CK>::HE;
   constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY, CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
-  constexpr int LX = CX + 3, LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + 3, LN = LX * LY * LZ;
+  constexpr int LX = CX + HL + 2, LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + HL + 2, LN = LX * LY * LZ;
   constexpr int OY = NDIM == 2 ? 0 : 1;  // local offset of the -1 halo along y
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -426,7 +435,7 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const long long nxy = (long long)a.nx * a.ny;
-  // the launcher only uses this kernel when every direction has at least 3 cells (halos fit)
+  // wrap_near takes any index, so the halos may wrap around grids smaller than the tile
   auto gsrc = [&](int c) -> const T* {
     switch (c) {
       case 0: return a.ex;
@@ -444,32 +453,47 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     const int c = row / (LY * LZ), r2 = row % (LY * LZ);
     const int ly = r2 % LY, lz = r2 / LY;
     const int gy = NDIM == 3 ? wrap_near(Y0 - 1 + ly, a.ny) : 0;
-    const int gz = wrap_near(Z0 - 1 + lz, a.nz);
+    const int gz = wrap_near(Z0 - HL + lz, a.nz);
     const T* srow = gsrc(c) + gz * nxy + (long long)gy * a.nx;
     T* drow = sm + c * LN + r2 * LX;
-    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) cp_async_el(drow + lx, srow + wrap_near(X0 - 1 + lx, a.nx));
+    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) cp_async_el(drow + lx, srow + wrap_near(X0 - HL + lx, a.nx));
   }
   cp_async_wait_all_fields();
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // x lane, row group
   const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
-  // B^{n+1/2} on local [0, C+2) per direction (cells -1 .. C)
+  // CK averaged forward differences at local node l (2D): along z averaged over x, along x over z
+  auto ck_dz = [&](const T* f, int l) -> T {
+    return a.wz0 * (f[l + sz] - f[l]) + a.wz1 * ((f[l + sz - 1] - f[l - 1]) + (f[l + sz + 1] - f[l + 1]));
+  };
+  auto ck_dx = [&](const T* f, int l) -> T {
+    return a.wx0 * (f[l + 1] - f[l]) + a.wx1 * ((f[l + 1 - sz] - f[l - sz]) + (f[l + 1 + sz] - f[l + sz]));
+  };
+  // B^{n+1/2} on cells [-HB, C+1) in x and z ([-1, C+1) in y)
   constexpr int NY2 = NDIM == 3 ? CY + 2 : 1, NY1 = NDIM == 3 ? CY + 1 : 1;
-  for (int row = ty; row < NY2 * (CZ + 2); row += YEE_THREADS / 32)
-    for (int lx = tx; lx < CX + 2; lx += 32) {
-    const int ly = row % NY2, lz = row / NY2;
+  constexpr int NBX = CX + 1 + HB, NBZ = CZ + 1 + HB;
+  for (int row = ty; row < NY2 * NBZ; row += YEE_THREADS / 32)
+    for (int q = tx; q < NBX; q += 32) {
+    const int lx = HL - HB + q, ly = row % NY2, lz = HL - HB + row / NY2;
     const int l = (lz * LY + ly) * LX + lx;
-    const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
-    b[0][l] -= hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey);
-    b[1][l] -= hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez);
-    b[2][l] -= hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex);
+    if (CK) {
+      b[0][l] += hcz * ck_dz(e[1], l);
+      b[1][l] -= hcz * ck_dz(e[0], l) - hcx * ck_dx(e[2], l);
+      b[2][l] -= hcx * ck_dx(e[1], l);
+    } else {
+      const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
+      b[0][l] -= hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey);
+      b[1][l] -= hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez);
+      b[2][l] -= hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex);
+    }
   }
   __syncthreads();
-  // E^{n+1} on local [1, C+2) (cells 0 .. C)
-  for (int row = ty; row < NY1 * (CZ + 1); row += YEE_THREADS / 32)
-    for (int qx = tx; qx < CX + 1; qx += 32) {
-    const int lx = 1 + qx, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = 1 + row / NY1;
+  // E^{n+1} on cells [-HE, C+1) in x and z ([0, C+1) in y)
+  constexpr int NEX = CX + 1 + HE, NEZ = CZ + 1 + HE;
+  for (int row = ty; row < NY1 * NEZ; row += YEE_THREADS / 32)
+    for (int q = tx; q < NEX; q += 32) {
+    const int lx = HL - HE + q, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = HL - HE + row / NY1;
     const int l = (lz * LY + ly) * LX + lx;
     const T bx = b[0][l], by = b[1][l], bz = b[2][l];
     e[0][l] += a.cy * (bz - b[2][l - sy]) - a.cz * (by - b[1][l - sz]) - a.h * j[0][l];
@@ -477,17 +501,24 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     e[2][l] += a.cx * (by - b[1][l - sx]) - a.cy * (bx - b[0][l - sy]) - a.h * j[2][l];
   }
   __syncthreads();
-  // B^{n+1} on local [1, C+1) (cells 0 .. C-1), then write E and B of the tile
+  // B^{n+1} on cells [0, C), then write E and B of the tile
   for (int row = ty; row < CY * CZ; row += YEE_THREADS / 32)
     for (int cx = tx; cx < CX; cx += 32) {
     const int cy = row % CY, cz = row / CY;
     const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
     if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-    const int l = ((cz + 1) * LY + cy + OY) * LX + cx + 1;
+    const int l = ((cz + HL) * LY + cy + OY) * LX + cx + HL;
     const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
-    const T nbx = b[0][l] - (hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey));
-    const T nby = b[1][l] - (hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez));
-    const T nbz = b[2][l] - (hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex));
+    T nbx, nby, nbz;
+    if (CK) {
+      nbx = b[0][l] + hcz * ck_dz(e[1], l);
+      nby = b[1][l] - (hcz * ck_dz(e[0], l) - hcx * ck_dx(e[2], l));
+      nbz = b[2][l] - hcx * ck_dx(e[1], l);
+    } else {
+      nbx = b[0][l] - (hcy * (e[2][l + sy] - ez) - hcz * (e[1][l + sz] - ey));
+      nby = b[1][l] - (hcz * (e[0][l + sz] - ex) - hcx * (e[2][l + sx] - ez));
+      nbz = b[2][l] - (hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex));
+    }
     const long long o = gz * nxy + (long long)gy * a.nx + gx;
     a.ex[o] = ex;
     a.ey[o] = ey;
@@ -498,9 +529,9 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   }
 }
 
-template <typename T, int NDIM>
+template <typename T, int NDIM, bool CK>
 __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty) {
-  yee_tile<T, NDIM>(a, blockIdx.x, ntx, nty);
+  yee_tile<T, NDIM, CK>(a, blockIdx.x, ntx, nty);
 }
 
 template <typename T, int NDIM>
@@ -510,7 +541,7 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_batch(const YeeArgs<T>* __r
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const YeeArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
-  yee_tile<T, NDIM>(a, blockIdx.x - tile_base[run], ntx, nty);
+  yee_tile<T, NDIM, false>(a, blockIdx.x - tile_base[run], ntx, nty);
 }
 
 int yee_tiles(int ndim, int nx, int ny, int nz) {
@@ -541,6 +572,16 @@ template cudaError_t launch_yee_batch<double>(const YeeArgs<double>*, const int*
 
 template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
+  if (ndim == 2 && a.ck) {  // any grid size: the staged halos wrap
+    constexpr int LN = (YEE2_CX + 5) * (YEE2_CZ + 5);
+    const size_t sm = sizeof(T) * 9 * LN;
+    const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2, true>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_fused<T, 2, true><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
+    return cudaGetLastError();
+  }
+  if (a.ck) return cudaErrorInvalidValue;  // 3D CK is not built (pic_create rejects it)
   if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {  // tiny grids: the three separate updates
     YeeArgs<T> hb = a;
     hb.cx = a.cx * T(0.5);
@@ -556,17 +597,17 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
     constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
     const size_t sm = sizeof(T) * 9 * LN;
     const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2>, sm);
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2, false>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, 2><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
+    k_yee_fused<T, 2, false><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
   } else {
     constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
     const size_t sm = sizeof(T) * 9 * LN;
     const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
               ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 3>, sm);
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 3, false>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, 3><<<ntx * nty * ntz, YEE_THREADS, sm, st>>>(a, ntx, nty);
+    k_yee_fused<T, 3, false><<<ntx * nty * ntz, YEE_THREADS, sm, st>>>(a, ntx, nty);
   }
   return cudaGetLastError();
 }

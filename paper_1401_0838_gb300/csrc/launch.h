@@ -39,6 +39,9 @@ struct YeeArgs {
   int nx, ny, nz;
   T cx, cy, cz;  // h / d for the curl differences (h = dt or dt/2)
   T h;           // coefficient of J in the E update
+  int ck = 0;                // 1: Cole-Karkkainen curl of E in the B updates (2D fused kernel only)
+  T wx0 = T(1), wx1 = T(0);  // CK weights of the x differences at z offsets 0 and +-1 (1 - 2 beta_x, beta_x)
+  T wz0 = T(1), wz1 = T(0);  // CK weights of the z differences at x offsets 0 and +-1 (1 - 2 beta_z, beta_z)
 };
 
 void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);

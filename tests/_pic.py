@@ -19,20 +19,21 @@ except Exception:  # the library may not be built on a CPU-only machine
 
 def make_cfg(ndim=2, nx=40, ny=1, nz=72, dt=0.5, gamma=130.0, scheme=0, precision=1, ppc=4, nbin=1, ncomp=1,
              calpha=3.0, targets=3, init_beam=0, track_ids=1, sigma_perp=0.0, seed=1, cap=0, dx=1.0, dy=1.0,
-             dz=1.0, u_th=1e-4, order=1, corr_mode=0):
+             dz=1.0, u_th=1e-4, order=1, corr_mode=0, solver=0, ck_beta=(0.125, 0.125)):
     return P.pic_config_default(ndim=ndim, nx=nx, ny=ny if ndim == 3 else 1, nz=nz, dt=dt, gamma=gamma,
                                 scheme=scheme, precision=precision, ppc_per_species=ppc, filter_nbin=nbin,
                                 filter_ncomp=ncomp, filter_comp_alpha=calpha, filter_targets=targets,
                                 init_beam=init_beam, track_ids=track_ids, sigma_perp=sigma_perp, seed=seed,
                                 bin_capacity=cap, dx=dx, dy=dy if ndim == 3 else 1.0, dz=dz, u_th=u_th,
-                                shape_order=order, correction_mode=corr_mode)
+                                shape_order=order, correction_mode=corr_mode, field_solver=solver,
+                                ck_beta_x=ck_beta[0], ck_beta_z=ck_beta[1])
 
 
 def oracle_for(cfg, psi_e=None, psi_b=None) -> O.Sim:
     return O.Sim(ndim=cfg.ndim, nx=cfg.nx, ny=cfg.ny, nz=cfg.nz, dx=cfg.dx, dy=cfg.dy, dz=cfg.dz, dt=cfg.dt,
                  scheme=cfg.scheme, psi_e=psi_e, psi_b=psi_b, f_nbin=cfg.filter_nbin, f_ncomp=cfg.filter_ncomp,
                  f_alpha=cfg.filter_comp_alpha, f_targets=cfg.filter_targets, order=cfg.shape_order,
-                 corr_mode=cfg.correction_mode)
+                 corr_mode=cfg.correction_mode, solver=cfg.field_solver, ck_beta=(cfg.ck_beta_x, cfg.ck_beta_z))
 
 
 def uniform_weight(cfg):

@@ -6,6 +6,7 @@ import re
 
 import numpy as np
 import pytest
+from pathlib import Path
 
 import oracle as O
 from oracle.fit import growth_rate
@@ -95,6 +96,46 @@ def test_create_validates_before_touching_the_gpu():
     with pytest.raises(P.PicError) as e:
         P.pic_create(cfg)
     assert e.value.code == P.PIC_E_CFL
+
+
+def test_create_validates_the_ck_solver():
+    # CK (2D): stable while dt^2 max(1/dx^2, 1/dz^2, (1-4bx)/dx^2 + (1-4bz)/dz^2) < 1, i.e. dt < 1 at
+    # beta = 1/8, dx = dz = 1; 3D and weights outside [0, 1/4] are rejected before any device work.
+    for kw, code in [(dict(dt=1.0), P.PIC_E_CFL), (dict(dt=0.9, ck_beta_x=0.3), P.PIC_E_ARG),
+                     (dict(dt=0.9, ck_beta_z=-0.01), P.PIC_E_ARG),
+                     (dict(dt=0.5, ndim=3, nx=8, ny=8, nz=8), P.PIC_E_ARG),
+                     (dict(dt=0.75, ck_beta_x=0.0, ck_beta_z=0.0), P.PIC_E_CFL),  # beta = 0 is Yee
+                     (dict(dt=0.9, field_solver=2), P.PIC_E_ARG)]:
+        kw.setdefault("field_solver", P.PIC_CK)
+        with pytest.raises(P.PicError) as e:
+            P.pic_create(P.pic_config_default(**kw))
+        assert e.value.code == code, kw
+    # a stable CK configuration passes validation (and then needs a GPU)
+    try:
+        P.pic_destroy(P.pic_create(P.pic_config_default(field_solver=P.PIC_CK, dt=0.99)))
+    except P.PicError as e:
+        assert e.code == P.PIC_E_CUDA
+
+
+def test_config_struct_layout_matches_header(tmp_path):
+    # the ctypes mirror of pic_config has the C compiler's size and field offsets
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in P.pic_config._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof(pic_config, {n}));\n' for n in names)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "pic.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(pic_config));\n' + body + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = Path(__file__).resolve().parents[1] / "include"
+    subprocess.run([cc, "-I", str(inc), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(P.pic_config)
+    assert out[1:] == [getattr(P.pic_config, n).offset for n in names]
 
 
 def test_destroy_null_is_noop():

@@ -39,6 +39,7 @@ struct pic_handle {
   long long lv_cap = 0;
   double* d_acc = nullptr;  // 8 doubles of reduction scratch
   double* d_red = nullptr;  // block partials of the field-energy reduction
+  double* d_red_yee = nullptr;  // block partials of the energies recorded by the Yee launch
   long long* d_offs = nullptr;
   long long* d_bsum = nullptr;
   long long* d_total = nullptr;
@@ -401,16 +402,22 @@ int step_once(pic_handle* h) {
     SepArgs<T> ja = sep_args<T>(h, false);
     CK(launch(h, PIC_K_FILTER, [&] { return launch_sep<T>(ja, st); }), "current filter");
   }
-  // 7. Yee: B half, E full, B half (one fused launch)
+  // 7. Yee: B half, E full, B half (one fused launch); 8. on diagnostic steps the same launch records
+  // the field energies of the new state into the history slot (a separate reduction on tiny grids)
   YeeArgs<T> ye = yee_args<T>(h, h->cfg.dt);
-  CK(launch(h, PIC_K_YEE, [&] { return launch_yee_fused<T>(ye, h->cfg.ndim, st); }), "yee");
-  // 8. diagnostics: field energies of the new state into the history slot
+  const pic_config& c = h->cfg;
+  HistCtl hc{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
+  const bool fused_diag = rec && yee_records_energy(c.ndim, c.nx, c.ny, c.nz, ye.ck);
+  CK(launch(h, PIC_K_YEE,
+            [&] { return launch_yee_fused<T>(ye, c.ndim, st, h->d_red_yee, fused_diag ? &hc : nullptr); }),
+     "yee");
   if (rec) {
-    const T* f6[6];
-    for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
-    HistCtl hc{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
-    CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, nullptr, h->d_red, hc, st); }),
-       "field energy");
+    if (!fused_diag) {
+      const T* f6[6];
+      for (int q = 0; q < 6; ++q) f6[q] = (const T*)h->f[q];
+      CK(launch(h, PIC_K_DIAG, [&] { return launch_field_energy<T>(f6, h->ncell, nullptr, h->d_red, hc, st); }),
+         "field energy");
+    }
     h->nhist++;
   }
   h->parity ^= 1;
@@ -744,6 +751,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
   if (ok) ok = (h->d_red = (double*)dalloc(h, field_energy_scratch_bytes())) != nullptr;
   if (ok) ok = cudaMemset(h->d_red, 0, field_energy_scratch_bytes()) == cudaSuccess;
+  if (ok) ok = (h->d_red_yee = (double*)dalloc(h, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz))) != nullptr;
+  if (ok) ok = cudaMemset(h->d_red_yee, 0, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz)) == cudaSuccess;
   if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
   if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
   if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;

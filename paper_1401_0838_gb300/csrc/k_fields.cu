@@ -159,9 +159,9 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
   constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
   constexpr int TXN = CX < 32 ? 32 : CX, TYN = SEP_THREADS / TXN;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* s0 = reinterpret_cast<T*>(smraw);  // [LZ][LY][LX]
-  T* s1 = s0 + LZ * LY * LX;            // [CZ][LY][LX]
-  T* s2 = s1 + CZ * LY * LX;            // [CZ][CY][LX] (3D)
+  T* s0 = reinterpret_cast<T*>(smraw);  // [LZ][LY][LX]; the z pass leaves its output in rows [0, CZ)
+  T* s1 = s0;                           // [CZ][LY][LX] (z pass output, in place)
+  T* s2 = s0 + LZ * LY * LX;            // [CZ][CY][LX] (3D)
   const T* __restrict__ src = a.src[comp];
   T* __restrict__ dst = a.dst[comp];
   const int zs = a.zset[comp];
@@ -187,17 +187,36 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
   }
   cp_async_wait_all_fields();
   __syncthreads();
-  for (int row = ty; row < CZ * LY; row += TYN) {  // z pass
-    const int ly = row % LY, lz = row / LY;
-    for (int lx = tx; lx < LX; lx += TXN) {
-      const T* p = s0 + (lz * LY + ly) * LX + lx;
-      T acc = T(0);
+  // z pass in place. A task is one (x, y) column of the staged tile and a segment of ZS output rows;
+  // it reads its ZS + 2 HZ inputs into registers before any task of its round writes, and a column's
+  // segment 0 (rows [0, ZS + 2 HZ) read, [0, ZS) written) always runs in a round no later than its
+  // segment 1 (rows [ZS, 2 ZS + 2 HZ) read), so no task reads a row that another has overwritten.
+  {
+    constexpr int NCOL = LX * LY, NSEG = NDIM == 2 ? 2 : 1, ZS = CZ / NSEG, NTASK = NCOL * NSEG;
+    static_assert(CZ % NSEG == 0, "z segments must tile the output rows");
+    for (int t0 = 0; t0 < NTASK; t0 += SEP_THREADS) {
+      const int t = t0 + threadIdx.x;
+      const bool act = t < NTASK;
+      const int col = t % NCOL, seg = t / NCOL;
+      T* base = s0 + seg * ZS * NCOL + col;
+      T w[ZS + 2 * HZ];
+      if (act) {
 #pragma unroll
-      for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * p[m * LY * LX];
-      s1[row * LX + lx] = acc;
+        for (int m = 0; m < ZS + 2 * HZ; ++m) w[m] = base[m * NCOL];
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < ZS; ++r) {
+          T acc = T(0);
+#pragma unroll
+          for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * w[r + m];
+          base[r * NCOL] = acc;
+        }
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
   const T* sx = s1;
   if (NDIM == 3) {  // y pass
     for (int row = ty; row < CZ * CY; row += TYN) {
@@ -265,7 +284,7 @@ static cudaError_t launch_sep_t(const SepArgs<T>& a, cudaStream_t st) {
   constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
   constexpr int HY = NDIM == 3 ? HX : 0;
   constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
-  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (size_t)CZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
+  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1, ntz = (a.nz + CZ - 1) / CZ;
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_t<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
@@ -295,7 +314,7 @@ static cudaError_t launch_sep_batch_t(const SepArgs<T>* args, const int* tile_ba
   constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
   constexpr int HY = NDIM == 3 ? HX : 0;
   constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
-  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (size_t)CZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
+  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_batch<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)total_tiles, (unsigned)ncomp);
@@ -350,6 +369,132 @@ cudaError_t launch_sep(const SepArgs<T>& a, cudaStream_t st) {
 }
 template cudaError_t launch_sep<float>(const SepArgs<float>&, cudaStream_t);
 template cudaError_t launch_sep<double>(const SepArgs<double>&, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// Field energies: per-thread sums of exact squares and the deterministic block / grid reduction.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int FE_THREADS = 256;
+constexpr int FE_BLOCKS = 8 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
+
+// FP32 sum of exact squares with an error-free running sum: x^2 = hi + lo exactly (lo from an FMA);
+// hi is added by TwoSum (s + hi = t + err exactly) and the small terms err and lo accumulate in c,
+// whose own rounding is O(eps^2) of the sum.
+struct FSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_sq(float x) {
+    const float hi = x * x;
+    const float lo = fmaf(x, x, -hi);
+    const float t = s + hi;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (hi - bb);
+    s = t;
+    c += err + lo;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// Per-thread sums of squares of the six field components: FP32 fields through FSum (exact squares,
+// error-free running sums), FP64 fields with FMAs.
+template <typename T>
+struct EnergyAcc {
+  FSum e2, b2, e2x, e2y, b2x, b2y;  // FP32 fields
+  double se = 0, sb = 0, sp = 0;    // FP64 fields
+  __device__ __forceinline__ void add(T x, T y, T z, T u, T v, T w) {
+    if (sizeof(T) == 4) {
+      e2x.add_sq((float)x);
+      e2y.add_sq((float)y);
+      e2.add_sq((float)z);
+      b2x.add_sq((float)u);
+      b2y.add_sq((float)v);
+      b2.add_sq((float)w);
+    } else {
+      const double dx = x, dy = y, dz = z, du = u, dv = v, dw = w;
+      const double t = fma(dx, dx, dy * dy), tb = fma(du, du, dv * dv);
+      se += fma(dz, dz, t);
+      sb += fma(dw, dw, tb);
+      sp += t + tb;
+    }
+  }
+  // (sum E^2, sum B^2, sum Ex^2 + Ey^2 + Bx^2 + By^2) of this thread
+  __device__ __forceinline__ void get(double& oe, double& ob, double& op) const {
+    if (sizeof(T) == 4) {
+      const double ax = e2x.get(), ay = e2y.get(), bxs = b2x.get(), bys = b2y.get();
+      oe = ax + ay + e2.get();
+      ob = bxs + bys + b2.get();
+      op = ax + ay + bxs + bys;
+    } else {
+      oe = se;
+      ob = sb;
+      op = sp;
+    }
+  }
+};
+
+// Block and grid stage of the energy sums (FE_THREADS threads per block): FP64 tree per block into
+// scratch[3 * block + r]; the last block to finish (counter at scratch + 3 * slots, slots >= the
+// grid size) adds the block partials in a fixed order and writes (sum E^2, sum B^2, sum Ex^2 + Ey^2
+// + Bx^2 + By^2) to out[0..2], or, with a history ring, into its next slot with the kinetic sums.
+__device__ __forceinline__ void energy_finish(double se, double sb, double sp, double* scratch, unsigned slots,
+                                              double* out, const HistCtl& hc) {
+  __shared__ double red[3][FE_THREADS / 32];
+  __shared__ bool last;
+  double dse = warp_sum(se), dsb = warp_sum(sb), dsp = warp_sum(sp);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = dse;
+    red[1][w] = dsb;
+    red[2][w] = dsp;
+  }
+  __syncthreads();
+  unsigned* done = reinterpret_cast<unsigned*>(scratch + 3 * (size_t)slots);
+  if (threadIdx.x < 3) {
+    double t = 0;
+    for (int q = 0; q < FE_THREADS / 32; ++q) t += red[threadIdx.x][q];
+    scratch[3 * blockIdx.x + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) {  // the whole last block adds the partials: strided per thread, then a fixed tree
+    __threadfence();
+    double t[3] = {0, 0, 0};
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += FE_THREADS)
+      for (int r = 0; r < 3; ++r) t[r] += ((volatile double*)scratch)[3 * q + r];
+    for (int r = 0; r < 3; ++r) t[r] = warp_sum(t[r]);
+    __syncthreads();
+    if (lane == 0)
+      for (int r = 0; r < 3; ++r) red[r][w] = t[r];
+    __syncthreads();
+    if (hc.hist) {
+      double* slot = hc.hist + 8 * (*hc.count % hc.cap);
+      if (threadIdx.x < 3) {
+        double acc = 0;
+        for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
+        slot[threadIdx.x] = acc;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        slot[3] = hc.kin[0];
+        slot[4] = hc.kin[1];
+        hc.kin[0] = 0.0;
+        hc.kin[1] = 0.0;
+        *hc.count += 1;
+      }
+    } else if (threadIdx.x < 3) {
+      double acc = 0;
+      for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
+      out[threadIdx.x] = acc;
+    }
+    if (threadIdx.x == 0) *done = 0u;  // ready for the next launch
+  }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Yee updates on the periodic staggered mesh (x fastest). One thread per cell.
@@ -420,8 +565,9 @@ struct YeeHalo {
   static constexpr int HL = CK ? 3 : 1, HB = CK ? 2 : 1, HE = CK ? 1 : 0;
 };
 
-template <typename T, int NDIM, bool CK>
-__device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty) {
+template <typename T, int NDIM, bool CK, bool DIAG>
+__device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty,
+                                         double* escratch = nullptr, const HistCtl* hc = nullptr) {
   static_assert(!CK || NDIM == 2, "the Cole-Karkkainen curl is built for 2D x-z runs");
   constexpr int HL = YeeHalo<CK>::HL, HB = YeeHalo<CK>::HB, HE = YeeHalo<CK>::HE;
   constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY, CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
@@ -501,7 +647,8 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     e[2][l] += a.cx * (by - b[1][l - sx]) - a.cy * (bx - b[0][l - sy]) - a.h * j[2][l];
   }
   __syncthreads();
-  // B^{n+1} on cells [0, C), then write E and B of the tile
+  // B^{n+1} on cells [0, C), then write E and B of the tile (and, with DIAG, sum their energies)
+  EnergyAcc<T> en;
   for (int row = ty; row < CY * CZ; row += YEE_THREADS / 32)
     for (int cx = tx; cx < CX; cx += 32) {
     const int cy = row % CY, cz = row / CY;
@@ -526,12 +673,19 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     a.bx[o] = nbx;
     a.by[o] = nby;
     a.bz[o] = nbz;
+    if (DIAG) en.add(ex, ey, ez, nbx, nby, nbz);
+  }
+  if (DIAG) {  // every thread reaches this (the loop above only skips cells)
+    double se, sb, sp;
+    en.get(se, sb, sp);
+    energy_finish(se, sb, sp, escratch, gridDim.x, nullptr, *hc);
   }
 }
 
-template <typename T, int NDIM, bool CK>
-__global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty) {
-  yee_tile<T, NDIM, CK>(a, blockIdx.x, ntx, nty);
+template <typename T, int NDIM, bool CK, bool DIAG>
+__global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty,
+                                                           double* escratch, const __grid_constant__ HistCtl hc) {
+  yee_tile<T, NDIM, CK, DIAG>(a, blockIdx.x, ntx, nty, escratch, &hc);
 }
 
 template <typename T, int NDIM>
@@ -541,7 +695,7 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_batch(const YeeArgs<T>* __r
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const YeeArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
-  yee_tile<T, NDIM, false>(a, blockIdx.x - tile_base[run], ntx, nty);
+  yee_tile<T, NDIM, false, false>(a, blockIdx.x - tile_base[run], ntx, nty);
 }
 
 int yee_tiles(int ndim, int nx, int ny, int nz) {
@@ -570,16 +724,36 @@ cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int n
 template cudaError_t launch_yee_batch<float>(const YeeArgs<float>*, const int*, int, int, int, cudaStream_t);
 template cudaError_t launch_yee_batch<double>(const YeeArgs<double>*, const int*, int, int, int, cudaStream_t);
 
+bool yee_records_energy(int ndim, int nx, int ny, int nz, int ck) {
+  return ck || !(nx < 3 || nz < 3 || (ndim == 3 && ny < 3));
+}
+size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz) {
+  return sizeof(double) * (3 * (size_t)yee_tiles(ndim, nx, ny, nz) + 2);
+}
+
+template <typename T, int NDIM, bool CK>
+static cudaError_t launch_yee_tiles(const YeeArgs<T>& a, int ntiles, int ntx, int nty, size_t sm, double* escratch,
+                                    const HistCtl* hc, cudaStream_t st) {
+  const HistCtl none{nullptr, 0, nullptr, nullptr};
+  if (hc) {
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, true>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_fused<T, NDIM, CK, true><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, escratch, *hc);
+  } else {
+    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, false>, sm);
+    if (e != cudaSuccess) return e;
+    k_yee_fused<T, NDIM, CK, false><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, nullptr, none);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
-cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
+cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, double* escratch, const HistCtl* hc) {
+  if (hc && (!escratch || !yee_records_energy(ndim, a.nx, a.ny, a.nz, a.ck))) return cudaErrorInvalidValue;
   if (ndim == 2 && a.ck) {  // any grid size: the staged halos wrap
     constexpr int LN = (YEE2_CX + 5) * (YEE2_CZ + 5);
-    const size_t sm = sizeof(T) * 9 * LN;
     const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2, true>, sm);
-    if (e != cudaSuccess) return e;
-    k_yee_fused<T, 2, true><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
-    return cudaGetLastError();
+    return launch_yee_tiles<T, 2, true>(a, ntx * ntz, ntx, 1, sizeof(T) * 9 * LN, escratch, hc, st);
   }
   if (a.ck) return cudaErrorInvalidValue;  // 3D CK is not built (pic_create rejects it)
   if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {  // tiny grids: the three separate updates
@@ -595,146 +769,34 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st) {
   }
   if (ndim == 2) {
     constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
-    const size_t sm = sizeof(T) * 9 * LN;
     const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 2, false>, sm);
-    if (e != cudaSuccess) return e;
-    k_yee_fused<T, 2, false><<<ntx * ntz, YEE_THREADS, sm, st>>>(a, ntx, 1);
-  } else {
-    constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
-    const size_t sm = sizeof(T) * 9 * LN;
-    const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
-              ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, 3, false>, sm);
-    if (e != cudaSuccess) return e;
-    k_yee_fused<T, 3, false><<<ntx * nty * ntz, YEE_THREADS, sm, st>>>(a, ntx, nty);
+    return launch_yee_tiles<T, 2, false>(a, ntx * ntz, ntx, 1, sizeof(T) * 9 * LN, escratch, hc, st);
   }
-  return cudaGetLastError();
+  constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
+  const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
+            ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
+  return launch_yee_tiles<T, 3, false>(a, ntx * nty * ntz, ntx, nty, sizeof(T) * 9 * LN, escratch, hc, st);
 }
-template cudaError_t launch_yee_fused<float>(const YeeArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_yee_fused<double>(const YeeArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_yee_fused<float>(const YeeArgs<float>&, int, cudaStream_t, double*, const HistCtl*);
+template cudaError_t launch_yee_fused<double>(const YeeArgs<double>&, int, cudaStream_t, double*, const HistCtl*);
 
 // ---------------------------------------------------------------------------------------------
 // FP64 reductions
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-constexpr int FE_THREADS = 256;
-constexpr int FE_BLOCKS = 8 * 152;  // partial sums per launch; scratch holds 3 * FE_BLOCKS + 1
-
-// FP32 sum of exact squares with an error-free running sum: x^2 = hi + lo exactly (lo from an FMA);
-// hi is added by TwoSum (s + hi = t + err exactly) and the small terms err and lo accumulate in c,
-// whose own rounding is O(eps^2) of the sum.
-struct FSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add_sq(float x) {
-    const float hi = x * x;
-    const float lo = fmaf(x, x, -hi);
-    const float t = s + hi;
-    const float bb = t - s;
-    const float err = (s - (t - bb)) + (hi - bb);
-    s = t;
-    c += err + lo;
-  }
-  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
-};
-
-// Per thread: FP64 sums of squares (exact products of FP32 values) over a grid-stride set of cells,
-// four per iteration so that several loads are in flight; per block: FP64 tree; the last block to
-// finish adds the block partials (deterministic) and writes out[0..2] = (sum E^2, sum B^2,
-// sum Ex^2+Ey^2+Bx^2+By^2).
+// Field energies of a whole grid: per-thread sums of exact squares over a grid-stride set of cells,
+// then energy_finish (deterministic block and grid stages).
 template <typename T>
 __device__ __forceinline__ void field_energy_body(const T* __restrict__ ex, const T* __restrict__ ey,
                                                   const T* __restrict__ ez, const T* __restrict__ bx,
                                                   const T* __restrict__ by, const T* __restrict__ bz, long long n,
                                                   double* out, double* scratch, const HistCtl& hc) {
-  double se = 0, sb = 0, sp = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (sizeof(T) == 4) {
-    // FP32 fields: each square is formed exactly as hi + lo and summed error-free (FSum), so the
-    // thread's partial equals the FP64 sum of exact squares to ~1e-14; only the cross-thread sums use
-    // the (slow) FP64 pipe.
-    FSum e2, b2, e2x, e2y, b2x, b2y;
-    for (; c < n; c += stride) {
-      const float x = (float)ex[c], y = (float)ey[c], z = (float)ez[c];
-      const float u = (float)bx[c], v = (float)by[c], w = (float)bz[c];
-      e2x.add_sq(x);
-      e2y.add_sq(y);
-      e2.add_sq(z);
-      b2x.add_sq(u);
-      b2y.add_sq(v);
-      b2.add_sq(w);
-    }
-    const double ax = e2x.get(), ay = e2y.get(), bxs = b2x.get(), bys = b2y.get();
-    se = ax + ay + e2.get();
-    sb = bxs + bys + b2.get();
-    sp = ax + ay + bxs + bys;
-  } else {
-    for (; c < n; c += stride) {
-      const double x = ex[c], y = ey[c], z = ez[c], u = bx[c], v = by[c], w = bz[c];
-      const double t = fma(x, x, y * y), tb = fma(u, u, v * v);
-      se += fma(z, z, t);
-      sb += fma(w, w, tb);
-      sp += t + tb;
-    }
-  }
-  __shared__ double red[3][FE_THREADS / 32];
-  __shared__ bool last;
-  double dse = warp_sum(se), dsb = warp_sum(sb), dsp = warp_sum(sp);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][w] = dse;
-    red[1][w] = dsb;
-    red[2][w] = dsp;
-  }
-  __syncthreads();
-  unsigned* done = reinterpret_cast<unsigned*>(scratch + 3 * FE_BLOCKS);
-  if (threadIdx.x < 3) {
-    double t = 0;
-    for (int q = 0; q < FE_THREADS / 32; ++q) t += red[threadIdx.x][q];
-    scratch[3 * blockIdx.x + threadIdx.x] = t;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (last) {  // the whole last block adds the partials: strided per thread, then a fixed tree
-    __threadfence();
-    double t[3] = {0, 0, 0};
-    for (unsigned q = threadIdx.x; q < gridDim.x; q += FE_THREADS)
-      for (int r = 0; r < 3; ++r) t[r] += ((volatile double*)scratch)[3 * q + r];
-    for (int r = 0; r < 3; ++r) t[r] = warp_sum(t[r]);
-    __syncthreads();
-    if (lane == 0)
-      for (int r = 0; r < 3; ++r) red[r][w] = t[r];
-    __syncthreads();
-    if (hc.hist) {
-      double* slot = hc.hist + 8 * (*hc.count % hc.cap);
-      if (threadIdx.x < 3) {
-        double acc = 0;
-        for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
-        slot[threadIdx.x] = acc;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        slot[3] = hc.kin[0];
-        slot[4] = hc.kin[1];
-        hc.kin[0] = 0.0;
-        hc.kin[1] = 0.0;
-        *hc.count += 1;
-      }
-    } else if (threadIdx.x < 3) {
-      double acc = 0;
-      for (int q = 0; q < FE_THREADS / 32; ++q) acc += red[threadIdx.x][q];
-      out[threadIdx.x] = acc;
-    }
-    if (threadIdx.x == 0) *done = 0u;  // ready for the next launch
-  }
+  EnergyAcc<T> acc;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += stride)
+    acc.add(ex[c], ey[c], ez[c], bx[c], by[c], bz[c]);
+  double se, sb, sp;
+  acc.get(se, sb, sp);
+  energy_finish(se, sb, sp, scratch, FE_BLOCKS, out, hc);
 }
 
 template <typename T>

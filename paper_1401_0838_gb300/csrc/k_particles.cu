@@ -60,18 +60,21 @@ __device__ __forceinline__ void read4(const unsigned* p, unsigned (&o)[4]) {
   o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 
-// Per-warp double-buffered stage: [stage][array][lane][4] for the 7 real arrays (ox oy oz dux
-// duy duz w), then [stage][lane][4] ids.
-template <typename T>
+// Per-warp double-buffered stage: [stage][slot][lane][4] for the particle arrays (slots ox oz dux
+// duy duz w in 2D; ox oy oz dux duy duz w in 3D), then [stage][lane][4] ids.
+template <typename T, int NDIM>
 struct PushStage {
+  static constexpr int NSLOT = NDIM == 3 ? 7 : 6;
+  // slot of array a (0 ox, 1 oy, 2 oz, 3 dux, 4 duy, 5 duz, 6 w); 2D stages no oy
+  static constexpr __host__ __device__ int slot(int a) { return NDIM == 3 ? a : (a > 1 ? a - 1 : a); }
   static constexpr __host__ __device__ size_t per_warp_elems() {
-    return 2 * 7 * 32 * 4 + (2 * 32 * 4 * sizeof(unsigned) + sizeof(T) - 1) / sizeof(T);
+    return 2 * NSLOT * 32 * 4 + (2 * 32 * 4 * sizeof(unsigned) + sizeof(T) - 1) / sizeof(T);
   }
   static __device__ __forceinline__ T* at(T* base, int stage, int arr, int lane) {
-    return base + ((stage * 7 + arr) * 32 + lane) * 4;
+    return base + ((stage * NSLOT + slot(arr)) * 32 + lane) * 4;
   }
   static __device__ __forceinline__ unsigned* id_at(T* base, int stage, int lane) {
-    return reinterpret_cast<unsigned*>(base + 2 * 7 * 32 * 4) + (stage * 32 + lane) * 4;
+    return reinterpret_cast<unsigned*>(base + 2 * NSLOT * 32 * 4) + (stage * 32 + lane) * 4;
   }
 };
 
@@ -86,7 +89,7 @@ struct PushSmem {
   static constexpr int JX = TX + 3, JY = (NDIM == 3 ? TY + 3 : 1), JZ = TZ + 3, JN = JX * JY * JZ;
   static constexpr size_t bytes() {
     return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (4 * NCL) + 16 +
-           sizeof(T) * PushStage<T>::per_warp_elems() * (PUSH_THREADS / 32);
+           sizeof(T) * PushStage<T, NDIM>::per_warp_elems() * (PUSH_THREADS / 32);
   }
 };
 
@@ -545,7 +548,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   constexpr int NGRP = NCL / CPW;
   // per-warp stages start on a 16-byte boundary after the counts (cp.async destinations)
   const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(scnt + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
-  T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * PushStage<T>::per_warp_elems();
+  using SG = PushStage<T, NDIM>;
+  T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * SG::per_warp_elems();
   auto group_iters = [&](int g) -> int {
     const int c = g * CPW + lane / LPC;
     const int nq = ((sn[c] + 3) >> 2) + ((sn[NCL + c] + 3) >> 2);
@@ -567,9 +571,9 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     for (int arr = 0; arr < 7; ++arr) {
       if (arr == 1 && NDIM == 2) continue;
       if (arr == 6 && !has_w) continue;
-      copy4_async(PushStage<T>::at(stg, stage, arr, lane), src[arr] + slot0);
+      copy4_async(SG::at(stg, stage, arr, lane), src[arr] + slot0);
     }
-    if (has_id) copy4_async(PushStage<T>::id_at(stg, stage, lane), pin.id + slot0);
+    if (has_id) copy4_async(SG::id_at(stg, stage, lane), pin.id + slot0);
   };
 
   int g = warp, it = 0;
@@ -617,8 +621,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
       const int cnt = has ? min(4, (s ? n1 : n0) - q4) : 0;
       const SpeciesBuf<T> pout = s ? r.out[1] : r.out[0];
       const T qs = s ? T(1) : T(-1);
-      const T* st_x = PushStage<T>::at(stg, stage, 0, lane);
-      const unsigned* st_id = PushStage<T>::id_at(stg, stage, lane);
+      const T* st_x = SG::at(stg, stage, 0, lane);  // array a of the lane's pack at st_x + slot(a) * 128
+      const unsigned* st_id = SG::id_at(stg, stage, lane);
 #pragma unroll 1
       for (int rnd = 0; rnd < 4; ++rnd) {
         // pack element of this round, rotated by lane / 8 so the 32 lanes' shared-memory reads of
@@ -628,12 +632,12 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         int dkey = -1 - lane;  // unique per lane when there is no particle
         bool leave = false;
         T nox = T(0), noy = T(0), noz = T(0), ux = T(0), uy = T(0), uz = T(0);
-        const T w = (has_w && valid) ? st_x[6 * 32 * 4 + jj] : r.wconst;
+        const T w = (has_w && valid) ? st_x[SG::slot(6) * 128 + jj] : r.wconst;
         if (valid) {
-          const T o_x = st_x[jj], o_y = NDIM == 3 ? st_x[1 * 32 * 4 + jj] : T(0), o_z = st_x[2 * 32 * 4 + jj];
-          ux = st_x[3 * 32 * 4 + jj];
-          uy = st_x[4 * 32 * 4 + jj];
-          uz = st_x[5 * 32 * 4 + jj];
+          const T o_x = st_x[jj], o_y = NDIM == 3 ? st_x[SG::slot(1) * 128 + jj] : T(0), o_z = st_x[SG::slot(2) * 128 + jj];
+          ux = st_x[SG::slot(3) * 128 + jj];
+          uy = st_x[SG::slot(4) * 128 + jj];
+          uz = st_x[SG::slot(5) * 128 + jj];
           // gather
           T F[6];
           if (SCHEME == 0) {

@@ -112,9 +112,14 @@ int sep_tiles(int ndim, int nx, int ny, int nz);
 int yee_tiles(int ndim, int nx, int ny, int nz);
 bool sep_fast_ok(int ndim, int nx, int ny, int nz, int hz, int hx);
 size_t field_energy_scratch_bytes();
-// B half step, E step, B half step in one launch
+// B half step, E step, B half step in one launch. With hc, the same launch also records the field
+// energies of the new E, B into the history ring (block partials in escratch, of
+// yee_energy_scratch_bytes, zeroed once); only where yee_records_energy (cudaErrorInvalidValue else).
+bool yee_records_energy(int ndim, int nx, int ny, int nz, int ck);
+size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz);
 template <typename T>
-cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st);
+cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, double* escratch = nullptr,
+                             const HistCtl* hc = nullptr);
 // out[0] += sum w (gamma - 1) over both species of the input buffers
 template <typename T>
 cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);

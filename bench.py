@@ -21,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -109,12 +110,19 @@ class ClockSampler:
         self.proc = None
 
     def start(self):
+        """Start sampling every 50 ms and return once the first sample is in, so that the samples
+        collected until stop() fall inside the timed region (the first one is not counted)."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        box = []
+        reader = threading.Thread(target=lambda: box.append(self.proc.stdout.readline()), daemon=True)
+        reader.start()
+        reader.join(timeout=10.0)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -266,18 +274,18 @@ def e2e_measure(P, torch, h, cfg, stream, steps: int):
 SAMPLE_NZ = 64  # the CPU sample is a 512 x 64 slab of the same beam (1/16 of the box)
 
 
-def oracle_sample():
+def oracle_sample(nz: int = SAMPLE_NZ):
     import oracle as O
     st, pe, pb = O.rational_coeffs(O.GALERKIN, ALPHA)
-    sim = O.Sim(ndim=2, nx=NX, nz=SAMPLE_NZ, dt=ALPHA, scheme=O.GALERKIN, psi_e=pe, psi_b=pb,
+    sim = O.Sim(ndim=2, nx=NX, nz=nz, dt=ALPHA, scheme=O.GALERKIN, psi_e=pe, psi_b=pb,
                 f_nbin=FILTER["filter_nbin"], f_ncomp=FILTER["filter_ncomp"], f_alpha=FILTER["filter_comp_alpha"],
                 f_targets=3)
     sim.init_beam(ppc=PPC, gamma=GAMMA, seed=2)
     return sim
 
 
-def oracle_time(steps: int, warmup: int):
-    sim = oracle_sample()
+def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ):
+    sim = oracle_sample(nz)
     for _ in range(warmup):
         sim.step(1)
         sim.energy()
@@ -303,7 +311,10 @@ def run_reference(args):
     if rank != 0:
         return
     steps, warmup = max(args.steps, 1), max(args.warmup, 0)
-    n, times = oracle_time(steps, warmup)
+    # one oracle step of the 512 x 64 slab takes about 0.3 s: past 400 steps the slab shrinks so that
+    # the whole run stays near two minutes (the unit is per particle-step either way)
+    nz = SAMPLE_NZ if steps + warmup <= 400 else max(8, SAMPLE_NZ * 400 // (steps + warmup) // 8 * 8)
+    n, times = oracle_time(steps, warmup, nz)
     total = sum(times)
     value = n * steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -311,7 +322,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one FP64 oracle step (one thread) of a 512x{SAMPLE_NZ} slab of "
+                             "sample": f"each step: one FP64 oracle step (one thread) of a 512x{nz} slab of "
                                        f"the workload ({n} particles) + energies"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -729,7 +740,7 @@ def run_variants(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--fp64-steps", type=int, default=10)

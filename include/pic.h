@@ -194,6 +194,16 @@ int pic_set_state(pic_handle* h, const pic_state* s);
 int pic_debug_gather_copies(pic_handle* h, int where, void* const* out6);
 int pic_debug_current(pic_handle* h, int where, void* const* out3);
 
+/* Charge conservation of the step (Sec. 2 cites Esirkepov's charge-conserving deposit; Eq. 6's
+ * filter acts on the current): the Yee E update with the filtered current keeps
+ * div E - F rho at its initial value, zero for the neutral beam, up to rounding. Computes, in FP64
+ * on the device from the current state, rho on the integer nodes from the particles' shapes (order
+ * shape_order B-splines, weight q w / dV), F rho with the current filter (identity when
+ * filter_targets lacks PIC_FILTER_J), and out[0] = max |div E - F rho|, out[1] = its RMS over the
+ * nodes, out[2] = max |F rho| (the scale). Synchronous; allocates 16 B per cell of device scratch on
+ * first use (PIC_E_OOM). */
+int pic_charge_residual(pic_handle* h, double out[3]);
+
 /* Maximum instability growth rate (Fig. 2/4 captions: from the transverse field energy):
  * Gamma = 1/2 d ln W / dt by an FP64 least-squares fit over the window from the first sample
  * two decades above the noise floor (median of log10 W over the first tenth of the samples) to

@@ -33,7 +33,7 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_batch_create", "pic_batch_size", "pic_batch_run", "pic_batch_set_correction_stencil",
            "pic_batch_set_stream", "pic_batch_step", "pic_batch_sync", "pic_batch_energy_history",
            "pic_batch_autotune", "pic_batch_destroy", "pic_batch_last_error", "pic_adjoint_forward",
-           "pic_adjoint_backward", "pic_adjoint_release")
+           "pic_adjoint_backward", "pic_adjoint_release", "pic_charge_residual")
 PIC_NKERNEL = 7
 KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
 
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.pic_debug_gather_copies.argtypes = [V, I, P(V)]
         L.pic_debug_current.argtypes = [V, I, P(V)]
         L.pic_fit_growth_rate.argtypes = [DP, DP, I, DP, P(I), P(I)]
+        L.pic_charge_residual.argtypes = [V, DP]
         L.pic_destroy.argtypes = [V]
         L.pic_destroy.restype = None
         L.pic_last_error.argtypes = [V]
@@ -241,6 +242,14 @@ def pic_debug_gather_copies(h, where: int, outs):
 def pic_debug_current(h, where: int, outs):
     arr = (ctypes.c_void_p * 3)(*[_ptr(o) for o in outs])
     _check(lib().pic_debug_current(h, where, arr), h)
+
+
+def pic_charge_residual(h) -> dict:
+    """Gauss-law residual of the current state (FP64, on the device): max and RMS of div E - F rho over
+    the nodes, and max |F rho| as the scale."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().pic_charge_residual(h, out), h)
+    return {"max": out[0], "rms": out[1], "rho_max": out[2]}
 
 
 def pic_fit_growth_rate(t, w):

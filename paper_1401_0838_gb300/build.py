@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpic_gb300.so")
-SOURCES = ["k_particles.cu", "k_push_ho.cu", "k_fields.cu", "k_adjoint.cu", "api.cu", "noalloc.cu",
+SOURCES = ["k_particles.cu", "k_push_ho.cu", "k_fields.cu", "k_adjoint.cu", "k_gauss.cu", "api.cu", "noalloc.cu",
            "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

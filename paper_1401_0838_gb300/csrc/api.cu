@@ -40,6 +40,8 @@ struct pic_handle {
   double* d_acc = nullptr;  // 8 doubles of reduction scratch
   double* d_red = nullptr;  // block partials of the field-energy reduction
   double* d_red_yee = nullptr;  // block partials of the energies recorded by the Yee launch
+  double* d_rho = nullptr;      // Gauss-law diagnostic: rho and F rho (FP64), then its scratch
+  double* d_gauss = nullptr;
   long long* d_offs = nullptr;
   long long* d_bsum = nullptr;
   long long* d_total = nullptr;
@@ -544,6 +546,49 @@ int count_particles(pic_handle* h, long long out[2]) {
 }
 
 template <typename T>
+int charge_residual_t(pic_handle* h, double out[3]) {
+  cudaStream_t st = h->stream;
+  const pic_config& c = h->cfg;
+  if (!h->d_rho) {
+    h->d_rho = (double*)dalloc(h, 2 * sizeof(double) * (size_t)h->ncell);
+    h->d_gauss = (double*)dalloc(h, gauss_scratch_bytes() + 4 * sizeof(double));
+    if (!h->d_rho || !h->d_gauss) return fail(h, PIC_E_OOM, "residual scratch allocation failed");
+    CK(cudaMemset(h->d_gauss, 0, gauss_scratch_bytes() + 4 * sizeof(double)), "clear residual scratch");
+  }
+  double* rho = h->d_rho;
+  double* rhof = h->d_rho + h->ncell;
+  double* dout = h->d_gauss + gauss_scratch_bytes() / sizeof(double);
+  CK(cudaMemsetAsync(rho, 0, sizeof(double) * (size_t)h->ncell, st), "clear rho");
+  RunDev<T> r = make_run<T>(h, h->parity);
+  const double dV = c.dx * c.dy * c.dz;
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_rho<T>(r, c.shape_order, 1.0 / dV, rho, st); }), "rho");
+  // F rho with the current filter's taps, in FP64
+  SepArgs<double> a;
+  memset(&a, 0, sizeof a);
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.nz = c.nz;
+  a.ndim = c.ndim;
+  a.ncomp = 1;
+  a.src[0] = rho;
+  a.dst[0] = rhof;
+  a.hz[0] = a.hz[1] = (int)(h->zt_j.size() / 2);
+  for (size_t i = 0; i < h->zt_j.size(); ++i) a.zt[0][i] = a.zt[1][i] = h->zt_j[i];
+  a.hx = a.hy = (int)(h->xt_j.size() / 2);
+  for (size_t i = 0; i < h->xt_j.size(); ++i) a.xt[i] = a.yt[i] = h->xt_j[i];
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_sep<double>(a, st); }), "filter rho");
+  CK(launch(h, PIC_K_OTHER,
+            [&] {
+              return launch_gauss_residual<T>((const T*)h->f[0], (const T*)h->f[1], (const T*)h->f[2], rhof, c.nx,
+                                              c.ny, c.nz, 1.0 / c.dx, 1.0 / c.dy, 1.0 / c.dz, h->d_gauss, dout, st);
+            }),
+     "gauss residual");
+  CK(cudaMemcpyAsync(out, dout, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "read residual");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  return check_err(h);
+}
+
+template <typename T>
 int get_state_t(pic_handle* h, pic_state* s) {
   int rc = check_err(h);
   if (rc) return rc;
@@ -963,6 +1008,13 @@ int pic_debug_current(pic_handle* h, int where, void* const* out3) {
   if (!(h->cfg.filter_targets & PIC_FILTER_J))
     for (int q = 0; q < 3; ++q) src[q] = h->f[6 + q];
   return debug_copy(h, where, out3, src, 3);
+}
+
+int pic_charge_residual(pic_handle* h, double out[3]) {
+  if (!h || !out) return PIC_E_ARG;
+  int rc = check_err(h);
+  if (rc) return rc;
+  return h->es == 4 ? charge_residual_t<float>(h, out) : charge_residual_t<double>(h, out);
 }
 
 int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_out, int* i0, int* i1) {

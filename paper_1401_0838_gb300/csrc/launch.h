@@ -124,6 +124,16 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, dou
 template <typename T>
 cudaError_t launch_kinetic(const RunDev<T>& r, double* out, cudaStream_t st);
 
+// Gauss-law residual (k_gauss.cu): rho += q w S / dV from the particle bins of r.in (shape order 1 or
+// 3, FP64 atomics; rho zeroed by the caller), and (max |div E - rhof|, rms, max |rhof|) into out[0..2]
+// (scratch of gauss_scratch_bytes, zeroed once).
+template <typename T>
+cudaError_t launch_rho(const RunDev<T>& r, int order, double inv_dv, double* rho, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gauss_residual(const T* ex, const T* ey, const T* ez, const double* rhof, int nx, int ny, int nz,
+                                  double idx, double idy, double idz, double* scratch, double* out, cudaStream_t st);
+size_t gauss_scratch_bytes();
+
 // Psi_E(D_z) Psi_B(D_z)^-1 applied in place to the two transverse E copies (k_fields.cu); work:
 // 2 x ncell complex doubles of scratch
 template <typename T>

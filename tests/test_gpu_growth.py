@@ -137,3 +137,38 @@ def test_correction_works_less_well_at_gamma_3():
         t = np.arange(1, len(w) + 1) * every * alpha
         rates[gamma] = P.pic_fit_growth_rate(t, w)[0]
     assert rates[3.0] > 1.5 * rates[130.0], rates
+
+
+def test_energy_history_config1_fp64():
+    # The 2D 64x128, 4 ppc/species, gamma = 130, alpha = 0.5 beam with the Psi correction and the filter,
+    # FP64, 200 steps: the device energy history (W_E, W_B, W_perp, K every 10 steps) follows the
+    # oracle's run from the same initial state, and the total energy stays within a few per cent
+    # (Sec. 4: with the correction the energy is essentially constant)
+    steps, every = 200, 10
+    cfg = make_cfg(nx=64, nz=128, dt=0.5, precision=1, ppc=4, init_beam=1, seed=1, track_ids=1)
+    cfg.diag_every = every
+    psi = P.pic_compute_correction_coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    try:
+        P.pic_set_correction_stencil(h, *psi)
+        _, p0 = _state_for_oracle(cfg, h)
+        o = O.Sim(ndim=2, nx=64, nz=128, dt=0.5, psi_e=psi[0], psi_b=psi[1])
+        o.set_particles(p0["x"], None, p0["z"], p0["ux"], p0["uy"], p0["uz"], p0["w"], p0["q"], pid=p0["id"])
+        ref = []
+        for _ in range(steps // every):
+            o.step(every)
+            ref.append(o.energy())
+        P.pic_step(h, steps)
+        hist = P.pic_energy_history(h, 4096)
+    finally:
+        P.pic_destroy(h)
+    assert len(hist) == steps // every
+    for e, r in zip(hist, ref):
+        w_e, w_b, w_p, k = r[0], r[1], r[2], r[3]
+        assert abs(e["k"] - k) <= 1e-12 * k
+        # the net fields of the neutral pair plasma are a cancellation of the two species' currents:
+        # their energies agree to FP64 roundoff of that cancellation, amplified by the slow growth
+        for got, want in ((e["w_e"], w_e), (e["w_b"], w_b), (e["w_perp"], w_p)):
+            assert abs(got - want) <= 1e-6 * want, (got, want)
+    tot = [e["total"] for e in hist]
+    assert max(abs(t / tot[0] - 1) for t in tot) < 0.02

@@ -42,12 +42,18 @@ PUSH_BYTES_PER_CELL = {4: 36, 8: 72}
 FALLBACK_HBM_GBS = 6800.0
 
 
-def config_dict(n_gpus: int, order: int = 1, scheme: str = "galerkin") -> dict:
+def config_dict(n_gpus: int, order: int = 1, scheme: str = "galerkin", solver: str = "yee",
+                correction: str = "split") -> dict:
     wl = WORKLOAD
     if order != 1 or scheme != "galerkin":
-        wl = WORKLOAD.replace("Galerkin gather", f"{scheme} gather, shape order {order}")
+        wl = wl.replace("Galerkin gather", f"{scheme} gather, shape order {order}")
+    if solver != "yee":
+        wl += ", Cole-Karkkainen solver"
+    if correction != "split":
+        wl += ", exact rational multiplier on the transverse E copies"
     return {"workload": wl, "grid": [NX, NZ], "ppc_per_species": PPC, "particles": NX * NZ * PPC * 2,
-            "alpha": ALPHA, "gamma": GAMMA, "scheme": scheme, "shape_order": order,
+            "alpha": ALPHA, "gamma": GAMMA, "scheme": scheme, "shape_order": order, "solver": solver,
+            "correction": correction,
             "filter": "2 bilinear + 1 compensation (a=2) per direction on J and on the field copies",
             "l2": "inputs larger than L2: 671 MB of particle state read + written per step (L2 129 MB)",
             "parallelism": "replicas" if n_gpus > 1 else "single"}
@@ -187,10 +193,13 @@ def measured_hbm_peak():
 SCHEMES = {"galerkin": 0, "uniform": 1, "momentum": 2}
 
 
-def make_handle(P, precision: int, seed: int, stream_ptr, order: int = 1, scheme: str = "galerkin"):
+def make_handle(P, precision: int, seed: int, stream_ptr, order: int = 1, scheme: str = "galerkin",
+                solver: str = "yee", correction: str = "split"):
     sc = SCHEMES[scheme]
     cfg = P.pic_config_default(nx=NX, nz=NZ, dt=ALPHA, gamma=GAMMA, scheme=sc, precision=precision,
                                ppc_per_species=PPC, seed=seed, init_beam=1, diag_every=1, shape_order=order,
+                               field_solver=P.PIC_CK if solver == "ck" else P.PIC_YEE,
+                               correction_mode=P.PIC_CORR_RATIONAL if correction == "rational" else P.PIC_CORR_SPLIT,
                                **FILTER)
     h = P.pic_create(cfg)
     pe, pb = P.pic_compute_correction_coeffs(sc, ALPHA)
@@ -348,7 +357,7 @@ def run_ours(args):
 
     # FP32: the headline
     h, cfg = make_handle(P, P.PIC_FP32, seed=2 + rank, stream_ptr=stream.cuda_stream, order=args.order,
-                         scheme=args.scheme)
+                         scheme=args.scheme, solver=args.solver, correction=args.correction)
     ncell = cfg.nx * cfg.ny * cfg.nz
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
@@ -380,7 +389,7 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         h64, _ = make_handle(P, P.PIC_FP64, seed=2 + rank, stream_ptr=stream.cuda_stream, order=args.order,
-                             scheme=args.scheme)
+                             scheme=args.scheme, solver=args.solver, correction=args.correction)
         for _ in range(2):
             P.pic_step(h64, 1)
         P.pic_sync(h64)
@@ -393,7 +402,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": agg["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(ws, args.order, args.scheme), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
+            "config": config_dict(ws, args.order, args.scheme, args.solver, args.correction), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
             "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
             "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -762,7 +771,9 @@ def main(argv=None):
                     help="c t / dz of each --gamma-sweep / --variants run")
     ap.add_argument("--variants", action="store_true", help="growth of the Sec. 3 correction variants instead")
     ap.add_argument("--solver", default="yee", choices=("yee", "ck"),
-                    help="field solver of --gamma-sweep / --variants (ck: Cole-Karkkainen, c dt/dz up to 0.95)")
+                    help="field solver (ck: Cole-Karkkainen; --gamma-sweep / --variants then run c dt/dz up to 0.95)")
+    ap.add_argument("--correction", default="split", choices=("split", "rational"),
+                    help="Psi_E / Psi_B on the copies (split) or the exact rational multiplier on E (rational)")
     ap.add_argument("--scheme", default="galerkin", choices=("galerkin", "uniform", "momentum"))
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per push launch from an ncu capture of this kernel (reported as is)")

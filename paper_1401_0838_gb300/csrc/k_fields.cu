@@ -956,10 +956,114 @@ __global__ void k_inverse_psi_z(InvPsiArgs<T> a) {
   for (int k = 0; k < nz; ++k) f[k * nxy + l] = (T)(a.scale * w[k * nxy + l].x);
 }
 
+// The same operator with one warp per z-line and the line in shared memory (FP64 complex, one
+// padding slot per 32 elements against bank conflicts). Each periodic first-order recursion
+// y_k = x_k + lam y_(k-1) is a blocked scan: every lane runs it over its own chunk of L = ceil(nz/32)
+// elements from zero, the 32 chunk maps y -> lam^len y + e are composed around the ring by a cyclic
+// doubling scan (Y_j = A_j Y_j + B_j after the full window, so Y_j = B_j / (1 - lam^nz)), and each
+// lane adds lam^(i+1) times the previous chunk's end value to its elements.
+constexpr int IPZ_LINES = 8;  // z-lines (warps) per block
+
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 c_fma(double2 a, double2 b, double2 c) {  // a b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 c_shfl(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ int ipz_pad(int k) { return k + (k >> 5); }
+
+__device__ __forceinline__ void periodic_recursion(double2* w, int nz, double2 lam, bool rev, int lane) {
+  const int L = (nz + 31) >> 5;
+  const int k0 = min(lane * L, nz), k1 = min(k0 + L, nz);
+  // 1. the chunk's recursion from zero; mu = lam^len
+  double2 y = make_double2(0.0, 0.0), mu = make_double2(1.0, 0.0);
+  for (int k = k0; k < k1; ++k) {
+    double2& v = w[ipz_pad(rev ? nz - 1 - k : k)];
+    y = c_fma(lam, y, v);
+    v = y;
+    mu = c_mul(mu, lam);
+  }
+  // 2. cyclic composition of the chunk maps: Y_j = A Y_(j - window) + B
+  double2 A = mu, B = y;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const double2 Ap = c_shfl(A, (lane - s) & 31), Bp = c_shfl(B, (lane - s) & 31);
+    B = c_fma(A, Bp, B);
+    A = c_mul(A, Ap);
+  }
+  const double dr = 1.0 - A.x, di = -A.y, dd = dr * dr + di * di;
+  const double2 Y = make_double2((B.x * dr + B.y * di) / dd, (B.y * dr - B.x * di) / dd);
+  // 3. the previous chunk's end value carried into this chunk
+  const double2 cin = c_shfl(Y, (lane - 1) & 31);
+  double2 p = lam;
+  for (int k = k0; k < k1; ++k) {
+    double2& v = w[ipz_pad(rev ? nz - 1 - k : k)];
+    v = c_fma(p, cin, v);
+    p = c_mul(p, lam);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * IPZ_LINES) k_inverse_psi_lines(const __grid_constant__ InvPsiArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char ipz_raw[];
+  const int nz = a.nz, lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int stride = ipz_pad(nz - 1) + 1;  // padded line length
+  double2* lines = reinterpret_cast<double2*>(ipz_raw);
+  T* f = blockIdx.y == 0 ? a.f[0] : a.f[1];
+  const long long l0 = (long long)blockIdx.x * IPZ_LINES;
+  const int nl = (int)min((long long)IPZ_LINES, a.nxy - l0);
+  // load the block's lines (consecutive l for each k: 8 values side by side) into the imaginary
+  // slots, which the Psi_E pass reads while it writes the real slots
+  for (int e = threadIdx.x; e < nz * IPZ_LINES; e += blockDim.x) {
+    const int k = e / IPZ_LINES, li = e % IPZ_LINES;
+    if (li < nl) lines[li * stride + ipz_pad(k)] = make_double2(0.0, (double)f[k * a.nxy + l0 + li]);
+  }
+  __syncthreads();
+  if (wl < nl) {
+    double2* w = lines + wl * stride;
+    for (int k = lane; k < nz; k += 32) {  // Psi_E(D_z), 9 taps, periodic, FP64
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 9; ++m) acc += a.pe_taps[m] * w[ipz_pad(wrapi(k + m - 4, nz))].y;
+      w[ipz_pad(k)].x = acc;
+    }
+    __syncwarp();
+    for (int k = lane; k < nz; k += 32) w[ipz_pad(k)].y = 0.0;
+    __syncwarp();
+    for (int i = 0; i < a.nf; ++i) {
+      const double2 lam = make_double2(a.lam_re[i], a.lam_im[i]);
+      periodic_recursion(w, nz, lam, false, lane);  // causal
+      __syncwarp();
+      periodic_recursion(w, nz, lam, true, lane);   // anticausal
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nz * IPZ_LINES; e += blockDim.x) {
+    const int k = e / IPZ_LINES, li = e % IPZ_LINES;
+    if (li < nl) f[k * a.nxy + l0 + li] = (T)(a.scale * lines[li * stride + ipz_pad(k)].x);
+  }
+}
+
+size_t inverse_psi_lines_smem(int nz) {
+  return sizeof(double2) * (size_t)IPZ_LINES * (size_t)((nz - 1) + ((nz - 1) >> 5) + 1);
+}
+
 template <typename T>
 cudaError_t launch_inverse_psi_z(const InvPsiArgs<T>& a, cudaStream_t st) {
   if (a.nxy <= 0 || a.nz <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((a.nxy + 63) / 64), 2);
+  const size_t sm = inverse_psi_lines_smem(a.nz);
+  if (sm <= 200 * 1024) {  // lines up to about 1500 cells: the warp-per-line kernel
+    cudaError_t e = ensure_dynamic_smem((const void*)k_inverse_psi_lines<T>, sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.nxy + IPZ_LINES - 1) / IPZ_LINES), 2);
+    k_inverse_psi_lines<T><<<grid, 32 * IPZ_LINES, sm, st>>>(a);
+    return cudaGetLastError();
+  }
+  dim3 grid((unsigned)((a.nxy + 63) / 64), 2);  // longer lines: one thread per line in global memory
   k_inverse_psi_z<T><<<grid, 64, 0, st>>>(a);
   return cudaGetLastError();
 }

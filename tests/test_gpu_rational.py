@@ -27,6 +27,24 @@ def test_rational_copies(precision, ndim, scheme, alpha):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("nx,nz", [(5, 7), (13, 33), (9, 100), (11, 1024), (3, 1600), (2, 2000)])
+def test_rational_copies_line_lengths(precision, nx, nz):
+    # the z-line solve at line lengths below one warp, with ragged and empty lane chunks, at the
+    # workload's 1024, near the shared-memory limit of the warp-per-line kernel (1600) and past it
+    # (2000: the thread-per-line kernel); line counts that leave a partial block
+    pair = _random_pair(2, precision, scheme=0, alpha=0.6, npart=0, nx=nx, nz=nz, corr_mode=1)
+    try:
+        expect = pair.o.gather_copies()
+        P.pic_step(pair.h, 1)
+        outs = [np.zeros(pair.o.shape, dtype=pair.T) for _ in range(6)]
+        P.pic_debug_gather_copies(pair.h, P.PIC_HOST, outs)
+        for c in range(2):  # the transverse E copies carry the inverse
+            assert rel_l2(outs[c], expect[c]) <= TOL[precision], (c, rel_l2(outs[c], expect[c]))
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_rational_step(precision, scheme):
     pair = _random_pair(2, precision, scheme=scheme, alpha=0.6 if scheme == 0 else 0.45, nx=32, nz=48, npart=12000,

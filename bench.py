@@ -310,7 +310,7 @@ def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ):
 def cpu_baseline(steps: int = 8) -> dict:
     n, times = oracle_time(steps, 1)
     t = sum(times) / len(times)
-    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n / t, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 C oracle, one thread: {steps} steps of a 512x{SAMPLE_NZ} slab of the same beam "
                       f"({n} particles, same density, gamma, alpha, correction and filter) + energies each step"}
 
@@ -330,7 +330,7 @@ def run_reference(args):
             "steps": steps, "warmup": warmup, "ms_per_step": total / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.gpus),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"each step: one FP64 oracle step (one thread) of a 512x{nz} slab of "
                                        f"the workload ({n} particles) + energies"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

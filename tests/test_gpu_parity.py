@@ -281,6 +281,49 @@ def test_beam_run_fp64_config1_size():
         P.pic_destroy(h)
 
 
+def test_step_full_size_fp32():
+    # the benchmark workload at full size (2D 512x1024, 16 ppc/species, 16.8M particles, FP32, Psi at
+    # alpha = 0.5, the 2-bilinear + 1-compensation (a = 2) filter, the launch configuration bench.py
+    # times): after 3 steps from the seeded beam, one more step of the same state in the library and in
+    # the FP64 oracle, every field and every particle compared. The pair plasma's net fields are a
+    # cancellation of the two species' currents, so field errors are normalised by the field change one
+    # step of one species' current makes (as in the FP64 beam test); particles at the FP32 bar.
+    nx, nz = 512, 1024
+    cfg = make_cfg(nx=nx, nz=nz, dt=0.5, precision=0, ppc=16, init_beam=1, seed=2, nbin=2, ncomp=1, calpha=2.0,
+                   track_ids=1)
+    psi = _coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    try:
+        P.pic_set_correction_stencil(h, *psi)
+        P.pic_step(h, 3)
+        pair = object.__new__(Pair)
+        pair.cfg, pair.h, pair.T = cfg, h, np.float32
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.o = O.Sim(ndim=2, nx=nx, nz=nz, dt=0.5, psi_e=psi[0], psi_b=psi[1], f_nbin=2, f_ncomp=1, f_alpha=2.0)
+        pair.npart = nx * nz * 32
+        f0, p0 = pair.gpu_state()
+        assert len(p0["x"]) == pair.npart
+        o = pair.o
+        o.set_particles(p0["x"], None, p0["z"], p0["ux"], p0["uy"], p0["uz"], p0["w"], p0["q"], pid=p0["id"])
+        o.f.update({n: f0[n].reshape(o.shape).copy() for n in FIELDS})
+        P.pic_step(h, 1)
+        o.step(1)
+        f, p = pair.gpu_state()
+        gross = math.sqrt(nx * nz) * 0.5 * 0.3868 ** 2 / 2
+        for n in FIELDS:
+            assert rel_l2(f[n], o.f[n], floor=gross) < 1e-6, (n, rel_l2(f[n], o.f[n], floor=gross))
+        order = np.argsort(o.pid, kind="stable")
+        np.testing.assert_array_equal(p["id"], o.pid[order])
+        assert np.abs(periodic_diff(p["x"], o.part["x"][order], nx)).max() < 1e-5
+        assert np.abs(periodic_diff(p["z"], o.part["z"][order], nz)).max() < 1e-5
+        for c in ("ux", "uy"):
+            assert rel_l2(p[c], o.part[c][order]) < 1e-5, c
+        # uz carries u0 = 130: compare the deviation from the drift, which FP32 stores
+        assert rel_l2(p["uz"] - pair.u0, o.part["uz"][order] - pair.u0) < 1e-5
+    finally:
+        P.pic_destroy(h)
+
+
 def test_gauss_law_full_size_fp32():
     # full benchmark size (2D 512x1024, 16 ppc/species, 16.8M particles, FP32): after steps from the
     # seeded beam, div E - F rho (oracle rho of the GPU particles, oracle filter) stays at roundoff

@@ -350,6 +350,54 @@ def test_gauss_law_full_size_fp32():
         P.pic_destroy(h)
 
 
+def test_push_sampled_full_size_3d_fp32():
+    # the 3D workload at full size (128x128x512, 8 ppc/species, 134M particles, Gaussian transverse
+    # weights, FP32, correction + filter): after 2 steps, one more step; 4096 particles drawn at random
+    # are pushed one by one by the oracle (its copies of the exported fields, its gather, its Boris,
+    # the move x + dt u / gamma) and compared by id with the library's step
+    nx, ny, nz = 128, 128, 512
+    cfg = make_cfg(ndim=3, nx=nx, ny=ny, nz=nz, dt=0.5, precision=0, ppc=8, init_beam=1, seed=3,
+                   sigma_perp=20.0, track_ids=1)
+    psi = _coeffs(0, 0.5)
+    h = P.pic_create(cfg)
+    try:
+        P.pic_set_correction_stencil(h, *psi)
+        P.pic_step(h, 2)
+        pair = object.__new__(Pair)
+        pair.cfg, pair.h, pair.T = cfg, h, np.float32
+        pair.u0 = math.sqrt(cfg.gamma ** 2 - 1)
+        pair.o = O.Sim(ndim=3, nx=nx, ny=ny, nz=nz, dt=0.5)
+        f0, p0 = pair.gpu_state()  # sorted by id; ids are 0 .. N-1
+        n = len(p0["x"])
+        assert n == nx * ny * nz * 16 and p0["id"][-1] == n - 1
+        sample = np.sort(np.random.default_rng(7).choice(n, 4096, replace=False))
+        ps = {k: v[sample].copy() for k, v in p0.items()}
+        del p0
+        o = O.Sim(ndim=3, nx=nx, ny=ny, nz=nz, dt=0.5, psi_e=psi[0], psi_b=psi[1])
+        o.f.update({k: f0[k].reshape(o.shape).copy() for k in FIELDS})
+        F = o.gather(o.gather_copies(), ps["x"], ps["y"], ps["z"])
+        want = {k: np.zeros(len(sample)) for k in ("x", "y", "z", "ux", "uy", "uz")}
+        for i in range(len(sample)):
+            u = O.boris(ps["q"][i], 0.5, [F[0][i], F[1][i], F[2][i]], [F[3][i], F[4][i], F[5][i]],
+                        [ps["ux"][i], ps["uy"][i], ps["uz"][i]])
+            g = math.sqrt(1.0 + u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+            for c, k in enumerate(("x", "y", "z")):
+                want[k][i] = ps[k][i] + 0.5 * u[c] / g
+            want["ux"][i], want["uy"][i], want["uz"][i] = u
+        P.pic_step(h, 1)
+        _, p1 = pair.gpu_state()
+        got = {k: v[sample] for k, v in p1.items()}
+        del p1
+    finally:
+        P.pic_destroy(h)
+    np.testing.assert_array_equal(got["id"], sample)
+    for k, m in (("x", nx), ("y", ny), ("z", nz)):
+        assert np.abs(periodic_diff(got[k], want[k], m)).max() < 1e-5, k
+    for k in ("ux", "uy"):
+        assert rel_l2(got[k], want[k]) < 1e-5, (k, rel_l2(got[k], want[k]))
+    assert rel_l2(got["uz"] - pair.u0, want["uz"] - pair.u0) < 1e-5
+
+
 def test_gauss_law_full_size_3d_fp32():
     # the 3D workload at full size (128x128x512, 8 ppc/species, 134M particles, Gaussian transverse
     # weights, FP32, correction + filter): after steps from the seeded beam, div E - F rho (oracle rho

@@ -103,7 +103,7 @@ def test_degenerate_uniform_half():
     assert list(pe) == [1, 0, 0, 0, 0] and list(pb) == [1, 0, 0, 0, 0]
 
 
-def test_survey_sanity_values():
+def test_galerkin_alpha_half_coefficient_values():
     # Galerkin alpha = 0.5 coefficients (4-digit sanity values recomputed independently with numpy).
     _, pe, pb = O.rational_coeffs(O.GALERKIN, 0.5)
     np.testing.assert_allclose(pe, [1, -2.3886, 1.8991, -0.5428, 0.0336], atol=1e-4)

@@ -1107,8 +1107,13 @@ __device__ __forceinline__ void fold(int& i, T& o, int n) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Seeded beam: one thread per lattice point; see pic.h / the oracle for the recipe. All random
-// numbers and the derived positions and momenta are computed in FP64 and rounded once.
+// Seeded beam: one thread per lattice point p (cell-major, ppc points per cell on an lx x ly x lz
+// lattice at offsets (l + 1/2) / n). Philox4x32-10 keyed by the seed with counter (p, 0, 0, 0) gives
+// the position jitter, uniform in +-jitter cells per coordinate; counter (p, 1 + s, 0, 0) gives
+// species s's two Box-Muller pairs for the thermal momenta (spread u_th per component, relative to
+// the drift). The electron and the positron of a point share its position, and with transverse
+// Gaussian weights w = w0 exp(-r_perp^2 / (2 sigma^2)) about the box axis. All random numbers and
+// the derived positions and momenta are computed in FP64 and rounded once.
 // ---------------------------------------------------------------------------------------------
 struct BeamDev {
   int ppc, lx, ly, lz;

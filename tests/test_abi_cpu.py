@@ -143,10 +143,11 @@ def test_destroy_null_is_noop():
 
 
 def test_breakdown_windows_agree_with_oracle():
-    # The (4,4) interpolation of the Galerkin multiplier (Yee solver) has a pole inside [0, 1] in
-    # narrow alpha windows (the counterpart of the window Sec. 3 excises for its CK setting). The
-    # library and the oracle, with different solvers, must refuse exactly the same alphas.
-    alphas = np.linspace(0.60, 0.706, 213)
+    # The (4,4) interpolation of the Galerkin multiplier has a pole inside [0, 1] in narrow alpha
+    # windows (the counterpart of the window Sec. 3 excises), below Yee's 2D limit and, reachable with
+    # the CK solver, near 0.77-0.78. The library and the oracle, with different solvers, must refuse
+    # exactly the same alphas.
+    alphas = np.linspace(0.60, 0.99, 781)
     lib_bad, orc_bad = [], []
     for a in alphas:
         try:
@@ -157,5 +158,7 @@ def test_breakdown_windows_agree_with_oracle():
         if O.rational_coeffs(0, a)[0] != 0:
             orc_bad.append(a)
     assert lib_bad == orc_bad
-    assert 5 <= len(lib_bad) < 60
-    assert min(lib_bad) > 0.64 and max(lib_bad) < 0.70
+    low = [a for a in lib_bad if a < 0.71]
+    high = [a for a in lib_bad if a >= 0.71]
+    assert 5 <= len(low) < 60 and min(low) > 0.64 and max(low) < 0.70
+    assert 5 <= len(high) < 40 and min(high) > 0.765 and max(high) < 0.79

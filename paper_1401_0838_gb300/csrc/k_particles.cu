@@ -87,9 +87,13 @@ struct PushSmem {
   static constexpr int GX = TX + 2, GY = (NDIM == 3 ? TY + 2 : 1), GZ = TZ + 2, GN = GX * GY * GZ;
   // current tile: nodes [X0-1, X0+TX+1]
   static constexpr int JX = TX + 3, JY = (NDIM == 3 ? TY + 3 : 1), JZ = TZ + 3, JN = JX * JY * JZ;
+  // particles leaving the tile, buffered per block: [7][LVB] values (ox oy oz dux duy duz w), LVB
+  // keys, LVB ids and the buffer's counter; written to the global leaver list once per tile
+  static constexpr int LVB = (NDIM == 3 && sizeof(T) == 8) ? 128 : 512;  // 3D FP64: within 227 KB
+  static constexpr size_t lv_bytes() { return (size_t)LVB * (7 * sizeof(T) + 2 * sizeof(int)) + 16; }
   static constexpr size_t bytes() {
     return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (4 * NCL) + 16 +
-           sizeof(T) * PushStage<T, NDIM>::per_warp_elems() * (PUSH_THREADS / 32);
+           sizeof(T) * PushStage<T, NDIM>::per_warp_elems() * (PUSH_THREADS / 32) + 16 + lv_bytes();
   }
 };
 
@@ -486,6 +490,16 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   int* scnt = sn + 2 * NCL;                          // [species][cell] output counts of this tile
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // per-warp stages start on a 16-byte boundary after the counts (cp.async destinations)
+  const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(scnt + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
+  using SG = PushStage<T, NDIM>;
+  T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * SG::per_warp_elems();
+  // the tile's leaver buffer follows every warp's stage
+  const size_t lv_off = (stage_off + sizeof(T) * SG::per_warp_elems() * NWARP + 15) & ~(size_t)15;
+  T* lvv = reinterpret_cast<T*>(smem_raw + lv_off);
+  int* lvk = reinterpret_cast<int*>(lvv + 7 * S::LVB);
+  unsigned* lvi = reinterpret_cast<unsigned*>(lvk + S::LVB);
+  int* lvn = reinterpret_cast<int*>(lvi + S::LVB);
   const int tix = tile % r.ntx;
   const int tiy = (tile / r.ntx) % r.nty;
   const int tiz = tile / (r.ntx * r.nty);
@@ -535,6 +549,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     scnt[cl] = 0;
     scnt[NCL + cl] = 0;
   }
+  if (tid == 0) *lvn = 0;
   __syncthreads();
 
   const bool has_w = r.in[0].w != nullptr;
@@ -546,10 +561,6 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   // Items of this warp: (cell group, pack round). The packs of the next item are copied into the
   // warp's shared-memory stage with cp.async while the current item is computed.
   constexpr int NGRP = NCL / CPW;
-  // per-warp stages start on a 16-byte boundary after the counts (cp.async destinations)
-  const size_t stage_off = ((size_t)(reinterpret_cast<unsigned char*>(scnt + 2 * NCL) - smem_raw) + 15) & ~(size_t)15;
-  using SG = PushStage<T, NDIM>;
-  T* stg = reinterpret_cast<T*>(smem_raw + stage_off) + (size_t)warp * SG::per_warp_elems();
   auto group_iters = [&](int g) -> int {
     const int c = g * CPW + lane / LPC;
     const int nq = ((sn[c] + 3) >> 2) + ((sn[NCL + c] + 3) >> 2);
@@ -722,12 +733,25 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         int base = 0;
         if (stay && lane == leader) base = atomicAdd(scnt + (dkey & 1) * NCL + (dkey >> 1), __popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
+        // leavers: a slot in the tile's shared-memory buffer (one shared atomic per warp), or, once
+        // the buffer is full, straight in the global list
         const unsigned lmask = __ballot_sync(0xffffffffu, valid && leave);
-        int lbase = 0;
+        int lslot = 0;
+        long long lglob = 0;
         if (lmask) {
           const int lleader = __ffs(lmask) - 1;
-          if (lane == lleader) lbase = atomicAdd(r.lv_count, __popc(lmask));
-          lbase = __shfl_sync(0xffffffffu, lbase, lleader);
+          int b = 0;
+          if (lane == lleader) b = atomicAdd(lvn, __popc(lmask));
+          b = __shfl_sync(0xffffffffu, b, lleader);
+          lslot = b + __popc(lmask & ((1u << lane) - 1u));
+          const unsigned gmask = __ballot_sync(0xffffffffu, valid && leave && lslot >= S::LVB);
+          if (gmask) {
+            const int gl = __ffs(gmask) - 1;
+            int gb = 0;
+            if (lane == gl) gb = atomicAdd(r.lv_count, __popc(gmask));
+            gb = __shfl_sync(0xffffffffu, gb, gl);
+            lglob = (long long)gb + __popc(gmask & ((1u << lane) - 1u));
+          }
         }
         if (stay) {
           const int j = base + rank;
@@ -747,8 +771,18 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           } else {
             flag_error(r.err, ERR_OVERFLOW);
           }
+        } else if (valid && lslot < S::LVB) {
+          lvk[lslot] = dkey;
+          lvv[lslot] = nox;
+          if (NDIM == 3) lvv[S::LVB + lslot] = noy;
+          lvv[2 * S::LVB + lslot] = noz;
+          lvv[3 * S::LVB + lslot] = ux;
+          lvv[4 * S::LVB + lslot] = uy;
+          lvv[5 * S::LVB + lslot] = uz;
+          if (has_w) lvv[6 * S::LVB + lslot] = w;
+          if (has_id) lvi[lslot] = st_id[jj];
         } else if (valid) {
-          const long long o = lbase + __popc(lmask & ((1u << lane) - 1u));
+          const long long o = lglob;
           if (o < r.lv_cap) {
             r.lv.key[o] = dkey;
             r.lv.ox[o] = nox;
@@ -796,7 +830,29 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   cp_async_wait_all();
   __syncthreads();
 
-  // 4. output counts of the tile's cells (leavers from other tiles are added by k_migrate)
+  // 4. the tile's buffered leavers: one reservation in the global list, then a coalesced copy
+  __shared__ int lv_base;
+  const int nlv = min(*lvn, S::LVB);
+  if (tid == 0) lv_base = nlv > 0 ? atomicAdd(r.lv_count, nlv) : 0;
+  __syncthreads();
+  for (int e = tid; e < nlv; e += PUSH_THREADS) {
+    const long long o = (long long)lv_base + e;
+    if (o < r.lv_cap) {
+      r.lv.key[o] = lvk[e];
+      r.lv.ox[o] = lvv[e];
+      if (NDIM == 3) r.lv.oy[o] = lvv[S::LVB + e];
+      r.lv.oz[o] = lvv[2 * S::LVB + e];
+      r.lv.dux[o] = lvv[3 * S::LVB + e];
+      r.lv.duy[o] = lvv[4 * S::LVB + e];
+      r.lv.duz[o] = lvv[5 * S::LVB + e];
+      if (has_w) r.lv.w[o] = lvv[6 * S::LVB + e];
+      if (has_id) r.lv.id[o] = lvi[e];
+    } else {
+      flag_error(r.err, ERR_OVERFLOW);
+    }
+  }
+
+  // 5. output counts of the tile's cells (leavers from other tiles are added by k_migrate)
   for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
     if (lx < wx && ly < wy && lz < wz) {
@@ -806,7 +862,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     }
   }
 
-  // 5. flush the tile's current to global memory
+  // 6. flush the tile's current to global memory
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) {
     T v = sj[e];
     if (v == T(0)) continue;
@@ -820,7 +876,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     atomicAdd(r.j[c] + (long long)gz * nxy + (long long)gy * r.nx + gx, v);
   }
 
-  // 6. kinetic energy and particle count of this step: per-thread partial sums in the working
+  // 7. kinetic energy and particle count of this step: per-thread partial sums in the working
   // precision, FP64 across the block and the grid
   if (r.kin) {
     double kd = (double)kin;

@@ -42,6 +42,10 @@ __device__ __forceinline__ void copy1_async(float* dst, const float* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
 }
+__device__ __forceinline__ void copy1_async(int* dst, const int* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
 __device__ __forceinline__ void copy1_async(double* dst, const double* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
@@ -530,24 +534,33 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     copy1_async(sg + e, src + (long long)gz * nxy + (long long)gy * r.nx + gx);
   }
   for (int e = tid; e < 3 * S::JN; e += PUSH_THREADS) sj[e] = T(0);
-  cp_async_commit();
-  cp_async_wait_all();
-  // 2. particle counts of the tile's cells; the input counts are zeroed (they are the next step's
-  // output counts)
+  // 2. particle counts of the tile's cells, copied in the same asynchronous batch as the fields (one
+  // global round trip for both); then clamped, and the input counts zeroed (they are the next
+  // step's output counts). Each thread reads back only the counts it copied itself.
   for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
-    int n0 = 0, n1 = 0;
     if (lx < wx && ly < wy && lz < wz) {
       const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
-      n0 = min(r.in[0].cnt[cell], r.cap);  // an overflow was flagged when it happened
-      n1 = min(r.in[1].cnt[cell], r.cap);
+      copy1_async(sn + cl, r.in[0].cnt + cell);
+      copy1_async(sn + NCL + cl, r.in[1].cnt + cell);
+    } else {
+      sn[cl] = 0;
+      sn[NCL + cl] = 0;
+    }
+    scnt[cl] = 0;
+    scnt[NCL + cl] = 0;
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
+      sn[cl] = min(sn[cl], r.cap);  // an overflow was flagged when it happened
+      sn[NCL + cl] = min(sn[NCL + cl], r.cap);
       r.in[0].cnt[cell] = 0;
       r.in[1].cnt[cell] = 0;
     }
-    sn[cl] = n0;
-    sn[NCL + cl] = n1;
-    scnt[cl] = 0;
-    scnt[NCL + cl] = 0;
   }
   if (tid == 0) *lvn = 0;
   __syncthreads();

@@ -511,6 +511,10 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   const int wx = min(S::TX, r.nx - X0), wy = min(S::TY, r.ny - Y0), wz = min(S::TZ, r.nz - Z0);
   const long long nxy = (long long)r.nx * r.ny;
 
+  const bool has_w = r.in[0].w != nullptr;
+  const bool has_id = r.in[0].id != nullptr;
+  const int sl = lane % LPC;  // lane within its cell group
+
   // 1. field copies of the tile and its halo into shared memory (periodic wrap); zero the current
   const bool near_ok = r.nx >= S::TX + 2 && r.nz >= S::TZ + 2 && (NDIM == 2 || r.ny >= S::TY + 2);
   for (int e = tid; e < 6 * S::GN; e += PUSH_THREADS) {
@@ -550,6 +554,28 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     scnt[cl] = 0;
     scnt[NCL + cl] = 0;
   }
+  // The first item of the warp's first cell group, in the same batch although the counts are not in
+  // yet: lane sl takes pack sl of species 0, as it does whenever its cell holds more than 4 sl
+  // particles of species 0 (slots below cap: inside the cell's own bin). A lane whose first pack is
+  // of species 1 copies it again once the counts are known.
+  {
+    const int c = warp * CPW + lane / LPC;  // every warp has a first group (NCL / CPW >= NWARP)
+    const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz && 4 * sl + 4 <= r.cap) {
+      const long long slot0 =
+          ((long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx) * r.cap + 4 * sl;
+      const SpeciesBuf<T>& pin = r.in[0];
+      const T* src[7] = {pin.ox, pin.oy, pin.oz, pin.dux, pin.duy, pin.duz, pin.w};
+#pragma unroll
+      for (int arr = 0; arr < 7; ++arr) {
+        if (arr == 1 && NDIM == 2) continue;
+        if (arr == 6 && !has_w) continue;
+        copy4_async(SG::at(stg, 0, arr, lane), src[arr] + slot0);
+      }
+      if (has_id) copy4_async(SG::id_at(stg, 0, lane), pin.id + slot0);
+    }
+  }
+  static_assert(NCL / CPW >= NWARP, "every warp needs a first cell group");
   cp_async_commit();
   cp_async_wait_all();
   for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
@@ -565,11 +591,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   if (tid == 0) *lvn = 0;
   __syncthreads();
 
-  const bool has_w = r.in[0].w != nullptr;
-  const bool has_id = r.in[0].id != nullptr;
   T kin = T(0);
   int npush = 0;
-  const int sl = lane % LPC;  // lane within its cell group
 
   // Items of this warp: (cell group, pack round). The packs of the next item are copied into the
   // warp's shared-memory stage with cp.async while the current item is computed.
@@ -579,7 +602,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     const int nq = ((sn[c] + 3) >> 2) + ((sn[NCL + c] + 3) >> 2);
     return __reduce_max_sync(0xffffffffu, (nq + LPC - 1) / LPC);
   };
-  auto issue = [&](int g, int it, int stage) {
+  // fix: only the packs the speculative first copy did not cover (species 1, or slots past cap)
+  auto issue = [&](int g, int it, int stage, bool fix) {
     const int c = g * CPW + lane / LPC;
     const int n0 = sn[c], n1 = sn[NCL + c];
     const int nq0 = (n0 + 3) >> 2, nq = nq0 + ((n1 + 3) >> 2);
@@ -587,6 +611,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     if (q >= nq) return;
     const int s = q >= nq0 ? 1 : 0;
     const int q4 = 4 * (s ? q - nq0 : q);
+    if (fix && s == 0 && q4 + 4 <= r.cap) return;
     const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
     const long long slot0 = ((long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx) * r.cap + q4;
     const SpeciesBuf<T> pin = s ? r.in[1] : r.in[0];
@@ -607,7 +632,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     giters = g < NGRP ? group_iters(g) : 0;
   }
   int stage = 0;
-  if (g < NGRP) issue(g, 0, 0);
+  if (g < NGRP) issue(g, 0, 0, g == warp);  // the first group's first item was copied speculatively
   cp_async_commit();
   T acc[NVP];
   GalCache<T, NDIM> gc;  // Galerkin nodes of the lane's cell, loaded once per cell group
@@ -621,7 +646,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         niters = ng < NGRP ? group_iters(ng) : 0;
       } while (ng < NGRP && niters == 0);
     }
-    if (ng < NGRP) issue(ng, nit, stage ^ 1);
+    if (ng < NGRP) issue(ng, nit, stage ^ 1, false);
     cp_async_commit();
     cp_async_wait_1();
     __syncwarp();

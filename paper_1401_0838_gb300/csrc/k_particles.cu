@@ -50,19 +50,6 @@ __device__ __forceinline__ void copy1_async(double* dst, const double* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
 }
-template <typename V>
-__device__ __forceinline__ void read4(const V* p, V (&o)[4]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) o[i] = p[i];
-}
-__device__ __forceinline__ void read4(const float* p, float (&o)[4]) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
-__device__ __forceinline__ void read4(const unsigned* p, unsigned (&o)[4]) {
-  const uint4 a = *reinterpret_cast<const uint4*>(p);
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
 
 // Per-warp double-buffered stage: [stage][slot][lane][4] for the particle arrays (slots ox oz dux
 // duy duz w in 2D; ox oy oz dux duy duz w in 3D), then [stage][lane][4] ids.
@@ -251,22 +238,6 @@ struct DepLayout<3> {
 // Periodic index of g in [-n, 2n) without a modulo (callers guarantee the range: near_ok, or a
 // neighbour cell index in [-1, n]).
 __device__ __forceinline__ int wrap_near_p(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
-
-// Vector loads of 4 consecutive slots (16-byte aligned: bins start on 64-byte boundaries and
-// packs start at multiples of 4 slots).
-__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
-__device__ __forceinline__ void load4(const unsigned* p, unsigned (&o)[4]) {
-  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
 
 // FP32 uses the hardware reciprocal square root and fast division (relative error ~1e-7, inside
 // the 1e-5 per-step bar); FP64 keeps IEEE division and square root.

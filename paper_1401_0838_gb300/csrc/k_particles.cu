@@ -24,33 +24,6 @@ struct PTile<3> {
 
 constexpr int PUSH_THREADS = 256;
 
-// cp.async (16-byte, L2 only) staging of particle packs into shared memory.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void copy4_async(float* dst, const float* src) { cp_async16(dst, src); }
-__device__ __forceinline__ void copy4_async(double* dst, const double* src) {
-  cp_async16(dst, src);
-  cp_async16(dst + 2, src + 2);
-}
-__device__ __forceinline__ void copy4_async(unsigned* dst, const unsigned* src) { cp_async16(dst, src); }
-__device__ __forceinline__ void copy1_async(float* dst, const float* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ __forceinline__ void copy1_async(int* dst, const int* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ __forceinline__ void copy1_async(double* dst, const double* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
-}
-
 // Per-warp double-buffered stage: [stage][slot][lane][4] for the particle arrays (slots ox oz dux
 // duy duz w in 2D; ox oy oz dux duy duz w in 3D), then [stage][lane][4] ids.
 template <typename T, int NDIM>

@@ -201,7 +201,8 @@ __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef&
   constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, H = G::H;
   const int tid = threadIdx.x;
   const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
-  // 1. field copies of the tile and its halo (periodic), current tile zeroed
+  // 1. field copies of the tile and its halo (periodic) and the cells' particle counts, as one
+  // asynchronous batch (one global round trip); current tile and output counts zeroed
   for (int e = tid; e < 6 * G::GN; e += HO_THREADS) {
     const int c = e / G::GN, rem = e - c * G::GN;
     const int lz = rem / (G::GX * G::GY), ly = (rem / G::GX) % G::GY, lx = rem % G::GX;
@@ -217,9 +218,36 @@ __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef&
       case 5: src = r.g[5]; break;
       default: break;
     }
-    sg[e] = src[(long long)gz * nxy + (long long)gy * r.nx + gx];
+    copy1_async(sg + e, src + (long long)gz * nxy + (long long)gy * r.nx + gx);
   }
   for (int e = tid; e < 3 * G::JN; e += HO_THREADS) sj[e] = T(0);
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
+      copy1_async(sn + cl, r.in[0].cnt + cell);
+      copy1_async(sn + NCL + cl, r.in[1].cnt + cell);
+    } else {
+      sn[cl] = 0;
+      sn[NCL + cl] = 0;
+    }
+    scnt[cl] = 0;
+    scnt[NCL + cl] = 0;
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  // 2. counts clamped (an overflow was flagged when it happened) and the input counts zeroed (they
+  // become the next step's output counts); each thread reads back only the counts it copied
+  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
+    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
+    if (lx < wx && ly < wy && lz < wz) {
+      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
+      sn[cl] = min(sn[cl], r.cap);
+      sn[NCL + cl] = min(sn[NCL + cl], r.cap);
+      r.in[0].cnt[cell] = 0;
+      r.in[1].cnt[cell] = 0;
+    }
+  }
   __syncthreads();
   if (SCHEME == 2) {
     // average each component from its Yee location to the nodes along its half-staggered
@@ -242,24 +270,6 @@ __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef&
       __syncthreads();
     }
   }
-  // 2. particle counts of the tile's cells (the input counts become the next step's output counts)
-  for (int cl = tid; cl < NCL; cl += HO_THREADS) {
-    const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
-    int n0 = 0, n1 = 0;
-    if (lx < wx && ly < wy && lz < wz) {
-      const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
-      n0 = min(r.in[0].cnt[cell], r.cap);
-      n1 = min(r.in[1].cnt[cell], r.cap);
-      r.in[0].cnt[cell] = 0;
-      r.in[1].cnt[cell] = 0;
-    }
-    sn[cl] = n0;
-    sn[NCL + cl] = n1;
-    scnt[cl] = 0;
-    scnt[NCL + cl] = 0;
-  }
-  __syncthreads();
-
 }
 
 // Phases 4-6: output counts, the tile's current into global memory, the step's kinetic sums.
@@ -327,7 +337,7 @@ template <typename T, int NDIM, int ORDER, int SCHEME>
 __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ RunDev<T> r) {
   using G = HoGeom<NDIM, ORDER>;
   using TL = HoTile<NDIM>;
-  constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
+  constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);
   T* sj = sg + 6 * G::GN;

@@ -595,19 +595,17 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
       default: return a.jz;
     }
   };
-  for (int row = threadIdx.x / 32; row < 9 * LY * LZ; row += YEE_THREADS / 32) {
-    const int c = row / (LY * LZ), r2 = row % (LY * LZ);
+  for (int idx = threadIdx.x; idx < 9 * LN; idx += YEE_THREADS) {  // flat: rows are wider than a warp
+    const int c = idx / LN, r3 = idx - c * LN;
+    const int lx = r3 % LX, r2 = r3 / LX;
     const int ly = r2 % LY, lz = r2 / LY;
     const int gy = NDIM == 3 ? wrap_near(Y0 - 1 + ly, a.ny) : 0;
     const int gz = wrap_near(Z0 - HL + lz, a.nz);
-    const T* srow = gsrc(c) + gz * nxy + (long long)gy * a.nx;
-    T* drow = sm + c * LN + r2 * LX;
-    for (int lx = threadIdx.x & 31; lx < LX; lx += 32) cp_async_el(drow + lx, srow + wrap_near(X0 - HL + lx, a.nx));
+    cp_async_el(sm + idx, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap_near(X0 - HL + lx, a.nx));
   }
   cp_async_wait_all_fields();
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // x lane, row group
   const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
   // CK averaged forward differences at local node l (2D): along z averaged over x, along x over z
   auto ck_dz = [&](const T* f, int l) -> T {
@@ -619,8 +617,9 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   // B^{n+1/2} on cells [-HB, C+1) in x and z ([-1, C+1) in y)
   constexpr int NY2 = NDIM == 3 ? CY + 2 : 1, NY1 = NDIM == 3 ? CY + 1 : 1;
   constexpr int NBX = CX + 1 + HB, NBZ = CZ + 1 + HB;
-  for (int row = ty; row < NY2 * NBZ; row += YEE_THREADS / 32)
-    for (int q = tx; q < NBX; q += 32) {
+  // each phase walks its cells with one flat index over all threads (rows are wider than a warp)
+  for (int idx = threadIdx.x; idx < NY2 * NBZ * NBX; idx += YEE_THREADS) {
+    const int q = idx % NBX, row = idx / NBX;
     const int lx = HL - HB + q, ly = row % NY2, lz = HL - HB + row / NY2;
     const int l = (lz * LY + ly) * LX + lx;
     if (CK) {
@@ -637,8 +636,8 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   __syncthreads();
   // E^{n+1} on cells [-HE, C+1) in x and z ([0, C+1) in y)
   constexpr int NEX = CX + 1 + HE, NEZ = CZ + 1 + HE;
-  for (int row = ty; row < NY1 * NEZ; row += YEE_THREADS / 32)
-    for (int q = tx; q < NEX; q += 32) {
+  for (int idx = threadIdx.x; idx < NY1 * NEZ * NEX; idx += YEE_THREADS) {
+    const int q = idx % NEX, row = idx / NEX;
     const int lx = HL - HE + q, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = HL - HE + row / NY1;
     const int l = (lz * LY + ly) * LX + lx;
     const T bx = b[0][l], by = b[1][l], bz = b[2][l];
@@ -649,8 +648,8 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   __syncthreads();
   // B^{n+1} on cells [0, C), then write E and B of the tile (and, with DIAG, sum their energies)
   EnergyAcc<T> en;
-  for (int row = ty; row < CY * CZ; row += YEE_THREADS / 32)
-    for (int cx = tx; cx < CX; cx += 32) {
+  for (int idx = threadIdx.x; idx < CY * CZ * CX; idx += YEE_THREADS) {
+    const int cx = idx % CX, row = idx / CX;
     const int cy = row % CY, cz = row / CY;
     const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
     if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;

@@ -56,6 +56,16 @@ __device__ __forceinline__ int wrap_near(int g, int n) {
   return g;
 }
 
+// Periodic index of g in [-n, 2n) with one compare and add (WrapOnce), or of any g (WrapNear). Tile
+// staging takes WrapOnce when the grid is at least as wide as the staged tile in every direction
+// (then every staged index lies in [-n, 2n)), behind a block-uniform branch.
+struct WrapOnce {
+  __device__ __forceinline__ int operator()(int g, int n) const { return g < 0 ? g + n : (g >= n ? g - n : g); }
+};
+struct WrapNear {
+  __device__ __forceinline__ int operator()(int g, int n) const { return wrap_near(g, n); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(SEP_THREADS) k_sep(SepArgs<T> a, int CX, int CY, int CZ, int ntx, int nty) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -178,13 +188,17 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
 #pragma unroll
   for (int m = 0; m <= 2 * HY; ++m) yt[m] = a.yt[m];
   // stage the tile and its halos (rows along x)
-  for (int row = ty; row < LZ * LY; row += TYN) {
-    const int ly = row % LY, lz = row / LY;
-    const int gy = NDIM == 3 ? wrap_near(Y0 - HY + ly, a.ny) : 0;
-    const int gz = wrap_near(Z0 - HZ + lz, a.nz);
-    const T* srow = src + gz * nxy + (long long)gy * a.nx;
-    for (int lx = tx; lx < LX; lx += TXN) cp_async_el(s0 + row * LX + lx, srow + wrap_near(X0 - HX + lx, a.nx));
-  }
+  auto stage = [&](auto wrap) {
+    for (int row = ty; row < LZ * LY; row += TYN) {
+      const int ly = row % LY, lz = row / LY;
+      const int gy = NDIM == 3 ? wrap(Y0 - HY + ly, a.ny) : 0;
+      const int gz = wrap(Z0 - HZ + lz, a.nz);
+      const T* srow = src + gz * nxy + (long long)gy * a.nx;
+      for (int lx = tx; lx < LX; lx += TXN) cp_async_el(s0 + row * LX + lx, srow + wrap(X0 - HX + lx, a.nx));
+    }
+  };
+  if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
+  else stage(WrapNear{});
   cp_async_wait_all_fields();
   __syncthreads();
   // z pass in place. A task is one (x, y) column of the staged tile and a segment of ZS output rows;
@@ -595,14 +609,18 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
       default: return a.jz;
     }
   };
-  for (int idx = threadIdx.x; idx < 9 * LN; idx += YEE_THREADS) {  // flat: rows are wider than a warp
-    const int c = idx / LN, r3 = idx - c * LN;
-    const int lx = r3 % LX, r2 = r3 / LX;
-    const int ly = r2 % LY, lz = r2 / LY;
-    const int gy = NDIM == 3 ? wrap_near(Y0 - 1 + ly, a.ny) : 0;
-    const int gz = wrap_near(Z0 - HL + lz, a.nz);
-    cp_async_el(sm + idx, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap_near(X0 - HL + lx, a.nx));
-  }
+  auto stage = [&](auto wrap) {
+    for (int idx = threadIdx.x; idx < 9 * LN; idx += YEE_THREADS) {  // flat: rows are wider than a warp
+      const int c = idx / LN, r3 = idx - c * LN;
+      const int lx = r3 % LX, r2 = r3 / LX;
+      const int ly = r2 % LY, lz = r2 / LY;
+      const int gy = NDIM == 3 ? wrap(Y0 - 1 + ly, a.ny) : 0;
+      const int gz = wrap(Z0 - HL + lz, a.nz);
+      cp_async_el(sm + idx, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap(X0 - HL + lx, a.nx));
+    }
+  };
+  if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
+  else stage(WrapNear{});
   cp_async_wait_all_fields();
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish

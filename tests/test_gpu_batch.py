@@ -101,10 +101,14 @@ def test_batch_matches_single_runs_fp64(autotune):
 
 
 def test_batch_matches_single_runs_fp32():
-    cfgs, b, singles = _run_both(0, 10)
+    # Two FP32 runs that differ only in the order of the deposit's atomics: their rounding
+    # differences grow over the 10 steps of this warm (u_th = 1e-2) beam, so the bar is the per-step
+    # FP32 bar (1e-5) accumulated over the steps; observed 0.5-2e-5 of the gross scale
+    steps = 10
+    cfgs, b, singles = _run_both(0, steps)
     try:
         for i, c in enumerate(cfgs):
-            _compare(c, P.pic_batch_run(b, i), singles[i], 1e-5)
+            _compare(c, P.pic_batch_run(b, i), singles[i], 1e-5 * steps)
     finally:
         P.pic_batch_destroy(b)
         for h in singles:

@@ -142,6 +142,15 @@ def test_destroy_null_is_noop():
     P.lib().pic_destroy(None)
 
 
+def test_null_handles_are_rejected_without_a_gpu():
+    import ctypes
+    out = (ctypes.c_double * 3)()
+    assert P.lib().pic_charge_residual(None, out) == P.PIC_E_ARG
+    assert P.lib().pic_step(None, 1) == P.PIC_E_ARG
+    w = ctypes.c_double()
+    assert P.lib().pic_adjoint_forward(None, 10, 5, ctypes.byref(w)) == P.PIC_E_ARG
+
+
 def test_breakdown_windows_agree_with_oracle():
     # The (4,4) interpolation of the Galerkin multiplier has a pole inside [0, 1] in narrow alpha
     # windows (the counterpart of the window Sec. 3 excises), below Yee's 2D limit and, reachable with

@@ -174,6 +174,30 @@ def test_edge_particles(precision, ndim):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
+def test_tile_with_more_leavers_than_its_buffer(precision):
+    # 1200 particles in the top cell row of one 16x16 particle tile (z in [15.6, 16)), all moving up:
+    # every one leaves the tile in the first step, more than the 512 the tile buffers in shared
+    # memory, so the rest take the direct path into the global leaver list
+    nx, nz, n = 32, 48, 1200
+    cfg = make_cfg(nx=nx, nz=nz, dt=0.5, precision=precision, cap=96)
+    rng = np.random.default_rng(31)
+    u0 = math.sqrt(cfg.gamma ** 2 - 1)
+    part = {"x": rng.uniform(0, 16, n), "y": np.zeros(n), "z": rng.uniform(15.6, 15.999, n),
+            "ux": rng.normal(0, 1e-3, n), "uy": rng.normal(0, 1e-3, n), "uz": u0 + rng.normal(0, 1e-3, n),
+            "w": np.ones(n), "q": rng.choice([-1.0, 1.0], n), "id": np.arange(n, dtype=np.int64)}
+    fields = synth.random_fields((nz, 1, nx), seed=33, scale=1e-3)
+    pair = Pair(cfg, psi=_coeffs(0, 0.5), fields=fields, part=part)
+    try:
+        pair.step(1)
+        _compare(pair, TOL[precision])
+        assert P.pic_num_particles(pair.h) == n
+        pair.step(2)
+        _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
 def test_empty_and_single(precision):
     cfg = make_cfg(nx=16, nz=16, precision=precision)
     pair = Pair(cfg, fields=synth.random_fields((16, 1, 16), seed=1))

@@ -139,30 +139,35 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_samples(out)
 
 
-def profiled_traffic():
+def parse_clock_samples(text: str) -> dict:
+    """Median SM clock, maximum clock and active throttle reasons from ClockSampler.QUERY CSV lines."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def profiled_traffic(prof=None, src=None):
     """DRAM bytes per launch of the push kernel from the committed ncu summary, if that summary was
     taken on the current kernel source (else None)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_push_2d_512x1024_fp32.md")
-    src = os.path.join(ROOT, "paper_1401_0838_gb300", "csrc", "k_particles.cu")
+    prof = prof or os.path.join(ROOT, "profiles", "k_push_2d_512x1024_fp32.md")
+    src = src or os.path.join(ROOT, "paper_1401_0838_gb300", "csrc", "k_particles.cu")
     try:
         text = open(prof).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()

@@ -1,0 +1,48 @@
+"""CPU checks of bench.py's measurement helpers: the roofline arithmetic (algorithmic bytes per launch
+over the push's event time), the rule that the profiled DRAM traffic is reported only for the kernel
+source it was captured on, and the clock-sample parsing."""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_roofline_arithmetic():
+    # 16.8M particles at 40 B and 0.5M cells at 36 B, 10 launches in 5 ms: 0.5 ms per launch
+    np_, ncell = 16777216, 524288
+    rf = bench.roofline({"push": (5.0, 10)}, np_, ncell, 4, 6791.4, "measured")
+    want_bytes = np_ * 40 + ncell * 36
+    assert rf["algorithmic_bytes_per_launch"] == want_bytes
+    assert abs(rf["achieved"] - want_bytes / 0.5e-3 / 1e9) < 0.1
+    assert abs(rf["frac"] - rf["achieved"] / 6791.4) < 1e-4
+    assert rf["launch_ms"] == 0.5 and rf["bound"] == "hbm" and rf["unit"] == "GB/s"
+
+
+def test_traffic_only_for_the_profiled_source(tmp_path):
+    src = tmp_path / "kernel.cu"
+    src.write_text("kernel source\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "profile.md"
+    prof.write_text(f"# summary\n\nsource_sha256: {digest}\ndram_bytes_per_launch: 123456\n")
+    assert bench.profiled_traffic(str(prof), str(src)) == 123456.0
+    src.write_text("kernel source, changed\n")
+    assert bench.profiled_traffic(str(prof), str(src)) is None
+    assert bench.profiled_traffic(str(tmp_path / "missing.md"), str(src)) is None
+
+
+def test_clock_sample_parsing():
+    text = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2040, 2070, 1380.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ])
+    c = bench.parse_clock_samples(text)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = bench.parse_clock_samples("0, 1500, 2070, 1400, 0x20, Not Active, Active, Not Active, Not Active")
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.parse_clock_samples("")["sm_mhz"] is None

@@ -160,6 +160,8 @@ def _ptr(a):
 # C ABI, same names
 # ------------------------------------------------------------------------------------------------
 def pic_config_default(**overrides) -> pic_config:
+    """Default pic_config (2D 64x128 FP64 Galerkin beam at gamma = 130, c dt/dz = 0.5) with keyword overrides set
+    on the struct."""
     c = pic_config()
     lib().pic_config_default(ctypes.byref(c))
     for k, v in overrides.items():
@@ -168,6 +170,8 @@ def pic_config_default(**overrides) -> pic_config:
 
 
 def pic_compute_correction_coeffs(scheme: int, alpha: float):
+    """Psi_E, Psi_B coefficients (powers of xi, constant first) of the (4,4) rational interpolant of Sec. 2 for the
+    gather scheme at alpha = c dt/dz; raises PicError (PIC_E_SINGULAR) when no interpolant exists."""
     pe = (ctypes.c_double * 5)()
     pb = (ctypes.c_double * 5)()
     _check(lib().pic_compute_correction_coeffs(scheme, alpha, pe, pb))
@@ -175,6 +179,8 @@ def pic_compute_correction_coeffs(scheme: int, alpha: float):
 
 
 def pic_create(cfg: pic_config):
+    """Validates cfg, allocates the run on the current device and returns its opaque handle (the seeded beam when
+    cfg.init_beam)."""
     h = ctypes.c_void_p()
     rc = lib().pic_create(ctypes.byref(cfg), ctypes.byref(h))
     if rc != PIC_OK:
@@ -183,30 +189,37 @@ def pic_create(cfg: pic_config):
 
 
 def pic_set_stream(h, stream_ptr: int | None):
+    """Queues the handle's later work on the cudaStream_t address stream_ptr (None: the handle's own stream)."""
     _check(lib().pic_set_stream(h, stream_ptr), h)
 
 
 def pic_set_correction_stencil(h, psi_e=None, psi_b=None):
+    """Sets the Psi_E / Psi_B coefficients (Sec. 2) of the gather correction; both None turns it off."""
     pe = None if psi_e is None else (ctypes.c_double * 5)(*[float(v) for v in psi_e])
     pb = None if psi_b is None else (ctypes.c_double * 5)(*[float(v) for v in psi_b])
     _check(lib().pic_set_correction_stencil(h, pe, pb), h)
 
 
 def pic_step(h, nsteps: int = 1):
+    """Advances nsteps time steps, asynchronously on the handle's stream."""
     _check(lib().pic_step(h, int(nsteps)), h)
 
 
 def pic_sync(h):
+    """Waits for the handle's stream and raises PicError on any kernel error of the queued steps."""
     _check(lib().pic_sync(h), h)
 
 
 def pic_energy(h) -> dict:
+    """FP64 energies of the current state: W_E, W_B, W_perp (the transverse field energy of Sec. 4), kinetic, total,
+    particle count."""
     e = pic_energy_t()
     _check(lib().pic_energy(h, ctypes.byref(e)), h)
     return {"w_e": e.w_e, "w_b": e.w_b, "w_perp": e.w_perp, "k": e.k, "total": e.total, "np": e.np}
 
 
 def pic_num_particles(h) -> int:
+    """Current number of particles (synchronises)."""
     n = ctypes.c_longlong()
     _check(lib().pic_num_particles(h, ctypes.byref(n)), h)
     return n.value
@@ -226,20 +239,25 @@ def make_state(where: int, fields=None, particles=None) -> pic_state:
 
 
 def pic_set_state(h, state: pic_state):
+    """Replaces the non-NULL fields and the particles of the run (state.np = -1 keeps the particles)."""
     _check(lib().pic_set_state(h, ctypes.byref(state)), h)
 
 
 def pic_get_state(h, state: pic_state) -> pic_state:
+    """Copies the state out into the arrays state points at (state.np in: their capacity) and returns state."""
     _check(lib().pic_get_state(h, ctypes.byref(state)), h)
     return state
 
 
 def pic_debug_gather_copies(h, where: int, outs):
+    """Test hook: copies the six field copies the particles gathered from in the last step into outs (Ex Ey Ez Bx By
+    Bz)."""
     arr = (ctypes.c_void_p * 6)(*[_ptr(o) for o in outs])
     _check(lib().pic_debug_gather_copies(h, where, arr), h)
 
 
 def pic_debug_current(h, where: int, outs):
+    """Test hook: copies the filtered current J^{n+1/2} of the last step into outs (Jx Jy Jz)."""
     arr = (ctypes.c_void_p * 3)(*[_ptr(o) for o in outs])
     _check(lib().pic_debug_current(h, where, arr), h)
 
@@ -253,6 +271,8 @@ def pic_charge_residual(h) -> dict:
 
 
 def pic_fit_growth_rate(t, w):
+    """Growth rate Gamma = 1/2 d ln W / dt fitted over the exponential window of the series (t, w); returns (Gamma,
+    first, last sample index of the window)."""
     t = np.ascontiguousarray(t, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     g = ctypes.c_double()
@@ -265,19 +285,24 @@ def pic_fit_growth_rate(t, w):
 
 
 def pic_destroy(h):
+    """Frees the handle and everything it owns (None is a no-op)."""
     if h is not None:
         lib().pic_destroy(h)
 
 
 def pic_last_error(h) -> str:
+    """Text of the last error on the handle (None: the last failed pic_create on this thread)."""
     return lib().pic_last_error(h).decode()
 
 
 def pic_strerror(code: int) -> str:
+    """Name of a PIC_E_* status code."""
     return lib().pic_strerror(code).decode()
 
 
 def pic_energy_history(h, max_samples: int = 4096):
+    """Energies recorded on the device every cfg.diag_every steps, oldest first, at most max_samples dicts as
+    pic_energy returns."""
     buf = (pic_energy_t * max(max_samples, 1))()
     n = ctypes.c_int()
     _check(lib().pic_energy_history(h, buf, max_samples, ctypes.byref(n)), h)
@@ -286,10 +311,12 @@ def pic_energy_history(h, max_samples: int = 4096):
 
 
 def pic_enable_timing(h, on: bool = True):
+    """Turns per-kernel-class CUDA-event timing of the handle's launches on (resetting the totals) or off."""
     _check(lib().pic_enable_timing(h, 1 if on else 0), h)
 
 
 def pic_kernel_times(h):
+    """Device milliseconds and launch counts per kernel class since timing was enabled: {class: (ms, launches)}."""
     ms = (ctypes.c_double * PIC_NKERNEL)()
     cnt = (ctypes.c_longlong * PIC_NKERNEL)()
     _check(lib().pic_kernel_times(h, ms, cnt), h)
@@ -297,6 +324,7 @@ def pic_kernel_times(h):
 
 
 def pic_launch_count(h) -> int:
+    """Number of kernel launches the handle has made since it was created."""
     n = ctypes.c_longlong()
     _check(lib().pic_launch_count(h, ctypes.byref(n)), h)
     return n.value
@@ -333,6 +361,7 @@ def pic_adjoint_backward(h, dw: float = 1.0, grad_fields=None):
 
 
 def pic_adjoint_release(h):
+    """Frees the adjoint's checkpoints and work storage of the handle."""
     lib().pic_adjoint_release(h)
 
 
@@ -347,6 +376,7 @@ def _bcheck(rc, b):
 
 
 def pic_batch_create(cfgs):
+    """Creates a batch of independent runs (a sequence of pic_config) advanced together by shared launches."""
     arr = (pic_config * len(cfgs))(*cfgs)
     b = ctypes.c_void_p()
     _check(lib().pic_batch_create(arr, len(cfgs), ctypes.byref(b)))
@@ -354,10 +384,12 @@ def pic_batch_create(cfgs):
 
 
 def pic_batch_size(b) -> int:
+    """Number of runs in the batch."""
     return lib().pic_batch_size(b)
 
 
 def pic_batch_run(b, run: int):
+    """Handle of one run of the batch (owned by the batch) for state copies and energies between steps."""
     h = lib().pic_batch_run(b, run)
     if not h:
         raise PicError(PIC_E_ARG, "no such run")
@@ -365,24 +397,29 @@ def pic_batch_run(b, run: int):
 
 
 def pic_batch_set_correction_stencil(b, run: int, psi_e=None, psi_b=None):
+    """Sets the Psi_E / Psi_B coefficients of one run of the batch; both None turns its correction off."""
     pe = None if psi_e is None else (ctypes.c_double * 5)(*[float(v) for v in psi_e])
     pb = None if psi_b is None else (ctypes.c_double * 5)(*[float(v) for v in psi_b])
     _bcheck(lib().pic_batch_set_correction_stencil(b, run, pe, pb), b)
 
 
 def pic_batch_set_stream(b, stream_ptr):
+    """Queues the batch's later work on the cudaStream_t address stream_ptr (None: the batch's own stream)."""
     _bcheck(lib().pic_batch_set_stream(b, stream_ptr), b)
 
 
 def pic_batch_step(b, nsteps: int = 1):
+    """Advances every run of the batch nsteps time steps (a replayed CUDA graph per step)."""
     _bcheck(lib().pic_batch_step(b, int(nsteps)), b)
 
 
 def pic_batch_sync(b):
+    """Waits for the batch's stream and raises PicError on any kernel error."""
     _bcheck(lib().pic_batch_sync(b), b)
 
 
 def pic_batch_energy_history(b, run: int, max_samples: int = 4096):
+    """Energy samples of one run of the batch, oldest first, as pic_energy_history returns."""
     buf = (pic_energy_t * max(max_samples, 1))()
     n = ctypes.c_int()
     _bcheck(lib().pic_batch_energy_history(b, run, buf, max_samples, ctypes.byref(n)), b)
@@ -391,11 +428,14 @@ def pic_batch_energy_history(b, run: int, max_samples: int = 4096):
 
 
 def pic_batch_autotune(b, trial_steps: int = 3, ngroups: int = 8):
+    """Times the lanes-per-cell and blocks-per-SM candidates of the persistent push for every group, keeps the
+    fastest, resets every run to its seeded start; returns the chosen lanes per cell per group."""
     out = (ctypes.c_int * ngroups)()
     _bcheck(lib().pic_batch_autotune(b, int(trial_steps), out), b)
     return list(out)
 
 
 def pic_batch_destroy(b):
+    """Frees the batch and all its runs (None is a no-op)."""
     if b is not None:
         lib().pic_batch_destroy(b)

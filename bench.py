@@ -288,36 +288,57 @@ def e2e_measure(P, torch, h, cfg, stream, steps: int):
 SAMPLE_NZ = 64  # the CPU sample is a 512 x 64 slab of the same beam (1/16 of the box)
 
 
-def oracle_sample(nz: int = SAMPLE_NZ):
+def oracle_sample(nz: int = SAMPLE_NZ, seed: int = 2):
     import oracle as O
     st, pe, pb = O.rational_coeffs(O.GALERKIN, ALPHA)
     sim = O.Sim(ndim=2, nx=NX, nz=nz, dt=ALPHA, scheme=O.GALERKIN, psi_e=pe, psi_b=pb,
                 f_nbin=FILTER["filter_nbin"], f_ncomp=FILTER["filter_ncomp"], f_alpha=FILTER["filter_comp_alpha"],
                 f_targets=3)
-    sim.init_beam(ppc=PPC, gamma=GAMMA, seed=2)
+    sim.init_beam(ppc=PPC, gamma=GAMMA, seed=seed)
     return sim
 
 
-def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ):
-    sim = oracle_sample(nz)
-    for _ in range(warmup):
-        sim.step(1)
-        sim.energy()
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        sim.step(1)
-        sim.energy()
-        times.append(time.perf_counter() - t0)
-    return sim.n, times
+def host_threads() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def cpu_baseline(steps: int = 8) -> dict:
-    n, times = oracle_time(steps, 1)
-    t = sum(times) / len(times)
-    return {"value": n / t, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 C oracle, one thread: {steps} steps of a 512x{SAMPLE_NZ} slab of the same beam "
-                      f"({n} particles, same density, gamma, alpha, correction and filter) + energies each step"}
+def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ, threads: int = 1):
+    """Wall time of each of `steps` oracle steps (+ energies) of `threads` independent slabs of the beam
+    (seeds 2, 3, ...), one slab per host thread; the oracle is one C call per step and releases the GIL,
+    so the slabs run concurrently. Returns (particles over all slabs, per-step seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(sim):
+        sim.step(1)
+        sim.energy()
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        sims = list(ex.map(lambda k: oracle_sample(nz, seed=2 + k), range(threads)))
+        for _ in range(warmup):
+            list(ex.map(one, sims))
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            list(ex.map(one, sims))
+            times.append(time.perf_counter() - t0)
+    return sum(s.n for s in sims), times
+
+
+def cpu_baseline(steps: int = 8, threads: int = 0) -> dict:
+    threads = threads if threads > 0 else host_threads()
+    n1, t1 = oracle_time(steps, 1)
+    one = n1 / (sum(t1) / len(t1))
+    n, times = oracle_time(steps, 1, threads=threads) if threads > 1 else (n1, t1)
+    value = n / (sum(times) / len(times))
+    return {"value": value, "unit": UNIT, "cores": threads, "host_cores": os.cpu_count(), "kind": "oracle",
+            "one_thread": one,
+            "sample": f"FP64 C oracle on {threads} host threads, each its own 512x{SAMPLE_NZ} slab of the same beam "
+                      f"(seeds 2..{1 + threads}; {n1} particles a slab, same density, gamma, alpha, correction and "
+                      f"filter): {steps} steps + energies each, all slabs concurrently; one_thread = one slab alone"}
 
 
 def run_reference(args):
@@ -325,19 +346,23 @@ def run_reference(args):
     if rank != 0:
         return
     steps, warmup = max(args.steps, 1), max(args.warmup, 0)
-    # one oracle step of the 512 x 64 slab takes about 0.3 s: past 400 steps the slab shrinks so that
-    # the whole run stays near two minutes (the unit is per particle-step either way)
+    threads = args.cpu_threads if args.cpu_threads > 0 else host_threads()
+    # one oracle step of a 512 x 64 slab takes about 0.5 s (every thread its own slab, concurrently):
+    # past 400 steps the slabs shrink so that the whole run stays near two minutes (the unit is per
+    # particle-step either way)
     nz = SAMPLE_NZ if steps + warmup <= 400 else max(8, SAMPLE_NZ * 400 // (steps + warmup) // 8 * 8)
-    n, times = oracle_time(steps, warmup, nz)
+    n, times = oracle_time(steps, warmup, nz, threads=threads)
     total = sum(times)
     value = n * steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warmup, "ms_per_step": total / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.gpus),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step: one FP64 oracle step (one thread) of a 512x{nz} slab of "
-                                       f"the workload ({n} particles) + energies"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "host_cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle step + energies of {threads} independent "
+                                       f"512x{nz} slabs of the workload ({n} particles in all), one per host "
+                                       f"thread, concurrently"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -411,7 +436,7 @@ def run_ours(args):
             "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
             "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps, args.cpu_threads)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
@@ -760,6 +785,7 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0: every host core)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")

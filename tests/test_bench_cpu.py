@@ -1,6 +1,6 @@
 """CPU checks of bench.py's measurement helpers: the roofline arithmetic (algorithmic bytes per launch
 over the push's event time), the rule that the profiled DRAM traffic is reported only for the kernel
-source it was captured on, and the clock-sample parsing."""
+source it was captured on, the clock-sample parsing, and the oracle timing over several host threads."""
 import hashlib
 import os
 import sys
@@ -46,3 +46,14 @@ def test_clock_sample_parsing():
     hot = bench.parse_clock_samples("0, 1500, 2070, 1400, 0x20, Not Active, Active, Not Active, Not Active")
     assert hot["reasons"] == ["hw_thermal_slowdown"]
     assert bench.parse_clock_samples("")["sm_mhz"] is None
+
+
+def test_oracle_timing_over_threads():
+    # two concurrent slabs (seeds 2 and 3) of a thin 512 x 8 sample: the particle count is both slabs',
+    # one wall time per timed step, and the slabs are distinct samples of the same beam
+    n1, t1 = bench.oracle_time(1, 0, nz=8, threads=1)
+    n2, t2 = bench.oracle_time(2, 1, nz=8, threads=2)
+    assert n1 == bench.NX * 8 * 2 * bench.PPC and n2 == 2 * n1
+    assert len(t1) == 1 and len(t2) == 2 and min(t2) > 0
+    a, b = bench.oracle_sample(8, seed=2), bench.oracle_sample(8, seed=3)
+    assert a.n == b.n and not (a.part["z"] == b.part["z"]).all()

@@ -884,7 +884,7 @@ static int build_graph(pic_handle* h) {
   drop_graph(h);
   const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
   int len = 2;
-  while (len % de) len += 2;
+  while (len % de && len <= 64) len += 2;  // past 64: no graph
   if (len > 64) return PIC_E_STATE;  // diagnostics too sparse to unroll into one graph
   const long long nstep0 = h->nstep, nhist0 = h->nhist;
   const int parity0 = h->parity;
@@ -923,7 +923,7 @@ int pic_step(pic_handle* h, int nsteps) {
   // Graph replay when at least two whole graphs fit and timing is off; single steps otherwise.
   const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
   int len = 2;
-  while (len % de) len += 2;
+  while (len % de && len <= 64) len += 2;  // past 64 the caller falls back to single steps
   if (h->timing || len > 64 || nsteps < 2 * len) return run_steps(h, nsteps);
   int lead = (int)((len - h->nstep % len) % len);
   int rc = run_steps(h, lead);
@@ -1263,7 +1263,7 @@ int batch_run_steps(pic_batch* b, int k) {
 int batch_graph_len(const pic_batch* b) {
   const int de = b->diag_every > 0 ? b->diag_every : 1;
   int len = 2;
-  while (len % de) len += 2;
+  while (len % de && len <= 64) len += 2;  // past 64 the caller falls back to single steps
   return len;
 }
 

@@ -67,10 +67,10 @@ typedef struct pic_config {
   int nx, ny, nz;           /* cells per direction; ny is forced to 1 in 2D */
   double dx, dy, dz, dt;    /* cell sizes and time step (c = 1); dy forced to 1 in 2D */
   double gamma;             /* Lorentz factor of the beam drift along +z */
-  int scheme;               /* PIC_GALERKIN or PIC_UNIFORM field gather */
+  int scheme;               /* field gather: PIC_GALERKIN, PIC_UNIFORM or PIC_MOMENTUM */
   int shape_order;          /* particle shape: 1 (linear) or 3 (cubic B-spline, the Sec. 3 setting) */
   int precision;            /* PIC_FP32 or PIC_FP64 (fields, particles and kernels) */
-  int ppc_per_species;      /* lattice points per cell per species of the initial beam */
+  int ppc_per_species;      /* lattice points per cell per species of the initial beam, 0 .. 2^20 */
   double omega_p_dz;        /* total plasma frequency (both species) times dz / c */
   double jitter;            /* uniform position jitter half-width, cells */
   double u_th;              /* Gaussian spread of each momentum component (u = gamma v) */
@@ -81,7 +81,7 @@ typedef struct pic_config {
   int filter_targets;       /* PIC_FILTER_J | PIC_FILTER_GATHER */
   unsigned long long seed;  /* Philox4x32-10 key of the initial beam */
   int init_beam;            /* 1: pic_create fills the seeded beam; 0: start empty */
-  int bin_capacity;         /* particle slots per cell per species; 0: automatic */
+  int bin_capacity;         /* particle slots per cell per species, up to 2^24; 0: automatic */
   int track_ids;            /* 1: carry a 32-bit id per particle (for tests) */
   int diag_every;           /* > 0: record the energies on the device every diag_every steps */
   int diag_capacity;        /* ring size of the energy history; 0: 4096 samples */

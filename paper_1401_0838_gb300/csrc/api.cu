@@ -721,7 +721,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       !(c.dz > 0) || !(c.dt > 0) || !(c.gamma >= 1.0) ||
       (c.scheme != PIC_GALERKIN && c.scheme != PIC_UNIFORM && c.scheme != PIC_MOMENTUM) ||
       (c.shape_order != 1 && c.shape_order != 3) || (c.precision != PIC_FP32 && c.precision != PIC_FP64) ||
-      c.ppc_per_species < 0 ||
+      c.ppc_per_species < 0 || c.ppc_per_species > (1 << 20) || c.bin_capacity > (1 << 24) ||
       c.filter_nbin < 0 || c.filter_ncomp < 0 || c.filter_nbin + c.filter_ncomp > 12 || c.bin_capacity < 0 ||
       c.diag_every < 0 || c.diag_capacity < 0 ||
       (c.correction_mode != PIC_CORR_SPLIT && c.correction_mode != PIC_CORR_RATIONAL) ||

@@ -96,6 +96,11 @@ def test_create_validates_before_touching_the_gpu():
     with pytest.raises(P.PicError) as e:
         P.pic_create(cfg)
     assert e.value.code == P.PIC_E_CFL
+    # sizes whose slot count would overflow the library's int arithmetic are refused up front
+    for kw in (dict(ppc_per_species=(1 << 20) + 1), dict(bin_capacity=(1 << 24) + 1), dict(ppc_per_species=-1)):
+        with pytest.raises(P.PicError) as e:
+            P.pic_create(P.pic_config_default(**kw))
+        assert e.value.code == P.PIC_E_ARG, kw
 
 
 def test_create_validates_the_ck_solver():

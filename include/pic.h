@@ -208,7 +208,10 @@ int pic_charge_residual(pic_handle* h, double out[3]);
  * Gamma = 1/2 d ln W / dt by an FP64 least-squares fit over the window from the first sample
  * two decades above the noise floor (median of log10 W over the first tenth of the samples) to
  * the first later sample within one decade of the maximum; if that window has fewer than 5
- * samples, the steepest window of max(5, n/5) samples after the first tenth. Host only. */
+ * samples, the steepest window of max(5, n/5) samples after the first tenth. Samples with w <= 0 or
+ * non-finite w are skipped; *i0, *i1 (either may be NULL) receive the window's first and last sample
+ * as indices into t and w. PIC_E_ARG when t is not finite and strictly increasing or fewer than 5
+ * samples are kept. Host only. */
 int pic_fit_growth_rate(const double* t, const double* w, int n, double* gamma_out, int* i0, int* i1);
 
 /* Energies recorded on the device every cfg.diag_every steps (fused into the step: the kinetic

@@ -1,10 +1,12 @@
 """Growth-rate fit of the transverse field energy (oracle side; test infrastructure only).
 
-The paper reports "maximum numerical instability growth rates" of the field energy (Fig. 2 and
-Fig. 4 captions) without stating how they were fitted. Reading used here and, independently
+The paper's Fig. 2 and Fig. 4 captions give the largest growth rates of the instability, taken from
+the field energy, without stating how they were fitted. Reading used here and, independently
 re-implemented, by the CUDA library's host code:
 
-* L(t) = log10 W_perp(t) over samples with W_perp > 0;
+* sample times finite and strictly increasing (an error otherwise);
+* L(t) = log10 W_perp(t) over the samples with finite W_perp > 0 (the others are skipped; the
+  window's indices i0, i1 refer to the caller's arrays);
 * noise floor = median of L over the first tenth of those samples (at least 3);
 * saturation = max L;
 * window = from the first sample with L >= floor + 2 to the first later sample with
@@ -26,10 +28,14 @@ def _slope(t: np.ndarray, y: np.ndarray) -> float:
 
 
 def growth_rate(t, w):
-    """Return (Gamma, i0, i1): amplitude growth rate and the inclusive sample window used."""
+    """Return (Gamma, i0, i1): amplitude growth rate and the inclusive sample window used, as indices
+    into t and w."""
     t = np.asarray(t, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
-    keep = w > 0
+    if not np.isfinite(t).all() or (np.diff(t) <= 0).any():
+        raise ValueError("the sample times must be finite and strictly increasing")
+    keep = (w > 0) & np.isfinite(w)
+    src = np.nonzero(keep)[0]  # index of each kept sample in the caller's arrays
     t, w = t[keep], w[keep]
     n = len(w)
     if n < 5:
@@ -44,11 +50,11 @@ def growth_rate(t, w):
     while i1 < n - 1 and lg[i1] < hi:
         i1 += 1
     if hi > lo and i1 - i0 + 1 >= 5:
-        return 0.5 * _slope(t[i0:i1 + 1], np.log(w[i0:i1 + 1])), i0, i1
+        return 0.5 * _slope(t[i0:i1 + 1], np.log(w[i0:i1 + 1])), int(src[i0]), int(src[i1])
     m = max(5, n // 5)
     best, bi = -np.inf, 0
     for s in range(min(head, n - m), n - m + 1):
         sl = _slope(t[s:s + m], np.log(w[s:s + m]))
         if sl > best:
             best, bi = sl, s
-    return 0.5 * best, bi, bi + m - 1
+    return 0.5 * best, int(src[bi]), int(src[bi + m - 1])

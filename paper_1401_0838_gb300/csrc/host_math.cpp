@@ -148,12 +148,16 @@ static double lsq_slope(const double* t, const double* y, int n) {
 }
 
 int growth_fit(const double* t_in, const double* w_in, int n_in, double* g, int* i0o, int* i1o) {
+  for (int i = 0; i < n_in; ++i)
+    if (!isfinite(t_in[i]) || (i > 0 && !(t_in[i] > t_in[i - 1]))) return PIC_E_ARG;  // times must increase
   std::vector<double> t, lnw, lg;
+  std::vector<int> src;  // index of each kept sample in the caller's arrays
   for (int i = 0; i < n_in; ++i)
     if (w_in[i] > 0 && isfinite(w_in[i])) {
       t.push_back(t_in[i]);
       lnw.push_back(log(w_in[i]));
       lg.push_back(log10(w_in[i]));
+      src.push_back(i);
     }
   const int n = (int)t.size();
   if (n < 5) return PIC_E_ARG;
@@ -173,8 +177,8 @@ int growth_fit(const double* t_in, const double* w_in, int n_in, double* g, int*
   while (b < n - 1 && lg[b] < hi) ++b;
   if (hi > lo && a < n && b - a + 1 >= 5) {
     *g = 0.5 * lsq_slope(&t[a], &lnw[a], b - a + 1);
-    if (i0o) *i0o = a;
-    if (i1o) *i1o = b;
+    if (i0o) *i0o = src[a];
+    if (i1o) *i1o = src[b];
     return PIC_OK;
   }
   const int m = std::max(5, n / 5);
@@ -188,8 +192,8 @@ int growth_fit(const double* t_in, const double* w_in, int n_in, double* g, int*
     }
   }
   *g = 0.5 * best;
-  if (i0o) *i0o = bi;
-  if (i1o) *i1o = bi + m - 1;
+  if (i0o) *i0o = src[bi];
+  if (i1o) *i1o = src[bi + m - 1];
   return PIC_OK;
 }
 

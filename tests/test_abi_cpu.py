@@ -83,6 +83,39 @@ def test_growth_fit_matches_oracle(seed):
     assert abs(a[0] - b[0]) < 1e-12 * abs(b[0])
 
 
+def test_growth_fit_indices_refer_to_the_callers_arrays():
+    # samples with w <= 0 or non-finite w are skipped by both fits; the window's indices still point
+    # into the arrays passed in, so t[i0] and t[i1] are its first and last times
+    t = np.arange(150) * 0.7
+    w = 1e-8 * (1 + 0.2 * np.random.default_rng(3).random(150)) + 1e-10 * np.exp(0.06 * t)
+    w = np.minimum(w, 1.0)
+    ref = growth_rate(t, w)
+    holes = w.copy()
+    holes[[0, 7, 40, 41]] = (0.0, -1.0, np.nan, np.inf)
+    a, b = P.pic_fit_growth_rate(t, holes), growth_rate(t, holes)
+    assert a[1:] == b[1:]
+    assert abs(a[0] - b[0]) < 1e-12 * abs(b[0])
+    assert 41 < b[1] and b[2] == ref[2]  # same window end; no skipped sample inside the window
+    assert holes[b[1]] > 0 and holes[b[2]] > 0
+
+
+@pytest.mark.parametrize("bad", ["repeat", "decrease", "nan"])
+def test_growth_fit_rejects_a_bad_time_axis(bad):
+    t = np.arange(50) * 0.5
+    w = np.exp(0.1 * t)
+    if bad == "repeat":
+        t[10] = t[9]
+    elif bad == "decrease":
+        t = t[::-1].copy()
+    else:
+        t[3] = np.nan
+    with pytest.raises(P.PicError) as e:
+        P.pic_fit_growth_rate(t, w)
+    assert e.value.code == P.PIC_E_ARG
+    with pytest.raises(ValueError):
+        growth_rate(t, w)
+
+
 def test_create_validates_before_touching_the_gpu():
     cfg = P.pic_config_default(dt=0.71)  # 2D Courant limit 1/sqrt(2)
     with pytest.raises(P.PicError) as e:

@@ -390,11 +390,12 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
         kin += w * u2 / (gam + T(1));
         ++npush;
         T ddx = r.dtdx * ux * ign, ddy = NDIM == 3 ? r.dtdy * uy * ign : T(0), ddz = r.dtdz * Uz * ign;
-        const T vy = uy * ign;
+        T vy = uy * ign;
         if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
           flag_error(r.err, ERR_NONFINITE);
           ddx = ddy = ddz = T(0);
           ux = uy = uz = T(0);
+          vy = T(0);  // nothing non-finite reaches the current
         }
         // Esirkepov on the window nodes K0 .. K0 + NW - 1 of the start cell
         T S0x[NW], dSx[NW], S0y[NW], dSy[NW], S0z[NW], dSz[NW];
@@ -613,11 +614,12 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
         ++npush;
       }
       T ddx = r.dtdx * ux * ign, ddz = r.dtdz * Uz * ign;
-      const T vy = uy * ign;
+      T vy = uy * ign;
       if (valid && !(ddx > T(-1) && ddx < T(1) && ddz > T(-1) && ddz < T(1))) {
         flag_error(r.err, ERR_NONFINITE);
         ddx = ddz = T(0);
         ux = uy = uz = T(0);
+        vy = T(0);  // nothing non-finite reaches the current
       }
       if (!valid) ddx = ddz = T(0);
       // Esirkepov on the cell's window

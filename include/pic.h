@@ -286,7 +286,8 @@ int pic_batch_sync(pic_batch* b);
 int pic_batch_energy_history(pic_batch* b, int run, pic_energy_t* out, int max, int* count);
 /* Autotuner: for every lanes-per-cell group, times 2*trial_steps batched steps with each candidate
  * (4, 8 or 16 lanes per cell; 1 or 2 resident blocks of the push kernel per SM) and keeps the
- * fastest (written to lpc_out[group] when not NULL); then every run is put back into its seeded
+ * fastest (written to lpc_out[group] when not NULL; the runs are grouped by their default lanes per
+ * cell, 4, 8 or 16, so lpc_out needs at most 3 entries); then every run is put back into its seeded
  * initial state (fields zero, beam from the seed), so tune before importing other states. */
 int pic_batch_autotune(pic_batch* b, int trial_steps, int* lpc_out);
 void pic_batch_destroy(pic_batch* b);

@@ -1,5 +1,6 @@
 """Replica aggregation of bench.py across ranks, on CPU with torch.distributed gloo (world size 2):
-the job's value is the units of all ranks over the slowest rank's time."""
+the job's value is the units of all ranks over the slowest rank's time; and the reference arm under
+torchrun, where rank 0 alone runs and prints."""
 import os
 import socket
 import sys
@@ -53,3 +54,28 @@ def test_single_process_aggregate_is_identity():
     import bench
     agg = bench.aggregate(50.0, 200.0, steps=4)
     assert agg["ms"] == 50.0 and agg["value"] == 200.0 * 4 / 0.05
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    # bench.py --impl reference launched as the multi-GPU command is: rank 0 alone times the oracle
+    # (here on 2 host threads, one slab each) and prints one JSON line; rank 1 exits 0 with no output
+    import json
+    import subprocess
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "0", "--cpu-threads", "2"]
+    res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, res.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

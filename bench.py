@@ -299,11 +299,28 @@ def oracle_sample(nz: int = SAMPLE_NZ, seed: int = 2):
 
 
 def host_threads() -> int:
-    """Cores this process may run on."""
+    """Cores this process may run on: its CPU affinity, capped by a cgroup v2 CPU quota if one is set."""
     try:
-        return len(os.sched_getaffinity(0))
+        n = len(os.sched_getaffinity(0))
     except AttributeError:
-        return os.cpu_count() or 1
+        n = os.cpu_count() or 1
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            cap = cgroup_cpu_limit(f.read())
+    except OSError:
+        cap = None
+    return min(n, cap) if cap else n
+
+
+def cgroup_cpu_limit(text: str):
+    """Whole cores allowed by a cgroup v2 cpu.max line ("quota period"; "max" = no limit), else None."""
+    parts = text.split()
+    if len(parts) < 2 or parts[0] == "max":
+        return None
+    try:
+        return max(1, int(parts[0]) // int(parts[1]))
+    except ValueError:
+        return None
 
 
 def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ, threads: int = 1):

@@ -57,3 +57,12 @@ def test_oracle_timing_over_threads():
     assert len(t1) == 1 and len(t2) == 2 and min(t2) > 0
     a, b = bench.oracle_sample(8, seed=2), bench.oracle_sample(8, seed=3)
     assert a.n == b.n and not (a.part["z"] == b.part["z"]).all()
+
+
+def test_cgroup_cpu_limit_parsing():
+    assert bench.cgroup_cpu_limit("max 100000\n") is None
+    assert bench.cgroup_cpu_limit("1600000 100000\n") == 16
+    assert bench.cgroup_cpu_limit("150000 100000") == 1
+    assert bench.cgroup_cpu_limit("50000 100000") == 1
+    assert bench.cgroup_cpu_limit("") is None and bench.cgroup_cpu_limit("x y") is None
+    assert 1 <= bench.host_threads() <= (os.cpu_count() or 1)

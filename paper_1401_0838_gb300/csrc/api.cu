@@ -177,7 +177,10 @@ cudaError_t launch(pic_handle* h, int cls, F&& go) {
 void* dalloc(pic_handle* h, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();  // reported by the null return; a later launch check must not see it
+    return nullptr;
+  }
   h->allocs.push_back(p);
   return p;
 }
@@ -1177,7 +1180,10 @@ int bfail(pic_batch* b, int code, const std::string& msg) {
 
 void* balloc(pic_batch* b, size_t bytes) {
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+    (void)cudaGetLastError();  // reported by the null return; a later launch check must not see it
+    return nullptr;
+  }
   b->allocs.push_back(p);
   return p;
 }
@@ -1618,7 +1624,10 @@ namespace {
 
 void* adj_malloc(pic_handle* h, size_t bytes) {
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+    (void)cudaGetLastError();  // reported by the null return; a later launch check must not see it
+    return nullptr;
+  }
   h->adj.mem.push_back(p);
   return p;
 }

@@ -1,8 +1,9 @@
-"""Failure detection on the GPU without a fault: the kernels turn a particle bin that overflows, an
-invalid imported particle and a non-finite particle into error flags (every access stays in bounds:
-the insertion checks the slot before writing, the import checks cell, species and offsets, the push
-stops a particle whose displacement is not finite). The host reads the flags as status codes at the
-next synchronising call, clears them, and the handle stays usable."""
+"""Failure detection on the GPU without a fault. A device allocation that fails is returned as
+PIC_E_OOM. The kernels turn a particle bin that overflows, an invalid imported particle and a
+non-finite particle into error flags, with every access in bounds: the insertion checks the slot
+before writing, the import checks cell, species and offsets, and the push stops a particle whose
+displacement is not finite. The host reads the flags as status codes at the next synchronising
+call and clears them; the handle stays usable."""
 import numpy as np
 import pytest
 
@@ -99,5 +100,24 @@ def test_non_finite_momentum_is_reported_and_stopped(precision, order, scheme):
         f = _fields(h, cfg)
         assert all(np.isfinite(f[c]).all() for c in FIELDS)
         assert max(np.abs(f[c]).max() for c in FIELDS) > 0  # the other particles did deposit
+    finally:
+        P.pic_destroy(h)
+
+
+def test_allocation_failure_is_reported_and_other_handles_keep_working():
+    # a run whose particle bins would need about 1 TB per array: pic_create frees what it allocated
+    # and returns PIC_E_OOM; a live handle on the same thread still counts (a launch outside the
+    # per-kernel wrapper, which would see a stale allocation error) and steps
+    ok = make_cfg(nx=16, nz=16, precision=0)
+    h = P.pic_create(ok)
+    try:
+        _import(h, _particles(ok, 8, cell=40))
+        with pytest.raises(P.PicError) as e:
+            P.pic_create(make_cfg(nx=128, nz=128, precision=0, cap=1 << 24))
+        assert e.value.code == P.PIC_E_OOM
+        assert "allocation" in P.pic_last_error(None)
+        assert P.pic_num_particles(h) == 8
+        P.pic_step(h, 1)
+        P.pic_sync(h)
     finally:
         P.pic_destroy(h)

@@ -3,6 +3,7 @@
 // the step and of its adjoint runs in the CUDA kernels of k_fields.cu, k_particles.cu and
 // k_adjoint.cu; this file only allocates, marshals and orders launches on one stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -155,9 +156,20 @@ cudaError_t collect_times(pic_handle* h) {
   return cudaSuccess;
 }
 
+// NVTX ranges for profilers (a no-op unless one is attached): one per kernel launch, named by its
+// class, and one around each pic_step / pic_batch_step call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+const char* const kKernelClassName[PIC_NKERNEL] = {"copies", "push", "filter", "yee", "diag", "other", "migrate"};
+
 // Launch one kernel of class `cls`, counted, and bracketed by events when timing is on.
 template <class F>
 cudaError_t launch(pic_handle* h, int cls, F&& go) {
+  NvtxRange range(kKernelClassName[cls]);
   (void)cudaGetLastError();  // a failed earlier query must not be reported as this launch's error
   h->launches++;
   h->tcount[cls]++;
@@ -923,6 +935,7 @@ extern "C" {
 
 int pic_step(pic_handle* h, int nsteps) {
   if (!h || nsteps < 0) return PIC_E_ARG;
+  NvtxRange range("pic_step");
   // Graph replay when at least two whole graphs fit and timing is off; single steps otherwise.
   const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
   int len = 2;
@@ -1495,6 +1508,7 @@ int pic_batch_set_stream(pic_batch* b, void* stream) {
 
 int pic_batch_step(pic_batch* b, int nsteps) {
   if (!b || nsteps < 0) return PIC_E_ARG;
+  NvtxRange range("pic_batch_step");
   for (pic_handle* h : b->runs)
     if (h->parity != b->parity) return bfail(b, PIC_E_STATE, "a run was stepped or reset on its own");
   if (b->tables_dirty) {

@@ -323,18 +323,32 @@ def cgroup_cpu_limit(text: str):
         return None
 
 
-def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ, threads: int = 1):
+def oracle_sample_3d(nz: int = 8, seed: int = 3):
+    """A 128 x 128 x nz slab of the 3D workload: 8 particles/cell/species, transverse Gaussian weights
+    (sigma 20 cells), gamma 130, c dt/dz 0.5, Galerkin, correction + filter (1, 1, a = 3)."""
+    import oracle as O
+    st, pe, pb = O.rational_coeffs(O.GALERKIN, 0.5)
+    sim = O.Sim(ndim=3, nx=128, ny=128, nz=nz, dt=0.5, scheme=O.GALERKIN, psi_e=pe, psi_b=pb, f_nbin=1,
+                f_ncomp=1, f_alpha=3.0, f_targets=3)
+    sim.init_beam(ppc=8, gamma=130.0, sigma_perp=20.0, seed=seed)
+    return sim
+
+
+def oracle_time(steps: int, warmup: int, nz: int = SAMPLE_NZ, threads: int = 1, sample=None):
     """Wall time of each of `steps` oracle steps (+ energies) of `threads` independent slabs of the beam
-    (seeds 2, 3, ...), one slab per host thread; the oracle is one C call per step and releases the GIL,
-    so the slabs run concurrently. Returns (particles over all slabs, per-step seconds)."""
+    (seeds 2, 3, ...; `sample(nz, seed)` builds one, default the 2D workload's), one slab per host
+    thread; the oracle is one C call per step and releases the GIL, so the slabs run concurrently.
+    Returns (particles over all slabs, per-step seconds)."""
     from concurrent.futures import ThreadPoolExecutor
+
+    sample = sample or oracle_sample
 
     def one(sim):
         sim.step(1)
         sim.energy()
 
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        sims = list(ex.map(lambda k: oracle_sample(nz, seed=2 + k), range(threads)))
+        sims = list(ex.map(lambda k: sample(nz, seed=2 + k), range(threads)))
         for _ in range(warmup):
             list(ex.map(one, sims))
         times = []
@@ -686,7 +700,21 @@ def run_3d(args):
                          "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": round(per_launch_s * 1e3, 4)},
             "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
             "cell_updates_per_s": ncell * args.steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_3d(args.cpu_steps_3d, args.cpu_threads)
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_3d(steps: int = 3, threads: int = 0, nz: int = 8) -> dict:
+    """The oracle on a few steps of thin slabs of the 3D workload, every host core one slab."""
+    threads = threads if threads > 0 else host_threads()
+    n, times = oracle_time(steps, 0, nz=nz, threads=threads, sample=oracle_sample_3d)
+    return {"value": n / (sum(times) / len(times)), "unit": UNIT, "cores": threads, "host_cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"FP64 C oracle on {threads} host threads, each its own 128x128x{nz} slab of the 3D workload "
+                      f"({n // threads} particles a slab, 1/{512 // nz} of the box; same density, weights, gamma, "
+                      f"alpha, correction and filter): {steps} steps + energies each, concurrently; a short "
+                      f"sample of the workload, per particle-step"}
 
 
 def run_gamma_sweep(args):
@@ -803,6 +831,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0: every host core)")
+    ap.add_argument("--cpu-steps-3d", type=int, default=3, help="oracle steps of the --config3d CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")

@@ -66,3 +66,11 @@ def test_cgroup_cpu_limit_parsing():
     assert bench.cgroup_cpu_limit("50000 100000") == 1
     assert bench.cgroup_cpu_limit("") is None and bench.cgroup_cpu_limit("x y") is None
     assert 1 <= bench.host_threads() <= (os.cpu_count() or 1)
+
+
+def test_oracle_baseline_of_the_3d_workload():
+    # two concurrent 128 x 128 x 2 slabs of the 3D workload, one step each: the count is both slabs'
+    # particles (8 per cell and species) and the line carries the baseline's keys
+    cb = bench.cpu_baseline_3d(steps=1, threads=2, nz=2)
+    assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] > 0
+    assert "128x128x2" in cb["sample"] and f"{128 * 128 * 2 * 16} particles a slab" in cb["sample"]

@@ -705,6 +705,64 @@ def run_3d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_config1(args):
+    """The small 2D workload: 64 x 128, 4 particles/cell/species (65,536 particles), gamma 130,
+    c dt/dz 0.5, Galerkin, correction + filter (1, 1, a = 3), FP64, energies every step, the steps
+    replayed from the step graph. Its 7 MB stay in L2, so it is bound by launch latency: the line
+    reports microseconds and launches per step, not an HBM roofline. The oracle runs the whole
+    workload for comparison."""
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    cfg = P.pic_config_default(nx=64, nz=128, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN, precision=P.PIC_FP64,
+                               ppc_per_species=4, seed=1, init_beam=1, diag_every=1)
+    h = P.pic_create(cfg)
+    P.pic_set_stream(h, stream.cuda_stream)
+    P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, 0.5))
+    np_ = P.pic_num_particles(h)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            P.pic_step(h, 1)
+    P.pic_sync(h)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
+    clk = clocks.stop()
+    P.pic_destroy(h)
+    line = {"metric": METRIC, "value": np_ * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2D 64x128, 4 particles/cell/species (65,536 particles), gamma 130, c dt/dz 0.5, "
+                                   "Galerkin, correction + filter (1,1,a=3), FP64, energies every step",
+                       "particles": np_, "l2": "L2 resident (7 MB): bound by launch latency, no flush"},
+            "us_per_step": 1e3 * ms / args.steps, "launches_per_step": launches / args.steps,
+            "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
+            "cell_updates_per_s": 64 * 128 * args.steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_config1(args.cpu_steps_c1)
+    print(json.dumps(line), flush=True)
+
+
+def oracle_config1(steps: int = 200) -> dict:
+    """The oracle running the whole 64 x 128 FP64 workload of run_config1 for `steps` steps (+ energies
+    each step) on one thread: a single run does not split over threads."""
+    import oracle as O
+    st, pe, pb = O.rational_coeffs(O.GALERKIN, 0.5)
+    sim = O.Sim(ndim=2, nx=64, nz=128, dt=0.5, scheme=O.GALERKIN, psi_e=pe, psi_b=pb, f_nbin=1, f_ncomp=1,
+                f_alpha=3.0, f_targets=3)
+    sim.init_beam(ppc=4, gamma=130.0, seed=1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step(1)
+        sim.energy()
+    t = time.perf_counter() - t0
+    return {"value": sim.n * steps / t, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the whole workload ({sim.n} particles), {steps} steps + energies each, one thread"}
+
+
 def cpu_baseline_3d(steps: int = 3, threads: int = 0, nz: int = 8) -> dict:
     """The oracle on a few steps of thin slabs of the 3D workload, every host core one slab."""
     threads = threads if threads > 0 else host_threads()
@@ -832,6 +890,7 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0: every host core)")
     ap.add_argument("--cpu-steps-3d", type=int, default=3, help="oracle steps of the --config3d CPU baseline")
+    ap.add_argument("--cpu-steps-c1", type=int, default=200, help="oracle steps of the --config1 CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")
@@ -842,6 +901,7 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
+    ap.add_argument("--config1", action="store_true", help="time the small 64x128 FP64 workload instead")
     ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
     ap.add_argument("--gamma-sweep", action="store_true", help="growth against c dt/dz at gamma 3 and 130 instead")
     ap.add_argument("--gamma-time", type=float, default=2000.0,
@@ -865,6 +925,8 @@ def main(argv=None):
         run_adjoint(args)
     elif args.config3d:
         run_3d(args)
+    elif args.config1:
+        run_config1(args)
     elif args.gamma_sweep:
         run_gamma_sweep(args)
     elif args.variants:

@@ -74,3 +74,9 @@ def test_oracle_baseline_of_the_3d_workload():
     cb = bench.cpu_baseline_3d(steps=1, threads=2, nz=2)
     assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] > 0
     assert "128x128x2" in cb["sample"] and f"{128 * 128 * 2 * 16} particles a slab" in cb["sample"]
+
+
+def test_oracle_baseline_of_the_small_workload():
+    cb = bench.oracle_config1(steps=2)
+    assert cb["cores"] == 1 and cb["kind"] == "oracle" and cb["value"] > 0
+    assert "65536 particles" in cb["sample"]

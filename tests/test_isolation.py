@@ -73,7 +73,7 @@ def test_built_libraries_reference_no_symbol_of_the_other():
 
 def test_only_the_baseline_legs_import_the_oracle():
     allowed = {
-        "bench.py": {"oracle_sample", "oracle_sample_3d"},
+        "bench.py": {"oracle_sample", "oracle_sample_3d", "oracle_config1"},
         "__graft_entry__.py": {"build", "smoke"},
     }
     for name, funcs in allowed.items():

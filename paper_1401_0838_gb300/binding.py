@@ -225,6 +225,11 @@ def pic_num_particles(h) -> int:
     return n.value
 
 
+def _itemsize(a) -> int:
+    """Bytes per element of a numpy array or torch tensor."""
+    return a.itemsize if isinstance(a, np.ndarray) else a.element_size()
+
+
 def make_state(where: int, fields=None, particles=None) -> pic_state:
     """pic_state from dicts of arrays: fields {ex..bz}, particles {cell, species, ox, oy, oz, dux, duy, duz, w, id}."""
     s = pic_state()
@@ -233,6 +238,14 @@ def make_state(where: int, fields=None, particles=None) -> pic_state:
         setattr(s, n, _ptr((fields or {}).get(n)))
     p = particles or {}
     s.np = len(p["cell"]) if "cell" in p else 0
+    # the library reads np elements of every particle array it is given: refuse shorter ones here
+    for n, a in p.items():
+        if a is not None and len(a) != s.np:
+            raise ValueError(f"particle array {n!r} has {len(a)} elements, cell has {s.np}")
+    for n in ("cell", "species", "id"):
+        a = p.get(n)
+        if a is not None and _itemsize(a) != 4:
+            raise ValueError(f"particle array {n!r} must hold 4-byte integers")
     for n in ("cell", "species", "ox", "oy", "oz", "dux", "duy", "duz", "w", "id"):
         setattr(s, n, _ptr(p.get(n)))
     return s
@@ -275,6 +288,8 @@ def pic_fit_growth_rate(t, w):
     first, last sample index of the window)."""
     t = np.ascontiguousarray(t, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
+    if t.shape != w.shape or t.ndim != 1:
+        raise ValueError(f"t and w must be 1-D arrays of one length (got {t.shape} and {w.shape})")
     g = ctypes.c_double()
     i0 = ctypes.c_int()
     i1 = ctypes.c_int()

@@ -209,3 +209,20 @@ def test_breakdown_windows_agree_with_oracle():
     high = [a for a in lib_bad if a >= 0.71]
     assert 5 <= len(low) < 60 and min(low) > 0.64 and max(low) < 0.70
     assert 5 <= len(high) < 40 and min(high) > 0.765 and max(high) < 0.79
+
+
+def test_binding_refuses_arrays_the_library_would_overrun():
+    # the library reads np (= len(cell)) elements of every particle array and n samples of t and w
+    n = 5
+    part = {"cell": np.zeros(n, np.int32), "species": np.zeros(n, np.int32), "ox": np.zeros(n, np.float32),
+            "oz": np.zeros(n, np.float32), "dux": np.zeros(n, np.float32), "duy": np.zeros(n, np.float32),
+            "duz": np.zeros(n, np.float32)}
+    assert P.make_state(P.PIC_HOST, None, part).np == n
+    with pytest.raises(ValueError):
+        P.make_state(P.PIC_HOST, None, dict(part, oz=np.zeros(n - 1, np.float32)))
+    with pytest.raises(ValueError):
+        P.make_state(P.PIC_HOST, None, dict(part, cell=np.zeros(n, np.int64)))
+    torch = pytest.importorskip("torch")
+    assert P.make_state(P.PIC_HOST, None, {k: torch.from_numpy(v) for k, v in part.items()}).np == n
+    with pytest.raises(ValueError):
+        P.pic_fit_growth_rate(np.arange(10.0), np.ones(9))

@@ -88,6 +88,29 @@ def test_correction_and_filter_suppress_growth():
     assert g_off > 0.01
 
 
+def test_uniform_magic_time_step():
+    # The magic time step of the paper's LPA section: at c dt/dz = 0.5 the Uniform multiplier is
+    # identically 1, and the uncorrected Uniform run (linear shapes, 128x128, gamma = 130, filter of one
+    # bilinear and one compensation pass) grows far slower than the uncorrected Galerkin run
+    steps, every, alpha = 2000, 10, 0.5
+    rates = {}
+    for scheme in (0, 1):
+        cfg = make_cfg(nx=128, nz=128, dt=alpha, scheme=scheme, precision=0, ppc=4, init_beam=1, seed=7,
+                       track_ids=0)
+        cfg.diag_every = every
+        h = P.pic_create(cfg)
+        try:
+            P.pic_step(h, steps)
+            w = [e["w_perp"] for e in P.pic_energy_history(h, 4096)]
+        finally:
+            P.pic_destroy(h)
+        t = np.arange(1, len(w) + 1) * every * alpha
+        rates[scheme] = P.pic_fit_growth_rate(t, w)[0]
+    assert np.allclose(P.pic_compute_correction_coeffs(1, alpha)[0], [1, 0, 0, 0, 0])
+    assert rates[0] > 0.01, rates
+    assert rates[1] < 0.4 * rates[0], rates
+
+
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_cubic_shapes_suppress_uniformly(scheme):
     # Sec. 3's setting: cubic shapes on a 128x128 periodic mesh, gamma = 130, the filter of Eq. 6 (one

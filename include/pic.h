@@ -24,8 +24,13 @@
  *   - The handle owns all device memory it allocates. Caller arrays are only read or written
  *     during the call (device-side copies are ordered on the handle's stream) and never kept.
  *   - pic_step and the state copies are asynchronous on the handle's stream. Errors raised by
- *     kernels (bin overflow, a wait that timed out) are sticky and reported by the next
+ *     kernels (a non-finite particle, an invalid import) are sticky and reported by the next
  *     pic_sync, pic_energy or pic_get_state.
+ *   - Particle bins never lose a particle: a particle whose cell bin is full waits in a spill
+ *     list of the handle, which every step pushes from (the same gather, push, move and deposit),
+ *     and the next synchronising call (or the next pic_step, once the previous one has finished)
+ *     re-bins every particle into larger bins. A run whose beam bunches (the instability this
+ *     library studies) therefore completes at any initial bin capacity.
  *   - A handle is not thread safe; different handles are independent.
  */
 #ifndef PIC_GB300_H
@@ -43,7 +48,7 @@ extern "C" {
 #define PIC_E_CUDA (-5)       /* a CUDA runtime call failed */
 #define PIC_E_TIMEOUT (-6)    /* a bounded device wait gave up */
 #define PIC_E_NONFINITE (-7)  /* NaN/Inf found in the state */
-#define PIC_E_OVERFLOW (-8)   /* a cell's particle bin overflowed (raise bin_capacity) */
+#define PIC_E_OVERFLOW (-8)   /* a particle found no room in a bin, the spill or the leaver list */
 #define PIC_E_STATE (-9)      /* call not valid in the handle's current state */
 
 #define PIC_GALERKIN 0
@@ -81,7 +86,8 @@ typedef struct pic_config {
   int filter_targets;       /* PIC_FILTER_J | PIC_FILTER_GATHER */
   unsigned long long seed;  /* Philox4x32-10 key of the initial beam */
   int init_beam;            /* 1: pic_create fills the seeded beam; 0: start empty */
-  int bin_capacity;         /* particle slots per cell per species, up to 2^24; 0: automatic */
+  int bin_capacity;         /* initial particle slots per cell per species, up to 2^24;
+                               0: automatic (2 ppc_per_species + 8); bins grow as cells fill */
   int track_ids;            /* 1: carry a 32-bit id per particle (for tests) */
   int diag_every;           /* > 0: record the energies on the device every diag_every steps */
   int diag_capacity;        /* ring size of the energy history; 0: 4096 samples */
@@ -176,6 +182,13 @@ int pic_energy(pic_handle* h, pic_energy_t* out);
 /* Current number of particles (synchronises). */
 int pic_num_particles(pic_handle* h, long long* np);
 
+/* Particle storage: *cap = the current slots per cell and species of the bins (the initial
+ * bin_capacity rounded up to 64 bytes, larger after the bins have grown); *spilled = the particle
+ * insertions since pic_create that found their bin full and went to the spill list (each such
+ * particle was still pushed every step). Either pointer may be NULL; reading *spilled
+ * synchronises. No counterpart in the paper: storage bookkeeping. */
+int pic_bin_stats(pic_handle* h, int* cap, long long* spilled);
+
 /* Copies the state out (s->np in: capacity of the particle arrays; PIC_E_ARG when too small,
  * with s->np set to the count needed). With every particle pointer NULL only the non-NULL fields
  * are copied and s->np returns the particle count. Particles come out grouped by species, then by
@@ -228,7 +241,8 @@ int pic_energy_history(pic_handle* h, pic_energy_t* out, int max, int* count);
 #define PIC_K_DIAG 4    /* energy reductions */
 #define PIC_K_OTHER 5   /* initialisation, import, export */
 #define PIC_K_MIGRATE 6 /* insertion of the particles that left their tile into their new bins */
-#define PIC_NKERNEL 7
+#define PIC_K_SPILL 7   /* push of the particles waiting in the spill list (their bin was full) */
+#define PIC_NKERNEL 8
 
 /* on = 1: bracket every later kernel launch with CUDA events on the handle's stream and reset the
  * totals; on = 0: stop. */

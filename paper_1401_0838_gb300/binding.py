@@ -33,9 +33,9 @@ EXPORTS = ("pic_config_default", "pic_compute_correction_coeffs", "pic_create", 
            "pic_batch_create", "pic_batch_size", "pic_batch_run", "pic_batch_set_correction_stencil",
            "pic_batch_set_stream", "pic_batch_step", "pic_batch_sync", "pic_batch_energy_history",
            "pic_batch_autotune", "pic_batch_destroy", "pic_batch_last_error", "pic_adjoint_forward",
-           "pic_adjoint_backward", "pic_adjoint_release", "pic_charge_residual")
-PIC_NKERNEL = 7
-KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate")
+           "pic_adjoint_backward", "pic_adjoint_release", "pic_charge_residual", "pic_bin_stats")
+PIC_NKERNEL = 8
+KERNEL_CLASSES = ("copies", "push", "filter", "yee", "diag", "other", "migrate", "spill")
 
 
 class pic_config(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         L.pic_sync.argtypes = [V]
         L.pic_energy.argtypes = [V, P(pic_energy_t)]
         L.pic_num_particles.argtypes = [V, P(ctypes.c_longlong)]
+        L.pic_bin_stats.argtypes = [V, P(I), P(ctypes.c_longlong)]
         L.pic_get_state.argtypes = [V, P(pic_state)]
         L.pic_set_state.argtypes = [V, P(pic_state)]
         L.pic_debug_gather_copies.argtypes = [V, I, P(V)]
@@ -223,6 +224,14 @@ def pic_num_particles(h) -> int:
     n = ctypes.c_longlong()
     _check(lib().pic_num_particles(h, ctypes.byref(n)), h)
     return n.value
+
+
+def pic_bin_stats(h) -> tuple[int, int]:
+    """(slots per cell and species of the bins, which grow as cells fill; insertions since creation
+    that found their bin full and went to the spill list). Synchronises."""
+    cap, spilled = ctypes.c_int(), ctypes.c_longlong()
+    _check(lib().pic_bin_stats(h, ctypes.byref(cap), ctypes.byref(spilled)), h)
+    return cap.value, spilled.value
 
 
 def _itemsize(a) -> int:

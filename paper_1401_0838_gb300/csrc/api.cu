@@ -38,6 +38,17 @@ struct pic_handle {
   void* lv[10] = {};        // leaver list: key, ox, oy, oz, dux, duy, duz, w, id
   int* d_lv_count = nullptr;  // two counters, one per step parity
   long long lv_cap = 0;
+  // spill list (particles whose bin was full; same layout as the leaver list), two counters by
+  // parity: [p] = waiting for the next step of parity p
+  void* sp[10] = {};
+  int* d_sp_count = nullptr;
+  long long sp_cap = 0;
+  int* d_maxc = nullptr;        // scratch of the bin growth (largest count)
+  unsigned long long* d_sp_total = nullptr;  // insertions that found their bin full, since creation
+  int* h_sp_mirror = nullptr;   // pinned copy of the waiting count, written after each pic_step
+  cudaEvent_t ev_sp = nullptr;  // completion of that copy
+  bool sp_pending = false;
+  int grow_gen = 0;             // reallocations of bins or lists (batched runs re-upload their tables)
   double* d_acc = nullptr;  // 8 doubles of reduction scratch
   double* d_red = nullptr;  // block partials of the field-energy reduction
   double* d_red_yee = nullptr;  // block partials of the energies recorded by the Yee launch
@@ -164,7 +175,8 @@ struct NvtxRange {
   NvtxRange(const NvtxRange&) = delete;
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
-const char* const kKernelClassName[PIC_NKERNEL] = {"copies", "push", "filter", "yee", "diag", "other", "migrate"};
+const char* const kKernelClassName[PIC_NKERNEL] = {"copies", "push", "filter", "yee", "diag", "other", "migrate",
+                                                   "spill"};
 
 // Launch one kernel of class `cls`, counted, and bracketed by events when timing is on.
 template <class F>
@@ -195,6 +207,41 @@ void* dalloc(pic_handle* h, size_t bytes) {
   }
   h->allocs.push_back(p);
   return p;
+}
+
+// Free one allocation of the handle's list.
+void dfree(pic_handle* h, void*& p) {
+  if (!p) return;
+  cudaFree(p);
+  for (auto& q : h->allocs)
+    if (q == p) q = nullptr;
+  p = nullptr;
+}
+
+// Leaver and spill lists with room for n particles each (every particle of the run fits, so a
+// step can hand all of them on, and nothing is dropped however many bins are full).
+int alloc_lists(pic_handle* h, long long n) {
+  const pic_config& c = h->cfg;
+  long long want = (long long)h->ncell * h->cap / 4;
+  if (want < n) want = n;
+  if (want < 65536) want = 65536;
+  if (want <= h->lv_cap && want <= h->sp_cap) return PIC_OK;
+  for (int a = 0; a < 9; ++a) {
+    dfree(h, h->lv[a]);
+    dfree(h, h->sp[a]);
+  }
+  h->lv_cap = h->sp_cap = 0;
+  for (int a = 0; a < 9; ++a) {
+    if (a == 2 && c.ndim == 2) continue;
+    if (a == 7 && !h->has_w) continue;
+    if (a == 8 && !h->has_id) continue;
+    const size_t bytes = (size_t)want * (a == 0 || a == 8 ? 4 : h->es);
+    if (!(h->lv[a] = dalloc(h, bytes)) || !(h->sp[a] = dalloc(h, bytes)))
+      return fail(h, PIC_E_OOM, "leaver / spill list allocation failed");
+  }
+  h->lv_cap = h->sp_cap = want;
+  h->grow_gen++;  // new list addresses: batched runs re-upload their tables
+  return PIC_OK;
 }
 
 void lattice_dims(int ndim, int ppc, int out[3]) {
@@ -300,6 +347,19 @@ RunDev<T> make_run(pic_handle* h, int parity) {
   r.lv_count = h->d_lv_count + parity;
   r.lv_other = h->d_lv_count + (1 - parity);
   r.lv_cap = h->lv_cap;
+  r.sp.key = (int*)h->sp[0];
+  r.sp.ox = (T*)h->sp[1];
+  r.sp.oy = (T*)h->sp[2];
+  r.sp.oz = (T*)h->sp[3];
+  r.sp.dux = (T*)h->sp[4];
+  r.sp.duy = (T*)h->sp[5];
+  r.sp.duz = (T*)h->sp[6];
+  r.sp.w = (T*)h->sp[7];
+  r.sp.id = (unsigned*)h->sp[8];
+  r.sp_in = h->d_sp_count + parity;
+  r.sp_out = h->d_sp_count + (1 - parity);
+  r.sp_cap = h->sp_cap;
+  r.sp_total = h->d_sp_total;
   r.err = h->d_err;
   r.kin = nullptr;
   return r;
@@ -412,6 +472,11 @@ int step_once(pic_handle* h) {
     CK(launch(h, PIC_K_PUSH, [&] { return launch_push<T>(r, 2 * h->cfg.ppc_per_species, st); }), "push");
   else
     CK(launch(h, PIC_K_PUSH, [&] { return launch_push_ho<T>(r, h->cfg.shape_order, h->cfg.scheme, st); }), "push");
+  // particles waiting in the spill list (their bin was full): pushed one per thread, handed to the
+  // leaver list
+  CK(launch(h, PIC_K_SPILL,
+            [&] { return launch_push_spill<T>(r, h->cfg.shape_order, h->cfg.scheme, st); }),
+     "spill push");
   CK(launch(h, PIC_K_MIGRATE, [&] { return launch_migrate<T>(r, h->d_lv_count + (1 - h->parity), st); }),
      "migrate");
   // 6. current filter
@@ -519,12 +584,19 @@ int set_state_t(pic_handle* h, const pic_state* s) {
   const long long n = s->np;
   if (n == -1) return PIC_OK;  // fields only: particles untouched
   if (n < 0) return fail(h, PIC_E_ARG, "negative particle count");
-  // particles: clear bins and leaver counters, stage, bin
+  // particles: clear bins, leaver and spill counters, stage, bin
   for (int sp = 0; sp < 2; ++sp)
     for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
   CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "clear leaver counters");
+  CK(cudaMemsetAsync(h->d_sp_count, 0, 2 * sizeof(int), st), "clear spill counters");
   h->parity = 0;
+  h->sp_pending = false;
   if (n == 0) return PIC_OK;
+  if (n > h->sp_cap) {  // room for every particle in the leaver and spill lists
+    CK(cudaStreamSynchronize(st), "synchronize");
+    int rc = alloc_lists(h, n);
+    if (rc) return rc;
+  }
   if (!s->cell || !s->species || !s->ox || !s->oz || !s->dux || !s->duy || !s->duz ||
       (h->cfg.ndim == 3 && !s->oy))
     return fail(h, PIC_E_ARG, "missing particle array");
@@ -549,8 +621,8 @@ int set_state_t(pic_handle* h, const pic_state* s) {
   return PIC_OK;
 }
 
-template <typename T>
-int count_particles(pic_handle* h, long long out[2]) {
+// Particles per species in the bins of the current buffers (the spill list not included).
+int count_bins(pic_handle* h, long long out[2]) {
   for (int s = 0; s < 2; ++s) {
     CK(launch_count_prefix(h->cnt[s][h->parity], h->ncell, h->cap, h->d_offs, h->d_bsum, h->d_total + s, h->stream),
        "count prefix");
@@ -560,8 +632,104 @@ int count_particles(pic_handle* h, long long out[2]) {
   return PIC_OK;
 }
 
+// Empty the spill list into larger bins. Particles whose bin was full wait in the spill list (the
+// step pushes them from there, so nothing is lost); here, at a synchronising call, every particle
+// (bins and list) is exported to the staging arrays, the bins of both buffers are reallocated with
+// a capacity a quarter above the fullest cell (and at least half again the old one), and the
+// particles are imported back into the current buffers. The step parity is kept. A failed
+// allocation keeps the old bins (and the list, which the step still pushes) and reports PIC_E_OOM.
+template <typename T>
+int settle(pic_handle* h) {
+  cudaStream_t st = h->stream;
+  int waiting = 0;
+  CK(cudaMemcpyAsync(&waiting, h->d_sp_count + h->parity, sizeof(int), cudaMemcpyDeviceToHost, st),
+     "read spill count");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  h->sp_pending = false;
+  if (waiting <= 0) return PIC_OK;
+  const long long nsp = waiting < h->sp_cap ? waiting : h->sp_cap;
+  // the fullest cell: the counts keep every insertion, the spilled ones included
+  CK(cudaMemsetAsync(h->d_maxc, 0, sizeof(int), st), "clear max count");
+  CK(launch(h, PIC_K_OTHER,
+            [&] { return launch_max_count(h->cnt[0][h->parity], h->cnt[1][h->parity], h->ncell, h->d_maxc, st); }),
+     "max count");
+  int maxc = 0;
+  CK(cudaMemcpyAsync(&maxc, h->d_maxc, sizeof(int), cudaMemcpyDeviceToHost, st), "read max count");
+  long long cnts[2];
+  int rc = count_bins(h, cnts);  // synchronises
+  if (rc) return rc;
+  const int align = (int)(64 / h->es);
+  long long nc = (long long)maxc + maxc / 4 + 8;
+  if (nc < (long long)h->cap + h->cap / 2) nc = (long long)h->cap + h->cap / 2;
+  nc = (nc + align - 1) / align * align;
+  if (nc > (1 << 24)) return fail(h, PIC_E_OOM, "a cell holds more particles than a bin can (2^24)");
+  // every particle into the staging arrays: bins by species, then the list
+  const long long n = cnts[0] + cnts[1] + nsp;
+  rc = ensure_stage(h, n);
+  if (rc) return rc;
+  FlatDev<T> f = stage_view<T>(h, n);
+  if (h->cfg.ndim != 3) f.oy = nullptr;
+  if (!h->has_w) f.w = nullptr;
+  if (!h->has_id) f.id = nullptr;
+  RunDev<T> r = make_run<T>(h, h->parity);
+  long long base = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    CK(launch_count_prefix(h->cnt[sp][h->parity], h->ncell, h->cap, h->d_offs, h->d_bsum, h->d_total, st),
+       "count prefix");
+    CK(launch(h, PIC_K_OTHER, [&] { return launch_export<T>(r, sp, h->d_offs, base, f, st); }), "export");
+    base += cnts[sp];
+  }
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_spill_export<T>(r, nsp, base, f, st); }), "spill export");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  // new bins for both buffers and species; the old ones are freed only once all are in place
+  const pic_config& c = h->cfg;
+  const size_t slots = (size_t)h->ncell * (size_t)nc;
+  void* np_[2][2][8] = {};
+  bool ok = true;
+  for (int sp = 0; sp < 2 && ok; ++sp)
+    for (int b = 0; b < 2 && ok; ++b)
+      for (int a = 0; a < 8 && ok; ++a) {
+        if (!h->parr[sp][b][a]) continue;  // arrays the run does not carry
+        ok = (np_[sp][b][a] = dalloc(h, slots * (a == 7 ? 4 : h->es))) != nullptr;
+      }
+  if (!ok) {
+    for (int sp = 0; sp < 2; ++sp)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 8; ++a) dfree(h, np_[sp][b][a]);
+    return fail(h, PIC_E_OOM, "particle bin growth: allocation failed");
+  }
+  for (int sp = 0; sp < 2; ++sp)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 8; ++a)
+        if (h->parr[sp][b][a]) {
+          dfree(h, h->parr[sp][b][a]);
+          h->parr[sp][b][a] = np_[sp][b][a];
+        }
+  (void)c;
+  h->cap = (int)nc;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
+  CK(cudaMemsetAsync(h->d_sp_count, 0, 2 * sizeof(int), st), "clear spill counters");
+  CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "clear leaver counters");
+  RunDev<T> r2 = make_run<T>(h, h->parity);
+  CK(launch(h, PIC_K_OTHER, [&] { return launch_import<T>(r2, f, st); }), "re-bin");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  drop_graph(h);
+  h->grow_gen++;
+  return PIC_OK;
+}
+
+template <typename T>
+int count_particles(pic_handle* h, long long out[2]) {
+  int rc = settle<T>(h);
+  if (rc) return rc;
+  return count_bins(h, out);
+}
+
 template <typename T>
 int charge_residual_t(pic_handle* h, double out[3]) {
+  int rc0 = settle<T>(h);
+  if (rc0) return rc0;
   cudaStream_t st = h->stream;
   const pic_config& c = h->cfg;
   if (!h->d_rho) {
@@ -606,6 +774,8 @@ int charge_residual_t(pic_handle* h, double out[3]) {
 template <typename T>
 int get_state_t(pic_handle* h, pic_state* s) {
   int rc = check_err(h);
+  if (rc) return rc;
+  rc = settle<T>(h);
   if (rc) return rc;
   cudaStream_t st = h->stream;
   const cudaMemcpyKind k = s->where == PIC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -657,6 +827,8 @@ int get_state_t(pic_handle* h, pic_state* s) {
 
 template <typename T>
 int energy_t(pic_handle* h, pic_energy_t* out) {
+  int rc0 = settle<T>(h);
+  if (rc0) return rc0;
   cudaStream_t st = h->stream;
   CK(cudaMemsetAsync(h->d_acc, 0, 8 * sizeof(double), st), "zero accumulators");
   const T* f6[6];
@@ -798,16 +970,16 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
       if (ok) ok = (h->cnt[s][b] = (int*)dalloc(h, sizeof(int) * h->ncell)) != nullptr;
     }
   if (ok) ok = (h->d_err = (int*)dalloc(h, 16)) != nullptr;
-  // leaver list: particles that leave their tile in one step
-  h->lv_cap = (long long)(2 * slots / 8);
-  if (h->lv_cap < 65536) h->lv_cap = 65536;
-  for (int a = 0; a < 9 && ok; ++a) {
-    if (a == 2 && c.ndim == 2) continue;
-    if (a == 7 && !h->has_w) continue;
-    if (a == 8 && !h->has_id) continue;
-    ok = (h->lv[a] = dalloc(h, (size_t)h->lv_cap * (a == 0 || a == 8 ? 4 : h->es))) != nullptr;
-  }
+  // leaver list (particles that leave their tile in one step) and spill list (particles whose bin
+  // was full), each with room for every particle of the seeded beam
+  if (ok) ok = alloc_lists(h, c.init_beam ? 2 * (long long)c.ppc_per_species * h->ncell : 0) == PIC_OK;
   if (ok) ok = (h->d_lv_count = (int*)dalloc(h, 2 * sizeof(int))) != nullptr;
+  if (ok) ok = (h->d_sp_count = (int*)dalloc(h, 2 * sizeof(int))) != nullptr;
+  if (ok) ok = (h->d_maxc = (int*)dalloc(h, 16)) != nullptr;
+  if (ok) ok = (h->d_sp_total = (unsigned long long*)dalloc(h, 16)) != nullptr;
+  if (ok) ok = cudaMemset(h->d_sp_total, 0, 16) == cudaSuccess;
+  if (ok) ok = cudaHostAlloc((void**)&h->h_sp_mirror, 16, cudaHostAllocDefault) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&h->ev_sp, cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
   if (ok) ok = (h->d_red = (double*)dalloc(h, field_energy_scratch_bytes())) != nullptr;
   if (ok) ok = cudaMemset(h->d_red, 0, field_energy_scratch_bytes()) == cudaSuccess;
@@ -831,6 +1003,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
     for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->cnt[s][b], 0, sizeof(int) * h->ncell, h->stream);
   cudaMemsetAsync(h->d_err, 0, 16, h->stream);
   cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), h->stream);
+  cudaMemsetAsync(h->d_sp_count, 0, 2 * sizeof(int), h->stream);
   rebuild_taps(h);
   int rc = PIC_OK;
   if (c.init_beam && c.ppc_per_species > 0)
@@ -931,11 +1104,36 @@ static int build_graph(pic_handle* h) {
   return PIC_OK;
 }
 
-extern "C" {
+// The spill list between pic_step calls: after a call, its waiting count is copied to pinned host
+// memory behind an event; the next call reads it once the event has completed (no wait) and, when
+// particles are waiting, grows the bins first. Under a caller's stream capture neither happens.
+static bool capturing(pic_handle* h) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
 
-int pic_step(pic_handle* h, int nsteps) {
-  if (!h || nsteps < 0) return PIC_E_ARG;
-  NvtxRange range("pic_step");
+static int spill_check(pic_handle* h) {
+  if (!h->sp_pending || capturing(h)) return PIC_OK;
+  const cudaError_t q = cudaEventQuery(h->ev_sp);
+  if (q == cudaErrorNotReady) {
+    (void)cudaGetLastError();
+    return PIC_OK;  // the previous call is still running: look again next time
+  }
+  h->sp_pending = false;
+  if (q != cudaSuccess) return cuda_fail(h, q, "spill count event");
+  if (*h->h_sp_mirror <= 0) return PIC_OK;
+  return h->es == 4 ? settle<float>(h) : settle<double>(h);
+}
+
+static void note_spill(pic_handle* h) {
+  if (capturing(h)) return;
+  if (cudaMemcpyAsync(h->h_sp_mirror, h->d_sp_count + h->parity, sizeof(int), cudaMemcpyDeviceToHost, h->stream) ==
+          cudaSuccess &&
+      cudaEventRecord(h->ev_sp, h->stream) == cudaSuccess)
+    h->sp_pending = true;
+}
+
+static int step_calls(pic_handle* h, int nsteps) {
   // Graph replay when at least two whole graphs fit and timing is off; single steps otherwise.
   const int de = h->cfg.diag_every > 0 ? h->cfg.diag_every : 1;
   int len = 2;
@@ -974,6 +1172,18 @@ int pic_step(pic_handle* h, int nsteps) {
   return run_steps(h, nsteps);
 }
 
+extern "C" {
+
+int pic_step(pic_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return PIC_E_ARG;
+  NvtxRange range("pic_step");
+  int rc = spill_check(h);
+  if (rc) return rc;
+  rc = step_calls(h, nsteps);
+  if (rc == PIC_OK && nsteps > 0) note_spill(h);
+  return rc;
+}
+
 int pic_sync(pic_handle* h) {
   if (!h) return PIC_E_ARG;
   return check_err(h);
@@ -991,6 +1201,18 @@ int pic_num_particles(pic_handle* h, long long* np) {
   if (rc) return rc;
   *np = c[0] + c[1];
   return check_err(h);
+}
+
+int pic_bin_stats(pic_handle* h, int* cap, long long* spilled) {
+  if (!h) return PIC_E_ARG;
+  if (cap) *cap = h->cap;
+  if (spilled) {
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_sp_total, sizeof v, cudaMemcpyDeviceToHost, h->stream), "read spill total");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    *spilled = (long long)v;
+  }
+  return PIC_OK;
 }
 
 int pic_get_state(pic_handle* h, pic_state* s) {
@@ -1110,6 +1332,8 @@ void pic_destroy(pic_handle* h) {
     cudaEventDestroy(p.b);
   }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_sp) cudaEventDestroy(h->ev_sp);
+  if (h->h_sp_mirror) cudaFreeHost(h->h_sp_mirror);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -1169,6 +1393,7 @@ struct pic_batch {
   };
   std::vector<Group> groups;
   bool tables_dirty = true;
+  std::vector<int> gens;  // each run's bin growths when its tables were uploaded
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0, graph_parity = 0;
   cudaStream_t graph_stream = nullptr;
@@ -1237,6 +1462,8 @@ int batch_tables(pic_batch* b) {
   BCK(cudaMemcpy(b->d_sep_j, sj.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "filter table");
   BCK(cudaMemcpy(b->d_yee, ya.data(), sizeof(YeeArgs<T>) * n, cudaMemcpyHostToDevice), "yee table");
   BCK(cudaMemcpy(b->d_energy, ea.data(), sizeof(EnergyArgs<T>) * n, cudaMemcpyHostToDevice), "energy table");
+  b->gens.resize(n);
+  for (int i = 0; i < n; ++i) b->gens[i] = b->runs[i]->grow_gen;
   b->tables_dirty = false;
   return PIC_OK;
 }
@@ -1254,6 +1481,7 @@ int batch_step_once(pic_batch* b) {
   for (auto& g : b->groups)
     BCK(launch_push_batch<T>(runs, g.d_items, g.nitems, g.d_queue, b->ndim, b->scheme, g.lpc, g.blocks, st),
         "batched push");
+  BCK(launch_push_spill_batch<T>(runs, n, b->ndim, b->scheme, st), "batched spill push");
   BCK(launch_migrate_batch<T>(runs, n, st), "batched migrate");
   if (b->filter_j)
     BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_j, b->d_sep_base, n, b->sep_total, 3, b->ndim, b->hzj, b->hxj,
@@ -1363,6 +1591,9 @@ int reseed(pic_handle* h) {
   for (int s = 0; s < 2; ++s)
     for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(h->cnt[s][k], 0, sizeof(int) * h->ncell, st), "reseed counts");
   CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "reseed leavers");
+  CK(cudaMemsetAsync(h->d_sp_count, 0, 2 * sizeof(int), st), "reseed spill list");
+  CK(cudaMemsetAsync(h->d_sp_total, 0, sizeof(unsigned long long), st), "reseed spill total");
+  h->sp_pending = false;
   CK(cudaMemsetAsync(h->d_hist_count, 0, 16, st), "reseed history");
   CK(cudaMemsetAsync(h->d_kin, 0, 2 * sizeof(double), st), "reseed kinetic");
   h->parity = 0;
@@ -1506,15 +1737,40 @@ int pic_batch_set_stream(pic_batch* b, void* stream) {
   return PIC_OK;
 }
 
+}  // extern "C"
+
+static int batch_steps(pic_batch* b, int nsteps);
+
+extern "C" {
+
 int pic_batch_step(pic_batch* b, int nsteps) {
   if (!b || nsteps < 0) return PIC_E_ARG;
   NvtxRange range("pic_batch_step");
   for (pic_handle* h : b->runs)
     if (h->parity != b->parity) return bfail(b, PIC_E_STATE, "a run was stepped or reset on its own");
+  // runs with particles waiting in their spill list grow their bins first (see pic_step)
+  for (pic_handle* h : b->runs) {
+    const int rc = spill_check(h);
+    if (rc) return bfail(b, rc, pic_last_error(h));
+  }
+  for (size_t i = 0; i < b->runs.size(); ++i)
+    if (i >= b->gens.size() || b->gens[i] != b->runs[i]->grow_gen) {
+      b->tables_dirty = true;
+      batch_drop_graph(b);
+    }
   if (b->tables_dirty) {
     int rc = b->es == 4 ? batch_tables<float>(b) : batch_tables<double>(b);
     if (rc) return rc;
   }
+  const int rc = batch_steps(b, nsteps);
+  if (rc == PIC_OK && nsteps > 0)
+    for (pic_handle* h : b->runs) note_spill(h);
+  return rc;
+}
+
+}  // extern "C"
+
+static int batch_steps(pic_batch* b, int nsteps) {
   const int len = batch_graph_len(b);
   if (len > 64 || nsteps < 2 * len) return batch_run_steps(b, nsteps);
   int lead = (int)((len - b->nstep % len) % len);
@@ -1539,6 +1795,8 @@ int pic_batch_step(pic_batch* b, int nsteps) {
   }
   return batch_run_steps(b, nsteps);
 }
+
+extern "C" {
 
 int pic_batch_sync(pic_batch* b) {
   if (!b) return PIC_E_ARG;
@@ -1718,6 +1976,8 @@ FlatDev<T> flat_view(const pic_handle::Flat& f, long long np) {
 // Fields and particles of the current state into (fields[6], flat) in id order.
 template <typename T>
 int adj_save(pic_handle* h, void* const* fields, const pic_handle::Flat& flat, bool check_ids) {
+  int rc0 = settle<T>(h);  // the tape reads the bins: no particle may wait in the spill list
+  if (rc0) return rc0;
   cudaStream_t st = h->stream;
   const size_t fb = (size_t)h->ncell * sizeof(T);
   for (int q = 0; q < 6; ++q)
@@ -1745,7 +2005,9 @@ int adj_restore(pic_handle* h, int j) {
   for (int sp = 0; sp < 2; ++sp)
     for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(h->cnt[sp][b], 0, sizeof(int) * h->ncell, st), "clear counts");
   CK(cudaMemsetAsync(h->d_lv_count, 0, 2 * sizeof(int), st), "clear leaver counters");
+  CK(cudaMemsetAsync(h->d_sp_count, 0, 2 * sizeof(int), st), "clear spill counters");
   h->parity = 0;
+  h->sp_pending = false;
   RunDev<T> r = make_run<T>(h, 0);
   FlatDev<T> f = flat_view<T>(A.ck_p[j], A.np);
   CK(launch(h, PIC_K_OTHER, [&] { return launch_import<T>(r, f, st); }), "restore particles");

@@ -8,7 +8,7 @@ namespace picgb {
 
 // Sticky error bits written by kernels (read by the host at pic_sync / pic_energy).
 enum : int {
-  ERR_OVERFLOW = 1,   // a particle found its destination cell bin full and was dropped
+  ERR_OVERFLOW = 1,   // a particle found its bin full and no room in the spill or leaver list: dropped
   ERR_NONFINITE = 2,  // a particle position or momentum became NaN/Inf or moved > 1 cell
   ERR_IMPORT = 4,     // an imported particle had an invalid cell or species
   ERR_TIMEOUT = 8,    // a bounded device wait gave up
@@ -30,13 +30,31 @@ struct SpeciesBuf {
 };
 
 // Particles that left their tile in a push (appended by the push kernel, inserted into their
-// destination bins by the migrate kernel). key = destination cell * 2 + species.
+// destination bins by the migrate kernel). key = destination cell * 2 + species. The same layout
+// holds the spill list: particles whose destination bin was full when they were inserted (by the
+// migrate kernel or the import); the next step pushes them from there (k_push_spill), and the
+// host moves them into larger bins at its next synchronising call.
 template <typename T>
 struct LeaverList {
   int* key;
   T *ox, *oy, *oz, *dux, *duy, *duz, *w;
   unsigned* id;
 };
+
+// Entry o of a leaver or spill list (the arrays a run does not carry are null).
+template <typename T>
+__device__ __forceinline__ void list_put(const LeaverList<T>& l, long long o, int key, T ox, T oy, T oz, T ux, T uy,
+                                         T uz, T w, unsigned id) {
+  l.key[o] = key;
+  l.ox[o] = ox;
+  if (l.oy) l.oy[o] = oy;
+  l.oz[o] = oz;
+  l.dux[o] = ux;
+  l.duy[o] = uy;
+  l.duz[o] = uz;
+  if (l.w) l.w[o] = w;
+  if (l.id) l.id[o] = id;
+}
 
 // Everything a kernel needs about one simulation (passed by value as a kernel parameter).
 template <typename T>
@@ -59,6 +77,11 @@ struct RunDev {
   int* lv_count;       // leavers appended in this step
   int* lv_other;       // the other parity's leaver counter (zeroed by this step's migrate)
   long long lv_cap;    // capacity of the leaver list
+  LeaverList<T> sp;    // spill list
+  int* sp_in;          // spilled particles waiting for this step's push (read by k_push_spill)
+  int* sp_out;         // particles spilled by this step's insertions (zeroed by k_push_spill)
+  long long sp_cap;    // capacity of the spill list
+  unsigned long long* sp_total;  // insertions that found their bin full, since creation
   int* err;
   double* kin;        // FP64 accumulators of this step: [0] sum w (gamma - 1), [1] particle count
                       // (nullptr: not recorded)

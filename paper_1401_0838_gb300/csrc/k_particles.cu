@@ -526,7 +526,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
     if (lx < wx && ly < wy && lz < wz) {
       const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
-      sn[cl] = min(sn[cl], r.cap);  // an overflow was flagged when it happened
+      sn[cl] = min(sn[cl], r.cap);  // the excess of a full bin waits in the spill list
       sn[NCL + cl] = min(sn[NCL + cl], r.cap);
       r.in[0].cnt[cell] = 0;
       r.in[1].cnt[cell] = 0;
@@ -715,6 +715,18 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         int base = 0;
         if (stay && lane == leader) base = atomicAdd(scnt + (dkey & 1) * NCL + (dkey >> 1), __popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
+        // a full destination bin: the particle goes through the global leaver list instead, and
+        // k_migrate spills it when the bin is still full there (nothing is dropped)
+        const bool full = stay && base + rank >= r.cap;
+        const unsigned fmask = __ballot_sync(0xffffffffu, full);
+        long long fglob = 0;
+        if (fmask) {
+          const int fl = __ffs(fmask) - 1;
+          int fb = 0;
+          if (lane == fl) fb = atomicAdd(r.lv_count, __popc(fmask));
+          fb = __shfl_sync(0xffffffffu, fb, fl);
+          fglob = (long long)fb + __popc(fmask & ((1u << lane) - 1u));
+        }
         // leavers: a slot in the tile's shared-memory buffer (one shared atomic per warp), or, once
         // the buffer is full, straight in the global list
         const unsigned lmask = __ballot_sync(0xffffffffu, valid && leave);
@@ -737,10 +749,10 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         }
         if (stay) {
           const int j = base + rank;
-          if (j < r.cap) {
-            const int dl = dkey >> 1;
-            const int dx = dl % TX, dy = (dl / TX) % TY, dz = dl / (TX * TY);
-            const int dcell = ((Z0 + dz) * r.ny + Y0 + dy) * r.nx + X0 + dx;  // cells < 2^30
+          const int dl = dkey >> 1;
+          const int dx = dl % TX, dy = (dl / TX) % TY, dz = dl / (TX * TY);
+          const int dcell = ((Z0 + dz) * r.ny + Y0 + dy) * r.nx + X0 + dx;  // cells < 2^30
+          if (!full) {
             const long long o = (long long)dcell * r.cap + j;
             pout.ox[o] = nox;
             if (NDIM == 3) pout.oy[o] = noy;
@@ -750,6 +762,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
             pout.duz[o] = uz;
             if (has_w) pout.w[o] = w;
             if (has_id) pout.id[o] = st_id[jj];
+          } else if (fglob < r.lv_cap) {
+            list_put(r.lv, fglob, dcell * 2 + (dkey & 1), nox, noy, noz, ux, uy, uz, w, has_id ? st_id[jj] : 0u);
           } else {
             flag_error(r.err, ERR_OVERFLOW);
           }
@@ -834,13 +848,14 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     }
   }
 
-  // 5. output counts of the tile's cells (leavers from other tiles are added by k_migrate)
+  // 5. output counts of the tile's cells (leavers from other tiles are added by k_migrate); a count
+  // past the capacity (particles sent on through the leaver list) is stored as the capacity
   for (int cl = tid; cl < NCL; cl += PUSH_THREADS) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
     if (lx < wx && ly < wy && lz < wz) {
       const long long cell = (long long)(Z0 + lz) * nxy + (long long)(Y0 + ly) * r.nx + X0 + lx;
-      r.out[0].cnt[cell] = scnt[cl];
-      r.out[1].cnt[cell] = scnt[NCL + cl];
+      r.out[0].cnt[cell] = min(scnt[cl], r.cap);
+      r.out[1].cnt[cell] = min(scnt[NCL + cl], r.cap);
     }
   }
 
@@ -1064,12 +1079,28 @@ __device__ __forceinline__ void migrate_body(const RunDev<T>& r, int* other_coun
     int j0 = 0;
     if (valid && lane == leader) j0 = atomicAdd(b.cnt + cell, __popc(peers));
     j0 = __shfl_sync(0xffffffffu, j0, leader);
+    // a full bin: the particle goes to the spill list, which the next step pushes from (the count
+    // keeps the excess, so the host sees how large the bin has to grow)
+    const bool full = valid && j0 + rank >= r.cap;
+    const unsigned fmask = __ballot_sync(0xffffffffu, full);
+    long long so = 0;
+    if (fmask) {
+      const int fl = __ffs(fmask) - 1;
+      int sb = 0;
+      if (lane == fl) {
+        sb = atomicAdd(r.sp_out, __popc(fmask));
+        atomicAdd(r.sp_total, (unsigned long long)__popc(fmask));
+      }
+      sb = __shfl_sync(0xffffffffu, sb, fl);
+      so = (long long)sb + __popc(fmask & ((1u << lane) - 1u));
+    }
     if (!valid) continue;
-    const int j = j0 + rank;
-    if (j >= r.cap) {
-      flag_error(r.err, ERR_OVERFLOW);
+    if (full) {
+      if (so < r.sp_cap) list_put(r.sp, so, key, ox, oy, oz, ux, uy, uz, w, id);
+      else flag_error(r.err, ERR_OVERFLOW);
       continue;
     }
+    const int j = j0 + rank;
     const long long o = cell * r.cap + j;
     b.ox[o] = ox;
     if (r.ndim == 3) b.oy[o] = oy;
@@ -1112,14 +1143,20 @@ template cudaError_t launch_migrate<float>(const RunDev<float>&, int*, cudaStrea
 template cudaError_t launch_migrate<double>(const RunDev<double>&, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
-// Insert one particle into its cell bin (used by init and import).
+// Insert one particle of species s into its cell bin of the input buffers (used by init and
+// import); a full bin puts it in the spill list that the next step pushes from.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void insert_particle(const SpeciesBuf<T>& b, int cap, long long cell, T ox, T oy, T oz,
-                                                T ux, T uy, T uz, T w, unsigned id, int* err) {
+__device__ __forceinline__ void insert_particle(const RunDev<T>& r, int s, long long cell, T ox, T oy, T oz, T ux,
+                                                T uy, T uz, T w, unsigned id) {
+  const SpeciesBuf<T>& b = s ? r.in[1] : r.in[0];
+  const int cap = r.cap;
   int j = atomicAdd(b.cnt + cell, 1);
   if (j >= cap) {
-    flag_error(err, ERR_OVERFLOW);
+    const long long o = atomicAdd(r.sp_in, 1);
+    atomicAdd(r.sp_total, 1ull);
+    if (o < r.sp_cap) list_put(r.sp, o, (int)(cell * 2 + s), ox, oy, oz, ux, uy, uz, w, id);
+    else flag_error(r.err, ERR_OVERFLOW);
     return;
   }
   long long o = cell * cap + j;
@@ -1200,8 +1237,7 @@ __global__ void k_init_beam(const __grid_constant__ RunDev<T> r, BeamDev b, long
     T ux = (T)(b.u_th * ra * cos(ta));
     T uy = (T)(b.u_th * ra * sin(ta));
     T uz = (T)(b.u_th * rb * cos(tb));
-    insert_particle(s ? r.in[1] : r.in[0], r.cap, dcell, tox, toy, toz, ux, uy, uz, (T)w, (unsigned)(p * 2 + s),
-                    r.err);
+    insert_particle(r, s, dcell, tox, toy, toz, ux, uy, uz, (T)w, (unsigned)(p * 2 + s));
   }
 }
 
@@ -1258,7 +1294,7 @@ __global__ void k_import(const __grid_constant__ RunDev<T> r, const __grid_const
   long long dcell = (long long)k * nxy + (long long)j * r.nx + i;
   T w = f.w ? f.w[p] : r.wconst;
   unsigned id = f.id ? f.id[p] : (unsigned)p;
-  insert_particle(s ? r.in[1] : r.in[0], r.cap, dcell, ox, oy, oz, f.dux[p], f.duy[p], f.duz[p], w, id, r.err);
+  insert_particle(r, s, dcell, ox, oy, oz, f.dux[p], f.duy[p], f.duz[p], w, id);
 }
 
 template <typename T>
@@ -1313,6 +1349,56 @@ template cudaError_t launch_export<float>(const RunDev<float>&, int, const long 
                                           cudaStream_t);
 template cudaError_t launch_export<double>(const RunDev<double>&, int, const long long*, long long,
                                            const FlatDev<double>&, cudaStream_t);
+
+// Spill list entries [0, n) -> flat arrays at [base, base + n) (cell and species from the key).
+template <typename T>
+__global__ void k_spill_export(const __grid_constant__ RunDev<T> r, long long n, long long base,
+                               const __grid_constant__ FlatDev<T> f) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n || base + i >= f.np) return;
+  const long long d = base + i;
+  const int key = r.sp.key[i];
+  f.cell[d] = key >> 1;
+  f.species[d] = key & 1;
+  f.ox[d] = r.sp.ox[i];
+  if (f.oy) f.oy[d] = r.ndim == 3 ? r.sp.oy[i] : T(0);
+  f.oz[d] = r.sp.oz[i];
+  f.dux[d] = r.sp.dux[i];
+  f.duy[d] = r.sp.duy[i];
+  f.duz[d] = r.sp.duz[i];
+  if (f.w) f.w[d] = r.sp.w ? r.sp.w[i] : r.wconst;
+  if (f.id) f.id[d] = r.sp.id ? r.sp.id[i] : 0u;
+}
+
+template <typename T>
+cudaError_t launch_spill_export(const RunDev<T>& r, long long n, long long base, const FlatDev<T>& f,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_spill_export<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r, n, base, f);
+  return cudaGetLastError();
+}
+template cudaError_t launch_spill_export<float>(const RunDev<float>&, long long, long long, const FlatDev<float>&,
+                                                cudaStream_t);
+template cudaError_t launch_spill_export<double>(const RunDev<double>&, long long, long long,
+                                                 const FlatDev<double>&, cudaStream_t);
+
+// Largest insertion count over the cells of two count arrays (counts keep every insertion, the
+// spilled ones too) into *out, which the caller zeroes.
+__global__ void k_max_count(const int* __restrict__ c0, const int* __restrict__ c1, long long ncell, int* out) {
+  int m = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+    m = max(m, max(c0[c], c1[c]));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+cudaError_t launch_max_count(const int* c0, const int* c1, long long ncell, int* out, cudaStream_t st) {
+  if (ncell <= 0) return cudaSuccess;
+  long long blocks = (ncell + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_max_count<<<(unsigned)blocks, 256, 0, st>>>(c0, c1, ncell, out);
+  return cudaGetLastError();
+}
 
 // Exclusive prefix of min(cnt, cap) over cells (two-level, block sums then scan), into offs.
 __global__ void k_count_blocks(const int* __restrict__ cnt, long long ncell, int cap, long long* bsum) {

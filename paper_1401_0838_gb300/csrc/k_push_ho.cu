@@ -236,7 +236,7 @@ __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef&
   }
   cp_async_commit();
   cp_async_wait_all();
-  // 2. counts clamped (an overflow was flagged when it happened) and the input counts zeroed (they
+  // 2. counts clamped (the excess of a full bin is in the spill list) and the input counts zeroed (they
   // become the next step's output counts); each thread reads back only the counts it copied
   for (int cl = tid; cl < NCL; cl += HO_THREADS) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
@@ -282,13 +282,14 @@ __device__ __forceinline__ void ho_epilogue(const RunDev<T>& r, const HoTileRef&
   const int tid = threadIdx.x;
   const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
   __syncthreads();
-  // 4. output counts of the tile's cells
+  // 4. output counts of the tile's cells (a count past the capacity, whose excess went on through
+  // the leaver list, is stored as the capacity)
   for (int cl = tid; cl < NCL; cl += HO_THREADS) {
     const int lx = cl % TX, ly = (cl / TX) % TY, lz = cl / (TX * TY);
     if (lx < wx && ly < wy && lz < wz) {
       const int cell = (Z0 + lz) * nxy + (Y0 + ly) * r.nx + X0 + lx;
-      r.out[0].cnt[cell] = scnt[cl];
-      r.out[1].cnt[cell] = scnt[NCL + cl];
+      r.out[0].cnt[cell] = min(scnt[cl], r.cap);
+      r.out[1].cnt[cell] = min(scnt[NCL + cl], r.cap);
     }
   }
   // 5. the tile's current into global memory
@@ -503,8 +504,8 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
         if (nlx >= 0 && nlx < wx && nly >= 0 && nly < wy && nlz >= 0 && nlz < wz) {
           const int ncl = (nlz * TY + nly) * TX + nlx;
           const int jj = atomicAdd(scnt + s * NCL + ncl, 1);
+          const int dcell = ((Z0 + nlz) * r.ny + Y0 + nly) * r.nx + X0 + nlx;
           if (jj < r.cap) {
-            const int dcell = ((Z0 + nlz) * r.ny + Y0 + nly) * r.nx + X0 + nlx;
             const long long o = (long long)dcell * r.cap + jj;
             pout.ox[o] = nox;
             if (NDIM == 3) pout.oy[o] = noy;
@@ -514,8 +515,10 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
             pout.duz[o] = uz;
             if (has_w) pout.w[o] = w;
             if (has_id) pout.id[o] = id;
-          } else {
-            flag_error(r.err, ERR_OVERFLOW);
+          } else {  // bin full: on through the leaver list (k_migrate spills it if still full)
+            const long long o = atomicAdd(r.lv_count, 1);
+            if (o < r.lv_cap) list_put(r.lv, o, dcell * 2 + s, nox, noy, noz, ux, uy, uz, w, id);
+            else flag_error(r.err, ERR_OVERFLOW);
           }
         } else {  // to another tile: the leaver list (inserted by k_migrate)
           const int ni = wrap_any(gi + shx, r.nx), nj = NDIM == 3 ? wrap_any(gj + shy, r.ny) : 0;
@@ -712,7 +715,10 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
       int slot_base = 0;
       if (stay && lane == leader) slot_base = atomicAdd(scnt + s * NCL + (dkey >> 1), __popc(peers));
       slot_base = __shfl_sync(0xffffffffu, slot_base, leader);
-      const unsigned lmask = __ballot_sync(0xffffffffu, leave);
+      // a full destination bin sends the particle on through the leaver list too (k_migrate spills
+      // it if the bin is still full there)
+      const bool full = stay && slot_base + rank >= r.cap;
+      const unsigned lmask = __ballot_sync(0xffffffffu, leave || full);
       int lbase = 0;
       if (lmask) {
         const int ll = __ffs(lmask) - 1;
@@ -722,8 +728,8 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
       if (stay) {
         const SpeciesBuf<T>& pout = s ? r.out[1] : r.out[0];
         const int jj = slot_base + rank;
-        if (jj < r.cap) {
-          const int dcell = (Z0 + nlz) * r.nx + X0 + nlx;
+        const int dcell = (Z0 + nlz) * r.nx + X0 + nlx;
+        if (!full) {
           const long long o = (long long)dcell * r.cap + jj;
           pout.ox[o] = nox;
           pout.oz[o] = noz;
@@ -733,7 +739,9 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
           if (has_w) pout.w[o] = w;
           if (has_id) pout.id[o] = id;
         } else {
-          flag_error(r.err, ERR_OVERFLOW);
+          const long long o = lbase + __popc(lmask & ((1u << lane) - 1u));
+          if (o < r.lv_cap) list_put(r.lv, o, dcell * 2 + s, nox, T(0), noz, ux, uy, uz, w, id);
+          else flag_error(r.err, ERR_OVERFLOW);
         }
       } else if (leave) {
         const long long o = lbase + __popc(lmask & ((1u << lane) - 1u));
@@ -754,6 +762,254 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
     }
   }
   ho_epilogue<T, 2, ORDER>(r, tr, sj, scnt, kin, npush);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spilled particles: those whose destination bin was full when they were inserted wait in the
+// spill list. One thread per spilled particle runs the step of the tile kernels on it (the same
+// gather rule, Boris push, move and Esirkepov deposit), with the field copies read from global
+// memory and the current added by global atomics, and hands it to the leaver list, from which
+// k_migrate inserts it (or spills it again while its bin is still full). Nothing is dropped; the
+// host grows the bins at its next synchronising call, so the list stays short.
+// ---------------------------------------------------------------------------------------------
+
+// Field copy at integer node (x, y, z) of the periodic grid, for a component with staggers
+// (sx, sy, sz); for the momentum-conserving gather the average from the component's Yee location to
+// the node, formed in the order of the tile prologue (x, then y, then z; upper neighbour first).
+template <typename T, int NDIM>
+__device__ __noinline__ T node_value(const T* g, const RunDev<T>& r, int scheme, int sx, int sy, int sz, int x, int y,
+                                     int z) {
+  const long long nxy = (long long)r.nx * r.ny;
+  auto at = [&](int a, int b, int c) -> T {
+    return g[(long long)wrap_any(c, r.nz) * nxy + (long long)(NDIM == 3 ? wrap_any(b, r.ny) : 0) * r.nx +
+             wrap_any(a, r.nx)];
+  };
+  if (scheme != 2) return at(x, y, z);
+  if (NDIM == 2) sy = 0;
+  T v[2][2];  // [z offset][y offset], x already averaged
+#pragma unroll 1
+  for (int dz = 0; dz <= sz; ++dz)
+#pragma unroll 1
+    for (int dy = 0; dy <= sy; ++dy)
+      v[dz][dy] = sx ? T(0.5) * (at(x, y - dy, z - dz) + at(x - 1, y - dy, z - dz)) : at(x, y - dy, z - dz);
+  if (sy) {
+    v[0][0] = T(0.5) * (v[0][0] + v[0][1]);
+    if (sz) v[1][0] = T(0.5) * (v[1][0] + v[1][1]);
+  }
+  return sz ? T(0.5) * (v[0][0] + v[1][0]) : v[0][0];
+}
+
+// Component c of the gather at offsets (ox, oy, oz) in cell (gi, gj, gk), from global memory (the
+// weights and node rule of gather_comp, with the order and scheme given at run time).
+template <typename T, int NDIM>
+__device__ __noinline__ T gather_global(const T* g, const RunDev<T>& r, int order, int scheme, int c, int gi, int gj,
+                                       int gk, T ox, T oy, T oz) {
+  const int stx = stag_ho(c, 0), sty = stag_ho(c, 1), stz = stag_ho(c, 2);
+  const int SX = scheme == 2 ? 0 : stx, SY = scheme == 2 ? 0 : sty, SZ = scheme == 2 ? 0 : stz;
+  const int OX = scheme == 0 ? order - SX : order, OZ = scheme == 0 ? order - SZ : order;
+  const int OY = NDIM == 3 ? (scheme == 0 ? order - SY : order) : 0;
+  int fx, fy = 0, fz;
+  T wx[4], wy[4] = {T(1), T(0), T(0), T(0)}, wz[4];
+  gweights(ox, SX, OX, fx, wx);
+  if (NDIM == 3) gweights(oy, SY, OY, fy, wy);
+  gweights(oz, SZ, OZ, fz, wz);
+  T acc = T(0);
+#pragma unroll 1
+  for (int c3 = 0; c3 <= OZ; ++c3) {
+#pragma unroll 1
+    for (int c2 = 0; c2 <= OY; ++c2) {
+      T row = T(0);
+#pragma unroll 1
+      for (int c1 = 0; c1 <= OX; ++c1)
+        row += wx[c1] * node_value<T, NDIM>(g, r, scheme, stx, sty, stz, gi + fx + c1, gj + fy + c2, gk + fz + c3);
+      acc += wz[c3] * wy[c2] * row;
+    }
+  }
+  return acc;
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void push_spill_body(const RunDev<T>& r, int order, int scheme, int bid, int nblk) {
+  constexpr int NWMAX = 6;
+  const int NW = order == 3 ? 6 : 4, K0 = order == 3 ? -2 : -1;  // deposit window (as HoGeom)
+  const int tid = threadIdx.x;
+  if (bid == 0 && tid == 0) *r.sp_out = 0;  // this step's k_migrate spills into a fresh list
+  const long long n = min((long long)*r.sp_in, r.sp_cap);
+  if (n == 0) return;
+  const long long nxy = (long long)r.nx * r.ny;
+  T kin = T(0);
+  int npush = 0;
+  for (long long i = (long long)bid * blockDim.x + tid; i < n; i += (long long)nblk * blockDim.x) {
+    const int key = r.sp.key[i];
+    const int s = key & 1;
+    const int cell = key >> 1;  // cells < 2^30
+    const int gi = cell % r.nx, gj = (cell / r.nx) % r.ny, gk = (int)(cell / nxy);
+    const T ox = r.sp.ox[i], oy = NDIM == 3 ? r.sp.oy[i] : T(0), oz = r.sp.oz[i];
+    T ux = r.sp.dux[i], uy = r.sp.duy[i], uz = r.sp.duz[i];
+    const T w = r.sp.w ? r.sp.w[i] : r.wconst;
+    const unsigned id = r.sp.id ? r.sp.id[i] : 0u;
+    const T qs = s ? T(1) : T(-1);
+    T F[6];
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c) F[c] = gather_global<T, NDIM>(r.g[c], r, order, scheme, c, gi, gj, gk, ox, oy, oz);
+    // relativistic Boris, momenta relative to the drift u0 z_hat
+    const T h = qs * r.hq;
+    const T mx = ux + h * F[0], my = uy + h * F[1], mz = uz + h * F[2];
+    const T Mz = r.u0 + mz;
+    const T ig = T(1) / sqrt(T(1) + mx * mx + my * my + Mz * Mz);
+    const T tx = h * F[3] * ig, ty = h * F[4] * ig, tz = h * F[5] * ig;
+    const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+    const T sx = sf * tx, sy = sf * ty, sz = sf * tz;
+    const T qx = mx + (my * tz - Mz * ty);
+    const T qy = my + (Mz * tx - mx * tz);
+    const T qz = Mz + (mx * ty - my * tx);
+    ux = mx + (qy * sz - qz * sy) + h * F[0];
+    uy = my + (qz * sx - qx * sz) + h * F[1];
+    uz = mz + (qx * sy - qy * sx) + h * F[2];
+    const T Uz = r.u0 + uz;
+    const T u2 = ux * ux + uy * uy + Uz * Uz;
+    const T gam = sqrt(T(1) + u2);
+    const T ign = T(1) / gam;
+    kin += w * u2 / (gam + T(1));
+    ++npush;
+    T ddx = r.dtdx * ux * ign, ddy = NDIM == 3 ? r.dtdy * uy * ign : T(0), ddz = r.dtdz * Uz * ign;
+    T vy = uy * ign;
+    if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
+      flag_error(r.err, ERR_NONFINITE);
+      ddx = ddy = ddz = T(0);
+      ux = uy = uz = T(0);
+      vy = T(0);  // nothing non-finite reaches the current
+    }
+    // Esirkepov on the window nodes K0 .. K0 + NW - 1 of the start cell, straight into J
+    T S0x[NWMAX], dSx[NWMAX], dSy[NWMAX], dSz[NWMAX], Tx[NWMAX], Ty[NWMAX], Tz[NWMAX];
+    int xs[NWMAX], ys[NWMAX], zs[NWMAX];  // periodic indices of the window nodes
+#pragma unroll 1
+    for (int a = 0; a < NW; ++a) {
+      const T node = T(K0 + a);
+      S0x[a] = bspl(order, node - ox);
+      dSx[a] = shape_change(order, node - ox, ddx);
+      Tx[a] = S0x[a] + T(0.5) * dSx[a];
+      const T s0z = bspl(order, node - oz);
+      dSz[a] = shape_change(order, node - oz, ddz);
+      Tz[a] = s0z + T(0.5) * dSz[a];
+      if (NDIM == 3) {
+        const T s0y = bspl(order, node - oy);
+        dSy[a] = shape_change(order, node - oy, ddy);
+        Ty[a] = s0y + T(0.5) * dSy[a];
+      } else {
+        dSy[a] = T(0);
+        Ty[a] = T(0);
+      }
+      xs[a] = wrap_any(gi + K0 + a, r.nx);
+      ys[a] = NDIM == 3 ? wrap_any(gj + K0 + a, r.ny) : 0;
+      zs[a] = wrap_any(gk + K0 + a, r.nz);
+    }
+    const T qw = qs * w;
+    T* const J0 = r.j[0];
+    T* const J1 = r.j[1];
+    T* const J2 = r.j[2];
+    auto idx = [&](int x, int y, int z) -> long long { return (long long)z * nxy + (long long)y * r.nx + x; };
+    if (NDIM == 2) {
+      const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
+#pragma unroll 1
+      for (int b = 0; b < NW; ++b) {  // Jx(a + 1/2, b): running sum over the x window
+        T acc = T(0);
+#pragma unroll 1
+        for (int a = 0; a < NW - 1; ++a) {
+          acc += dSx[a];
+          const T v = cx * acc * Tz[b];
+          if (v != T(0)) atomicAdd(J0 + idx(xs[a], 0, zs[b]), v);
+        }
+      }
+#pragma unroll 1
+      for (int a = 0; a < NW; ++a) {  // Jz(a, b + 1/2): running sum over the z window
+        T acc = T(0);
+#pragma unroll 1
+        for (int b = 0; b < NW - 1; ++b) {
+          acc += dSz[b];
+          const T v = cz * acc * Tx[a];
+          if (v != T(0)) atomicAdd(J2 + idx(xs[a], 0, zs[b]), v);
+        }
+      }
+#pragma unroll 1
+      for (int b = 0; b < NW; ++b)  // Jy(a, b): out-of-plane weight Tx Tz + dSx dSz / 12
+#pragma unroll 1
+        for (int a = 0; a < NW; ++a) {
+          const T v = cy * (Tx[a] * Tz[b] + dSx[a] * dSz[b] * T(1.0 / 12.0));
+          if (v != T(0)) atomicAdd(J1 + idx(xs[a], 0, zs[b]), v);
+        }
+    } else {
+      const T cxq = qw * r.jfx, cyq = qw * r.jfy, czq = qw * r.jfz;
+#pragma unroll 1
+      for (int t2 = 0; t2 < NW; ++t2)
+#pragma unroll 1
+        for (int t1 = 0; t1 < NW; ++t1) {
+          const T wx_ = Ty[t1] * Tz[t2] + dSy[t1] * dSz[t2] * T(1.0 / 12.0);  // Jx: (y, z) = (t1, t2)
+          const T wy_ = Tx[t1] * Tz[t2] + dSx[t1] * dSz[t2] * T(1.0 / 12.0);  // Jy: (x, z) = (t1, t2)
+          const T wz_ = Tx[t1] * Ty[t2] + dSx[t1] * dSy[t2] * T(1.0 / 12.0);  // Jz: (x, y) = (t1, t2)
+          T ax_ = T(0), ay_ = T(0), az_ = T(0);
+#pragma unroll 1
+          for (int a = 0; a < NW - 1; ++a) {
+            ax_ += dSx[a];
+            ay_ += dSy[a];
+            az_ += dSz[a];
+            const T vx = cxq * ax_ * wx_, vyv = cyq * ay_ * wy_, vz = czq * az_ * wz_;
+            if (vx != T(0)) atomicAdd(J0 + idx(xs[a], ys[t1], zs[t2]), vx);
+            if (vyv != T(0)) atomicAdd(J1 + idx(xs[t1], ys[a], zs[t2]), vyv);
+            if (vz != T(0)) atomicAdd(J2 + idx(xs[t1], ys[t2], zs[a]), vz);
+          }
+        }
+    }
+    // new cell and offsets, then on to k_migrate through the leaver list
+    auto fold = [](T o, T d, int& sh) -> T {
+      const T t = o + d;
+      sh = t < T(0) ? -1 : (t >= T(1) ? 1 : 0);
+      T no = t - T(sh);
+      if (no >= T(1)) {  // rounding of t - sh
+        no = T(0);
+        sh += 1;
+      }
+      if (no < T(0)) no = T(0);
+      return no;
+    };
+    int shx, shy = 0, shz;
+    const T nox = fold(ox, ddx, shx);
+    const T noy = NDIM == 3 ? fold(oy, ddy, shy) : T(0);
+    const T noz = fold(oz, ddz, shz);
+    const int ni = wrap_any(gi + shx, r.nx), nj = NDIM == 3 ? wrap_any(gj + shy, r.ny) : 0;
+    const int nk = wrap_any(gk + shz, r.nz);
+    const long long o = atomicAdd(r.lv_count, 1);
+    if (o < r.lv_cap) list_put(r.lv, o, ((nk * r.ny + nj) * r.nx + ni) * 2 + s, nox, noy, noz, ux, uy, uz, w, id);
+    else flag_error(r.err, ERR_OVERFLOW);
+  }
+  // kinetic energy and particle count of the step (FP64, one atomic per warp)
+  if (r.kin) {
+    double kd = (double)kin;
+    int nd = npush;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kd += __shfl_xor_sync(0xffffffffu, kd, o);
+      nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    if ((tid & 31) == 0 && nd > 0) {
+      atomicAdd(r.kin, kd);
+      atomicAdd(r.kin + 1, (double)nd);
+    }
+  }
+}
+
+constexpr int SPILL_THREADS = 256;
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(SPILL_THREADS) k_push_spill(const __grid_constant__ RunDev<T> r, int order,
+                                                              int scheme) {
+  push_spill_body<T, NDIM>(r, order, scheme, blockIdx.x, gridDim.x);
+}
+
+// Many runs: run blockIdx.y (the batched step covers linear shapes).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(SPILL_THREADS) k_push_spill_batch(const RunDev<T>* __restrict__ runs, int scheme) {
+  push_spill_body<T, NDIM>(runs[blockIdx.y], 1, scheme, blockIdx.x, gridDim.x);
 }
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
@@ -789,5 +1045,27 @@ cudaError_t launch_push_ho(const RunDev<T>& r, int order, int scheme, cudaStream
 }
 template cudaError_t launch_push_ho<float>(const RunDev<float>&, int, int, cudaStream_t);
 template cudaError_t launch_push_ho<double>(const RunDev<double>&, int, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_push_spill(const RunDev<T>& r, int order, int scheme, cudaStream_t st) {
+  // a fixed grid (the count is on the device): every block exits at once when the list is empty
+  constexpr int blocks = 152;
+  if (r.ndim == 2) k_push_spill<T, 2><<<blocks, SPILL_THREADS, 0, st>>>(r, order, scheme);
+  else k_push_spill<T, 3><<<blocks, SPILL_THREADS, 0, st>>>(r, order, scheme);
+  return cudaGetLastError();
+}
+template cudaError_t launch_push_spill<float>(const RunDev<float>&, int, int, cudaStream_t);
+template cudaError_t launch_push_spill<double>(const RunDev<double>&, int, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_push_spill_batch(const RunDev<T>* runs, int nruns, int ndim, int scheme, cudaStream_t st) {
+  if (nruns <= 0) return cudaSuccess;
+  const dim3 grid(152 / (nruns < 8 ? 1 : nruns / 8) + 1, (unsigned)nruns);
+  if (ndim == 2) k_push_spill_batch<T, 2><<<grid, SPILL_THREADS, 0, st>>>(runs, scheme);
+  else k_push_spill_batch<T, 3><<<grid, SPILL_THREADS, 0, st>>>(runs, scheme);
+  return cudaGetLastError();
+}
+template cudaError_t launch_push_spill_batch<float>(const RunDev<float>*, int, int, int, cudaStream_t);
+template cudaError_t launch_push_spill_batch<double>(const RunDev<double>*, int, int, int, cudaStream_t);
 
 }  // namespace picgb

@@ -69,6 +69,19 @@ cudaError_t launch_init_beam(const RunDev<T>& r, int ppc, const int lat[3], doub
                              double u_th, double sigma_perp, unsigned long long seed, cudaStream_t st);
 template <typename T>
 cudaError_t launch_import(const RunDev<T>& r, const FlatDev<T>& f, cudaStream_t st);
+// Spilled particles (full bins): the step of the tile kernels, one thread per spilled particle
+// (k_push_ho.cu); zeroes *r.sp_out for this step's k_migrate. Batched: one run per blockIdx.y,
+// linear shapes, Galerkin or Uniform.
+template <typename T>
+cudaError_t launch_push_spill(const RunDev<T>& r, int order, int scheme, cudaStream_t st);
+template <typename T>
+cudaError_t launch_push_spill_batch(const RunDev<T>* runs, int nruns, int ndim, int scheme, cudaStream_t st);
+// spill list entries [0, n) into flat arrays at [base, base + n)
+template <typename T>
+cudaError_t launch_spill_export(const RunDev<T>& r, long long n, long long base, const FlatDev<T>& f,
+                                cudaStream_t st);
+// *out = max(*out, max over cells of c0, c1)
+cudaError_t launch_max_count(const int* c0, const int* c1, long long ncell, int* out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_export(const RunDev<T>& r, int s, const long long* offs, long long base, const FlatDev<T>& f,
                           cudaStream_t st);

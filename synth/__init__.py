@@ -48,6 +48,27 @@ def random_particles(ndim: int, nx: int, ny: int, nz: int, n: int, seed: int, ga
     return p
 
 
+def clustered_particles(ndim: int, nx: int, ny: int, nz: int, n: int, seed: int, corner=(0, 0, 0), size: int = 2,
+                        gamma: float = 130.0, spread: float = 0.05, weight: float = 0.01) -> dict:
+    """n particles uniformly in the block of size^ndim cells whose lowest corner is the cell `corner`
+    (x, y, z), with momenta (N, N, u0 + N) * spread and random charges +-1: far more particles per cell
+    than a uniform load, for the full-bin paths of the particle storage."""
+    rng = np.random.default_rng(seed)
+    u0 = math.sqrt(gamma * gamma - 1.0)
+    x0, y0, z0 = corner
+    return {
+        "x": (x0 + rng.uniform(0, size, n)) % nx,
+        "y": ((y0 + rng.uniform(0, size, n)) % ny) if ndim == 3 else np.zeros(n),
+        "z": (z0 + rng.uniform(0, size, n)) % nz,
+        "ux": rng.normal(0, spread, n),
+        "uy": rng.normal(0, spread, n),
+        "uz": u0 + rng.normal(0, spread, n),
+        "w": weight * np.ones(n),
+        "q": rng.choice([-1.0, 1.0], n),
+        "id": np.arange(n, dtype=np.int64),
+    }
+
+
 def edge_particles(ndim: int, nx: int, ny: int, nz: int, gamma: float = 130.0) -> dict:
     """Hand-placed particles on the awkward spots: exactly on cell faces and nodes, next to the periodic
     wrap on both sides, at the last representable offset below a face, moving backwards."""

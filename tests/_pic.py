@@ -91,13 +91,16 @@ def from_native(cfg, nat: dict, u0: float, w_const: float | None = None) -> dict
 class Pair:
     """The same simulation in the oracle (FP64) and in a CUDA handle."""
 
-    def __init__(self, cfg, psi=None, fields=None, part=None):
+    def __init__(self, cfg, psi=None, fields=None, part=None, handle=None):
+        """handle: an existing handle (a run of a batch) whose correction stencil the caller has set;
+        it is not destroyed by close()."""
         self.cfg = cfg
         self.T = dtype_of(cfg)
         self.u0 = math.sqrt(cfg.gamma ** 2 - 1.0)
         pe, pb = psi if psi is not None else (None, None)
-        self.h = P.pic_create(cfg)
-        if pe is not None:
+        self.owns = handle is None
+        self.h = P.pic_create(cfg) if handle is None else handle
+        if pe is not None and self.owns:
             P.pic_set_correction_stencil(self.h, pe, pb)
         self.o = oracle_for(cfg, pe, pb)
         shape = self.o.shape
@@ -123,7 +126,8 @@ class Pair:
         self.npart = 0 if part is None else len(part["x"])
 
     def close(self):
-        P.pic_destroy(self.h)
+        if self.owns:
+            P.pic_destroy(self.h)
         self.h = None
 
     def step(self, n=1):

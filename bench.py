@@ -35,9 +35,12 @@ NX, NZ, PPC, ALPHA, GAMMA = 512, 1024, 16, 0.5, 130.0
 FILTER = dict(filter_nbin=2, filter_ncomp=1, filter_comp_alpha=2.0)
 WORKLOAD = ("2D x-z 512x1024 periodic beam, 16 particles/cell/species (16.8M particles), gamma=130, "
             "c dt/dz=0.5, Galerkin gather, Psi correction + 3-pass binomial/compensation filter, FP32")
-# algorithmic bytes of the fused particle kernel (2D): per particle 2 offsets + 3 momenta read and
-# written (cell index implicit in the per-cell bins); per cell 6 field copies read, 3 currents written
-PUSH_BYTES_PER_PARTICLE = {4: 40, 8: 80}
+# algorithmic bytes of the fused particle kernel (2D), per particle-step: the cell index, 2 offsets and
+# 3 momenta read and written (48 B in FP32, 88 B in FP64); the storage keeps the cell index implicit
+# in the per-cell bins, so what the layout must move is 40 B (80 B). Per cell: 6 field copies read,
+# 3 currents written.
+PUSH_BYTES_PER_PARTICLE = {4: 48, 8: 88}
+PUSH_LAYOUT_BYTES_PER_PARTICLE = {4: 40, 8: 80}
 PUSH_BYTES_PER_CELL = {4: 36, 8: 72}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -130,16 +133,35 @@ class ClockSampler:
         reader.start()
         reader.join(timeout=10.0)
 
-    def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
+    def sample(self) -> str:
+        """One synchronous sample (a CSV line), or "" when nvidia-smi is unavailable."""
         try:
-            out, _ = self.proc.communicate(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-            out, _ = self.proc.communicate()
-        return parse_clock_samples(out)
+            r = subprocess.run(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-i",
+                                str(self.gpu)], capture_output=True, text=True, timeout=20)
+            return r.stdout.strip()
+        except (OSError, subprocess.TimeoutExpired):
+            return ""
+
+    def stop(self, before: str = "", after: str = "") -> dict:
+        """Samples of the stream, plus the synchronous `before` / `after` samples taken right around
+        the timed region (a short region may hold no stream sample at all)."""
+        if self.proc is None:
+            out = ""
+        else:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+        res = parse_clock_samples("\n".join(x for x in (before, out, after) if x))
+        inside = parse_clock_samples(out)
+        res["samples_inside"] = inside["samples"]
+        res["sm_mhz_before"] = parse_clock_samples(before)["sm_mhz"]
+        res["sm_mhz_after"] = parse_clock_samples(after)["sm_mhz"]
+        if res["sm_mhz"] is None:
+            res["reasons"] = res["reasons"] + ["nvidia-smi unavailable"]
+        return res
 
 
 def parse_clock_samples(text: str) -> dict:
@@ -240,15 +262,37 @@ def timed_steps(P, torch, h, stream, steps: int, device):
     return ms, kt, launches
 
 
-def roofline(kt: dict, np_: int, ncell: int, es: int, peak: float, peak_kind: str, traffic=None) -> dict:
+def push_time_in_step(kt: dict, step_ms: float):
+    """The push kernel's time inside the graph-replayed step: the step's time less the event-timed
+    times of every other kernel of a step (gaps between launches count against the push)."""
     ms, cnt = kt["push"]
-    per_launch_s = ms / 1e3 / max(cnt, 1)
+    if not cnt or step_ms is None:
+        return None
+    others = sum(v[0] for k, v in kt.items() if k != "push") / cnt  # one push per step in the timed pass
+    t = step_ms - others
+    return t if t > 0 else None
+
+
+def roofline(kt: dict, np_: int, ncell: int, es: int, peak: float, peak_kind: str, traffic=None,
+             step_ms=None) -> dict:
+    ms, cnt = kt["push"]
+    ev_s = ms / 1e3 / max(cnt, 1)
+    in_step = push_time_in_step(kt, step_ms)
+    per_launch_s = in_step / 1e3 if in_step else ev_s
     bytes_per_launch = np_ * PUSH_BYTES_PER_PARTICLE[es] + ncell * PUSH_BYTES_PER_CELL[es]
+    layout_bytes = np_ * PUSH_LAYOUT_BYTES_PER_PARTICLE[es] + ncell * PUSH_BYTES_PER_CELL[es]
     achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    achieved_layout = layout_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     return {"kernel": "k_push (fused gather + Boris + move + Esirkepov + rebin)", "bound": "hbm",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "launch_ms": round(per_launch_s * 1e3, 4)}
+            "bytes_basis": f"{PUSH_BYTES_PER_PARTICLE[es]} B/particle (cell index + offsets + momenta, each way) + "
+                           f"{PUSH_BYTES_PER_CELL[es]} B/cell (6 field copies read, 3 currents written)",
+            "frac_layout_bytes": round(achieved_layout / peak, 4),
+            "layout_bytes_per_launch": layout_bytes,
+            "launch_ms": round(per_launch_s * 1e3, 4), "launch_ms_events": round(ev_s * 1e3, 4),
+            "time_basis": ("graph-replayed step time less the event-timed other kernels of a step" if in_step
+                           else "event-bracketed launches")}
 
 
 def e2e_measure(P, torch, h, cfg, stream, steps: int):
@@ -426,9 +470,10 @@ def run_ours(args):
             P.pic_step(h, 1)
     P.pic_sync(h)
     clocks = ClockSampler(local)
+    before = clocks.sample()
     clocks.start()
     ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
-    clk = clocks.stop()
+    clk = clocks.stop(before, clocks.sample())
     hist = P.pic_energy_history(h, 1)
     assert hist and hist[-1]["np"] == np_, "particle count changed"
     agg = aggregate(ms, np_, args.steps, device)
@@ -436,7 +481,7 @@ def run_ours(args):
     launches_all = int(reduce_sum(launches, device))
     traffic = args.traffic if args.traffic is not None else (
         profiled_traffic() if args.order == 1 and args.scheme == "galerkin" else None)
-    rf = roofline(kt, np_, ncell, 4, peak, peak_kind, traffic=traffic)
+    rf = roofline(kt, np_, ncell, 4, peak, peak_kind, traffic=traffic, step_ms=ms / args.steps)
     kernel_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]}
 
     e2e = None
@@ -457,7 +502,7 @@ def run_ours(args):
         ms64, kt64, _ = timed_steps(P, torch, h64, stream, args.fp64_steps, device)
         a64 = aggregate(ms64, np_, args.fp64_steps, device)
         fp64 = {"value": a64["value"], "unit": UNIT, "ms_per_step": a64["ms"] / args.fp64_steps,
-                "roofline": roofline(kt64, np_, ncell, 8, peak, peak_kind)}
+                "roofline": roofline(kt64, np_, ncell, 8, peak, peak_kind, step_ms=ms64 / args.fp64_steps)}
         P.pic_destroy(h64)
 
     line = {"metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -466,6 +511,12 @@ def run_ours(args):
             "config": config_dict(ws, args.order, args.scheme, args.solver, args.correction), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
             "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
             "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the other workloads, each measured here so that every one has a record from the same run
+        line["config1"] = measure_config1(P, torch, 200, 5)
+        line["config3d"] = measure_3d(P, torch, 10, 3, peak, peak_kind)
+        line["sweep"] = measure_sweep(P, torch, 64, 20, 10)
+        line["adjoint"] = measure_adjoint(P, torch, 100, 1, fd=True)
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps, args.cpu_threads)
     if rank == 0:
@@ -495,14 +546,12 @@ def sweep_configs(P, nruns=64, seed=4):
     return out
 
 
-def run_sweep(args):
+def measure_sweep(P, torch, nruns: int, steps: int, seq_steps: int, autotune: bool = True) -> dict:
+    """The batched sweep (one persistent push launch per lanes-per-cell group per step, replayed from a
+    CUDA graph) against the same runs stepped one after another with plain per-step launches."""
     import numpy as np
-    import torch
-
-    import paper_1401_0838_gb300 as P
-    torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    runs = sweep_configs(P, args.sweep_runs)
+    runs = sweep_configs(P, nruns)
     cfgs = [c for c, _ in runs]
     particles = sum(c.nx * c.nz * c.ppc_per_species * 2 for c in cfgs)
     b = P.pic_batch_create(cfgs)
@@ -517,13 +566,13 @@ def run_sweep(args):
                 skipped += 1
                 continue
             P.pic_batch_set_correction_stencil(b, i, *coeffs)
-    lpcs = P.pic_batch_autotune(b, trial_steps=2)
+    lpcs = P.pic_batch_autotune(b, trial_steps=2) if autotune else None
     P.pic_batch_step(b, 10)  # warm-up (includes the graph capture)
     P.pic_batch_sync(b)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    P.pic_batch_step(b, args.steps)
+    P.pic_batch_step(b, steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1)
@@ -538,7 +587,6 @@ def run_sweep(args):
             rates.append(float("nan"))
     P.pic_batch_destroy(b)
     # the same runs one after another, each with plain per-step launches
-    seq_steps = max(2, min(args.steps, args.sweep_seq_steps))
     handles = []
     for c, corr in runs:
         h = P.pic_create(c)
@@ -557,35 +605,46 @@ def run_sweep(args):
     ms_s = e0.elapsed_time(e1)
     for h in handles:
         P.pic_destroy(h)
-    vb = particles * args.steps / (ms_b / 1e3)
+    vb = particles * steps / (ms_b / 1e3)
     vs = particles * seq_steps / (ms_s / 1e3)
-    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 10,
-            "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched sweep: {len(runs)} independent 2D runs, grids 64-256 x 128-1024 "
-                                   "(seeded mix), 4-16 particles/cell/species, c dt/dz U[0.1,0.7), gamma in "
-                                   "{10,50,130}, correction on/off, FP32, one persistent push launch per "
-                                   "lanes-per-cell group per step, CUDA graph", "runs": len(runs),
-                       "particles": particles},
+    finite = [r for r in rates if r == r]
+    return {"value": vb, "unit": UNIT, "steps": steps, "ms_per_step": ms_b / steps, "runs": len(runs),
+            "particles": particles,
+            "workload": f"batched sweep: {len(runs)} independent 2D runs, grids 64-256 x 128-1024 (seeded mix), "
+                        "4-16 particles/cell/species, c dt/dz U[0.1,0.7), gamma in {10,50,130}, correction on/off, "
+                        "FP32, one persistent push launch per lanes-per-cell group per step, CUDA graph",
             "sequential": {"value": vs, "unit": UNIT, "steps": seq_steps, "ms_per_step": ms_s / seq_steps,
                            "how": "each run alone, pic_step(1) per step (plain launches), runs one after another"},
             "speedup_vs_sequential": vb / vs, "autotune_lanes_per_cell": lpcs,
             "corrections_skipped_in_breakdown_windows": skipped,
-            "growth_rates": {"min": float(np.nanmin(rates)), "median": float(np.nanmedian(rates)),
-                             "max": float(np.nanmax(rates))}}
-    print(json.dumps(line), flush=True)
+            "growth_rates": {"min": float(min(finite)), "median": float(np.median(finite)),
+                             "max": float(max(finite))} if finite else None}
 
 
-def run_adjoint(args):
-    """Adjoint of the 2D step on 256 x 512, 8 particles/cell/species, gamma 130, 100 steps with a
-    checkpoint every 10: the time of the forward run with checkpoints and of the backward pass
-    against the plain forward run, and the Psi_E gradient against central differences (h = 1e-3)."""
-    import numpy as np
+def run_sweep(args):
     import torch
 
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
-    nsteps, every, alpha = args.adjoint_steps, 10, 0.5
+    m = measure_sweep(P, torch, args.sweep_runs, args.steps, max(2, min(args.steps, args.sweep_seq_steps)))
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 10,
+            "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "runs": m["runs"], "particles": m["particles"]},
+            "sequential": m["sequential"], "speedup_vs_sequential": m["speedup_vs_sequential"],
+            "autotune_lanes_per_cell": m["autotune_lanes_per_cell"],
+            "corrections_skipped_in_breakdown_windows": m["corrections_skipped_in_breakdown_windows"],
+            "growth_rates": m["growth_rates"]}
+    print(json.dumps(line), flush=True)
+
+
+def measure_adjoint(P, torch, nsteps: int = 100, reps: int = 1, fd: bool = True) -> dict:
+    """Adjoint of the 2D step on 256 x 512, 8 particles/cell/species, gamma 130, `nsteps` steps with a
+    checkpoint every 10: the time of the forward run with checkpoints and of the backward pass
+    against the plain forward run, and the Psi_E gradient against central differences (h = 1e-3) of
+    the FP64 forward run."""
+    import numpy as np
+    every, alpha = 10, 0.5
     pe, pb = P.pic_compute_correction_coeffs(P.PIC_GALERKIN, alpha)
 
     def cfg(prec):
@@ -611,8 +670,8 @@ def run_adjoint(args):
 
     res = {}
     for prec, name in ((P.PIC_FP32, "f32"), (P.PIC_FP64, "f64")):
-        reps = []
-        for _ in range(max(1, args.adjoint_reps)):
+        rs = []
+        for _ in range(max(1, reps)):
             h = P.pic_create(cfg(prec))
             P.pic_set_correction_stencil(h, pe, pb)
             P.pic_sync(h)  # the library's stream is synchronised by every call that returns data
@@ -624,49 +683,61 @@ def run_adjoint(args):
             P.pic_sync(h)
             _, t_p = timed(lambda: (P.pic_step(h, nsteps), P.pic_sync(h)))
             P.pic_destroy(h)
-            reps.append((t_f, t_b, t_p))
-        t_f, t_b, t_p = (float(np.median([r[i] for r in reps])) for i in range(3))
+            rs.append((t_f, t_b, t_p))
+        t_f, t_b, t_p = (float(np.median([r[i] for r in rs])) for i in range(3))
         res[name] = {"w_perp": w, "grad_psi_e": ge.tolist(), "grad_psi_b": gb.tolist(), "ms_forward_checkpointed": t_f,
                      "ms_backward": t_b, "ms_plain_forward": t_p, "adjoint_over_forward": (t_f + t_b) / t_p}
-    fd = None
-    if not args.no_fd:
-        fd = []
+    fdv = None
+    if fd:
+        fdv = []
         for n in range(5):
             d = np.zeros(5)
             d[n] = 1e-3
-            fd.append((w_after(P.PIC_FP64, pe + d) - w_after(P.PIC_FP64, pe - d)) / 2e-3)
-        fd = np.array(fd)
+            fdv.append((w_after(P.PIC_FP64, pe + d) - w_after(P.PIC_FP64, pe - d)) / 2e-3)
+        fdv = np.array(fdv)
         for name in ("f32", "f64"):
             ge = np.array(res[name]["grad_psi_e"])
-            res[name]["max_rel_err_vs_central_differences"] = float(np.abs(ge - fd).max() / np.abs(fd).max())
+            res[name]["max_rel_err_vs_central_differences"] = float(np.abs(ge - fdv).max() / np.abs(fdv).max())
     np_ = 256 * 512 * 8 * 2
     r32 = res["f32"]
-    value = np_ * nsteps / ((r32["ms_forward_checkpointed"] + r32["ms_backward"]) / 1e3)
-    line = {"metric": "particle-steps/s through forward + adjoint (gradient of W_perp(T))", "value": value,
-            "unit": "particle-steps/s", "n_gpus": 1, "steps": nsteps, "warmup": 0,
-            "ms_per_step": (r32["ms_forward_checkpointed"] + r32["ms_backward"]) / nsteps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "adjoint: 2D 256x512, 8 particles/cell/species (2,097,152 particles), gamma 130, "
-                                   f"c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), {nsteps} steps, checkpoint "
-                                   "every 10; gradient of W_perp(T) w.r.t. Psi_E, Psi_B and E0/B0",
-                       "central_differences": None if fd is None else
-                       {"h": 1e-3, "forward": "FP64 library run", "grad_psi_e": fd.tolist()}},
+    return {"value": np_ * nsteps / ((r32["ms_forward_checkpointed"] + r32["ms_backward"]) / 1e3),
+            "unit": "particle-steps/s through forward + adjoint", "steps": nsteps, "particles": np_,
+            "workload": "adjoint: 2D 256x512, 8 particles/cell/species (2,097,152 particles), gamma 130, c dt/dz "
+                        f"0.5, Galerkin, correction + filter (1,1,a=3), {nsteps} steps, checkpoint every 10; "
+                        "gradient of W_perp(T) w.r.t. Psi_E, Psi_B and E0/B0",
+            "central_differences": None if fdv is None else
+            {"h": 1e-3, "forward": "FP64 library run", "grad_psi_e": fdv.tolist()},
             "f32": r32, "f64": res["f64"]}
-    print(json.dumps(line), flush=True)
 
 
-def run_3d(args):
-    """The 3D workload: 128 x 128 x 512, 8 particles/cell/species (134,217,728 particles), transverse
-    Gaussian weights (sigma 20 cells), gamma 130, c dt/dz 0.5, Galerkin, correction + filter
-    (1, 1, a = 3), FP32. Same timing as the default line; roofline with the 3D bytes per particle."""
+def run_adjoint(args):
     import torch
 
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
-    device = torch.device("cuda", 0)
+    m = measure_adjoint(P, torch, args.adjoint_steps, args.adjoint_reps, fd=not args.no_fd)
+    r32 = m["f32"]
+    line = {"metric": "particle-steps/s through forward + adjoint (gradient of W_perp(T))", "value": m["value"],
+            "unit": "particle-steps/s", "n_gpus": 1, "steps": m["steps"], "warmup": 0,
+            "ms_per_step": (r32["ms_forward_checkpointed"] + r32["ms_backward"]) / m["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "central_differences": m["central_differences"]},
+            "f32": r32, "f64": m["f64"]}
+    print(json.dumps(line), flush=True)
+
+
+# 3D bytes per particle-step: cell index, 3 offsets, 3 momenta and the weight, each way (survey's 64 B);
+# the per-cell bins keep the cell index implicit (56 B)
+PUSH3D_BYTES_PER_PARTICLE, PUSH3D_LAYOUT_BYTES_PER_PARTICLE = 64, 56
+
+
+def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, nz: int = 512) -> dict:
+    """The 3D workload: 128 x 128 x 512, 8 particles/cell/species (134,217,728 particles), transverse
+    Gaussian weights (sigma 20 cells), gamma 130, c dt/dz 0.5, Galerkin, correction + filter
+    (1, 1, a = 3), FP32. Same timing as the default line; roofline with the 3D bytes per particle."""
+    device = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
-    peak, peak_kind = measured_hbm_peak()
-    cfg = P.pic_config_default(ndim=3, nx=128, ny=128, nz=512, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN,
+    cfg = P.pic_config_default(ndim=3, nx=128, ny=128, nz=nz, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN,
                                precision=P.PIC_FP32, ppc_per_species=8, sigma_perp=20.0, seed=3, init_beam=1,
                                diag_every=1)
     h = P.pic_create(cfg)
@@ -675,47 +746,60 @@ def run_3d(args):
     ncell = cfg.nx * cfg.ny * cfg.nz
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             P.pic_step(h, 1)
     P.pic_sync(h)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(device.index)
+    before = clocks.sample()
     clocks.start()
-    ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
-    clk = clocks.stop()
+    ms, kt, launches = timed_steps(P, torch, h, stream, steps, device)
+    clk = clocks.stop(before, clocks.sample())
     hist = P.pic_energy_history(h, 1)
     assert hist and hist[-1]["np"] == np_, "particle count changed"
     P.pic_destroy(h)
-    push_ms, push_n = kt["push"]
-    per_launch_s = push_ms / 1e3 / max(push_n, 1)
-    bytes_per_launch = np_ * 56 + ncell * 36  # 3 offsets + 3 momenta + weight each way; gather + J
+    ev_s = kt["push"][0] / 1e3 / max(kt["push"][1], 1)
+    in_step = push_time_in_step(kt, ms / steps)
+    per_launch_s = in_step / 1e3 if in_step else ev_s
+    bytes_per_launch = np_ * PUSH3D_BYTES_PER_PARTICLE + ncell * 36
+    layout_bytes = np_ * PUSH3D_LAYOUT_BYTES_PER_PARTICLE + ncell * 36
     achieved = bytes_per_launch / per_launch_s / 1e9
-    line = {"metric": METRIC, "value": np_ * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "3D 128x128x512, 8 particles/cell/species (134M particles), Gaussian transverse "
-                                   "weights sigma 20 cells, gamma 130, c dt/dz 0.5, Galerkin, correction + filter "
-                                   "(1,1,a=3), FP32", "particles": np_},
+    return {"value": np_ * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "particles": np_,
+            "workload": f"3D 128x128x{nz}, 8 particles/cell/species ({np_} particles), Gaussian transverse weights "
+                        "sigma 20 cells, gamma 130, c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), FP32",
             "roofline": {"kernel": "k_push", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                         "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": round(per_launch_s * 1e3, 4)},
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "frac_layout_bytes": round(layout_bytes / per_launch_s / 1e9 / peak, 4),
+                         "launch_ms": round(per_launch_s * 1e3, 4), "launch_ms_events": round(ev_s * 1e3, 4)},
             "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
-            "cell_updates_per_s": ncell * args.steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+            "cell_updates_per_s": ncell * steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+
+
+def run_3d(args):
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    peak, peak_kind = measured_hbm_peak()
+    m = measure_3d(P, torch, args.steps, args.warmup, peak, peak_kind, nz=args.config3d_nz)
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "particles": m["particles"]}, "roofline": m["roofline"],
+            "kernel_ms_per_launch": m["kernel_ms_per_launch"], "cell_updates_per_s": m["cell_updates_per_s"],
+            "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_3d(args.cpu_steps_3d, args.cpu_threads)
     print(json.dumps(line), flush=True)
 
 
-def run_config1(args):
+def measure_config1(P, torch, steps: int, warmup: int) -> dict:
     """The small 2D workload: 64 x 128, 4 particles/cell/species (65,536 particles), gamma 130,
     c dt/dz 0.5, Galerkin, correction + filter (1, 1, a = 3), FP64, energies every step, the steps
-    replayed from the step graph. Its 7 MB stay in L2, so it is bound by launch latency: the line
-    reports microseconds and launches per step, not an HBM roofline. The oracle runs the whole
-    workload for comparison."""
-    import torch
-
-    import paper_1401_0838_gb300 as P
-    torch.cuda.set_device(0)
-    device = torch.device("cuda", 0)
+    replayed from the step graph. Its 7 MB stay in L2, so it is bound by launch latency: microseconds
+    and launches per step, not an HBM roofline."""
+    device = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
     cfg = P.pic_config_default(nx=64, nz=128, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN, precision=P.PIC_FP64,
                                ppc_per_species=4, seed=1, init_beam=1, diag_every=1)
@@ -724,23 +808,39 @@ def run_config1(args):
     P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, 0.5))
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             P.pic_step(h, 1)
     P.pic_sync(h)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(device.index)
+    before = clocks.sample()
     clocks.start()
-    ms, kt, launches = timed_steps(P, torch, h, stream, args.steps, device)
-    clk = clocks.stop()
+    ms, kt, launches = timed_steps(P, torch, h, stream, steps, device)
+    clk = clocks.stop(before, clocks.sample())
     P.pic_destroy(h)
-    line = {"metric": METRIC, "value": np_ * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "2D 64x128, 4 particles/cell/species (65,536 particles), gamma 130, c dt/dz 0.5, "
-                                   "Galerkin, correction + filter (1,1,a=3), FP64, energies every step",
-                       "particles": np_, "l2": "L2 resident (7 MB): bound by launch latency, no flush"},
-            "us_per_step": 1e3 * ms / args.steps, "launches_per_step": launches / args.steps,
+    return {"value": np_ * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "particles": np_,
+            "workload": "2D 64x128, 4 particles/cell/species (65,536 particles), gamma 130, c dt/dz 0.5, Galerkin, "
+                        "correction + filter (1,1,a=3), FP64, energies every step",
+            "l2": "L2 resident (7 MB): bound by launch latency, no flush",
+            "us_per_step": 1e3 * ms / steps, "launches_per_step": launches / steps,
             "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
-            "cell_updates_per_s": 64 * 128 * args.steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+            "cell_updates_per_s": 64 * 128 * steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
+
+
+def run_config1(args):
+    """The small 64 x 128 FP64 workload alone, beside the oracle running the whole workload."""
+    import torch
+
+    import paper_1401_0838_gb300 as P
+    torch.cuda.set_device(0)
+    m = measure_config1(P, torch, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": m["workload"], "particles": m["particles"], "l2": m["l2"]},
+            "us_per_step": m["us_per_step"], "launches_per_step": m["launches_per_step"],
+            "kernel_ms_per_launch": m["kernel_ms_per_launch"], "cell_updates_per_s": m["cell_updates_per_s"],
+            "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_config1(args.cpu_steps_c1)
     print(json.dumps(line), flush=True)
@@ -893,6 +993,8 @@ def main(argv=None):
     ap.add_argument("--cpu-steps-c1", type=int, default=200, help="oracle steps of the --config1 CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the config1 / config3d / sweep / adjoint keys of the default line")
     ap.add_argument("--sweep", action="store_true", help="time the batched 64-run sweep instead")
     ap.add_argument("--sweep-runs", type=int, default=64)
     ap.add_argument("--sweep-seq-steps", type=int, default=40)
@@ -901,6 +1003,7 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
+    ap.add_argument("--config3d-nz", type=int, default=512, help="z cells of the --config3d grid (profiling: fewer)")
     ap.add_argument("--config1", action="store_true", help="time the small 64x128 FP64 workload instead")
     ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
     ap.add_argument("--gamma-sweep", action="store_true", help="growth against c dt/dz at gamma 3 and 130 instead")

@@ -257,9 +257,10 @@ int pic_launch_count(pic_handle* h, long long* n);
 
 /*
  * Field energies with no memory allocation. The paper has no counterpart: this entry point is for
- * callers that cannot allocate device memory where they need the energies (a loop being built
- * into a CUDA graph, a host application that owns every allocation, a monitor that must not change
- * the footprint of the run it watches). It returns the same W_E, W_B, W_perp as pic_energy
+ * callers that cannot allocate device memory where they need the energies (a plugin whose host
+ * application owns every device allocation, a monitor that must not change the memory footprint of
+ * the run it watches, code running when the device is nearly full). It returns the same W_E, W_B,
+ * W_perp as pic_energy
  * (1/2 sum E^2 dV, 1/2 sum B^2 dV, 1/2 sum (Ex^2+Ey^2+Bx^2+By^2) dV, FP64 sums) for six device
  * arrays of ncell elements each (Ex Ey Ez Bx By Bz; float for PIC_FP32, double for PIC_FP64) and
  * writes them to the host array out[3]; dv is the cell volume. It calls no cudaMalloc or cudaFree:
@@ -267,10 +268,13 @@ int pic_launch_count(pic_handle* h, long long* n);
  * every GPU that loads the library until the process exits), which limits a call to
  * 16,777,216 cells (larger ncell: PIC_E_ARG). The first call on a device looks that array's address
  * up (cudaGetSymbolAddress) with the device current, so make it before any stream capture on that
- * device. Every call shares the array: calls that overlap on the GPU (other streams or threads)
- * race and must be serialised by the caller; nothing in it has to start at zero, because each call
- * overwrites every partial sum it reads. Work is queued on `stream` (a cudaStream_t; NULL = the
- * default stream), which the call synchronises before returning.
+ * device; the address is kept for the life of the process, so do not call this entry point on a
+ * device after a cudaDeviceReset of it. Every call shares the array: calls that overlap on the GPU
+ * (other streams or threads) race and must be serialised by the caller; nothing in it has to start
+ * at zero, because each call overwrites every partial sum it reads. Work is queued on `stream` (a
+ * cudaStream_t; NULL = the default stream); the call synchronises that stream and copies the three
+ * sums into out before returning. A CUDA error pending before the call makes it return PIC_E_CUDA
+ * and is left pending.
  */
 int pic_field_energy_noalloc(const void* const fields[6], long long ncell, int precision, double dv,
                              double out[3], void* stream);

@@ -423,6 +423,19 @@ struct PushMinBlocks {
   static constexpr int value = (sizeof(T) == 4 && NDIM == 2) ? 2 : 1;
 };
 
+// FP32 2D: each lane takes the particles of its pack two at a time, with the arithmetic of the pair
+// in packed FP32x2 instructions (one instruction advances both particles) and the two rebins
+// interleaved, so one dependent chain carries two particles.
+template <typename T, int NDIM>
+struct PushPaired {
+  static constexpr bool value = sizeof(T) == 4 && NDIM == 2;
+};
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 template <typename T, int NDIM, int SCHEME, int LPC>
 __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   using S = PushSmem<T, NDIM>;
@@ -616,6 +629,198 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
       const T qs = s ? T(1) : T(-1);
       const T* st_x = SG::at(stg, stage, 0, lane);  // array a of the lane's pack at st_x + slot(a) * 128
       const unsigned* st_id = SG::id_at(stg, stage, lane);
+      if constexpr (PushPaired<T, NDIM>::value) {
+        const float2 hh = make_float2(qs * r.hq, qs * r.hq);
+        const float2 u02 = make_float2(r.u0, r.u0), one2 = make_float2(1.f, 1.f);
+        const float2 dtdx2 = make_float2(r.dtdx, r.dtdx), dtdz2 = make_float2(r.dtdz, r.dtdz);
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll 1
+        for (int rp = 0; rp < 4; rp += 2) {
+          // the pack elements (ja, ja + 1) of this pair, one 8-byte load per array; lanes 8-15 and
+          // 24-31 take the other pair first, so a half-warp's loads cover all 32 banks
+          const int ja = 2 * (((rp >> 1) + (lane >> 3)) & 1), jb = ja + 1;
+          const bool va = ja < cnt, vb = jb < cnt;
+          const float2 pox = *reinterpret_cast<const float2*>(st_x + ja);
+          const float2 poz = *reinterpret_cast<const float2*>(st_x + SG::slot(2) * 128 + ja);
+          const float2 pux = *reinterpret_cast<const float2*>(st_x + SG::slot(3) * 128 + ja);
+          const float2 puy = *reinterpret_cast<const float2*>(st_x + SG::slot(4) * 128 + ja);
+          const float2 puz = *reinterpret_cast<const float2*>(st_x + SG::slot(5) * 128 + ja);
+          // an empty slot stands in as a particle at rest with no weight (finite, deposits nothing)
+          const float oxa = va ? pox.x : 0.5f, oza = va ? poz.x : 0.5f;
+          const float uxa = va ? pux.x : 0.f, uya = va ? puy.x : 0.f, uza = va ? puz.x : 0.f;
+          const float oxb = vb ? pox.y : 0.5f, ozb = vb ? poz.y : 0.5f;
+          const float uxb = vb ? pux.y : 0.f, uyb = vb ? puy.y : 0.f, uzb = vb ? puz.y : 0.f;
+          float wa = 0.f, wb = 0.f;
+          if (has_w) {
+            const float2 pw = *reinterpret_cast<const float2*>(st_x + SG::slot(6) * 128 + ja);
+            wa = va ? pw.x : 0.f;
+            wb = vb ? pw.y : 0.f;
+          } else {
+            wa = va ? r.wconst : 0.f;
+            wb = vb ? r.wconst : 0.f;
+          }
+          // gather
+          float Fa[6], Fb[6];
+          if (SCHEME == 0) {
+            gc.interp(oxa, 0.f, oza, Fa);
+            gc.interp(oxb, 0.f, ozb, Fb);
+          } else {
+            const DirW<float> xa = dir_weights(oxa), za = dir_weights(oza), xb = dir_weights(oxb),
+                              zb = dir_weights(ozb), y0 = dir_weights(0.f);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              Fa[c] = gather_comp<float, 2, SCHEME>(sg + c * S::GN, c, lx, 0, lz, xa, y0, za);
+              Fb[c] = gather_comp<float, 2, SCHEME>(sg + c * S::GN, c, lx, 0, lz, xb, y0, zb);
+            }
+          }
+          const float2 Ex = make_float2(Fa[0], Fb[0]), Ey = make_float2(Fa[1], Fb[1]), Ez = make_float2(Fa[2], Fb[2]);
+          const float2 Bx = make_float2(Fa[3], Fb[3]), By = make_float2(Fa[4], Fb[4]), Bz = make_float2(Fa[5], Fb[5]);
+          // relativistic Boris of the pair, momenta relative to the drift u0 z_hat
+          const float2 mx = fma2(hh, Ex, make_float2(uxa, uxb));
+          const float2 my = fma2(hh, Ey, make_float2(uya, uyb));
+          const float2 mz = fma2(hh, Ez, make_float2(uza, uzb));
+          const float2 Mz = add2(u02, mz);
+          float2 m2 = fma2(mx, mx, one2);
+          m2 = fma2(my, my, m2);
+          m2 = fma2(Mz, Mz, m2);
+          const float2 hig = mul2(hh, make_float2(fast_rsqrt(m2.x), fast_rsqrt(m2.y)));
+          const float2 tx = mul2(hig, Bx), ty = mul2(hig, By), tz = mul2(hig, Bz);
+          float2 t2 = fma2(tx, tx, one2);
+          t2 = fma2(ty, ty, t2);
+          t2 = fma2(tz, tz, t2);
+          const float2 sf = make_float2(fast_div(2.f, t2.x), fast_div(2.f, t2.y));
+          const float2 sx = mul2(sf, tx), sy = mul2(sf, ty), sz = mul2(sf, tz);
+          const float2 qx = fma2(my, tz, fma2(neg2(Mz), ty, mx));
+          const float2 qy = fma2(Mz, tx, fma2(neg2(mx), tz, my));
+          const float2 qz = fma2(mx, ty, fma2(neg2(my), tx, Mz));
+          const float2 ux2 = fma2(qy, sz, fma2(neg2(qz), sy, fma2(hh, Ex, mx)));
+          const float2 uy2 = fma2(qz, sx, fma2(neg2(qx), sz, fma2(hh, Ey, my)));
+          const float2 uz2 = fma2(qx, sy, fma2(neg2(qy), sx, fma2(hh, Ez, mz)));
+          const float2 Uz = add2(u02, uz2);
+          float2 u2 = mul2(ux2, ux2);
+          u2 = fma2(uy2, uy2, u2);
+          u2 = fma2(Uz, Uz, u2);
+          const float2 gp = add2(one2, u2);
+          const float2 ign = make_float2(fast_rsqrt(gp.x), fast_rsqrt(gp.y));
+          const float2 g1 = fma2(gp, ign, one2);  // gamma + 1; gamma - 1 = u^2 / (gamma + 1)
+          kin = fmaf(wa, fast_div(u2.x, g1.x), kin);
+          kin = fmaf(wb, fast_div(u2.y, g1.y), kin);
+          npush += (va ? 1 : 0) + (vb ? 1 : 0);
+          const float2 vy2 = mul2(uy2, ign);
+          const float2 ddx2 = mul2(dtdx2, mul2(ux2, ign)), ddz2 = mul2(dtdz2, mul2(Uz, ign));
+          float dxa = ddx2.x, dza = ddz2.x, dxb = ddx2.y, dzb = ddz2.y;
+          float nuxa = ux2.x, nuya = uy2.x, nuza = uz2.x, vya = vy2.x;
+          float nuxb = ux2.y, nuyb = uy2.y, nuzb = uz2.y, vyb = vy2.y;
+          if (!(dxa > -1.f && dxa < 1.f && dza > -1.f && dza < 1.f)) {
+            flag_error(r.err, ERR_NONFINITE);
+            dxa = dza = nuxa = nuya = nuza = vya = 0.f;
+          }
+          if (!(dxb > -1.f && dxb < 1.f && dzb > -1.f && dzb < 1.f)) {
+            flag_error(r.err, ERR_NONFINITE);
+            dxb = dzb = nuxb = nuyb = nuzb = vyb = 0.f;
+          }
+          // Esirkepov deposits
+          const EsirDir<float> exa = esir_dir(oxa, dxa), eza = esir_dir(oza, dza);
+          const EsirDir<float> exb = esir_dir(oxb, dxb), ezb = esir_dir(ozb, dzb);
+          if (va) {
+            const float qw = qs * wa;
+            const float cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vya * r.jfy2d;
+            if ((exa.a | eza.a) == 0) deposit2<float, NVP>(acc, exa, eza, cx, cy, cz);
+            else deposit2_smem<float, NDIM>(sj, lx + exa.a + 1, lz + eza.a + 1, exa, eza, cx, cy, cz);
+          }
+          if (vb) {
+            const float qw = qs * wb;
+            const float cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vyb * r.jfy2d;
+            if ((exb.a | ezb.a) == 0) deposit2<float, NVP>(acc, exb, ezb, cx, cy, cz);
+            else deposit2_smem<float, NDIM>(sj, lx + exb.a + 1, lz + ezb.a + 1, exb, ezb, cx, cy, cz);
+          }
+          // destinations: a cell of this tile (key (cell * 2 + species) in the tile) or, leaving
+          // the tile, the global cell (key global cell * 2 + species)
+          int dka = -1 - lane, dkb = -1 - lane;
+          bool lva = false, lvb = false;
+          if (va) {
+            const int nlx = lx + exa.shift, nlz = lz + eza.shift;
+            if (nlx >= 0 && nlx < wx && nlz >= 0 && nlz < wz) {
+              dka = (nlz * TX + nlx) * 2 + s;
+            } else {
+              lva = true;
+              dka = (wrap_near_p(gk + eza.shift, r.nz) * r.nx + wrap_near_p(gi + exa.shift, r.nx)) * 2 + s;
+            }
+          }
+          if (vb) {
+            const int nlx = lx + exb.shift, nlz = lz + ezb.shift;
+            if (nlx >= 0 && nlx < wx && nlz >= 0 && nlz < wz) {
+              dkb = (nlz * TX + nlx) * 2 + s;
+            } else {
+              lvb = true;
+              dkb = (wrap_near_p(gk + ezb.shift, r.nz) * r.nx + wrap_near_p(gi + exb.shift, r.nx)) * 2 + s;
+            }
+          }
+          // rebin of the pair: consecutive slots per (destination, species) for each particle of the
+          // pair, the two reservations interleaved
+          const bool sta = va && !lva, stb = vb && !lvb;
+          const unsigned pa = __match_any_sync(0xffffffffu, sta ? dka : -1 - lane);
+          const unsigned pb = __match_any_sync(0xffffffffu, stb ? dkb : -1 - lane);
+          const int lda = __ffs(pa) - 1, ldb = __ffs(pb) - 1;
+          int ba = 0, bb = 0;
+          if (sta && lane == lda) ba = atomicAdd(scnt + (dka & 1) * NCL + (dka >> 1), __popc(pa));
+          if (stb && lane == ldb) bb = atomicAdd(scnt + (dkb & 1) * NCL + (dkb >> 1), __popc(pb));
+          ba = __shfl_sync(0xffffffffu, ba, lda) + __popc(pa & lt);
+          bb = __shfl_sync(0xffffffffu, bb, ldb) + __popc(pb & lt);
+          const bool fa = sta && ba >= r.cap, fb = stb && bb >= r.cap;  // full bins: on to k_migrate
+          // leavers: the tile's shared buffer (one reservation for the pair), then the global list
+          // for full bins and once the shared buffer is full
+          const unsigned lma = __ballot_sync(0xffffffffu, lva), lmb = __ballot_sync(0xffffffffu, lvb);
+          int lsa = 0, lsb = 0;
+          if (lma | lmb) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(lvn, __popc(lma) + __popc(lmb));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            lsa = b0 + __popc(lma & lt);
+            lsb = b0 + __popc(lma) + __popc(lmb & lt);
+          }
+          const bool ga = fa || (lva && lsa >= S::LVB), gb = fb || (lvb && lsb >= S::LVB);
+          const unsigned gma = __ballot_sync(0xffffffffu, ga), gmb = __ballot_sync(0xffffffffu, gb);
+          long long goa = 0, gob = 0;
+          if (gma | gmb) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(r.lv_count, __popc(gma) + __popc(gmb));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            goa = (long long)b0 + __popc(gma & lt);
+            gob = (long long)b0 + __popc(gma) + __popc(gmb & lt);
+          }
+          auto place = [&](bool st, bool full, bool lv, bool g, int dk, int jo, int ls, long long go, float nox,
+                           float noz, float ux, float uy, float uz, float w, unsigned id) {
+            const int dcell = st ? (Z0 + (dk >> 1) / TX) * r.nx + X0 + (dk >> 1) % TX : 0;  // cells < 2^30
+            if (st && !full) {
+              const long long o = (long long)dcell * r.cap + jo;
+              pout.ox[o] = nox;
+              pout.oz[o] = noz;
+              pout.dux[o] = ux;
+              pout.duy[o] = uy;
+              pout.duz[o] = uz;
+              if (has_w) pout.w[o] = w;
+              if (has_id) pout.id[o] = id;
+            } else if (g) {
+              if (go < r.lv_cap) list_put(r.lv, go, full ? dcell * 2 + (dk & 1) : dk, nox, 0.f, noz, ux, uy, uz, w, id);
+              else flag_error(r.err, ERR_OVERFLOW);
+            } else if (lv) {
+              lvk[ls] = dk;
+              lvv[ls] = nox;
+              lvv[2 * S::LVB + ls] = noz;
+              lvv[3 * S::LVB + ls] = ux;
+              lvv[4 * S::LVB + ls] = uy;
+              lvv[5 * S::LVB + ls] = uz;
+              if (has_w) lvv[6 * S::LVB + ls] = w;
+              if (has_id) lvi[ls] = id;
+            }
+          };
+          if (va)
+            place(sta, fa, lva, ga, dka, ba, lsa, goa, exa.off, eza.off, nuxa, nuya, nuza, wa, has_id ? st_id[ja] : 0u);
+          if (vb)
+            place(stb, fb, lvb, gb, dkb, bb, lsb, gob, exb.off, ezb.off, nuxb, nuyb, nuzb, wb, has_id ? st_id[jb] : 0u);
+        }
+      } else {
 #pragma unroll 1
       for (int rnd = 0; rnd < 4; ++rnd) {
         // pack element of this round, rotated by lane / 8 so the 32 lanes' shared-memory reads of
@@ -793,6 +998,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
             flag_error(r.err, ERR_OVERFLOW);
           }
         }
+      }
       }
     }
     if (it == giters - 1) {

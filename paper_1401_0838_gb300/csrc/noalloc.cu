@@ -1,12 +1,13 @@
 // Field energies without any memory allocation (pic_field_energy_noalloc in include/pic.h).
 //
-// Some callers cannot allocate device memory at the point where they want the energies: code
-// running inside a CUDA-graph-building or real-time loop that forbids cudaMalloc, plugins whose
-// host application owns every allocation, and monitoring hooks that must not change the memory
-// footprint of the run they observe. This entry point serves them: the caller passes the six
-// field arrays and a host array for the three results, and the per-block partial sums live in
-// one fixed array of this library's device memory (kFeScratchBlocks x 3 doubles, 96 KiB, held by
-// every GPU that loads the library until the process exits).
+// Some callers cannot allocate device memory at the point where they want the energies: plugins
+// whose host application owns every device allocation (its own pool, cudaMalloc not theirs to
+// call), monitoring hooks that must not change the memory footprint of the run they observe, and
+// code that runs when the device is nearly full, where an allocation could fail or evict. This
+// entry point serves them: the caller passes the six field arrays and a host array for the three
+// results, and the per-block partial sums live in one fixed array of this library's device memory
+// (kFeScratchBlocks x 3 doubles, 96 KiB, held by every GPU that loads the library until the
+// process exits).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -74,7 +75,8 @@ __global__ void k_fe_final(double* scratch, int nblocks) {
   scratch[3 * kFeScratchBlocks + r] = t;
 }
 
-// Address of g_fe_scratch on the current device, looked up once per device.
+// Address of g_fe_scratch on the current device, looked up once per device (on the first call there)
+// and kept for the life of the process; a cudaDeviceReset of that device invalidates it.
 int fe_scratch(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kFeMaxDevices) return PIC_E_CUDA;
@@ -110,7 +112,8 @@ extern "C" int pic_field_energy_noalloc(const void* const fields[6], long long n
   }
   k_fe_final<<<1, 32, 0, st>>>(scratch, nblocks);
   double sums[3];
-  if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+  // peek, not get: an error the caller left pending stays theirs to read (and fails this call too)
+  if (cudaPeekAtLastError() != cudaSuccess) return PIC_E_CUDA;
   if (cudaMemcpyAsync(sums, scratch + 3 * kFeScratchBlocks, sizeof sums, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PIC_E_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PIC_E_CUDA;

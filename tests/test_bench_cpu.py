@@ -11,14 +11,28 @@ import bench  # noqa: E402
 
 
 def test_roofline_arithmetic():
-    # 16.8M particles at 40 B and 0.5M cells at 36 B, 10 launches in 5 ms: 0.5 ms per launch
+    # 16.8M particles at 48 B (cell index, offsets, momenta each way) and 0.5M cells at 36 B, 10
+    # launches in 5 ms: 0.5 ms per launch; the layout's own 40 B per particle beside it
     np_, ncell = 16777216, 524288
     rf = bench.roofline({"push": (5.0, 10)}, np_, ncell, 4, 6791.4, "measured")
-    want_bytes = np_ * 40 + ncell * 36
+    want_bytes = np_ * 48 + ncell * 36
     assert rf["algorithmic_bytes_per_launch"] == want_bytes
     assert abs(rf["achieved"] - want_bytes / 0.5e-3 / 1e9) < 0.1
     assert abs(rf["frac"] - rf["achieved"] / 6791.4) < 1e-4
     assert rf["launch_ms"] == 0.5 and rf["bound"] == "hbm" and rf["unit"] == "GB/s"
+    assert abs(rf["frac_layout_bytes"] - (np_ * 40 + ncell * 36) / 0.5e-3 / 1e9 / 6791.4) < 1e-4
+    assert rf["time_basis"] == "event-bracketed launches"
+
+
+def test_push_time_from_the_graph_replayed_step():
+    # step of 0.6 ms in the graph; the timed pass of 10 single steps: push 5 ms, the rest 1 ms in all,
+    # so the push takes 0.6 - 0.1 = 0.5 ms of a replayed step
+    kt = {"push": (5.0, 10), "copies": (0.4, 10), "yee": (0.5, 10), "migrate": (0.1, 10)}
+    assert abs(bench.push_time_in_step(kt, 0.6) - 0.5) < 1e-12
+    rf = bench.roofline(kt, 16777216, 524288, 4, 6791.4, "measured", step_ms=0.6)
+    assert rf["launch_ms"] == 0.5 and rf["launch_ms_events"] == 0.5
+    assert rf["time_basis"].startswith("graph-replayed")
+    assert bench.push_time_in_step(kt, 0.05) is None  # less than the other kernels: no estimate
 
 
 def test_traffic_only_for_the_profiled_source(tmp_path):

@@ -47,6 +47,23 @@ def test_noalloc_energy_matches_pic_energy(precision):
         assert again == got  # deterministic: fixed chunks summed in a fixed order
 
 
+@pytest.mark.parametrize("nx,nz", [(329, 249), (4096, 4096)])
+def test_noalloc_partial_last_chunk_and_largest_size(nx, nz):
+    # 81,921 = 4096 * 20 + 1 cells: the last of the fixed 4096-cell chunks holds one cell; 16,777,216
+    # cells: every one of the 4096 partial-sum slots of the fixed array is used (the largest size)
+    torch = pytest.importorskip("torch")
+    cfg = make_cfg(nx=nx, nz=nz, precision=P.PIC_FP32, ppc=0)
+    host = synth.random_fields((nz, 1, nx), seed=23, scale=0.3)
+    dev = {k: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for k, v in host.items()}
+    torch.cuda.synchronize()
+    ref = _energies_via_handle(cfg, dev)
+    for _ in range(2):
+        got = P.pic_field_energy_noalloc([dev[k] for k in ("ex", "ey", "ez", "bx", "by", "bz")], nx * nz,
+                                         P.PIC_FP32, cfg.dx * cfg.dy * cfg.dz)
+        for a, b in zip(got, ref):
+            assert abs(a - b) <= TOL * abs(b), (got, ref)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(P.PicError) as e:
         P.pic_field_energy_noalloc([1, 1, 1, 1, 1, 1], 16_777_216 + 1, P.PIC_FP32, 1.0)

@@ -28,7 +28,8 @@ struct pic_handle {
   double u0 = 0, w0 = 0;
   bool has_w = false, has_id = false;
   std::vector<void*> allocs;
-  void* f[9] = {};   // ex ey ez bx by bz jx jy jz
+  void* f[9] = {};   // ex ey ez bx by bz jx jy jz (E and B: the current step's)
+  void* fb[6] = {};  // the other E, B buffers: the fused Yee update writes there, then the two swap
   void* g[6] = {};   // gather copies
   void* jf[3] = {};  // filtered current (aliases f[6..8] when J is not filtered)
   void* parr[2][2][8] = {};  // [species][buffer][ox oy oz dux duy duz w id]
@@ -79,6 +80,7 @@ struct pic_handle {
   int graph_len = 0;
   cudaStream_t graph_stream = nullptr;
   int graph_parity = 0;               // parity of the first captured step
+  void* graph_f0 = nullptr;           // Ex buffer current when the graph was captured
   long long graph_launch_count = 0;   // kernel launches in one replay
   long long graph_counts[PIC_NKERNEL] = {};
   // kernel timing
@@ -374,6 +376,7 @@ SepArgs<T> sep_args(pic_handle* h, bool copies) {
   a.ny = c.ny;
   a.nz = c.nz;
   a.ndim = c.ndim;
+  a.err = h->d_err;
   auto put = [](T* dst, const std::vector<double>& v) {
     for (size_t i = 0; i < v.size(); ++i) dst[i] = (T)v[i];
   };
@@ -419,6 +422,12 @@ YeeArgs<T> yee_args(pic_handle* h, double hstep) {
   a.bx = (T*)h->f[3];
   a.by = (T*)h->f[4];
   a.bz = (T*)h->f[5];
+  a.oex = (T*)h->fb[0];
+  a.oey = (T*)h->fb[1];
+  a.oez = (T*)h->fb[2];
+  a.obx = (T*)h->fb[3];
+  a.oby = (T*)h->fb[4];
+  a.obz = (T*)h->fb[5];
   void* const* js = (h->cfg.filter_targets & PIC_FILTER_J) ? h->jf : h->f + 6;
   a.jx = (const T*)js[0];
   a.jy = (const T*)js[1];
@@ -430,6 +439,7 @@ YeeArgs<T> yee_args(pic_handle* h, double hstep) {
   a.cy = (T)(hstep / c.dy);
   a.cz = (T)(hstep / c.dz);
   a.h = (T)hstep;
+  a.err = h->d_err;
   if (c.field_solver == PIC_CK) {
     a.ck = 1;
     a.wx0 = (T)(1.0 - 2.0 * c.ck_beta_x);
@@ -439,6 +449,8 @@ YeeArgs<T> yee_args(pic_handle* h, double hstep) {
   }
   return a;
 }
+
+void swap_fields(pic_handle* h);
 
 template <typename T>
 int step_once(pic_handle* h) {
@@ -493,6 +505,7 @@ int step_once(pic_handle* h) {
   CK(launch(h, PIC_K_YEE,
             [&] { return launch_yee_fused<T>(ye, c.ndim, st, h->d_red_yee, fused_diag ? &hc : nullptr); }),
      "yee");
+  swap_fields(h);  // the new E, B are in the other buffers
   if (rec) {
     if (!fused_diag) {
       const T* f6[6];
@@ -505,6 +518,15 @@ int step_once(pic_handle* h) {
   h->parity ^= 1;
   h->nstep++;
   return PIC_OK;
+}
+
+// E and B of the new step were written to the other buffers: they become the current ones.
+void swap_fields(pic_handle* h) {
+  for (int q = 0; q < 6; ++q) {
+    void* t = h->f[q];
+    h->f[q] = h->fb[q];
+    h->fb[q] = t;
+  }
 }
 
 int check_err(pic_handle* h) {
@@ -954,6 +976,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   const size_t fb = (size_t)h->ncell * h->es;
   bool ok = true;
   for (int q = 0; q < 9 && ok; ++q) ok = (h->f[q] = dalloc(h, fb)) != nullptr;
+  for (int q = 0; q < 6 && ok; ++q) ok = (h->fb[q] = dalloc(h, fb)) != nullptr;
   for (int q = 0; q < 6 && ok; ++q) ok = (h->g[q] = dalloc(h, fb)) != nullptr;
   for (int q = 0; q < 3 && ok; ++q) ok = (h->jf[q] = dalloc(h, fb)) != nullptr;
   if (ok && c.correction_mode == PIC_CORR_RATIONAL)  // complex scratch of the z-solves, two components
@@ -1076,6 +1099,12 @@ static int build_graph(pic_handle* h) {
   if (len > 64) return PIC_E_STATE;  // diagnostics too sparse to unroll into one graph
   const long long nstep0 = h->nstep, nhist0 = h->nhist;
   const int parity0 = h->parity;
+  void* f0[6];
+  void* fb0[6];
+  for (int q = 0; q < 6; ++q) {
+    f0[q] = h->f[q];
+    fb0[q] = h->fb[q];
+  }
   const long long launches0 = h->launches;
   long long counts0[PIC_NKERNEL];
   for (int q = 0; q < PIC_NKERNEL; ++q) counts0[q] = h->tcount[q];
@@ -1086,6 +1115,10 @@ static int build_graph(pic_handle* h) {
   h->nstep = nstep0;
   h->nhist = nhist0;
   h->parity = parity0;
+  for (int q = 0; q < 6; ++q) {  // an even number of steps: the captured swaps cancel
+    h->f[q] = f0[q];
+    h->fb[q] = fb0[q];
+  }
   h->launches = launches0;
   for (int q = 0; q < PIC_NKERNEL; ++q) h->tcount[q] = counts0[q];
   if (rc != PIC_OK || e != cudaSuccess) {
@@ -1098,6 +1131,7 @@ static int build_graph(pic_handle* h) {
   h->graph_len = len;
   h->graph_stream = h->stream;
   h->graph_parity = parity0;
+  h->graph_f0 = f0[0];
   h->graph_launch_count = 0;
   for (int q = 0; q < PIC_NKERNEL; ++q) h->graph_counts[q] = 0;
   // launches per replay, for pic_launch_count / pic_kernel_times bookkeeping
@@ -1143,7 +1177,8 @@ static int step_calls(pic_handle* h, int nsteps) {
   int rc = run_steps(h, lead);
   if (rc) return rc;
   nsteps -= lead;
-  if (!h->graph || h->graph_len != len || h->graph_stream != h->stream || h->graph_parity != h->parity) {
+  if (!h->graph || h->graph_len != len || h->graph_stream != h->stream || h->graph_parity != h->parity ||
+      h->graph_f0 != h->f[0]) {
     // counts of one replay: run one graph's worth of steps while counting, then capture
     const long long l0 = h->launches;
     long long c0[PIC_NKERNEL];
@@ -1376,10 +1411,10 @@ struct pic_batch {
   int diag_every = 0;
   std::vector<void*> allocs;
   void* d_run[2][2] = {};  // RunDev<T>[nruns] by [parity][recording]
-  void* d_sep_copy = nullptr;
+  void* d_sep_copy[2] = {};  // by step parity: the E, B buffers each run reads and (Yee) writes alternate
   void* d_sep_j = nullptr;
-  void* d_yee = nullptr;
-  void* d_energy = nullptr;
+  void* d_yee[2] = {};
+  void* d_energy[2] = {};
   int* d_sep_base = nullptr;
   int sep_total = 0;
   int* d_yee_base = nullptr;
@@ -1445,23 +1480,43 @@ int batch_tables(pic_batch* b) {
       }
       BCK(cudaMemcpy(b->d_run[p][rec], rd.data(), sizeof(RunDev<T>) * n, cudaMemcpyHostToDevice), "run table");
     }
+  // the E, B buffers current now (X) are read by steps of the batch's present parity and written by
+  // the other parity's steps; the other buffers (Y) the reverse
   std::vector<SepArgs<T>> sc(n), sj(n);
   std::vector<YeeArgs<T>> ya(n);
   std::vector<EnergyArgs<T>> ea(n);
-  for (int i = 0; i < n; ++i) {
-    pic_handle* h = b->runs[i];
-    sc[i] = sep_args<T>(h, true);
-    sj[i] = sep_args<T>(h, false);
-    ya[i] = yee_args<T>(h, h->cfg.dt);
-    for (int q = 0; q < 6; ++q) ea[i].f[q] = (const T*)h->f[q];
-    ea[i].ncell = h->ncell;
-    ea[i].scratch = h->d_red;
-    ea[i].hc = HistCtl{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
+  for (int p = 0; p < 2; ++p) {
+    for (int i = 0; i < n; ++i) {
+      pic_handle* h = b->runs[i];
+      const bool cur = p == b->parity;
+      void* const* in = cur ? h->f : h->fb;
+      void* const* out = cur ? h->fb : h->f;
+      sc[i] = sep_args<T>(h, true);
+      for (int q = 0; q < 6; ++q) sc[i].src[q] = (const T*)in[q];
+      ya[i] = yee_args<T>(h, h->cfg.dt);
+      ya[i].ex = (T*)in[0];
+      ya[i].ey = (T*)in[1];
+      ya[i].ez = (T*)in[2];
+      ya[i].bx = (T*)in[3];
+      ya[i].by = (T*)in[4];
+      ya[i].bz = (T*)in[5];
+      ya[i].oex = (T*)out[0];
+      ya[i].oey = (T*)out[1];
+      ya[i].oez = (T*)out[2];
+      ya[i].obx = (T*)out[3];
+      ya[i].oby = (T*)out[4];
+      ya[i].obz = (T*)out[5];
+      for (int q = 0; q < 6; ++q) ea[i].f[q] = (const T*)out[q];  // the energies of the new step
+      ea[i].ncell = h->ncell;
+      ea[i].scratch = h->d_red;
+      ea[i].hc = HistCtl{h->d_hist, h->hist_cap, h->d_hist_count, h->d_kin};
+    }
+    BCK(cudaMemcpy(b->d_sep_copy[p], sc.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "copy table");
+    BCK(cudaMemcpy(b->d_yee[p], ya.data(), sizeof(YeeArgs<T>) * n, cudaMemcpyHostToDevice), "yee table");
+    BCK(cudaMemcpy(b->d_energy[p], ea.data(), sizeof(EnergyArgs<T>) * n, cudaMemcpyHostToDevice), "energy table");
   }
-  BCK(cudaMemcpy(b->d_sep_copy, sc.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "copy table");
+  for (int i = 0; i < n; ++i) sj[i] = sep_args<T>(b->runs[i], false);
   BCK(cudaMemcpy(b->d_sep_j, sj.data(), sizeof(SepArgs<T>) * n, cudaMemcpyHostToDevice), "filter table");
-  BCK(cudaMemcpy(b->d_yee, ya.data(), sizeof(YeeArgs<T>) * n, cudaMemcpyHostToDevice), "yee table");
-  BCK(cudaMemcpy(b->d_energy, ea.data(), sizeof(EnergyArgs<T>) * n, cudaMemcpyHostToDevice), "energy table");
   b->gens.resize(n);
   for (int i = 0; i < n; ++i) b->gens[i] = b->runs[i]->grow_gen;
   b->tables_dirty = false;
@@ -1475,7 +1530,8 @@ int batch_step_once(pic_batch* b) {
   pic_handle* h0 = b->runs[0];
   const bool rec = b->diag_every > 0 && (h0->nstep + 1) % b->diag_every == 0;
   const RunDev<T>* runs = (const RunDev<T>*)b->d_run[b->parity][rec ? 1 : 0];
-  BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_copy, b->d_sep_base, n, b->sep_total, 6, b->ndim, b->hz, b->hx,
+  BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_copy[b->parity], b->d_sep_base, n, b->sep_total, 6, b->ndim,
+                          b->hz, b->hx,
                           st),
       "batched copy stencil");
   for (auto& g : b->groups)
@@ -1487,9 +1543,11 @@ int batch_step_once(pic_batch* b) {
     BCK(launch_sep_batch<T>((const SepArgs<T>*)b->d_sep_j, b->d_sep_base, n, b->sep_total, 3, b->ndim, b->hzj, b->hxj,
                             st),
         "batched current filter");
-  BCK(launch_yee_batch<T>((const YeeArgs<T>*)b->d_yee, b->d_yee_base, n, b->yee_total, b->ndim, st), "batched yee");
-  if (rec) BCK(launch_field_energy_batch<T>((const EnergyArgs<T>*)b->d_energy, n, st), "batched energy");
+  BCK(launch_yee_batch<T>((const YeeArgs<T>*)b->d_yee[b->parity], b->d_yee_base, n, b->yee_total, b->ndim, st),
+      "batched yee");
+  if (rec) BCK(launch_field_energy_batch<T>((const EnergyArgs<T>*)b->d_energy[b->parity], n, st), "batched energy");
   for (pic_handle* h : b->runs) {
+    swap_fields(h);
     h->parity ^= 1;
     h->nstep++;
     if (rec) h->nhist++;
@@ -1521,10 +1579,13 @@ int batch_build_graph(pic_batch* b) {
   const int parity0 = b->parity;
   std::vector<long long> ns(b->runs.size()), nh(b->runs.size());
   std::vector<int> pa(b->runs.size());
+  std::vector<std::vector<void*>> fs(b->runs.size());
   for (size_t i = 0; i < b->runs.size(); ++i) {
     ns[i] = b->runs[i]->nstep;
     nh[i] = b->runs[i]->nhist;
     pa[i] = b->runs[i]->parity;
+    fs[i].assign(b->runs[i]->f, b->runs[i]->f + 6);
+    fs[i].insert(fs[i].end(), b->runs[i]->fb, b->runs[i]->fb + 6);
   }
   BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = batch_run_steps(b, len);
@@ -1536,6 +1597,10 @@ int batch_build_graph(pic_batch* b) {
     b->runs[i]->nstep = ns[i];
     b->runs[i]->nhist = nh[i];
     b->runs[i]->parity = pa[i];
+    for (int q = 0; q < 6; ++q) {  // an even number of steps: the captured swaps cancel
+      b->runs[i]->f[q] = fs[i][q];
+      b->runs[i]->fb[q] = fs[i][6 + q];
+    }
   }
   if (rc != PIC_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -1675,8 +1740,10 @@ int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
   bool ok = true;
   for (int p = 0; p < 2 && ok; ++p)
     for (int r = 0; r < 2 && ok; ++r) ok = (b->d_run[p][r] = balloc(b, rd * nruns)) != nullptr;
-  if (ok) ok = (b->d_sep_copy = balloc(b, sa * nruns)) && (b->d_sep_j = balloc(b, sa * nruns)) &&
-               (b->d_yee = balloc(b, ya * nruns)) && (b->d_energy = balloc(b, ea * nruns)) &&
+  for (int p = 0; p < 2 && ok; ++p)
+    ok = (b->d_sep_copy[p] = balloc(b, sa * nruns)) && (b->d_yee[p] = balloc(b, ya * nruns)) &&
+         (b->d_energy[p] = balloc(b, ea * nruns));
+  if (ok) ok = (b->d_sep_j = balloc(b, sa * nruns)) &&
                (b->d_sep_base = (int*)balloc(b, sizeof(int) * (nruns + 1))) &&
                (b->d_yee_base = (int*)balloc(b, sizeof(int) * (nruns + 1)));
   if (!ok) {
@@ -1862,6 +1929,7 @@ int pic_batch_autotune(pic_batch* b, int trial_steps, int* lpc_out) {
   }
   b->parity = 0;
   b->nstep = 0;
+  b->tables_dirty = true;  // the field buffers current at parity 0 may have changed roles
   batch_drop_graph(b);
   return pic_batch_sync(b);
 }

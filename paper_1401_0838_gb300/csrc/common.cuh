@@ -174,4 +174,49 @@ __device__ __forceinline__ void copy1_async(double* dst, const double* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tensor-memory-access (TMA) staging: one thread starts a tiled bulk copy of a box of a field into
+// shared memory, completed on an mbarrier that every thread of the block waits on. The tensor map
+// (a CUtensorMap encoded on the host) lives in the kernel's parameter space.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the copy engine
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// box of a 2D / 3D tensor at element coordinates (x, y[, z]); x * element size a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+          "r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier to complete, giving up after `limit` polls (each poll may
+// suspend the thread for a short, hardware-chosen time). Returns whether it completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr int TMA_WAIT_POLLS = 1 << 20;  // each poll returns within microseconds: a second or so in all
+
 }  // namespace picgb

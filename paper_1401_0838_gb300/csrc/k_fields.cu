@@ -1,5 +1,7 @@
 // Grid kernels: the Psi z-stencil + binomial/compensation filter (one separable stencil kernel),
 // the Yee curl updates and the FP64 energy reductions.
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -17,6 +19,54 @@ cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) enabled[kernel] = bytes;
   return e;
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    (void)cudaGetLastError();  // a failed lookup leaves the element-copy staging in use
+  });
+  return fn;
+}
+
+bool tma_encode(CUtensorMap* m, const void* base, int es, int ndim, int nx, int ny, int nz, int bx, int by, int bz) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tma_encoder();
+  if (!fn || !base || (es != 4 && es != 8)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((long long)nx * es) % 16 != 0) return false;
+  if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256 || (bx * es) % 16 != 0) return false;
+  const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  cuuint64_t dims[3], strides[2];
+  cuuint32_t box[3], estr[3] = {1, 1, 1};
+  cuuint32_t rank;
+  if (ndim == 2) {  // (x, z), one y plane
+    rank = 2;
+    dims[0] = (cuuint64_t)nx;
+    dims[1] = (cuuint64_t)nz;
+    strides[0] = (cuuint64_t)nx * es;
+    box[0] = (cuuint32_t)bx;
+    box[1] = (cuuint32_t)bz;
+  } else {
+    rank = 3;
+    dims[0] = (cuuint64_t)nx;
+    dims[1] = (cuuint64_t)ny;
+    dims[2] = (cuuint64_t)nz;
+    strides[0] = (cuuint64_t)nx * es;
+    strides[1] = (cuuint64_t)nx * ny * es;
+    box[0] = (cuuint32_t)bx;
+    box[1] = (cuuint32_t)by;
+    box[2] = (cuuint32_t)bz;
+  }
+  const CUresult r = fn(m, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -161,17 +211,78 @@ cudaError_t launch_sep_generic(const SepArgs<T>& a, cudaStream_t st) {
 // a fixed 2D thread map: no integer division by runtime sizes, taps in registers. Valid when
 // every halo fits in one period of the grid (the dispatcher checks; tiny grids use the generic
 // kernel above).
+// Staged x range of a tile: from X0 - XA to X0 + CX + XA, XA = HX rounded up to a 16-byte multiple
+// of elements, so that the start of every staged row (and a TMA box's x coordinate) is 16-byte
+// aligned when X0 is; the stencil reads the columns from XA - HX on.
+template <typename T, int HX>
+struct SepPitch {
+  static constexpr int AL = 16 / (int)sizeof(T);
+  static constexpr int XA = (HX + AL - 1) / AL * AL;
+};
+
+template <typename T, int NDIM, int HZ, int HX>
+struct SepGeom {
+  static constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY;
+  static constexpr int CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
+  static constexpr int HY = NDIM == 3 ? HX : 0;
+  static constexpr int XA = SepPitch<T, HX>::XA;
+  static constexpr int PX = CX + 2 * XA, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
+  static constexpr size_t STAGE_BYTES = sizeof(T) * (size_t)LZ * LY * PX;
+  // dynamic shared memory: the staged tile (128-byte aligned for TMA), the y-pass output in 3D
+  static constexpr size_t SMEM_BYTES = 128 + STAGE_BYTES + (NDIM == 3 ? sizeof(T) * (size_t)CZ * CY * PX : 0);
+};
+
+// Overwrite the staged elements that lie outside the grid (a TMA box reads them as zero) with their
+// periodic images: columns, rows and (3D) planes past either end. The grid is at least as wide as
+// the staged region in every direction, so every index is within one period of the grid. Elements
+// on two edges are written twice, with the same value.
+template <typename T, int NDIM, int NT>
+__device__ __forceinline__ void patch_wrapped(T* s0, const T* __restrict__ src, int xs, int ys, int zs, int PX, int LY,
+                                              int LZ, int nx, int ny, int nz) {
+  const WrapOnce w;
+  const int xlo = max(0, -xs), xhi = max(0, xs + PX - nx);
+  const int ylo = NDIM == 3 ? max(0, -ys) : 0, yhi = NDIM == 3 ? max(0, ys + LY - ny) : 0;
+  const int zlo = max(0, -zs), zhi = max(0, zs + LZ - nz);
+  if (!(xlo | xhi | ylo | yhi | zlo | zhi)) return;
+  const long long nxy = (long long)nx * ny;
+  auto fix = [&](int lx, int ly, int lz) {
+    const int gx = w(xs + lx, nx), gy = NDIM == 3 ? w(ys + ly, ny) : 0, gz = w(zs + lz, nz);
+    s0[(lz * LY + ly) * PX + lx] = src[gz * nxy + (long long)gy * nx + gx];
+  };
+  const int nxe = xlo + xhi;  // outside columns, every row
+  for (int i = threadIdx.x; i < nxe * LY * LZ; i += NT) {
+    const int c = i % nxe, row = i / nxe;
+    fix(c < xlo ? c : PX - xhi + (c - xlo), row % LY, row / LY);
+  }
+  const int nze = zlo + zhi;  // outside rows, every column
+  for (int i = threadIdx.x; i < nze * LY * PX; i += NT) {
+    const int lx = i % PX, r = i / PX;
+    const int zr = r / LY;
+    fix(lx, r % LY, zr < zlo ? zr : LZ - zhi + (zr - zlo));
+  }
+  if constexpr (NDIM == 3) {
+    const int nye = ylo + yhi;  // outside y planes
+    for (int i = threadIdx.x; i < nye * LZ * PX; i += NT) {
+      const int lx = i % PX, r = i / PX;
+      const int yr = r % nye, lz = r / nye;
+      fix(lx, yr < ylo ? yr : LY - yhi + (yr - ylo), lz);
+    }
+  }
+}
+
 template <typename T, int NDIM, int HZ, int HX>
 __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, const int comp, const int ntx,
                                          const int nty) {
-  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
-  constexpr int HY = NDIM == 3 ? HX : 0;
-  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
+  using G = SepGeom<T, NDIM, HZ, HX>;
+  constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ, HY = G::HY, XA = G::XA;
+  constexpr int PX = G::PX, LY = G::LY, LZ = G::LZ;
   constexpr int TXN = CX < 32 ? 32 : CX, TYN = SEP_THREADS / TXN;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* s0 = reinterpret_cast<T*>(smraw);  // [LZ][LY][LX]; the z pass leaves its output in rows [0, CZ)
-  T* s1 = s0;                           // [CZ][LY][LX] (z pass output, in place)
-  T* s2 = s0 + LZ * LY * LX;            // [CZ][CY][LX] (3D)
+  __shared__ __align__(8) unsigned long long mbar;
+  // [LZ][LY][PX]; the z pass leaves its output in rows [0, CZ)
+  T* s0 = reinterpret_cast<T*>(smraw + ((128 - (smem_u32(smraw) & 127)) & 127));
+  T* s1 = s0;                   // [CZ][LY][PX] (z pass output, in place)
+  T* s2 = s0 + LZ * LY * PX;    // [CZ][CY][PX] (3D)
   const T* __restrict__ src = a.src[comp];
   T* __restrict__ dst = a.dst[comp];
   const int zs = a.zset[comp];
@@ -187,36 +298,58 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
   for (int m = 0; m <= 2 * HX; ++m) xt[m] = a.xt[m];
 #pragma unroll
   for (int m = 0; m <= 2 * HY; ++m) yt[m] = a.yt[m];
-  // stage the tile and its halos (rows along x)
-  auto stage = [&](auto wrap) {
-    for (int row = ty; row < LZ * LY; row += TYN) {
-      const int ly = row % LY, lz = row / LY;
-      const int gy = NDIM == 3 ? wrap(Y0 - HY + ly, a.ny) : 0;
-      const int gz = wrap(Z0 - HZ + lz, a.nz);
-      const T* srow = src + gz * nxy + (long long)gy * a.nx;
-      for (int lx = tx; lx < LX; lx += TXN) cp_async_el(s0 + row * LX + lx, srow + wrap(X0 - HX + lx, a.nx));
+  // stage the tile and its halos: x from X0 - XA (16-byte aligned), y from Y0 - HY, z from Z0 - HZ
+  const int xs = X0 - XA, ys = Y0 - HY, zs0 = Z0 - HZ;
+  if (a.use_tma) {
+    // one box for the whole region (periodic images patched below); the host enabled TMA only
+    // where the grid spans the region in every direction
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      mbar_expect_tx(&mbar, (unsigned)G::STAGE_BYTES);
+      if (NDIM == 2) tma_load_2d(s0, &a.tm[comp], xs, zs0, &mbar);
+      else tma_load_3d(s0, &a.tm[comp], xs, ys, zs0, &mbar);
     }
-  };
-  if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
-  else stage(WrapNear{});
-  cp_async_wait_all_fields();
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    const bool ok = __syncthreads_and(mbar_wait(&mbar, 0, TMA_WAIT_POLLS));
+    if (!ok) {  // give up: record it, let the copy land (bounded), and leave the tile
+      if (threadIdx.x == 0) flag_error(a.err, ERR_TIMEOUT);
+      mbar_wait(&mbar, 0, TMA_WAIT_POLLS);
+      return;
+    }
+    patch_wrapped<T, NDIM, SEP_THREADS>(s0, src, xs, ys, zs0, PX, LY, LZ, a.nx, a.ny, a.nz);
+  } else {
+    auto stage = [&](auto wrap) {
+      for (int row = ty; row < LZ * LY; row += TYN) {
+        const int ly = row % LY, lz = row / LY;
+        const int gy = NDIM == 3 ? wrap(ys + ly, a.ny) : 0;
+        const int gz = wrap(zs0 + lz, a.nz);
+        const T* srow = src + gz * nxy + (long long)gy * a.nx;
+        for (int lx = tx; lx < PX; lx += TXN) cp_async_el(s0 + row * PX + lx, srow + wrap(xs + lx, a.nx));
+      }
+    };
+    if (a.nx >= PX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
+    else stage(WrapNear{});
+    cp_async_wait_all_fields();
+  }
   __syncthreads();
   // z pass in place. A task is one (x, y) column of the staged tile and a segment of ZS output rows;
   // it reads its ZS + 2 HZ inputs into registers before any task of its round writes, and a column's
   // segment 0 (rows [0, ZS + 2 HZ) read, [0, ZS) written) always runs in a round no later than its
   // segment 1 (rows [ZS, 2 ZS + 2 HZ) read), so no task reads a row that another has overwritten.
+  // The columns before XA - HX and past CX + XA + HX are staged for alignment only and skipped.
   {
-    constexpr int NCOL = LX * LY, NSEG = NDIM == 2 ? 2 : 1, ZS = CZ / NSEG, NTASK = NCOL * NSEG;
+    constexpr int C0 = XA - HX, NX = CX + 2 * HX;
+    constexpr int NCOL = NX * LY, NSEG = NDIM == 2 ? 2 : 1, ZS = CZ / NSEG, NTASK = NCOL * NSEG;
     static_assert(CZ % NSEG == 0, "z segments must tile the output rows");
     for (int t0 = 0; t0 < NTASK; t0 += SEP_THREADS) {
       const int t = t0 + threadIdx.x;
       const bool act = t < NTASK;
       const int col = t % NCOL, seg = t / NCOL;
-      T* base = s0 + seg * ZS * NCOL + col;
+      T* base = s0 + seg * ZS * LY * PX + (col / NX) * PX + C0 + col % NX;
       T w[ZS + 2 * HZ];
       if (act) {
 #pragma unroll
-        for (int m = 0; m < ZS + 2 * HZ; ++m) w[m] = base[m * NCOL];
+        for (int m = 0; m < ZS + 2 * HZ; ++m) w[m] = base[m * LY * PX];
       }
       __syncthreads();
       if (act) {
@@ -225,7 +358,7 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
           T acc = T(0);
 #pragma unroll
           for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * w[r + m];
-          base[r * NCOL] = acc;
+          base[r * LY * PX] = acc;
         }
       }
       __syncthreads();
@@ -235,12 +368,12 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
   if (NDIM == 3) {  // y pass
     for (int row = ty; row < CZ * CY; row += TYN) {
       const int ly = row % CY, lz = row / CY;
-      for (int lx = tx; lx < LX; lx += TXN) {
-        const T* p = s1 + (lz * LY + ly) * LX + lx;
+      for (int lx = XA - HX + tx; lx < XA + HX + CX; lx += TXN) {
+        const T* p = s1 + (lz * LY + ly) * PX + lx;
         T acc = T(0);
 #pragma unroll
-        for (int m = 0; m <= 2 * HY; ++m) acc += yt[m] * p[m * LX];
-        s2[row * LX + lx] = acc;
+        for (int m = 0; m <= 2 * HY; ++m) acc += yt[m] * p[m * PX];
+        s2[row * PX + lx] = acc;
       }
     }
     __syncthreads();
@@ -253,7 +386,7 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
     for (int lx = tx; lx < CX; lx += TXN) {
       const int gx = X0 + lx;
       if (gx >= a.nx) continue;
-      const T* p = sx + row * LX + lx;
+      const T* p = sx + row * PX + XA - HX + lx;
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m <= 2 * HX; ++m) acc += xt[m] * p[m];
@@ -294,12 +427,22 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep_batch(const SepArgs<T>* __r
 }
 
 template <typename T, int NDIM, int HZ, int HX>
-static cudaError_t launch_sep_t(const SepArgs<T>& a, cudaStream_t st) {
-  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
-  constexpr int HY = NDIM == 3 ? HX : 0;
-  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
-  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
-  const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1, ntz = (a.nz + CZ - 1) / CZ;
+static cudaError_t launch_sep_t(const SepArgs<T>& a_in, cudaStream_t st) {
+  using G = SepGeom<T, NDIM, HZ, HX>;
+  constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ;
+  const size_t sm = G::SMEM_BYTES;
+  const int ntx = (a_in.nx + CX - 1) / CX, nty = NDIM == 3 ? (a_in.ny + CY - 1) / CY : 1,
+            ntz = (a_in.nz + CZ - 1) / CZ;
+  // TMA staging where the grid spans a staged region in every direction (its periodic images are
+  // then one period away) and the rows are 16-byte multiples; element copies otherwise
+  SepArgs<T> a = a_in;
+  a.use_tma = 0;
+  if (a.nx >= G::PX && a.nz >= G::LZ && (NDIM == 2 || a.ny >= G::LY)) {
+    bool ok = true;
+    for (int c = 0; c < a.ncomp && ok; ++c)
+      ok = tma_encode(&a.tm[c], a.src[c], (int)sizeof(T), NDIM, a.nx, a.ny, a.nz, G::PX, G::LY, G::LZ);
+    a.use_tma = ok ? 1 : 0;
+  }
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_t<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
@@ -325,10 +468,7 @@ int sep_tiles(int ndim, int nx, int ny, int nz) {
 template <typename T, int NDIM, int HZ, int HX>
 static cudaError_t launch_sep_batch_t(const SepArgs<T>* args, const int* tile_base, int nruns, int total_tiles,
                                       int ncomp, cudaStream_t st) {
-  constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY, CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
-  constexpr int HY = NDIM == 3 ? HX : 0;
-  constexpr int LX = CX + 2 * HX, LY = CY + 2 * HY, LZ = CZ + 2 * HZ;
-  const size_t sm = sizeof(T) * ((size_t)LZ * LY * LX + (NDIM == 3 ? (size_t)CZ * CY * LX : 0));
+  const size_t sm = SepGeom<T, NDIM, HZ, HX>::SMEM_BYTES;  // the tables carry use_tma = 0
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_batch<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)total_tiles, (unsigned)ncomp);
@@ -579,22 +719,44 @@ struct YeeHalo {
   static constexpr int HL = CK ? 3 : 1, HB = CK ? 2 : 1, HE = CK ? 1 : 0;
 };
 
+// Staged region of a Yee tile: x from X0 - XAL (HL rounded up to a 16-byte multiple of elements, so
+// that a TMA box starts on a 16-byte boundary) over PX columns, local column OX = XAL - HL holding
+// x = X0 - HL; y from Y0 - 1 over LY, z from Z0 - HL over LZ.
+template <typename T, int NDIM, bool CK>
+struct YeeGeom {
+  static constexpr int HL = YeeHalo<CK>::HL;
+  static constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY;
+  static constexpr int CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
+  static constexpr int AL = 16 / (int)sizeof(T);
+  static constexpr int XAL = (HL + AL - 1) / AL * AL, OX = XAL - HL;
+  static constexpr int PX = (XAL + CX + 2 + AL - 1) / AL * AL;
+  static constexpr int LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + HL + 2;
+  static constexpr size_t BOX_BYTES = sizeof(T) * (size_t)PX * LY * LZ;
+  // arrays spaced by whole 128-byte units: a bulk tensor copy's shared-memory destination must start
+  // on a 128-byte boundary
+  static constexpr int LN = (int)((BOX_BYTES + 127) / 128 * 128 / sizeof(T));
+  static constexpr size_t SMEM_BYTES = 128 + 9 * sizeof(T) * (size_t)LN;
+};
+
 template <typename T, int NDIM, bool CK, bool DIAG>
 __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty,
                                          double* escratch = nullptr, const HistCtl* hc = nullptr) {
   static_assert(!CK || NDIM == 2, "the Cole-Karkkainen curl is built for 2D x-z runs");
+  using G = YeeGeom<T, NDIM, CK>;
   constexpr int HL = YeeHalo<CK>::HL, HB = YeeHalo<CK>::HB, HE = YeeHalo<CK>::HE;
-  constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY, CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
-  constexpr int LX = CX + HL + 2, LY = NDIM == 2 ? 1 : CY + 3, LZ = CZ + HL + 2, LN = LX * LY * LZ;
+  constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ;
+  constexpr int LX = G::PX, LY = G::LY, LZ = G::LZ, LN = G::LN, OX = G::OX;
   constexpr int OY = NDIM == 2 ? 0 : 1;  // local offset of the -1 halo along y
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ __align__(8) unsigned long long mbar;
+  T* sm = reinterpret_cast<T*>(smraw + ((128 - (smem_u32(smraw) & 127)) & 127));
   T* e[3] = {sm, sm + LN, sm + 2 * LN};
   T* b[3] = {sm + 3 * LN, sm + 4 * LN, sm + 5 * LN};
   T* j[3] = {sm + 6 * LN, sm + 7 * LN, sm + 8 * LN};
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
   const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
   const long long nxy = (long long)a.nx * a.ny;
+  const int xs = X0 - G::XAL, ys = NDIM == 3 ? Y0 - 1 : 0, zs = Z0 - HL;
   // wrap_near takes any index, so the halos may wrap around grids smaller than the tile
   auto gsrc = [&](int c) -> const T* {
     switch (c) {
@@ -609,19 +771,43 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
       default: return a.jz;
     }
   };
-  auto stage = [&](auto wrap) {
-    for (int idx = threadIdx.x; idx < 9 * LN; idx += YEE_THREADS) {  // flat: rows are wider than a warp
-      const int c = idx / LN, r3 = idx - c * LN;
-      const int lx = r3 % LX, r2 = r3 / LX;
-      const int ly = r2 % LY, lz = r2 / LY;
-      const int gy = NDIM == 3 ? wrap(Y0 - 1 + ly, a.ny) : 0;
-      const int gz = wrap(Z0 - HL + lz, a.nz);
-      cp_async_el(sm + idx, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap(X0 - HL + lx, a.nx));
+  if (a.use_tma) {
+    // one box per array (periodic images patched below); the host enabled TMA only where the grid
+    // spans the staged region in every direction
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      mbar_expect_tx(&mbar, (unsigned)(9 * G::BOX_BYTES));
+      for (int c = 0; c < 9; ++c) {
+        if (NDIM == 2) tma_load_2d(sm + c * LN, &a.tm[c], xs, zs, &mbar);
+        else tma_load_3d(sm + c * LN, &a.tm[c], xs, ys, zs, &mbar);
+      }
     }
-  };
-  if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
-  else stage(WrapNear{});
-  cp_async_wait_all_fields();
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    const bool ok = __syncthreads_and(mbar_wait(&mbar, 0, TMA_WAIT_POLLS));
+    if (!ok) {  // give up: record it, let the copies land (bounded), and leave the tile unchanged
+      if (threadIdx.x == 0) flag_error(a.err, ERR_TIMEOUT);
+      mbar_wait(&mbar, 0, TMA_WAIT_POLLS);
+      if (DIAG) energy_finish(0.0, 0.0, 0.0, escratch, gridDim.x, nullptr, *hc);
+      return;
+    }
+    for (int c = 0; c < 9; ++c)
+      patch_wrapped<T, NDIM, YEE_THREADS>(sm + c * LN, gsrc(c), xs, ys, zs, LX, LY, LZ, a.nx, a.ny, a.nz);
+  } else {
+    auto stage = [&](auto wrap) {
+      constexpr int NB = LX * LY * LZ;  // staged elements of one array (its padding is not copied)
+      for (int idx = threadIdx.x; idx < 9 * NB; idx += YEE_THREADS) {  // flat: rows are wider than a warp
+        const int c = idx / NB, r3 = idx - c * NB;
+        const int lx = r3 % LX, r2 = r3 / LX;
+        const int ly = r2 % LY, lz = r2 / LY;
+        const int gy = NDIM == 3 ? wrap(ys + ly, a.ny) : 0;
+        const int gz = wrap(zs + lz, a.nz);
+        cp_async_el(sm + c * LN + r3, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap(xs + lx, a.nx));
+      }
+    };
+    if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
+    else stage(WrapNear{});
+    cp_async_wait_all_fields();
+  }
   __syncthreads();
   const int sx = 1, sy = NDIM == 3 ? LX : 0, sz = LX * LY;  // sy = 0 in 2D: y differences vanish
   const T hcx = a.cx * T(0.5), hcy = a.cy * T(0.5), hcz = a.cz * T(0.5);
@@ -638,7 +824,7 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   // each phase walks its cells with one flat index over all threads (rows are wider than a warp)
   for (int idx = threadIdx.x; idx < NY2 * NBZ * NBX; idx += YEE_THREADS) {
     const int q = idx % NBX, row = idx / NBX;
-    const int lx = HL - HB + q, ly = row % NY2, lz = HL - HB + row / NY2;
+    const int lx = OX + HL - HB + q, ly = row % NY2, lz = HL - HB + row / NY2;
     const int l = (lz * LY + ly) * LX + lx;
     if (CK) {
       b[0][l] += hcz * ck_dz(e[1], l);
@@ -656,7 +842,7 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   constexpr int NEX = CX + 1 + HE, NEZ = CZ + 1 + HE;
   for (int idx = threadIdx.x; idx < NY1 * NEZ * NEX; idx += YEE_THREADS) {
     const int q = idx % NEX, row = idx / NEX;
-    const int lx = HL - HE + q, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = HL - HE + row / NY1;
+    const int lx = OX + HL - HE + q, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = HL - HE + row / NY1;
     const int l = (lz * LY + ly) * LX + lx;
     const T bx = b[0][l], by = b[1][l], bz = b[2][l];
     e[0][l] += a.cy * (bz - b[2][l - sy]) - a.cz * (by - b[1][l - sz]) - a.h * j[0][l];
@@ -671,7 +857,7 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     const int cy = row % CY, cz = row / CY;
     const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
     if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-    const int l = ((cz + HL) * LY + cy + OY) * LX + cx + HL;
+    const int l = ((cz + HL) * LY + cy + OY) * LX + cx + HL + OX;
     const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
     T nbx, nby, nbz;
     if (CK) {
@@ -684,12 +870,12 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
       nbz = b[2][l] - (hcx * (e[1][l + sx] - ey) - hcy * (e[0][l + sy] - ex));
     }
     const long long o = gz * nxy + (long long)gy * a.nx + gx;
-    a.ex[o] = ex;
-    a.ey[o] = ey;
-    a.ez[o] = ez;
-    a.bx[o] = nbx;
-    a.by[o] = nby;
-    a.bz[o] = nbz;
+    a.oex[o] = ex;
+    a.oey[o] = ey;
+    a.oez[o] = ez;
+    a.obx[o] = nbx;
+    a.oby[o] = nby;
+    a.obz[o] = nbz;
     if (DIAG) en.add(ex, ey, ez, nbx, nby, nbz);
   }
   if (DIAG) {  // every thread reaches this (the loop above only skips cells)
@@ -723,15 +909,13 @@ int yee_tiles(int ndim, int nx, int ny, int nz) {
 template <typename T>
 cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int nruns, int total_tiles, int ndim,
                              cudaStream_t st) {
-  if (ndim == 2) {
-    constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
-    const size_t sm = sizeof(T) * 9 * LN;
+  if (ndim == 2) {  // the tables carry use_tma = 0: element-copy staging
+    const size_t sm = YeeGeom<T, 2, false>::SMEM_BYTES;
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 2>, sm);
     if (e != cudaSuccess) return e;
     k_yee_batch<T, 2><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
   } else {
-    constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
-    const size_t sm = sizeof(T) * 9 * LN;
+    const size_t sm = YeeGeom<T, 3, false>::SMEM_BYTES;
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 3>, sm);
     if (e != cudaSuccess) return e;
     k_yee_batch<T, 3><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
@@ -749,9 +933,22 @@ size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz) {
 }
 
 template <typename T, int NDIM, bool CK>
-static cudaError_t launch_yee_tiles(const YeeArgs<T>& a, int ntiles, int ntx, int nty, size_t sm, double* escratch,
+static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, int ntiles, int ntx, int nty, double* escratch,
                                     const HistCtl* hc, cudaStream_t st) {
+  using G = YeeGeom<T, NDIM, CK>;
+  const size_t sm = G::SMEM_BYTES;
   const HistCtl none{nullptr, 0, nullptr, nullptr};
+  // TMA staging where the grid spans the staged region in every direction and the rows are 16-byte
+  // multiples; element copies otherwise
+  YeeArgs<T> a = a_in;
+  a.use_tma = 0;
+  if (a.nx >= G::PX && a.nz >= G::LZ && (NDIM == 2 || a.ny >= G::LY)) {
+    const T* src[9] = {a.ex, a.ey, a.ez, a.bx, a.by, a.bz, a.jx, a.jy, a.jz};
+    bool ok = true;
+    for (int c = 0; c < 9 && ok; ++c)
+      ok = tma_encode(&a.tm[c], src[c], (int)sizeof(T), NDIM, a.nx, a.ny, a.nz, G::PX, G::LY, G::LZ);
+    a.use_tma = ok ? 1 : 0;
+  }
   if (hc) {
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, true>, sm);
     if (e != cudaSuccess) return e;
@@ -768,31 +965,43 @@ template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, double* escratch, const HistCtl* hc) {
   if (hc && (!escratch || !yee_records_energy(ndim, a.nx, a.ny, a.nz, a.ck))) return cudaErrorInvalidValue;
   if (ndim == 2 && a.ck) {  // any grid size: the staged halos wrap
-    constexpr int LN = (YEE2_CX + 5) * (YEE2_CZ + 5);
     const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    return launch_yee_tiles<T, 2, true>(a, ntx * ntz, ntx, 1, sizeof(T) * 9 * LN, escratch, hc, st);
+    return launch_yee_tiles<T, 2, true>(a, ntx * ntz, ntx, 1, escratch, hc, st);
   }
   if (a.ck) return cudaErrorInvalidValue;  // 3D CK is not built (pic_create rejects it)
-  if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {  // tiny grids: the three separate updates
-    YeeArgs<T> hb = a;
+  if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {
+    // tiny grids: the inputs copied to the outputs, then the three separate updates in place there
+    const size_t bytes = sizeof(T) * (size_t)a.nx * a.ny * a.nz;
+    const T* in[6] = {a.ex, a.ey, a.ez, a.bx, a.by, a.bz};
+    T* out[6] = {a.oex, a.oey, a.oez, a.obx, a.oby, a.obz};
+    for (int q = 0; q < 6; ++q) {
+      cudaError_t e = cudaMemcpyAsync(out[q], in[q], bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    YeeArgs<T> o = a;
+    o.ex = a.oex;
+    o.ey = a.oey;
+    o.ez = a.oez;
+    o.bx = a.obx;
+    o.by = a.oby;
+    o.bz = a.obz;
+    YeeArgs<T> hb = o;
     hb.cx = a.cx * T(0.5);
     hb.cy = a.cy * T(0.5);
     hb.cz = a.cz * T(0.5);
     hb.h = a.h * T(0.5);
     cudaError_t e = launch_yee_b<T>(hb, st);
-    if (e == cudaSuccess) e = launch_yee_e<T>(a, st);
+    if (e == cudaSuccess) e = launch_yee_e<T>(o, st);
     if (e == cudaSuccess) e = launch_yee_b<T>(hb, st);
     return e;
   }
   if (ndim == 2) {
-    constexpr int LN = (YEE2_CX + 3) * (YEE2_CZ + 3);
     const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    return launch_yee_tiles<T, 2, false>(a, ntx * ntz, ntx, 1, sizeof(T) * 9 * LN, escratch, hc, st);
+    return launch_yee_tiles<T, 2, false>(a, ntx * ntz, ntx, 1, escratch, hc, st);
   }
-  constexpr int LN = (YEE3_CX + 3) * (YEE3_CY + 3) * (YEE3_CZ + 3);
   const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
             ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
-  return launch_yee_tiles<T, 3, false>(a, ntx * nty * ntz, ntx, nty, sizeof(T) * 9 * LN, escratch, hc, st);
+  return launch_yee_tiles<T, 3, false>(a, ntx * nty * ntz, ntx, nty, escratch, hc, st);
 }
 template cudaError_t launch_yee_fused<float>(const YeeArgs<float>&, int, cudaStream_t, double*, const HistCtl*);
 template cudaError_t launch_yee_fused<double>(const YeeArgs<double>&, int, cudaStream_t, double*, const HistCtl*);

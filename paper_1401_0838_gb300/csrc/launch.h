@@ -1,5 +1,6 @@
 // Host-side launchers of the CUDA kernels (internal; the public ABI is include/pic.h).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -30,11 +31,18 @@ struct SepArgs {
   T zt[2][MAX_ZTAPS];
   T xt[MAX_XTAPS];
   T yt[MAX_XTAPS];
+  // TMA staging (set by launch_sep when the grid allows it): one tensor map per source component
+  int use_tma;
+  int* err;  // device error flags (ERR_TIMEOUT when a staging wait gives up)
+  CUtensorMap tm[6];
 };
 
 template <typename T>
 struct YeeArgs {
-  T *ex, *ey, *ez, *bx, *by, *bz;
+  T *ex, *ey, *ez, *bx, *by, *bz;  // fields at the start of the step (the separate updates: in place)
+  // the fused step's output E^{n+1}, B^{n+1}: arrays other than the inputs, because a tile reads
+  // its neighbours' cells as halo while they may already have written theirs
+  T *oex = nullptr, *oey = nullptr, *oez = nullptr, *obx = nullptr, *oby = nullptr, *obz = nullptr;
   const T *jx, *jy, *jz;
   int nx, ny, nz;
   T cx, cy, cz;  // h / d for the curl differences (h = dt or dt/2)
@@ -42,7 +50,18 @@ struct YeeArgs {
   int ck = 0;                // 1: Cole-Karkkainen curl of E in the B updates (2D fused kernel only)
   T wx0 = T(1), wx1 = T(0);  // CK weights of the x differences at z offsets 0 and +-1 (1 - 2 beta_x, beta_x)
   T wz0 = T(1), wz1 = T(0);  // CK weights of the z differences at x offsets 0 and +-1 (1 - 2 beta_z, beta_z)
+  // TMA staging of the fused kernel (set by launch_yee_fused when the grid allows it): tensor maps of
+  // Ex Ey Ez Bx By Bz Jx Jy Jz
+  int use_tma = 0;
+  int* err = nullptr;  // device error flags (ERR_TIMEOUT when a staging wait gives up)
+  CUtensorMap tm[9];
 };
+
+// Tensor map of a periodic field array (x fastest; nx*ny*nz elements of es bytes) for boxes of
+// (bx, by[, bz]) elements: rank 2 for ndim 2 (x, z), 3 for ndim 3. Out-of-range box elements read
+// as zero. Returns false when the layout does not allow TMA (row bytes not a multiple of 16, an
+// unaligned base, a box past the limits) or the driver has no encoder.
+bool tma_encode(CUtensorMap* m, const void* base, int es, int ndim, int nx, int ny, int nz, int bx, int by, int bz);
 
 void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);
 

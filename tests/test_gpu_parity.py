@@ -92,6 +92,29 @@ def test_gather_copies(precision, ndim, nbin, ncomp, calpha, targets):
 
 @pytest.mark.parametrize("precision", [1, 0])
 @pytest.mark.parametrize("ndim", [2, 3])
+def test_step_on_grids_staged_by_tma(precision, ndim):
+    # Grids that span the tiles the stencil and Yee kernels stage by one bulk tensor copy (TMA) in
+    # every direction, with ragged edge tiles (200 = 128 + 72 columns, 100 = 3 x 32 + 4 rows): a box's
+    # elements outside the grid read as zero and are replaced by their periodic images. The copies the
+    # particles see after the first step, then every field and particle after three steps.
+    nx, ny, nz = (200, 1, 100) if ndim == 2 else (48, 16, 24)
+    pair = _random_pair(ndim, precision, nx=nx, ny=ny, nz=nz, npart=8000, sigma=1.0 if ndim == 3 else 0.0)
+    try:
+        expect = pair.o.gather_copies()
+        pair.step(1)
+        outs = [np.zeros(pair.o.shape, dtype=pair.T) for _ in range(6)]
+        P.pic_debug_gather_copies(pair.h, P.PIC_HOST, outs)
+        for c in range(6):
+            assert rel_l2(outs[c], expect[c]) <= TOL[precision], c
+        _compare(pair, TOL[precision])
+        pair.step(2)
+        _compare(pair, TOL[precision])
+    finally:
+        pair.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("ndim", [2, 3])
 def test_yee_vacuum(precision, ndim):
     # field-only steps (no particles, J = 0)
     pair = _random_pair(ndim, precision, npart=0, nx=24, ny=8, nz=40)

@@ -545,7 +545,13 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
       r.in[1].cnt[cell] = 0;
     }
   }
-  if (tid == 0) *lvn = 0;
+  // cell groups after each warp's first one are handed out in the order warps ask for them, so
+  // warps whose groups hold more packs do fewer groups
+  __shared__ int s_next_group;
+  if (tid == 0) {
+    *lvn = 0;
+    s_next_group = PUSH_THREADS / 32;
+  }
   __syncthreads();
 
   T kin = T(0);
@@ -582,10 +588,15 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     if (has_id) copy4_async(SG::id_at(stg, stage, lane), pin.id + slot0);
   };
 
+  auto take_group = [&]() -> int {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(&s_next_group, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
+  };
   int g = warp, it = 0;
   int giters = g < NGRP ? group_iters(g) : 0;
   while (g < NGRP && giters == 0) {
-    g += NWARP;
+    g = take_group();
     giters = g < NGRP ? group_iters(g) : 0;
   }
   int stage = 0;
@@ -599,7 +610,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
     if (nit >= giters) {
       nit = 0;
       do {
-        ng += NWARP;
+        ng = take_group();
         niters = ng < NGRP ? group_iters(ng) : 0;
       } while (ng < NGRP && niters == 0);
     }
@@ -789,9 +800,10 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
             goa = (long long)b0 + __popc(gma & lt);
             gob = (long long)b0 + __popc(gma) + __popc(gmb & lt);
           }
+          const int gcell = gk * r.nx + gi;  // cells < 2^30
           auto place = [&](bool st, bool full, bool lv, bool g, int dk, int jo, int ls, long long go, float nox,
-                           float noz, float ux, float uy, float uz, float w, unsigned id) {
-            const int dcell = st ? (Z0 + (dk >> 1) / TX) * r.nx + X0 + (dk >> 1) % TX : 0;  // cells < 2^30
+                           float noz, float ux, float uy, float uz, float w, unsigned id, int shx, int shz) {
+            const int dcell = gcell + shz * r.nx + shx;  // a cell of this tile when st
             if (st && !full) {
               const long long o = (long long)dcell * r.cap + jo;
               pout.ox[o] = nox;
@@ -816,9 +828,11 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
             }
           };
           if (va)
-            place(sta, fa, lva, ga, dka, ba, lsa, goa, exa.off, eza.off, nuxa, nuya, nuza, wa, has_id ? st_id[ja] : 0u);
+            place(sta, fa, lva, ga, dka, ba, lsa, goa, exa.off, eza.off, nuxa, nuya, nuza, wa, has_id ? st_id[ja] : 0u,
+                  exa.shift, eza.shift);
           if (vb)
-            place(stb, fb, lvb, gb, dkb, bb, lsb, gob, exb.off, ezb.off, nuxb, nuyb, nuzb, wb, has_id ? st_id[jb] : 0u);
+            place(stb, fb, lvb, gb, dkb, bb, lsb, gob, exb.off, ezb.off, nuxb, nuyb, nuzb, wb, has_id ? st_id[jb] : 0u,
+                  exb.shift, ezb.shift);
         }
       } else {
 #pragma unroll 1

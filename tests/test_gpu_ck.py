@@ -172,6 +172,9 @@ def test_ck_growth_rate_matches_oracle(precision):
     tt, lw = t[sel], np.log(np.asarray(w_g)[sel])
     g_same = 0.5 * float(((tt - tt.mean()) * (lw - lw.mean())).sum() / ((tt - tt.mean()) ** 2).sum())
     assert abs(g_same / g_o - 1) < 0.05, (g_same, g_o, (a, b))
+    # and over the window the fit rule picks on the GPU run's own history
+    g_g, c, d = growth_rate(t, w_g)
+    assert abs(g_g / g_o - 1) < 0.05, (g_g, g_o, (a, b), (c, d))
 
 
 @pytest.mark.parametrize("scheme", [0, 1])

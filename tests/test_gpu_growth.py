@@ -56,15 +56,14 @@ def test_growth_rate_matches_oracle(precision):
     g_o, a, b = growth_rate(t, w_o)
     g_g, c, d = growth_rate(t, w_g)
     assert w_o[-1] > 1e3 * w_o[10]  # a clear exponential phase
-    # the late-time growth rate over the same window as the oracle's fit agrees within 5 %; each
-    # run's own automatically chosen window can start a sample earlier or later (the FP32 run's
-    # noise differs at roundoff, and so does the deposit's summation order), which alone moves the
-    # fitted rate by a few percent, so that comparison gets a looser bar
+    # the late-time growth rate agrees within 5 %, both over the oracle's fit window and over the
+    # window the fit rule picks on the GPU run's own history (which may start or end a sample away
+    # at FP32 roundoff; measured on GB300 over seeds 1-3: within 0.3 % either way)
     sel = slice(a, b + 1)
     tt, lw = t[sel], np.log(np.asarray(w_g)[sel])
     g_same = 0.5 * float(((tt - tt.mean()) * (lw - lw.mean())).sum() / ((tt - tt.mean()) ** 2).sum())
     assert abs(g_same / g_o - 1) < 0.05, (g_same, g_o, (a, b))
-    assert abs(g_g / g_o - 1) < 0.10, (g_g, g_o, (a, b), (c, d))
+    assert abs(g_g / g_o - 1) < 0.05, (g_g, g_o, (a, b), (c, d))
     # the library's own fit agrees with the oracle's fit of the same samples
     g_lib, i0, i1 = P.pic_fit_growth_rate(t, w_g)
     assert (i0, i1) == (c, d) and abs(g_lib - g_g) < 1e-12 * abs(g_g)

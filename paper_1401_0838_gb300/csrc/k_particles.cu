@@ -400,18 +400,113 @@ __device__ __noinline__ void deposit3_smem(T* sj, int wx, int wy, int wz, EsirDi
   }
 }
 
+// The sums each lane keeps in registers: the Esirkepov window of a particle that starts in its own
+// cell, does not step back across a face, and does not cross its cell's upper face in x (nor, in
+// 3D, in y). Such a particle's shape changes vanish at the window's third transverse node (S0 and
+// dS are zero there), so its contributions there are exactly zero: of the 3-node window only
+// x nodes 0-1 (2D: 13 of the 21 sums; 3D: y nodes 0-1 too, 20 of the 54) carry it. Every other
+// particle (a transverse face crossed, or a step back) adds its full window to shared memory.
+// 2D layout: 3 Jx (node a = 0, z node c = i), 4 Jz (3 + a*2 + c), 6 Jy (7 + c*2 + a).
+// 3D layout: 6 Jx (a = 0; c*2 + b), 6 Jy (b = 0; 6 + c*2 + a), 8 Jz (12 + (b*2 + a)*2 + c).
+template <int NDIM>
+struct RegLayout;
+template <>
+struct RegLayout<2> {
+  static constexpr int NV = 13;
+  static __device__ __forceinline__ void at(int i, int& comp, int& a, int& b, int& c) {
+    b = 0;
+    if (i < 3) { comp = 0; a = 0; c = i; }
+    else if (i < 7) { comp = 2; a = (i - 3) >> 1; c = (i - 3) & 1; }
+    else { comp = 1; c = (i - 7) >> 1; a = (i - 7) & 1; }
+  }
+};
+template <>
+struct RegLayout<3> {
+  static constexpr int NV = 20;
+  static __device__ __forceinline__ void at(int i, int& comp, int& a, int& b, int& c) {
+    if (i < 6) { comp = 0; a = 0; b = i & 1; c = i >> 1; }
+    else if (i < 12) { const int k = i - 6; comp = 1; b = 0; a = k & 1; c = k >> 1; }
+    else { const int k = i - 12; comp = 2; c = k & 1; a = (k >> 1) & 1; b = k >> 2; }
+  }
+};
+
+// Whether a particle's window fits the register sums (see RegLayout).
+template <typename T, int NDIM>
+__device__ __forceinline__ bool reg_window(const EsirDir<T>& X, const EsirDir<T>& Y, const EsirDir<T>& Z) {
+  if (NDIM == 3) return (X.a | Y.a | Z.a) == 0 && X.dS[2] == T(0) && Y.dS[2] == T(0);
+  return (X.a | Z.a) == 0 && X.dS[2] == T(0);
+}
+
+// The contributions of deposit2 / deposit3 that can be nonzero for such a particle, into the
+// register layout (the same products and sums as the full window).
+template <typename T, int NVP>
+__device__ __forceinline__ void deposit2_reg(T (&acc)[NVP], const EsirDir<T>& X, const EsirDir<T>& Z, T cx, T cy,
+                                             T cz) {
+  const T fx0 = X.S0[0] + T(0.5) * X.dS[0], fx1 = X.S0[1] + T(0.5) * X.dS[1];
+  T fz[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) fz[b] = Z.S0[b] + T(0.5) * Z.dS[b];
+  const T gx0 = cx * X.dS[0];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) acc[b] += gx0 * fz[b];
+  const T gz0 = cz * Z.dS[0], gz1 = -cz * Z.dS[2];
+  acc[3] += gz0 * fx0;
+  acc[4] += gz1 * fx0;
+  acc[5] += gz0 * fx1;
+  acc[6] += gz1 * fx1;
+  const T hx0 = cy * fx0, hx1 = cy * fx1;
+  const T kx0 = cy * X.dS[0] * T(1.0 / 12.0), kx1 = cy * X.dS[1] * T(1.0 / 12.0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    acc[7 + 2 * b] += hx0 * fz[b] + kx0 * Z.dS[b];
+    acc[8 + 2 * b] += hx1 * fz[b] + kx1 * Z.dS[b];
+  }
+}
+
+template <typename T, int NVP>
+__device__ __forceinline__ void deposit3_reg(T (&acc)[NVP], const EsirDir<T>& X, const EsirDir<T>& Y,
+                                             const EsirDir<T>& Z, T cx, T cy, T cz) {
+  T fx[2], fy[2], fz[3], kx[2], ky[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    fx[a] = X.S0[a] + T(0.5) * X.dS[a];
+    fy[a] = Y.S0[a] + T(0.5) * Y.dS[a];
+    kx[a] = X.dS[a] * T(1.0 / 12.0);
+    ky[a] = Y.dS[a] * T(1.0 / 12.0);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fz[c] = Z.S0[c] + T(0.5) * Z.dS[c];
+  const T gx0 = cx * X.dS[0], gy0 = cy * Y.dS[0];
+  const T gz0 = cz * Z.dS[0], gz1 = -cz * Z.dS[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[c * 2 + b] += gx0 * (fy[b] * fz[c] + ky[b] * Z.dS[c]);  // Jx(1/2, b, c)
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) acc[6 + c * 2 + a] += gy0 * (fx[a] * fz[c] + kx[a] * Z.dS[c]);  // Jy(a, 1/2, c)
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {  // Jz(a, b, c + 1/2)
+      const T t = fx[a] * fy[b] + kx[a] * Y.dS[b];
+      acc[12 + (b * 2 + a) * 2 + 0] += gz0 * t;
+      acc[12 + (b * 2 + a) * 2 + 1] += gz1 * t;
+    }
+}
+
 // Work assignment of the push kernel: a warp takes CPW = 32/LPC cells of its tile at a time,
 // LPC lanes per cell. The cell's particles are split into packs of 4 consecutive slots of one
 // species (electron packs first); lane l of the cell takes packs l, l + LPC, ... . Each lane sums
-// the Esirkepov contributions of its particles in registers (all particles whose 3-node window
-// starts at their own cell, which is every particle that does not step back across a cell face);
-// at the end one segmented butterfly transpose-reduction over the cell's LPC lanes leaves
-// PER = NVP/LPC of the cell's NVP (padded) sums in each lane, added to shared memory with distinct
-// addresses. Particles that step back (window origin -1 in some direction) add their
-// contributions to shared memory directly.
+// the Esirkepov contributions of its particles in registers (the window of RegLayout: every
+// particle that neither steps back across a face nor crosses a transverse face); at the end one
+// segmented butterfly transpose-reduction over the cell's LPC lanes leaves PER = NVP/LPC of the
+// cell's NVP (padded) sums in each lane, added to shared memory with distinct addresses. The other
+// particles add their full 3-node window to shared memory directly.
 template <int NDIM, int LPC>
 struct PushPlan {
-  static constexpr int NV = DepLayout<NDIM>::NV;
+  static constexpr int NV = RegLayout<NDIM>::NV;
   static constexpr int PER = (NV + LPC - 1) / LPC;
   static constexpr int NVP = PER * LPC;
   static constexpr int CPW = 32 / LPC;
@@ -736,13 +831,13 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           if (va) {
             const float qw = qs * wa;
             const float cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vya * r.jfy2d;
-            if ((exa.a | eza.a) == 0) deposit2<float, NVP>(acc, exa, eza, cx, cy, cz);
+            if (reg_window<float, 2>(exa, exa, eza)) deposit2_reg<float, NVP>(acc, exa, eza, cx, cy, cz);
             else deposit2_smem<float, NDIM>(sj, lx + exa.a + 1, lz + eza.a + 1, exa, eza, cx, cy, cz);
           }
           if (vb) {
             const float qw = qs * wb;
             const float cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vyb * r.jfy2d;
-            if ((exb.a | ezb.a) == 0) deposit2<float, NVP>(acc, exb, ezb, cx, cy, cz);
+            if (reg_window<float, 2>(exb, exb, ezb)) deposit2_reg<float, NVP>(acc, exb, ezb, cx, cy, cz);
             else deposit2_smem<float, NDIM>(sj, lx + exb.a + 1, lz + ezb.a + 1, exb, ezb, cx, cy, cz);
           }
           // destinations: a cell of this tile (key (cell * 2 + species) in the tile) or, leaving
@@ -894,17 +989,17 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           EsirDir<T> ey_;
           if (NDIM == 3) ey_ = esir_dir(o_y, ddy);
           else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
-          // Esirkepov deposit: summed in registers when the 3-node window starts at the own cell
+          // Esirkepov deposit: summed in registers when the window fits RegLayout
           // (every particle that does not step back across a face), else straight to shared memory
           const T qw = qs * w;
-          const bool own = (ex_.a | ez_.a | (NDIM == 3 ? ey_.a : 0)) == 0;
+          const bool own = reg_window<T, NDIM>(ex_, NDIM == 3 ? ey_ : ex_, ez_);
           if (NDIM == 2) {
             const T cx = qw * r.jfx, cz = qw * r.jfz, cy = qw * vy * r.jfy2d;
-            if (own) deposit2<T, NVP>(acc, ex_, ez_, cx, cy, cz);
+            if (own) deposit2_reg<T, NVP>(acc, ex_, ez_, cx, cy, cz);
             else deposit2_smem<T, NDIM>(sj, lx + ex_.a + 1, lz + ez_.a + 1, ex_, ez_, cx, cy, cz);
           } else {
             const T cx = qw * r.jfx, cy = qw * r.jfy, cz = qw * r.jfz;
-            if (own) deposit3<T, NVP>(acc, ex_, ey_, ez_, cx, cy, cz);
+            if (own) deposit3_reg<T, NVP>(acc, ex_, ey_, ez_, cx, cy, cz);
             else deposit3_smem<T, NDIM>(sj, lx + ex_.a + 1, ly + ey_.a + 1, lz + ez_.a + 1, ex_, ey_, ez_, cx, cy, cz);
           }
           // new cell and offsets
@@ -1032,7 +1127,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
         const int i = sl * PER + m;
         if (i < NV && acc[m] != T(0)) {
           int comp, a, b, c;
-          DepLayout<NDIM>::at(i, comp, a, b, c);
+          RegLayout<NDIM>::at(i, comp, a, b, c);
           atomicAdd(sj + comp * S::JN + okey + (c * S::JY + b) * S::JX + a, acc[m]);
         }
       }

@@ -989,8 +989,8 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           EsirDir<T> ey_;
           if (NDIM == 3) ey_ = esir_dir(o_y, ddy);
           else { ey_.a = 0; ey_.shift = 0; ey_.off = T(0); }
-          // Esirkepov deposit: summed in registers when the window fits RegLayout
-          // (every particle that does not step back across a face), else straight to shared memory
+          // Esirkepov deposit: summed in registers when the window fits RegLayout (no step back across
+          // a face and no transverse crossing), else straight to shared memory
           const T qw = qs * w;
           const bool own = reg_window<T, NDIM>(ex_, NDIM == 3 ? ey_ : ex_, ez_);
           if (NDIM == 2) {

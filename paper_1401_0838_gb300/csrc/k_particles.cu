@@ -22,7 +22,11 @@ struct PTile<3> {
   static constexpr int TX = 8, TY = 8, TZ = 8;
 };
 
-constexpr int PUSH_THREADS = 256;
+// Threads per push block: 8 warps; the 3D FP32 kernel, one block per SM, takes 12 warps.
+template <typename T, int NDIM>
+struct PushThreads {
+  static constexpr int value = (NDIM == 3 && sizeof(T) == 4) ? 384 : 256;
+};
 
 // Per-warp double-buffered stage: [stage][slot][lane][4] for the particle arrays (slots ox oz dux
 // duy duz w in 2D; ox oy oz dux duy duz w in 3D), then [stage][lane][4] ids.
@@ -57,7 +61,7 @@ struct PushSmem {
   static constexpr size_t lv_bytes() { return (size_t)LVB * (7 * sizeof(T) + 2 * sizeof(int)) + 16; }
   static constexpr size_t bytes() {
     return sizeof(T) * (6 * GN + 3 * JN) + sizeof(int) * (4 * NCL) + 16 +
-           sizeof(T) * PushStage<T, NDIM>::per_warp_elems() * (PUSH_THREADS / 32) + 16 + lv_bytes();
+           sizeof(T) * PushStage<T, NDIM>::per_warp_elems() * (PushThreads<T, NDIM>::value / 32) + 16 + lv_bytes();
   }
 };
 
@@ -537,7 +541,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   using PL = PushPlan<NDIM, LPC>;
   constexpr int TX = S::TX, TY = S::TY, NCL = S::NCL;
   constexpr int NV = PL::NV, PER = PL::PER, NVP = PL::NVP, CPW = PL::CPW;
-  constexpr int NWARP = PUSH_THREADS / 32;
+  constexpr int PUSH_THREADS = PushThreads<T, NDIM>::value, NWARP = PUSH_THREADS / 32;
   static_assert(NCL % CPW == 0, "cells per tile must be a multiple of the cells per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);
@@ -1220,7 +1224,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
 
 // One tile per block.
 template <typename T, int NDIM, int SCHEME, int LPC>
-__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
+__global__ void __launch_bounds__(PushThreads<T, NDIM>::value, PushMinBlocks<T, NDIM>::value)
     k_push(const __grid_constant__ RunDev<T> r) {
   push_tile<T, NDIM, SCHEME, LPC>(r, blockIdx.x);
 }
@@ -1230,7 +1234,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
 // shared memory when the run changes. Work-list counter reset: the caller zeroes *queue before the
 // launch.
 template <typename T, int NDIM, int SCHEME, int LPC>
-__global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
+__global__ void __launch_bounds__(PushThreads<T, NDIM>::value, PushMinBlocks<T, NDIM>::value)
     k_push_batch(const RunDev<T>* __restrict__ runs, const int2* __restrict__ items, int nitems, int* queue) {
   __shared__ RunDev<T> rs;
   __shared__ int cur, cur_run;
@@ -1247,7 +1251,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, PushMinBlocks<T, NDIM>::value)
       constexpr int NW = (int)(sizeof(RunDev<T>) / 4);
       const int* src = reinterpret_cast<const int*>(runs + w.x);
       int* dst = reinterpret_cast<int*>(&rs);
-      for (int k = threadIdx.x; k < NW; k += PUSH_THREADS) dst[k] = src[k];
+      for (int k = threadIdx.x; k < NW; k += PushThreads<T, NDIM>::value) dst[k] = src[k];
       __syncthreads();
       if (threadIdx.x == 0) cur_run = w.x;
     }
@@ -1274,7 +1278,7 @@ static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
   auto go = [&](void (*kern)(const RunDev<T>)) -> cudaError_t {
     cudaError_t e = ensure_dynamic_smem((const void*)kern, sm);
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, PUSH_THREADS, sm, st>>>(r);
+    kern<<<ntiles, PushThreads<T, NDIM>::value, sm, st>>>(r);
     return cudaGetLastError();
   };
   if (lpc == 4) return go(k_push<T, NDIM, SCHEME, 4>);
@@ -1301,7 +1305,7 @@ static cudaError_t launch_push_batch_t(const RunDev<T>* runs, const int2* items,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, PUSH_THREADS, sm, st>>>(runs, items, nitems, queue);
+    kern<<<blocks, PushThreads<T, NDIM>::value, sm, st>>>(runs, items, nitems, queue);
     return cudaGetLastError();
   };
   if (lpc == 4) return go(k_push_batch<T, NDIM, SCHEME, 4>);
@@ -1337,7 +1341,8 @@ int push_max_blocks_per_sm(int ndim, int scheme, int lpc) {
     k = scheme == 0 ? (lpc == 4 ? (const void*)k_push_batch<T, 3, 0, 4> : lpc == 8 ? (const void*)k_push_batch<T, 3, 0, 8> : (const void*)k_push_batch<T, 3, 0, 16>)
                     : (lpc == 4 ? (const void*)k_push_batch<T, 3, 1, 4> : lpc == 8 ? (const void*)k_push_batch<T, 3, 1, 8> : (const void*)k_push_batch<T, 3, 1, 16>);
   if (ensure_dynamic_smem(k, sm) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, PUSH_THREADS, sm) != cudaSuccess || n < 1) return 1;
+  const int nt = ndim == 2 ? PushThreads<T, 2>::value : PushThreads<T, 3>::value;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nt, sm) != cudaSuccess || n < 1) return 1;
   return n;
 }
 template int push_max_blocks_per_sm<float>(int, int, int);

@@ -25,6 +25,7 @@ struct pic_handle {
   long long ncell = 0;
   int cap = 0;
   int ntx = 1, nty = 1, ntz = 1;
+  int tex = 16, tey = 1, tez = 16;  // cells per particle tile and direction
   double u0 = 0, w0 = 0;
   bool has_w = false, has_id = false;
   std::vector<void*> allocs;
@@ -294,6 +295,18 @@ void rebuild_taps(pic_handle* h) {
   h->xt_j = Fj;
 }
 
+// Particle tiles of the run's grid (push_tiles), spread over up to `spread` blocks.
+static void set_tiles(pic_handle* h, int spread) {
+  int nt[3], te[3];
+  push_tiles(h->cfg.ndim, h->cfg.nx, h->cfg.ny, h->cfg.nz, spread, nt, te);
+  h->ntx = nt[0];
+  h->nty = nt[1];
+  h->ntz = nt[2];
+  h->tex = te[0];
+  h->tey = te[1];
+  h->tez = te[2];
+}
+
 template <typename T>
 RunDev<T> make_run(pic_handle* h, int parity) {
   RunDev<T> r;
@@ -307,6 +320,9 @@ RunDev<T> make_run(pic_handle* h, int parity) {
   r.ntx = h->ntx;
   r.nty = h->nty;
   r.ntz = h->ntz;
+  r.tex = h->tex;
+  r.tey = h->tey;
+  r.tez = h->tez;
   r.cap = h->cap;
   r.scheme = c.scheme;
   r.dtdx = (T)(c.dt / c.dx);
@@ -954,7 +970,13 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   h->cfg = c;
   h->es = c.precision == PIC_FP32 ? 4 : 8;
   h->ncell = (long long)c.nx * c.ny * c.nz;
-  push_tiles(c.ndim, c.nx, c.ny, c.nz, &h->ntx, &h->nty, &h->ntz);
+  {
+    // a grid of few tiles takes smaller ones, spread over the SMs
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 0;
+    set_tiles(h, nsm);
+  }
   h->u0 = sqrt(c.gamma * c.gamma - 1.0);
   const double wp = c.omega_p_dz / c.dz;
   h->w0 = c.ppc_per_species > 0 ? wp * wp * c.dx * c.dy * c.dz / (2.0 * c.ppc_per_species) : 0.0;
@@ -1708,6 +1730,7 @@ int pic_batch_create(const pic_config* cfgs, int nruns, pic_batch** out) {
     if (rc == PIC_OK) {
       b->runs.push_back(h);
       h->stream = b->stream;
+      set_tiles(h, 0);  // the sweep fills the GPU with many runs: full tiles
     }
   }
   if (rc != PIC_OK) {

@@ -62,6 +62,7 @@ struct RunDev {
   int ndim, nx, ny, nz;
   long long ncell;
   int ntx, nty, ntz;  // particle tiles per direction
+  int tex, tey, tez;  // cells per particle tile and direction (at most the kernel's tile; origins at multiples)
   int cap;            // slots per cell per species
   int scheme;         // 0 Galerkin, 1 Uniform, 2 momentum-conserving
   T dtdx, dtdy, dtdz; // dt / d (grid units per unit velocity)

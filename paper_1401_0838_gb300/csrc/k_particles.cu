@@ -563,8 +563,9 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
   const int tix = tile % r.ntx;
   const int tiy = (tile / r.ntx) % r.nty;
   const int tiz = tile / (r.ntx * r.nty);
-  const int X0 = tix * S::TX, Y0 = tiy * S::TY, Z0 = tiz * S::TZ;
-  const int wx = min(S::TX, r.nx - X0), wy = min(S::TY, r.ny - Y0), wz = min(S::TZ, r.nz - Z0);
+  // the run's tile extents (r.tex <= TX ...): cells past them stay empty, as at the grid's edge
+  const int X0 = tix * r.tex, Y0 = tiy * r.tey, Z0 = tiz * r.tez;
+  const int wx = min(r.tex, r.nx - X0), wy = min(r.tey, r.ny - Y0), wz = min(r.tez, r.nz - Z0);
   const long long nxy = (long long)r.nx * r.ny;
 
   const bool has_w = r.in[0].w != nullptr;
@@ -1349,15 +1350,33 @@ template int push_max_blocks_per_sm<float>(int, int, int);
 template int push_max_blocks_per_sm<double>(int, int, int);
 template cudaError_t launch_push<double>(const RunDev<double>&, int, cudaStream_t);
 
-void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz) {
+void push_tiles(int ndim, int nx, int ny, int nz, int spread, int nt[3], int te[3]) {
+  const int n[3] = {nx, ndim == 3 ? ny : 1, nz};
   if (ndim == 2) {
-    *ntx = (nx + PTile<2>::TX - 1) / PTile<2>::TX;
-    *nty = 1;
-    *ntz = (nz + PTile<2>::TZ - 1) / PTile<2>::TZ;
+    te[0] = PTile<2>::TX;
+    te[1] = 1;
+    te[2] = PTile<2>::TZ;
   } else {
-    *ntx = (nx + PTile<3>::TX - 1) / PTile<3>::TX;
-    *nty = (ny + PTile<3>::TY - 1) / PTile<3>::TY;
-    *ntz = (nz + PTile<3>::TZ - 1) / PTile<3>::TZ;
+    te[0] = PTile<3>::TX;
+    te[1] = PTile<3>::TY;
+    te[2] = PTile<3>::TZ;
+  }
+  auto count = [&]() {
+    long long t = 1;
+    for (int d = 0; d < 3; ++d) {
+      nt[d] = (n[d] + te[d] - 1) / te[d];
+      t *= nt[d];
+    }
+    return t;
+  };
+  long long tiles = count();
+  while (spread > 0 && 2 * tiles <= spread) {
+    int d = -1;  // the longest extent above 4 that still splits the grid further
+    for (int k = 0; k < 3; ++k)
+      if (te[k] > 4 && n[k] > te[k] / 2 && (d < 0 || te[k] > te[d])) d = k;
+    if (d < 0) break;
+    te[d] /= 2;
+    tiles = count();
   }
 }
 

@@ -175,19 +175,18 @@ struct HoTileRef {
   int X0, Y0, Z0, wx, wy, wz, nxy;
 };
 
-template <int NDIM>
-__device__ __forceinline__ HoTileRef ho_tile(const int ntx, const int nty, const int nx, const int ny, const int nz) {
-  using TL = HoTile<NDIM>;
+template <typename T>
+__device__ __forceinline__ HoTileRef ho_tile(const RunDev<T>& r) {
   const int tile = blockIdx.x;
-  const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
-  HoTileRef t;
-  t.X0 = tix * TL::TX;
-  t.Y0 = tiy * TL::TY;
-  t.Z0 = tiz * TL::TZ;
-  t.wx = min(TL::TX, nx - t.X0);
-  t.wy = min(TL::TY, ny - t.Y0);
-  t.wz = min(TL::TZ, nz - t.Z0);
-  t.nxy = nx * ny;  // cells < 2^30
+  const int tix = tile % r.ntx, tiy = (tile / r.ntx) % r.nty, tiz = tile / (r.ntx * r.nty);
+  HoTileRef t;  // the run's tile extents are at most HoTile's; cells past them stay empty
+  t.X0 = tix * r.tex;
+  t.Y0 = tiy * r.tey;
+  t.Z0 = tiz * r.tez;
+  t.wx = min(r.tex, r.nx - t.X0);
+  t.wy = min(r.tey, r.ny - t.Y0);
+  t.wz = min(r.tez, r.nz - t.Z0);
+  t.nxy = r.nx * r.ny;  // cells < 2^30
   return t;
 }
 
@@ -345,7 +344,7 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
   int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);  // [species][cell] input counts
   int* scnt = sn + 2 * NCL;                          // [species][cell] output counts
   const int tid = threadIdx.x;
-  const HoTileRef tr = ho_tile<NDIM>(r.ntx, r.nty, r.nx, r.ny, r.nz);
+  const HoTileRef tr = ho_tile(r);
   const int X0 = tr.X0, Y0 = tr.Y0, Z0 = tr.Z0, wx = tr.wx, wy = tr.wy, wz = tr.wz;
   ho_prologue<T, NDIM, ORDER, SCHEME>(r, tr, sg, sj, sn, scnt);
   const bool has_w = r.in[0].w != nullptr, has_id = r.in[0].id != nullptr;
@@ -561,7 +560,7 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant
   int* sn = reinterpret_cast<int*>(sj + 3 * G::JN);
   int* scnt = sn + 2 * NCL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const HoTileRef tr = ho_tile<2>(r.ntx, r.nty, r.nx, r.ny, r.nz);
+  const HoTileRef tr = ho_tile(r);
   const int X0 = tr.X0, Z0 = tr.Z0, wx = tr.wx, wz = tr.wz;
   ho_prologue<T, 2, ORDER, SCHEME>(r, tr, sg, sj, sn, scnt);
   const bool has_w = r.in[0].w != nullptr, has_id = r.in[0].id != nullptr;

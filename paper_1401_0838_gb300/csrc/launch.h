@@ -63,7 +63,10 @@ struct YeeArgs {
 // unaligned base, a box past the limits) or the driver has no encoder.
 bool tma_encode(CUtensorMap* m, const void* base, int es, int ndim, int nx, int ny, int nz, int bx, int by, int bz);
 
-void push_tiles(int ndim, int nx, int ny, int nz, int* ntx, int* nty, int* ntz);
+// Particle tiles of a grid: the kernels' tile (16x16 in 2D, 8x8x8 in 3D), halved (down to 4 cells,
+// the longest extent first) while twice the tiles still fit in `spread` blocks, so that a small grid
+// spreads over the SMs. spread = 0 keeps the full tile. te: cells per tile and direction.
+void push_tiles(int ndim, int nx, int ny, int nz, int spread, int nt[3], int te[3]);
 
 // Raise a kernel's dynamic shared memory limit to `bytes` (once per kernel and size).
 cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);

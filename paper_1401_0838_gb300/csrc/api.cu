@@ -26,6 +26,7 @@ struct pic_handle {
   int cap = 0;
   int ntx = 1, nty = 1, ntz = 1;
   int tex = 16, tey = 1, tez = 16;  // cells per particle tile and direction
+  int nsm = 0;                       // the device's SMs: small grids spread their tiles over them
   double u0 = 0, w0 = 0;
   bool has_w = false, has_id = false;
   std::vector<void*> allocs;
@@ -393,6 +394,7 @@ SepArgs<T> sep_args(pic_handle* h, bool copies) {
   a.nz = c.nz;
   a.ndim = c.ndim;
   a.err = h->d_err;
+  a.spread = h->nsm;
   auto put = [](T* dst, const std::vector<double>& v) {
     for (size_t i = 0; i < v.size(); ++i) dst[i] = (T)v[i];
   };
@@ -456,6 +458,7 @@ YeeArgs<T> yee_args(pic_handle* h, double hstep) {
   a.cz = (T)(hstep / c.dz);
   a.h = (T)hstep;
   a.err = h->d_err;
+  a.spread = h->nsm;
   if (c.field_solver == PIC_CK) {
     a.ck = 1;
     a.wx0 = (T)(1.0 - 2.0 * c.ck_beta_x);
@@ -975,6 +978,7 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       nsm = 0;
+    h->nsm = nsm;
     set_tiles(h, nsm);
   }
   h->u0 = sqrt(c.gamma * c.gamma - 1.0);
@@ -1028,8 +1032,8 @@ int pic_create(const pic_config* cfg_in, pic_handle** out) {
   if (ok) ok = (h->d_acc = (double*)dalloc(h, 8 * sizeof(double))) != nullptr;
   if (ok) ok = (h->d_red = (double*)dalloc(h, field_energy_scratch_bytes())) != nullptr;
   if (ok) ok = cudaMemset(h->d_red, 0, field_energy_scratch_bytes()) == cudaSuccess;
-  if (ok) ok = (h->d_red_yee = (double*)dalloc(h, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz))) != nullptr;
-  if (ok) ok = cudaMemset(h->d_red_yee, 0, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz)) == cudaSuccess;
+  if (ok) ok = (h->d_red_yee = (double*)dalloc(h, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz, h->nsm))) != nullptr;
+  if (ok) ok = cudaMemset(h->d_red_yee, 0, yee_energy_scratch_bytes(c.ndim, c.nx, c.ny, c.nz, h->nsm)) == cudaSuccess;
   if (ok) ok = (h->d_offs = (long long*)dalloc(h, sizeof(long long) * h->ncell)) != nullptr;
   if (ok) ok = (h->d_bsum = (long long*)dalloc(h, sizeof(long long) * (count_prefix_blocks(h->ncell) + 1))) != nullptr;
   if (ok) ok = (h->d_total = (long long*)dalloc(h, 4 * sizeof(long long))) != nullptr;

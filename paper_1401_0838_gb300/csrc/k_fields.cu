@@ -214,6 +214,47 @@ cudaError_t launch_sep_generic(const SepArgs<T>& a, cudaStream_t st) {
 // Staged x range of a tile: from X0 - XA to X0 + CX + XA, XA = HX rounded up to a 16-byte multiple
 // of elements, so that the start of every staged row (and a TMA box's x coordinate) is 16-byte
 // aligned when X0 is; the stencil reads the columns from XA - HX on.
+// An int known at compile time, passed where a runtime extent is otherwise taken.
+template <int V>
+struct CInt {
+  __host__ __device__ constexpr operator int() const { return V; }
+};
+
+// Tile extents of a field kernel over a grid n: the kernel's tile c, halved along z, then x, then y
+// (each not below lo) while twice the blocks (tiles x mult) still fit in `spread`; a halving that
+// adds no tile is skipped. spread = 0 keeps c. e: cells per tile; nt: tiles per direction.
+static long long field_tiles(const int n[3], const int c[3], const int lo[3], int mult, int spread, int e[3],
+                             int nt[3]) {
+  for (int d = 0; d < 3; ++d) e[d] = c[d];
+  auto count = [&]() {
+    long long t = 1;
+    for (int d = 0; d < 3; ++d) {
+      nt[d] = (n[d] + e[d] - 1) / e[d];
+      t *= nt[d];
+    }
+    return t;
+  };
+  long long tiles = count();
+  const int order[3] = {2, 0, 1};
+  for (int k = 0; k < 3 && spread > 0 && 2 * tiles * mult <= spread;) {
+    const int d = order[k];
+    if (e[d] / 2 < lo[d]) {
+      ++k;
+      continue;
+    }
+    e[d] /= 2;
+    const long long t2 = count();
+    if (t2 == tiles) {  // no more tiles along d: undo, next direction
+      e[d] *= 2;
+      count();
+      ++k;
+      continue;
+    }
+    tiles = t2;
+  }
+  return tiles;
+}
+
 template <typename T, int HX>
 struct SepPitch {
   static constexpr int AL = 16 / (int)sizeof(T);
@@ -272,7 +313,7 @@ __device__ __forceinline__ void patch_wrapped(T* s0, const T* __restrict__ src, 
 
 template <typename T, int NDIM, int HZ, int HX>
 __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, const int comp, const int ntx,
-                                         const int nty) {
+                                         const int nty, const int ex, const int ey, const int ez) {
   using G = SepGeom<T, NDIM, HZ, HX>;
   constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ, HY = G::HY, XA = G::XA;
   constexpr int PX = G::PX, LY = G::LY, LZ = G::LZ;
@@ -289,8 +330,16 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
   const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
   const bool zero_j = comp == 0 && a.zero[0] != nullptr;
-  const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
+  // tiles of ex * ey * ez cells (at most the compile-time tile); this one writes wx * wy * wz of them
+  const int X0 = tix * ex, Y0 = tiy * ey, Z0 = tiz * ez;
+  const int wx = min(ex, a.nx - X0), wy = NDIM == 3 ? min(ey, a.ny - Y0) : 1, wz = min(ez, a.nz - Z0);
   const long long nxy = (long long)a.nx * a.ny;
+  // z pass tasks: (x, y) columns of the staged tile that the y and x passes read, times segments of
+  // ZS output rows covering the wz written ones
+  constexpr int C0 = XA - HX, NSEG = NDIM == 2 ? 2 : 1, ZS = CZ / NSEG;
+  static_assert(CZ % NSEG == 0, "z segments must tile the output rows");
+  const int ncx = wx + 2 * HX, ncy = NDIM == 3 ? wy + 2 * HY : 1;
+  const int nseg = (wz + ZS - 1) / ZS, rows_staged = min(LZ, nseg * ZS + 2 * HZ);
   T zt[2 * HZ + 1], xt[2 * HX + 1], yt[2 * HY + 1];
 #pragma unroll
   for (int m = 0; m <= 2 * HZ; ++m) zt[m] = a.zt[zs][m];
@@ -318,13 +367,15 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
     }
     patch_wrapped<T, NDIM, SEP_THREADS>(s0, src, xs, ys, zs0, PX, LY, LZ, a.nx, a.ny, a.nz);
   } else {
-    auto stage = [&](auto wrap) {
-      for (int row = ty; row < LZ * LY; row += TYN) {
+    auto stage = [&](auto wrap) {  // the rows and columns the passes read
+      for (int row = ty; row < rows_staged * LY; row += TYN) {
         const int ly = row % LY, lz = row / LY;
+        if (ly >= ncy) continue;
         const int gy = NDIM == 3 ? wrap(ys + ly, a.ny) : 0;
         const int gz = wrap(zs0 + lz, a.nz);
         const T* srow = src + gz * nxy + (long long)gy * a.nx;
-        for (int lx = tx; lx < PX; lx += TXN) cp_async_el(s0 + row * PX + lx, srow + wrap(xs + lx, a.nx));
+        for (int lx = C0 + tx; lx < C0 + ncx; lx += TXN)
+          cp_async_el(s0 + row * PX + lx, srow + wrap(xs + lx, a.nx));
       }
     };
     if (a.nx >= PX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
@@ -332,78 +383,86 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
     cp_async_wait_all_fields();
   }
   __syncthreads();
-  // z pass in place. A task is one (x, y) column of the staged tile and a segment of ZS output rows;
-  // it reads its ZS + 2 HZ inputs into registers before any task of its round writes, and a column's
-  // segment 0 (rows [0, ZS + 2 HZ) read, [0, ZS) written) always runs in a round no later than its
-  // segment 1 (rows [ZS, 2 ZS + 2 HZ) read), so no task reads a row that another has overwritten.
-  // The columns before XA - HX and past CX + XA + HX are staged for alignment only and skipped.
-  {
-    constexpr int C0 = XA - HX, NX = CX + 2 * HX;
-    constexpr int NCOL = NX * LY, NSEG = NDIM == 2 ? 2 : 1, ZS = CZ / NSEG, NTASK = NCOL * NSEG;
-    static_assert(CZ % NSEG == 0, "z segments must tile the output rows");
-    for (int t0 = 0; t0 < NTASK; t0 += SEP_THREADS) {
-      const int t = t0 + threadIdx.x;
-      const bool act = t < NTASK;
-      const int col = t % NCOL, seg = t / NCOL;
-      T* base = s0 + seg * ZS * LY * PX + (col / NX) * PX + C0 + col % NX;
-      T w[ZS + 2 * HZ];
-      if (act) {
+  // the passes, on the written extent: compile-time constants for a full tile (constant divisions
+  // and loop bounds), the tile's own extents otherwise
+  auto passes = [&](auto wx_, auto wy_, auto wz_) {
+    // z pass in place. A task is one (x, y) column of the staged tile and a segment of ZS output rows;
+    // it reads its ZS + 2 HZ inputs into registers before any task of its round writes, and a column's
+    // segment 0 (rows [0, ZS + 2 HZ) read, [0, ZS) written) always runs in a round no later than its
+    // segment 1 (rows [ZS, 2 ZS + 2 HZ) read), so no task reads a row that another has overwritten.
+    // The columns before XA - HX and past wx + XA + HX are staged for alignment only (or not at all)
+    // and skipped; rows past wz are not computed.
+    {
+      const int ncx = wx_ + 2 * HX, ncy = NDIM == 3 ? wy_ + 2 * HY : 1, nseg = (wz_ + ZS - 1) / ZS;
+      const int ncol = ncx * ncy, ntask = ncol * nseg;
+      for (int t0 = 0; t0 < ntask; t0 += SEP_THREADS) {
+        const int t = t0 + threadIdx.x;
+        const bool act = t < ntask;
+        const int col = t % ncol, seg = t / ncol;
+        T* base = s0 + seg * ZS * LY * PX + (col / ncx) * PX + C0 + col % ncx;
+        T w[ZS + 2 * HZ];
+        if (act) {
 #pragma unroll
-        for (int m = 0; m < ZS + 2 * HZ; ++m) w[m] = base[m * LY * PX];
+          for (int m = 0; m < ZS + 2 * HZ; ++m) w[m] = base[m * LY * PX];
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+          for (int r = 0; r < ZS; ++r) {
+            if (seg * ZS + r >= wz_) break;
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * w[r + m];
+            base[r * LY * PX] = acc;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      if (act) {
-#pragma unroll
-        for (int r = 0; r < ZS; ++r) {
+    }
+    const T* sx = s1;
+    if (NDIM == 3) {  // y pass
+      for (int row = ty; row < CZ * CY; row += TYN) {
+        const int ly = row % CY, lz = row / CY;
+        if (ly >= wy_ || lz >= wz_) continue;
+        for (int lx = XA - HX + tx; lx < XA + HX + wx_; lx += TXN) {
+          const T* p = s1 + (lz * LY + ly) * PX + lx;
           T acc = T(0);
 #pragma unroll
-          for (int m = 0; m <= 2 * HZ; ++m) acc += zt[m] * w[r + m];
-          base[r * LY * PX] = acc;
+          for (int m = 0; m <= 2 * HY; ++m) acc += yt[m] * p[m * PX];
+          s2[row * PX + lx] = acc;
         }
       }
       __syncthreads();
+      sx = s2;
     }
-  }
-  const T* sx = s1;
-  if (NDIM == 3) {  // y pass
-    for (int row = ty; row < CZ * CY; row += TYN) {
+    for (int row = ty; row < CZ * CY; row += TYN) {  // x pass -> global
       const int ly = row % CY, lz = row / CY;
-      for (int lx = XA - HX + tx; lx < XA + HX + CX; lx += TXN) {
-        const T* p = s1 + (lz * LY + ly) * PX + lx;
+      if (ly >= wy_ || lz >= wz_) continue;
+      const int gy = Y0 + ly, gz = Z0 + lz;
+      for (int lx = tx; lx < wx_; lx += TXN) {
+        const int gx = X0 + lx;
+        const T* p = sx + row * PX + XA - HX + lx;
         T acc = T(0);
 #pragma unroll
-        for (int m = 0; m <= 2 * HY; ++m) acc += yt[m] * p[m * PX];
-        s2[row * PX + lx] = acc;
+        for (int m = 0; m <= 2 * HX; ++m) acc += xt[m] * p[m];
+        const long long o = gz * nxy + (long long)gy * a.nx + gx;
+        dst[o] = acc;
+        if (zero_j) {
+          a.zero[0][o] = T(0);
+          a.zero[1][o] = T(0);
+          a.zero[2][o] = T(0);
+        }
       }
     }
-    __syncthreads();
-    sx = s2;
-  }
-  for (int row = ty; row < CZ * CY; row += TYN) {  // x pass -> global
-    const int ly = row % CY, lz = row / CY;
-    const int gy = Y0 + ly, gz = Z0 + lz;
-    if (gz >= a.nz || (NDIM == 3 && gy >= a.ny)) continue;
-    for (int lx = tx; lx < CX; lx += TXN) {
-      const int gx = X0 + lx;
-      if (gx >= a.nx) continue;
-      const T* p = sx + row * PX + XA - HX + lx;
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m <= 2 * HX; ++m) acc += xt[m] * p[m];
-      const long long o = gz * nxy + (long long)gy * a.nx + gx;
-      dst[o] = acc;
-      if (zero_j) {
-        a.zero[0][o] = T(0);
-        a.zero[1][o] = T(0);
-        a.zero[2][o] = T(0);
-      }
-    }
-  }
+  };
+  if (wx == CX && wy == CY && wz == CZ) passes(CInt<CX>{}, CInt<CY>{}, CInt<CZ>{});
+  else passes(wx, wy, wz);
 }
 
 template <typename T, int NDIM, int HZ, int HX>
-__global__ void __launch_bounds__(SEP_THREADS) k_sep_t(const __grid_constant__ SepArgs<T> a, int ntx, int nty) {
-  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x, blockIdx.y, ntx, nty);
+__global__ void __launch_bounds__(SEP_THREADS) k_sep_t(const __grid_constant__ SepArgs<T> a, int ntx, int nty,
+                                                       int ex, int ey, int ez) {
+  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x, blockIdx.y, ntx, nty, ex, ey, ez);
 }
 
 // Run of a flat tile index: largest r with tile_base[r] <= t.
@@ -420,10 +479,11 @@ template <typename T, int NDIM, int HZ, int HX>
 __global__ void __launch_bounds__(SEP_THREADS) k_sep_batch(const SepArgs<T>* __restrict__ args,
                                                            const int* __restrict__ tile_base, int nruns) {
   constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY;
+  constexpr int CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const SepArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
-  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x - tile_base[run], blockIdx.y, ntx, nty);
+  sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x - tile_base[run], blockIdx.y, ntx, nty, CX, CY, CZ);
 }
 
 template <typename T, int NDIM, int HZ, int HX>
@@ -431,8 +491,12 @@ static cudaError_t launch_sep_t(const SepArgs<T>& a_in, cudaStream_t st) {
   using G = SepGeom<T, NDIM, HZ, HX>;
   constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ;
   const size_t sm = G::SMEM_BYTES;
-  const int ntx = (a_in.nx + CX - 1) / CX, nty = NDIM == 3 ? (a_in.ny + CY - 1) / CY : 1,
-            ntz = (a_in.nz + CZ - 1) / CZ;
+  // a small grid's tiles shrink (z first, down to 8 rows in 2D; x not below a warp's 32 columns)
+  const int n[3] = {a_in.nx, a_in.ny, a_in.nz}, c[3] = {CX, CY, CZ};
+  const int lo[3] = {32, NDIM == 3 ? 2 : 1, NDIM == 3 ? 2 : 8};
+  int te[3], nt[3];
+  field_tiles(n, c, lo, a_in.ncomp, a_in.spread, te, nt);
+  const int ntx = nt[0], nty = nt[1], ntz = nt[2];
   // TMA staging where the grid spans a staged region in every direction (its periodic images are
   // then one period away) and the rows are 16-byte multiples; element copies otherwise
   SepArgs<T> a = a_in;
@@ -446,7 +510,7 @@ static cudaError_t launch_sep_t(const SepArgs<T>& a_in, cudaStream_t st) {
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_t<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
-  k_sep_t<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(a, ntx, nty);
+  k_sep_t<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2]);
   return cudaGetLastError();
 }
 
@@ -740,11 +804,11 @@ struct YeeGeom {
 
 template <typename T, int NDIM, bool CK, bool DIAG>
 __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, const int ntx, const int nty,
-                                         double* escratch = nullptr, const HistCtl* hc = nullptr) {
+                                         const int ex, const int ey, const int ez, double* escratch = nullptr,
+                                         const HistCtl* hc = nullptr) {
   static_assert(!CK || NDIM == 2, "the Cole-Karkkainen curl is built for 2D x-z runs");
   using G = YeeGeom<T, NDIM, CK>;
   constexpr int HL = YeeHalo<CK>::HL, HB = YeeHalo<CK>::HB, HE = YeeHalo<CK>::HE;
-  constexpr int CX = G::CX, CY = G::CY, CZ = G::CZ;
   constexpr int LX = G::PX, LY = G::LY, LZ = G::LZ, LN = G::LN, OX = G::OX;
   constexpr int OY = NDIM == 2 ? 0 : 1;  // local offset of the -1 halo along y
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -754,7 +818,9 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   T* b[3] = {sm + 3 * LN, sm + 4 * LN, sm + 5 * LN};
   T* j[3] = {sm + 6 * LN, sm + 7 * LN, sm + 8 * LN};
   const int tix = tile % ntx, tiy = (tile / ntx) % nty, tiz = tile / (ntx * nty);
-  const int X0 = tix * CX, Y0 = tiy * CY, Z0 = tiz * CZ;
+  // tiles of ex * ey * ez cells (at most the compile-time tile); this one updates wx * wy * wz of them
+  const int X0 = tix * ex, Y0 = tiy * ey, Z0 = tiz * ez;
+  const int wx = min(ex, a.nx - X0), wy = NDIM == 3 ? min(ey, a.ny - Y0) : 1, wz = min(ez, a.nz - Z0);
   const long long nxy = (long long)a.nx * a.ny;
   const int xs = X0 - G::XAL, ys = NDIM == 3 ? Y0 - 1 : 0, zs = Z0 - HL;
   // wrap_near takes any index, so the halos may wrap around grids smaller than the tile
@@ -794,14 +860,17 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
       patch_wrapped<T, NDIM, YEE_THREADS>(sm + c * LN, gsrc(c), xs, ys, zs, LX, LY, LZ, a.nx, a.ny, a.nz);
   } else {
     auto stage = [&](auto wrap) {
-      constexpr int NB = LX * LY * LZ;  // staged elements of one array (its padding is not copied)
-      for (int idx = threadIdx.x; idx < 9 * NB; idx += YEE_THREADS) {  // flat: rows are wider than a warp
-        const int c = idx / NB, r3 = idx - c * NB;
-        const int lx = r3 % LX, r2 = r3 / LX;
-        const int ly = r2 % LY, lz = r2 / LY;
+      // the region the phases read: columns [0, XAL + wx + 2), y rows [0, wy + 3), z rows [0, wz + HL + 2)
+      const int nbx = G::XAL + wx + 2, nby = NDIM == 3 ? wy + 3 : 1, nbz = wz + HL + 2;
+      const int nb = nbx * nby * nbz;
+      for (int idx = threadIdx.x; idx < 9 * nb; idx += YEE_THREADS) {  // flat: rows are wider than a warp
+        const int c = idx / nb, r3 = idx - c * nb;
+        const int lx = r3 % nbx, r2 = r3 / nbx;
+        const int ly = r2 % nby, lz = r2 / nby;
         const int gy = NDIM == 3 ? wrap(ys + ly, a.ny) : 0;
         const int gz = wrap(zs + lz, a.nz);
-        cp_async_el(sm + c * LN + r3, gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap(xs + lx, a.nx));
+        cp_async_el(sm + c * LN + (lz * LY + ly) * LX + lx,
+                    gsrc(c) + gz * nxy + (long long)gy * a.nx + wrap(xs + lx, a.nx));
       }
     };
     if (a.nx >= LX && a.nz >= LZ && (NDIM == 2 || a.ny >= LY)) stage(WrapOnce{});
@@ -818,13 +887,13 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
   auto ck_dx = [&](const T* f, int l) -> T {
     return a.wx0 * (f[l + 1] - f[l]) + a.wx1 * ((f[l + 1 - sz] - f[l - sz]) + (f[l + 1 + sz] - f[l + sz]));
   };
-  // B^{n+1/2} on cells [-HB, C+1) in x and z ([-1, C+1) in y)
-  constexpr int NY2 = NDIM == 3 ? CY + 2 : 1, NY1 = NDIM == 3 ? CY + 1 : 1;
-  constexpr int NBX = CX + 1 + HB, NBZ = CZ + 1 + HB;
+  // B^{n+1/2} on cells [-HB, w+1) in x and z ([-1, w+1) in y)
+  const int ny2 = NDIM == 3 ? wy + 2 : 1, ny1 = NDIM == 3 ? wy + 1 : 1;
+  const int nbx = wx + 1 + HB, nbz = wz + 1 + HB;
   // each phase walks its cells with one flat index over all threads (rows are wider than a warp)
-  for (int idx = threadIdx.x; idx < NY2 * NBZ * NBX; idx += YEE_THREADS) {
-    const int q = idx % NBX, row = idx / NBX;
-    const int lx = OX + HL - HB + q, ly = row % NY2, lz = HL - HB + row / NY2;
+  for (int idx = threadIdx.x; idx < ny2 * nbz * nbx; idx += YEE_THREADS) {
+    const int q = idx % nbx, row = idx / nbx;
+    const int lx = OX + HL - HB + q, ly = row % ny2, lz = HL - HB + row / ny2;
     const int l = (lz * LY + ly) * LX + lx;
     if (CK) {
       b[0][l] += hcz * ck_dz(e[1], l);
@@ -838,11 +907,11 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     }
   }
   __syncthreads();
-  // E^{n+1} on cells [-HE, C+1) in x and z ([0, C+1) in y)
-  constexpr int NEX = CX + 1 + HE, NEZ = CZ + 1 + HE;
-  for (int idx = threadIdx.x; idx < NY1 * NEZ * NEX; idx += YEE_THREADS) {
-    const int q = idx % NEX, row = idx / NEX;
-    const int lx = OX + HL - HE + q, ly = NDIM == 3 ? 1 + row % NY1 : 0, lz = HL - HE + row / NY1;
+  // E^{n+1} on cells [-HE, w+1) in x and z ([0, w+1) in y)
+  const int nex = wx + 1 + HE, nez = wz + 1 + HE;
+  for (int idx = threadIdx.x; idx < ny1 * nez * nex; idx += YEE_THREADS) {
+    const int q = idx % nex, row = idx / nex;
+    const int lx = OX + HL - HE + q, ly = NDIM == 3 ? 1 + row % ny1 : 0, lz = HL - HE + row / ny1;
     const int l = (lz * LY + ly) * LX + lx;
     const T bx = b[0][l], by = b[1][l], bz = b[2][l];
     e[0][l] += a.cy * (bz - b[2][l - sy]) - a.cz * (by - b[1][l - sz]) - a.h * j[0][l];
@@ -850,13 +919,12 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     e[2][l] += a.cx * (by - b[1][l - sx]) - a.cy * (bx - b[0][l - sy]) - a.h * j[2][l];
   }
   __syncthreads();
-  // B^{n+1} on cells [0, C), then write E and B of the tile (and, with DIAG, sum their energies)
+  // B^{n+1} on cells [0, w), then write E and B of the tile (and, with DIAG, sum their energies)
   EnergyAcc<T> en;
-  for (int idx = threadIdx.x; idx < CY * CZ * CX; idx += YEE_THREADS) {
-    const int cx = idx % CX, row = idx / CX;
-    const int cy = row % CY, cz = row / CY;
+  for (int idx = threadIdx.x; idx < wy * wz * wx; idx += YEE_THREADS) {
+    const int cx = idx % wx, row = idx / wx;
+    const int cy = row % wy, cz = row / wy;
     const int gx = X0 + cx, gy = Y0 + cy, gz = Z0 + cz;
-    if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
     const int l = ((cz + HL) * LY + cy + OY) * LX + cx + HL + OX;
     const T ex = e[0][l], ey = e[1][l], ez = e[2][l];
     T nbx, nby, nbz;
@@ -887,18 +955,20 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
 
 template <typename T, int NDIM, bool CK, bool DIAG>
 __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty,
-                                                           double* escratch, const __grid_constant__ HistCtl hc) {
-  yee_tile<T, NDIM, CK, DIAG>(a, blockIdx.x, ntx, nty, escratch, &hc);
+                                                           int ex, int ey, int ez, double* escratch,
+                                                           const __grid_constant__ HistCtl hc) {
+  yee_tile<T, NDIM, CK, DIAG>(a, blockIdx.x, ntx, nty, ex, ey, ez, escratch, &hc);
 }
 
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(YEE_THREADS) k_yee_batch(const YeeArgs<T>* __restrict__ args,
                                                            const int* __restrict__ tile_base, int nruns) {
   constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY;
+  constexpr int CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const YeeArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
-  yee_tile<T, NDIM, false, false>(a, blockIdx.x - tile_base[run], ntx, nty);
+  yee_tile<T, NDIM, false, false>(a, blockIdx.x - tile_base[run], ntx, nty, CX, CY, CZ);
 }
 
 int yee_tiles(int ndim, int nx, int ny, int nz) {
@@ -928,15 +998,26 @@ template cudaError_t launch_yee_batch<double>(const YeeArgs<double>*, const int*
 bool yee_records_energy(int ndim, int nx, int ny, int nz, int ck) {
   return ck || !(nx < 3 || nz < 3 || (ndim == 3 && ny < 3));
 }
-size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz) {
-  return sizeof(double) * (3 * (size_t)yee_tiles(ndim, nx, ny, nz) + 2);
+// Tiles of the fused Yee launch: a small grid's tiles shrink (not below 8 cells in x and z, 2 in y).
+static long long yee_launch_tiles(int ndim, int nx, int ny, int nz, int spread, int te[3], int nt[3]) {
+  const int n[3] = {nx, ny, nz};
+  const int c[3] = {ndim == 2 ? YEE2_CX : YEE3_CX, ndim == 2 ? 1 : YEE3_CY, ndim == 2 ? YEE2_CZ : YEE3_CZ};
+  const int lo[3] = {8, ndim == 2 ? 1 : 2, ndim == 2 ? 8 : 2};
+  return field_tiles(n, c, lo, 1, spread, te, nt);
+}
+
+size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz, int spread) {
+  int te[3], nt[3];
+  return sizeof(double) * (3 * (size_t)yee_launch_tiles(ndim, nx, ny, nz, spread, te, nt) + 2);
 }
 
 template <typename T, int NDIM, bool CK>
-static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, int ntiles, int ntx, int nty, double* escratch,
-                                    const HistCtl* hc, cudaStream_t st) {
+static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, double* escratch, const HistCtl* hc, cudaStream_t st) {
   using G = YeeGeom<T, NDIM, CK>;
   const size_t sm = G::SMEM_BYTES;
+  int te[3], nt[3];
+  const int ntiles = (int)yee_launch_tiles(NDIM, a_in.nx, a_in.ny, a_in.nz, a_in.spread, te, nt);
+  const int ntx = nt[0], nty = nt[1];
   const HistCtl none{nullptr, 0, nullptr, nullptr};
   // TMA staging where the grid spans the staged region in every direction and the rows are 16-byte
   // multiples; element copies otherwise
@@ -952,11 +1033,12 @@ static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, int ntiles, int ntx,
   if (hc) {
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, true>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, NDIM, CK, true><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, escratch, *hc);
+    k_yee_fused<T, NDIM, CK, true><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2], escratch, *hc);
   } else {
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, false>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, NDIM, CK, false><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, nullptr, none);
+    k_yee_fused<T, NDIM, CK, false><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2], nullptr,
+                                                                     none);
   }
   return cudaGetLastError();
 }
@@ -964,10 +1046,7 @@ static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, int ntiles, int ntx,
 template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, double* escratch, const HistCtl* hc) {
   if (hc && (!escratch || !yee_records_energy(ndim, a.nx, a.ny, a.nz, a.ck))) return cudaErrorInvalidValue;
-  if (ndim == 2 && a.ck) {  // any grid size: the staged halos wrap
-    const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    return launch_yee_tiles<T, 2, true>(a, ntx * ntz, ntx, 1, escratch, hc, st);
-  }
+  if (ndim == 2 && a.ck) return launch_yee_tiles<T, 2, true>(a, escratch, hc, st);  // any grid: the halos wrap
   if (a.ck) return cudaErrorInvalidValue;  // 3D CK is not built (pic_create rejects it)
   if (a.nx < 3 || a.nz < 3 || (ndim == 3 && a.ny < 3)) {
     // tiny grids: the inputs copied to the outputs, then the three separate updates in place there
@@ -995,13 +1074,8 @@ cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, dou
     if (e == cudaSuccess) e = launch_yee_b<T>(hb, st);
     return e;
   }
-  if (ndim == 2) {
-    const int ntx = (a.nx + YEE2_CX - 1) / YEE2_CX, ntz = (a.nz + YEE2_CZ - 1) / YEE2_CZ;
-    return launch_yee_tiles<T, 2, false>(a, ntx * ntz, ntx, 1, escratch, hc, st);
-  }
-  const int ntx = (a.nx + YEE3_CX - 1) / YEE3_CX, nty = (a.ny + YEE3_CY - 1) / YEE3_CY,
-            ntz = (a.nz + YEE3_CZ - 1) / YEE3_CZ;
-  return launch_yee_tiles<T, 3, false>(a, ntx * nty * ntz, ntx, nty, escratch, hc, st);
+  if (ndim == 2) return launch_yee_tiles<T, 2, false>(a, escratch, hc, st);
+  return launch_yee_tiles<T, 3, false>(a, escratch, hc, st);
 }
 template cudaError_t launch_yee_fused<float>(const YeeArgs<float>&, int, cudaStream_t, double*, const HistCtl*);
 template cudaError_t launch_yee_fused<double>(const YeeArgs<double>&, int, cudaStream_t, double*, const HistCtl*);

@@ -31,6 +31,7 @@ struct SepArgs {
   T zt[2][MAX_ZTAPS];
   T xt[MAX_XTAPS];
   T yt[MAX_XTAPS];
+  int spread;  // blocks to spread a small grid over (the SM count); 0: the kernel's full tiles
   // TMA staging (set by launch_sep when the grid allows it): one tensor map per source component
   int use_tma;
   int* err;  // device error flags (ERR_TIMEOUT when a staging wait gives up)
@@ -52,6 +53,7 @@ struct YeeArgs {
   T wz0 = T(1), wz1 = T(0);  // CK weights of the z differences at x offsets 0 and +-1 (1 - 2 beta_z, beta_z)
   // TMA staging of the fused kernel (set by launch_yee_fused when the grid allows it): tensor maps of
   // Ex Ey Ez Bx By Bz Jx Jy Jz
+  int spread = 0;      // blocks to spread a small grid over (the SM count); 0: the kernel's full tiles
   int use_tma = 0;
   int* err = nullptr;  // device error flags (ERR_TIMEOUT when a staging wait gives up)
   CUtensorMap tm[9];
@@ -142,7 +144,7 @@ cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int n
                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_migrate_batch(const RunDev<T>* runs, int nruns, cudaStream_t st);
-// tiles of the fast stencil / Yee kernels for a grid
+// tiles of the fast stencil / Yee kernels for a grid (the kernels' full tiles, as the batched launches use)
 int sep_tiles(int ndim, int nx, int ny, int nz);
 int yee_tiles(int ndim, int nx, int ny, int nz);
 bool sep_fast_ok(int ndim, int nx, int ny, int nz, int hz, int hx);
@@ -151,7 +153,7 @@ size_t field_energy_scratch_bytes();
 // energies of the new E, B into the history ring (block partials in escratch, of
 // yee_energy_scratch_bytes, zeroed once); only where yee_records_energy (cudaErrorInvalidValue else).
 bool yee_records_energy(int ndim, int nx, int ny, int nz, int ck);
-size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz);
+size_t yee_energy_scratch_bytes(int ndim, int nx, int ny, int nz, int spread);
 template <typename T>
 cudaError_t launch_yee_fused(const YeeArgs<T>& a, int ndim, cudaStream_t st, double* escratch = nullptr,
                              const HistCtl* hc = nullptr);

@@ -186,13 +186,16 @@ def parse_clock_samples(text: str) -> dict:
 
 def profiled_traffic(prof=None, src=None):
     """DRAM bytes per launch of the push kernel from the committed ncu summary, if that summary was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel source (else None). src: a file or a list of files, hashed as one
+    byte string in order (the push: its kernel file, then the header that fixes its tile shape)."""
     import hashlib
     prof = prof or os.path.join(ROOT, "profiles", "k_push_2d_512x1024_fp32.md")
-    src = src or os.path.join(ROOT, "paper_1401_0838_gb300", "csrc", "k_particles.cu")
+    csrc = os.path.join(ROOT, "paper_1401_0838_gb300", "csrc")
+    src = src or [os.path.join(csrc, "k_particles.cu"), os.path.join(csrc, "common.cuh")]
+    files = [src] if isinstance(src, str) else list(src)
     try:
         text = open(prof).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = hashlib.sha256(b"".join(open(f, "rb").read() for f in files)).hexdigest()
     except OSError:
         return None
     sha, traffic = None, None

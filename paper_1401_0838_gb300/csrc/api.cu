@@ -299,7 +299,8 @@ void rebuild_taps(pic_handle* h) {
 // Particle tiles of the run's grid (push_tiles), spread over up to `spread` blocks.
 static void set_tiles(pic_handle* h, int spread) {
   int nt[3], te[3];
-  push_tiles(h->cfg.ndim, h->cfg.nx, h->cfg.ny, h->cfg.nz, spread, nt, te);
+  const bool ho = h->cfg.shape_order != 1 || h->cfg.scheme == PIC_MOMENTUM;  // the run's push is k_push_ho
+  push_tiles(h->cfg.ndim, h->es, ho, h->cfg.nx, h->cfg.ny, h->cfg.nz, spread, nt, te);
   h->ntx = nt[0];
   h->nty = nt[1];
   h->ntz = nt[2];
@@ -1503,6 +1504,7 @@ int batch_tables(pic_batch* b) {
       for (int i = 0; i < n; ++i) {
         rd[i] = make_run<T>(b->runs[i], p);
         rd[i].kin = rec ? b->runs[i]->d_kin : nullptr;
+        if (!tiles_fit<PTile>(rd[i])) BCK(cudaErrorInvalidValue, "run tiles");
       }
       BCK(cudaMemcpy(b->d_run[p][rec], rd.data(), sizeof(RunDev<T>) * n, cudaMemcpyHostToDevice), "run table");
     }

@@ -56,13 +56,45 @@ __device__ __forceinline__ void list_put(const LeaverList<T>& l, long long o, in
   if (l.id) l.id[o] = id;
 }
 
+// Particle tile of the linear push (cells per direction, the shared-memory tiles' size). A run's
+// tiles are at most this (push_tiles); the launchers check it. Tall and narrow, along the drift:
+// few particles leave a tile through a z face per step, and a warp's cell group spans several z
+// rows, so a particle crossing into the next z cell mostly lands in a cell of its own group (one
+// slot reservation for both). 3D FP64 keeps a cube: its shared-memory tiles are twice as large.
+template <typename T, int NDIM>
+struct PTile;
+template <typename T>
+struct PTile<T, 2> {
+  static constexpr int TX = 4, TY = 1, TZ = 64;
+};
+template <>
+struct PTile<float, 3> {
+  static constexpr int TX = 2, TY = 2, TZ = 128;
+};
+template <>
+struct PTile<double, 3> {
+  static constexpr int TX = 8, TY = 8, TZ = 8;
+};
+
+// Particle tile of the cubic and momentum-conserving push (k_push_ho).
+template <typename T, int NDIM>
+struct HoTile;
+template <typename T>
+struct HoTile<T, 2> {
+  static constexpr int TX = 16, TY = 1, TZ = 16;
+};
+template <typename T>
+struct HoTile<T, 3> {
+  static constexpr int TX = 8, TY = 8, TZ = 8;
+};
+
 // Everything a kernel needs about one simulation (passed by value as a kernel parameter).
 template <typename T>
 struct RunDev {
   int ndim, nx, ny, nz;
   long long ncell;
   int ntx, nty, ntz;  // particle tiles per direction
-  int tex, tey, tez;  // cells per particle tile and direction (at most the kernel's tile; origins at multiples)
+  int tex, tey, tez;  // cells per particle tile and direction (at most PTile; origins at multiples)
   int cap;            // slots per cell per species
   int scheme;         // 0 Galerkin, 1 Uniform, 2 momentum-conserving
   T dtdx, dtdy, dtdz; // dt / d (grid units per unit velocity)
@@ -87,6 +119,14 @@ struct RunDev {
   double* kin;        // FP64 accumulators of this step: [0] sum w (gamma - 1), [1] particle count
                       // (nullptr: not recorded)
 };
+
+// A run's tile extents lie within a push kernel's compile-time tile TL (its shared-memory size).
+template <template <typename, int> class TL, typename T>
+inline bool tiles_fit(const RunDev<T>& r) {
+  if (r.tex < 1 || r.tey < 1 || r.tez < 1) return false;
+  if (r.ndim == 2) return r.tex <= TL<T, 2>::TX && r.tey == 1 && r.tez <= TL<T, 2>::TZ;
+  return r.tex <= TL<T, 3>::TX && r.tey <= TL<T, 3>::TY && r.tez <= TL<T, 3>::TZ;
+}
 
 // Device-side energy history of one run: the energy kernel writes sample (*count % cap) from its
 // field sums and the kinetic accumulator kin[0..1] (filled by the push kernel), zeroes kin and

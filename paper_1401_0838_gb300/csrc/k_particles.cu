@@ -11,17 +11,6 @@
 
 namespace picgb {
 
-template <int NDIM>
-struct PTile;
-template <>
-struct PTile<2> {
-  static constexpr int TX = 16, TY = 1, TZ = 16;
-};
-template <>
-struct PTile<3> {
-  static constexpr int TX = 8, TY = 8, TZ = 8;
-};
-
 // Threads per push block: 8 warps; the 3D FP32 kernel, one block per SM, takes 12 warps.
 template <typename T, int NDIM>
 struct PushThreads {
@@ -49,7 +38,7 @@ struct PushStage {
 
 template <typename T, int NDIM>
 struct PushSmem {
-  static constexpr int TX = PTile<NDIM>::TX, TY = PTile<NDIM>::TY, TZ = PTile<NDIM>::TZ;
+  static constexpr int TX = PTile<T, NDIM>::TX, TY = PTile<T, NDIM>::TY, TZ = PTile<T, NDIM>::TZ;
   static constexpr int NCL = TX * TY * TZ;
   // gather tile: nodes [X0-1, X0+TX] per direction (y only in 3D)
   static constexpr int GX = TX + 2, GY = (NDIM == 3 ? TY + 2 : 1), GZ = TZ + 2, GN = GX * GY * GZ;
@@ -1266,6 +1255,9 @@ static int lanes_per_cell(int ndim, int ppc_total) {
   const int packs = 2 * ((ppc_total / 2 + 3) / 4);  // packs of 4 per species
   // 2D: four lanes per cell up to 8 packs (two packs per lane halve the per-cell reduction cost;
   // measured 3 % faster than eight lanes at 16 particles/cell/species on GB300)
+  // 3D up to 4 packs: two lanes per cell (a lane's two packs halve the per-cell reduction and
+  // Galerkin loads per particle; measured 5 % faster than four lanes at 8 particles/cell/species)
+  if (ndim == 3 && packs <= 4) return 2;
   if (packs <= 4 || (ndim == 2 && packs <= 8)) return 4;
   if (packs <= 8) return 8;
   return 16;
@@ -1282,6 +1274,9 @@ static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
     kern<<<ntiles, PushThreads<T, NDIM>::value, sm, st>>>(r);
     return cudaGetLastError();
   };
+  if constexpr (NDIM == 3) {
+    if (lpc == 2) return go(k_push<T, NDIM, SCHEME, 2>);
+  }
   if (lpc == 4) return go(k_push<T, NDIM, SCHEME, 4>);
   if (lpc == 8) return go(k_push<T, NDIM, SCHEME, 8>);
   return go(k_push<T, NDIM, SCHEME, 16>);
@@ -1289,6 +1284,7 @@ static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_push(const RunDev<T>& r, int ppc_total, cudaStream_t st) {
+  if (!tiles_fit<PTile>(r)) return cudaErrorInvalidValue;
   const int lpc = lanes_per_cell(r.ndim, ppc_total);
   if (r.ndim == 2)
     return r.scheme == 0 ? launch_push_t<T, 2, 0>(r, lpc, st) : launch_push_t<T, 2, 1>(r, lpc, st);
@@ -1328,7 +1324,11 @@ template cudaError_t launch_push_batch<float>(const RunDev<float>*, const int2*,
 template cudaError_t launch_push_batch<double>(const RunDev<double>*, const int2*, int, int*, int, int, int, int,
                                                cudaStream_t);
 
-int push_lanes_per_cell(int ndim, int ppc_total) { return lanes_per_cell(ndim, ppc_total); }
+// The batched kernel is built for 4, 8 and 16 lanes per cell.
+int push_lanes_per_cell(int ndim, int ppc_total) {
+  const int l = lanes_per_cell(ndim, ppc_total);
+  return l < 4 ? 4 : l;
+}
 
 template <typename T>
 int push_max_blocks_per_sm(int ndim, int scheme, int lpc) {
@@ -1350,17 +1350,24 @@ template int push_max_blocks_per_sm<float>(int, int, int);
 template int push_max_blocks_per_sm<double>(int, int, int);
 template cudaError_t launch_push<double>(const RunDev<double>&, int, cudaStream_t);
 
-void push_tiles(int ndim, int nx, int ny, int nz, int spread, int nt[3], int te[3]) {
-  const int n[3] = {nx, ndim == 3 ? ny : 1, nz};
+// The compile-time tile TL of the working precision T.
+template <template <typename, int> class TL, typename T>
+static void tile_of(int ndim, int te[3]) {
   if (ndim == 2) {
-    te[0] = PTile<2>::TX;
+    te[0] = TL<T, 2>::TX;
     te[1] = 1;
-    te[2] = PTile<2>::TZ;
+    te[2] = TL<T, 2>::TZ;
   } else {
-    te[0] = PTile<3>::TX;
-    te[1] = PTile<3>::TY;
-    te[2] = PTile<3>::TZ;
+    te[0] = TL<T, 3>::TX;
+    te[1] = TL<T, 3>::TY;
+    te[2] = TL<T, 3>::TZ;
   }
+}
+
+void push_tiles(int ndim, int es, bool ho, int nx, int ny, int nz, int spread, int nt[3], int te[3]) {
+  const int n[3] = {nx, ndim == 3 ? ny : 1, nz};
+  if (es == 4) ho ? tile_of<HoTile, float>(ndim, te) : tile_of<PTile, float>(ndim, te);
+  else ho ? tile_of<HoTile, double>(ndim, te) : tile_of<PTile, double>(ndim, te);
   auto count = [&]() {
     long long t = 1;
     for (int d = 0; d < 3; ++d) {

@@ -23,22 +23,12 @@ namespace {
 
 constexpr int HO_THREADS = 256;
 
-template <int NDIM>
-struct HoTile;
-template <>
-struct HoTile<2> {
-  static constexpr int TX = 16, TY = 1, TZ = 16;  // the particle tiles of push_tiles()
-};
-template <>
-struct HoTile<3> {
-  static constexpr int TX = 8, TY = 8, TZ = 8;
-};
 
 // Geometry of the shared-memory tiles for shape order ORDER: the field tile holds nodes
 // [-H, T + H) per direction, the current tile nodes [-H, T + H + 1), H = (ORDER + 1) / 2.
-template <int NDIM, int ORDER>
+template <typename T, int NDIM, int ORDER>
 struct HoGeom {
-  using TL = HoTile<NDIM>;
+  using TL = HoTile<T, NDIM>;
   static constexpr int H = (ORDER + 1) / 2;
   static constexpr int GX = TL::TX + 2 * H, GY = NDIM == 3 ? TL::TY + 2 * H : 1, GZ = TL::TZ + 2 * H;
   static constexpr int GN = GX * GY * GZ;
@@ -47,7 +37,6 @@ struct HoGeom {
   static constexpr int NCL = TL::TX * TL::TY * TL::TZ;
   static constexpr int NW = ORDER == 3 ? 6 : 4;   // deposit window nodes per direction
   static constexpr int K0 = ORDER == 3 ? -2 : -1;  // first window node relative to the start cell
-  template <typename T>
   static constexpr size_t bytes() {
     return sizeof(T) * (6 * (size_t)GN + 3 * (size_t)JN) + sizeof(int) * 4 * (size_t)NCL;
   }
@@ -130,7 +119,7 @@ __host__ __device__ constexpr int stag_ho(int c, int axis) {
 
 template <typename T, int NDIM, int ORDER, int SCHEME, int C>
 __device__ __forceinline__ T gather_comp(const T* sgc, int lx, int ly, int lz, T ox, T oy, T oz) {
-  using G = HoGeom<NDIM, ORDER>;
+  using G = HoGeom<T, NDIM, ORDER>;
   // momentum-conserving: integer nodes of the averaged tile; Galerkin: one order lower along the
   // component's half-staggered directions; Uniform: the shape order at the component's nodes
   constexpr int SX = SCHEME == 2 ? 0 : stag_ho(C, 0), SY = SCHEME == 2 ? 0 : stag_ho(C, 1);
@@ -161,7 +150,7 @@ __device__ __forceinline__ T gather_comp(const T* sgc, int lx, int ly, int lz, T
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
 __device__ __forceinline__ void gather6(const T* sg, int lx, int ly, int lz, T ox, T oy, T oz, T (&F)[6]) {
-  using G = HoGeom<NDIM, ORDER>;
+  using G = HoGeom<T, NDIM, ORDER>;
   F[0] = gather_comp<T, NDIM, ORDER, SCHEME, 0>(sg, lx, ly, lz, ox, oy, oz);
   F[1] = gather_comp<T, NDIM, ORDER, SCHEME, 1>(sg + G::GN, lx, ly, lz, ox, oy, oz);
   F[2] = gather_comp<T, NDIM, ORDER, SCHEME, 2>(sg + 2 * G::GN, lx, ly, lz, ox, oy, oz);
@@ -195,8 +184,8 @@ __device__ __forceinline__ HoTileRef ho_tile(const RunDev<T>& r) {
 template <typename T, int NDIM, int ORDER, int SCHEME>
 __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef& t, T* sg, T* sj, int* sn,
                                             int* scnt) {
-  using G = HoGeom<NDIM, ORDER>;
-  using TL = HoTile<NDIM>;
+  using G = HoGeom<T, NDIM, ORDER>;
+  using TL = HoTile<T, NDIM>;
   constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, H = G::H;
   const int tid = threadIdx.x;
   const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
@@ -275,8 +264,8 @@ __device__ __forceinline__ void ho_prologue(const RunDev<T>& r, const HoTileRef&
 template <typename T, int NDIM, int ORDER>
 __device__ __forceinline__ void ho_epilogue(const RunDev<T>& r, const HoTileRef& t, T* sj, int* scnt, T kin,
                                             int npush) {
-  using G = HoGeom<NDIM, ORDER>;
-  using TL = HoTile<NDIM>;
+  using G = HoGeom<T, NDIM, ORDER>;
+  using TL = HoTile<T, NDIM>;
   constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, H = G::H;
   const int tid = threadIdx.x;
   const int X0 = t.X0, Y0 = t.Y0, Z0 = t.Z0, wx = t.wx, wy = t.wy, wz = t.wz, nxy = t.nxy;
@@ -335,8 +324,8 @@ __device__ __forceinline__ void ho_epilogue(const RunDev<T>& r, const HoTileRef&
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
 __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ RunDev<T> r) {
-  using G = HoGeom<NDIM, ORDER>;
-  using TL = HoTile<NDIM>;
+  using G = HoGeom<T, NDIM, ORDER>;
+  using TL = HoTile<T, NDIM>;
   constexpr int TX = TL::TX, TY = TL::TY, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);
@@ -550,8 +539,8 @@ __global__ void __launch_bounds__(HO_THREADS) k_push_ho(const __grid_constant__ 
 // of the chunk) and added to the tile's current with one shared-memory atomic per lane and chunk.
 template <typename T, int ORDER, int SCHEME>
 __global__ void __launch_bounds__(HO_THREADS) k_push_ho_w2(const __grid_constant__ RunDev<T> r) {
-  using G = HoGeom<2, ORDER>;
-  constexpr int TX = HoTile<2>::TX, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
+  using G = HoGeom<T, 2, ORDER>;
+  constexpr int TX = HoTile<T, 2>::TX, NCL = G::NCL, NW = G::NW, K0 = G::K0, H = G::H;
   constexpr int NVX = (NW - 1) * NW, NVZ = NW * (NW - 1), NVY = NW * NW, NV = NVX + NVZ + NVY;
   constexpr int NCH = (NV + 31) / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1013,8 +1002,8 @@ __global__ void __launch_bounds__(SPILL_THREADS) k_push_spill_batch(const RunDev
 
 template <typename T, int NDIM, int ORDER, int SCHEME>
 cudaError_t launch_ho_t(const RunDev<T>& r, cudaStream_t st) {
-  using G = HoGeom<NDIM, ORDER>;
-  const size_t sm = G::template bytes<T>();
+  using G = HoGeom<T, NDIM, ORDER>;
+  const size_t sm = G::bytes();
   const int ntiles = r.ntx * r.nty * r.ntz;
   if (NDIM == 2) {  // one warp per cell
     cudaError_t e = ensure_dynamic_smem((const void*)k_push_ho_w2<T, ORDER, SCHEME>, sm);
@@ -1039,6 +1028,7 @@ cudaError_t launch_ho_scheme(const RunDev<T>& r, int scheme, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_push_ho(const RunDev<T>& r, int order, int scheme, cudaStream_t st) {
+  if (!tiles_fit<HoTile>(r)) return cudaErrorInvalidValue;
   if (r.ndim == 2) return order == 3 ? launch_ho_scheme<T, 2, 3>(r, scheme, st) : launch_ho_scheme<T, 2, 1>(r, scheme, st);
   return order == 3 ? launch_ho_scheme<T, 3, 3>(r, scheme, st) : launch_ho_scheme<T, 3, 1>(r, scheme, st);
 }

@@ -65,10 +65,11 @@ struct YeeArgs {
 // unaligned base, a box past the limits) or the driver has no encoder.
 bool tma_encode(CUtensorMap* m, const void* base, int es, int ndim, int nx, int ny, int nz, int bx, int by, int bz);
 
-// Particle tiles of a grid: the kernels' tile (16x16 in 2D, 8x8x8 in 3D), halved (down to 4 cells,
-// the longest extent first) while twice the tiles still fit in `spread` blocks, so that a small grid
-// spreads over the SMs. spread = 0 keeps the full tile. te: cells per tile and direction.
-void push_tiles(int ndim, int nx, int ny, int nz, int spread, int nt[3], int te[3]);
+// Particle tiles of a grid: the push kernel's tile (PTile, or HoTile for the cubic and momentum-
+// conserving push) for the precision (es bytes per value), halved (down to 4 cells, the longest
+// extent first) while twice the tiles still fit in `spread` blocks, so that a small grid spreads over
+// the SMs. spread = 0 keeps the full tile. te: cells per tile and direction.
+void push_tiles(int ndim, int es, bool ho, int nx, int ny, int nz, int spread, int nt[3], int te[3]);
 
 // Raise a kernel's dynamic shared memory limit to `bytes` (once per kernel and size).
 cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
@@ -85,6 +86,7 @@ cudaError_t launch_push_ho(const RunDev<T>& r, int order, int scheme, cudaStream
 template <typename T>
 cudaError_t launch_push_batch(const RunDev<T>* runs, const int2* items, int nitems, int* queue, int ndim, int scheme,
                               int lpc, int blocks, cudaStream_t st);
+// Lanes per cell of the batched push (4, 8 or 16) for the expected particles per cell.
 int push_lanes_per_cell(int ndim, int ppc_total);
 template <typename T>
 int push_max_blocks_per_sm(int ndim, int scheme, int lpc);

@@ -45,6 +45,14 @@ def test_traffic_only_for_the_profiled_source(tmp_path):
     src.write_text("kernel source, changed\n")
     assert bench.profiled_traffic(str(prof), str(src)) is None
     assert bench.profiled_traffic(str(tmp_path / "missing.md"), str(src)) is None
+    # several files: one digest over their bytes in order; a change in any of them drops the figure
+    hdr = tmp_path / "tile.cuh"
+    hdr.write_text("tile shape\n")
+    both = hashlib.sha256(src.read_bytes() + hdr.read_bytes()).hexdigest()
+    prof.write_text(f"source_sha256: {both}\ndram_bytes_per_launch: 42\n")
+    assert bench.profiled_traffic(str(prof), [str(src), str(hdr)]) == 42.0
+    hdr.write_text("tile shape, changed\n")
+    assert bench.profiled_traffic(str(prof), [str(src), str(hdr)]) is None
 
 
 def test_clock_sample_parsing():

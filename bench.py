@@ -734,13 +734,14 @@ def run_adjoint(args):
 PUSH3D_BYTES_PER_PARTICLE, PUSH3D_LAYOUT_BYTES_PER_PARTICLE = 64, 56
 
 
-def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, nz: int = 512) -> dict:
+def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, nz: int = 512,
+               nxy: int = 128) -> dict:
     """The 3D workload: 128 x 128 x 512, 8 particles/cell/species (134,217,728 particles), transverse
     Gaussian weights (sigma 20 cells), gamma 130, c dt/dz 0.5, Galerkin, correction + filter
     (1, 1, a = 3), FP32. Same timing as the default line; roofline with the 3D bytes per particle."""
     device = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
-    cfg = P.pic_config_default(ndim=3, nx=128, ny=128, nz=nz, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN,
+    cfg = P.pic_config_default(ndim=3, nx=nxy, ny=nxy, nz=nz, dt=0.5, gamma=130.0, scheme=P.PIC_GALERKIN,
                                precision=P.PIC_FP32, ppc_per_species=8, sigma_perp=20.0, seed=3, init_beam=1,
                                diag_every=1)
     h = P.pic_create(cfg)
@@ -768,7 +769,7 @@ def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, n
     achieved = bytes_per_launch / per_launch_s / 1e9
     return {"value": np_ * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
             "ms_per_step": ms / steps, "particles": np_,
-            "workload": f"3D 128x128x{nz}, 8 particles/cell/species ({np_} particles), Gaussian transverse weights "
+            "workload": f"3D {nxy}x{nxy}x{nz}, 8 particles/cell/species ({np_} particles), Gaussian transverse weights "
                         "sigma 20 cells, gamma 130, c dt/dz 0.5, Galerkin, correction + filter (1,1,a=3), FP32",
             "roofline": {"kernel": "k_push", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
@@ -785,7 +786,7 @@ def run_3d(args):
     import paper_1401_0838_gb300 as P
     torch.cuda.set_device(0)
     peak, peak_kind = measured_hbm_peak()
-    m = measure_3d(P, torch, args.steps, args.warmup, peak, peak_kind, nz=args.config3d_nz)
+    m = measure_3d(P, torch, args.steps, args.warmup, peak, peak_kind, nz=args.config3d_nz, nxy=args.config3d_nxy)
     line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -1007,6 +1008,8 @@ def main(argv=None):
     ap.add_argument("--no-fd", action="store_true", help="--adjoint without the central differences")
     ap.add_argument("--config3d", action="store_true", help="time the 3D 128x128x512 workload instead")
     ap.add_argument("--config3d-nz", type=int, default=512, help="z cells of the --config3d grid (profiling: fewer)")
+    ap.add_argument("--config3d-nxy", type=int, default=128,
+                    help="x and y cells of the --config3d grid (profiling: fewer)")
     ap.add_argument("--config1", action="store_true", help="time the small 64x128 FP64 workload instead")
     ap.add_argument("--order", type=int, default=1, choices=(1, 3), help="particle shape order of the workload")
     ap.add_argument("--gamma-sweep", action="store_true", help="growth against c dt/dz at gamma 3 and 130 instead")

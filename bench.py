@@ -241,7 +241,9 @@ def make_handle(P, precision: int, seed: int, stream_ptr, order: int = 1, scheme
 def timed_steps(P, torch, h, stream, steps: int, device):
     """Device time of `steps` whole steps run by one pic_step call (CUDA events on the launching
     stream; the library replays its captured step graph), then per-kernel times from a second,
-    separately timed pass of `steps` single steps with event-bracketed launches."""
+    separately timed pass of `steps` single steps with event-bracketed launches: per kernel class,
+    the median over the steps of its time in one step (so one stray slow launch does not move it),
+    returned as (median x steps, launches)."""
     l0 = P.pic_launch_count(h)
     barrier(device)
     torch.cuda.synchronize()
@@ -256,13 +258,26 @@ def timed_steps(P, torch, h, stream, steps: int, device):
     ms = e0.elapsed_time(e1)
     launches = P.pic_launch_count(h) - l0
     P.pic_sync(h)
-    P.pic_enable_timing(h, True)
+    per_step = []
     for _ in range(steps):
+        P.pic_enable_timing(h, True)  # resets the totals
         P.pic_step(h, 1)
-    P.pic_sync(h)
-    kt = P.pic_kernel_times(h)
+        P.pic_sync(h)
+        per_step.append(P.pic_kernel_times(h))
     P.pic_enable_timing(h, False)
+    kt = median_kernel_times(per_step)
     return ms, kt, launches
+
+
+def median_kernel_times(per_step: list) -> dict:
+    """{class: (median over steps of the class's ms in a step x steps, launches over all steps)}."""
+    out = {}
+    for k in per_step[0]:
+        ms = sorted(t[k][0] for t in per_step)
+        n = len(ms)
+        med = ms[n // 2] if n % 2 else 0.5 * (ms[n // 2 - 1] + ms[n // 2])
+        out[k] = (med * n, sum(t[k][1] for t in per_step))
+    return out
 
 
 def push_time_in_step(kt: dict, step_ms: float):

@@ -35,6 +35,17 @@ def test_push_time_from_the_graph_replayed_step():
     assert bench.push_time_in_step(kt, 0.05) is None  # less than the other kernels: no estimate
 
 
+def test_median_kernel_times_ignores_one_stray_launch():
+    # five steps; one of them caught a slow spill launch: the median per class is unmoved
+    steps = [{"push": (0.33, 1), "spill": (0.006, 1)} for _ in range(5)]
+    steps[2] = {"push": (0.33, 1), "spill": (0.089, 1)}
+    kt = bench.median_kernel_times(steps)
+    assert abs(kt["spill"][0] / 5 - 0.006) < 1e-12 and kt["spill"][1] == 5
+    assert abs(kt["push"][0] - 5 * 0.33) < 1e-12
+    even = bench.median_kernel_times(steps[:4])
+    assert abs(even["spill"][0] / 4 - 0.006) < 1e-12
+
+
 def test_traffic_only_for_the_profiled_source(tmp_path):
     src = tmp_path / "kernel.cu"
     src.write_text("kernel source\n")

@@ -269,6 +269,19 @@ def timed_steps(P, torch, h, stream, steps: int, device):
     return ms, kt, launches
 
 
+def warm_up(P, h, n: int):
+    """n untimed steps (at least 4) in one pic_step call: besides warming up, it captures the step
+    graph that the timed call then replays (a call of fewer than two graphs' worth of steps runs
+    single steps, and a timed call would otherwise capture the graph inside its timed region)."""
+    P.pic_step(h, max(n, 4))
+
+
+def bin_stats(P, h) -> dict:
+    """Slots per cell and species, and particles sent through the spill list so far (full bins)."""
+    cap, spilled = P.pic_bin_stats(h)
+    return {"capacity": cap, "spilled": spilled}
+
+
 def median_kernel_times(per_step: list) -> dict:
     """{class: (median over steps of the class's ms in a step x steps, launches over all steps)}."""
     out = {}
@@ -484,8 +497,7 @@ def run_ours(args):
     ncell = cfg.nx * cfg.ny * cfg.nz
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            P.pic_step(h, 1)
+        warm_up(P, h, args.warmup)
     P.pic_sync(h)
     clocks = ClockSampler(local)
     before = clocks.sample()
@@ -494,6 +506,7 @@ def run_ours(args):
     clk = clocks.stop(before, clocks.sample())
     hist = P.pic_energy_history(h, 1)
     assert hist and hist[-1]["np"] == np_, "particle count changed"
+    bins = bin_stats(P, h)
     agg = aggregate(ms, np_, args.steps, device)
     cells = aggregate(ms, ncell, args.steps, device)
     launches_all = int(reduce_sum(launches, device))
@@ -514,8 +527,7 @@ def run_ours(args):
     if args.fp64_steps > 0:
         h64, _ = make_handle(P, P.PIC_FP64, seed=2 + rank, stream_ptr=stream.cuda_stream, order=args.order,
                              scheme=args.scheme, solver=args.solver, correction=args.correction)
-        for _ in range(2):
-            P.pic_step(h64, 1)
+        warm_up(P, h64, 2)
         P.pic_sync(h64)
         ms64, kt64, _ = timed_steps(P, torch, h64, stream, args.fp64_steps, device)
         a64 = aggregate(ms64, np_, args.fp64_steps, device)
@@ -528,6 +540,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(ws, args.order, args.scheme, args.solver, args.correction), "roofline": rf, "kernel_ms_per_launch": kernel_ms,
             "cell_updates_per_s": cells["value"], "fp64": fp64, "e2e": e2e, "gpu_launches": launches_all,
+            "bins": bins,
             "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_extras:
         # the other workloads, each measured here so that every one has a record from the same run
@@ -765,8 +778,7 @@ def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, n
     ncell = cfg.nx * cfg.ny * cfg.nz
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            P.pic_step(h, 1)
+        warm_up(P, h, warmup)
     P.pic_sync(h)
     clocks = ClockSampler(device.index)
     before = clocks.sample()
@@ -775,6 +787,7 @@ def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, n
     clk = clocks.stop(before, clocks.sample())
     hist = P.pic_energy_history(h, 1)
     assert hist and hist[-1]["np"] == np_, "particle count changed"
+    bins = bin_stats(P, h)
     P.pic_destroy(h)
     ev_s = kt["push"][0] / 1e3 / max(kt["push"][1], 1)
     in_step = push_time_in_step(kt, ms / steps)
@@ -791,6 +804,7 @@ def measure_3d(P, torch, steps: int, warmup: int, peak: float, peak_kind: str, n
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "frac_layout_bytes": round(layout_bytes / per_launch_s / 1e9 / peak, 4),
                          "launch_ms": round(per_launch_s * 1e3, 4), "launch_ms_events": round(ev_s * 1e3, 4)},
+            "bins": bins,
             "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt.items() if v[1]},
             "cell_updates_per_s": ncell * steps / (ms / 1e3), "gpu_launches": launches, "clocks": clk}
 
@@ -827,8 +841,7 @@ def measure_config1(P, torch, steps: int, warmup: int) -> dict:
     P.pic_set_correction_stencil(h, *P.pic_compute_correction_coeffs(P.PIC_GALERKIN, 0.5))
     np_ = P.pic_num_particles(h)
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            P.pic_step(h, 1)
+        warm_up(P, h, warmup)
     P.pic_sync(h)
     clocks = ClockSampler(device.index)
     before = clocks.sample()

@@ -821,7 +821,7 @@ def run_3d(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": m["workload"], "particles": m["particles"]}, "roofline": m["roofline"],
             "kernel_ms_per_launch": m["kernel_ms_per_launch"], "cell_updates_per_s": m["cell_updates_per_s"],
-            "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
+            "gpu_launches": m["gpu_launches"], "bins": m["bins"], "clocks": m["clocks"]}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_3d(args.cpu_steps_3d, args.cpu_threads)
     print(json.dumps(line), flush=True)

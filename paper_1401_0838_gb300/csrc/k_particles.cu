@@ -7,6 +7,7 @@
 // cell at no extra HBM pass. Positions are cell-relative offsets in [0,1); momenta are stored
 // relative to the drift u0 z_hat so that FP32 keeps the thermal spread (u0 = 130, spread 1e-4).
 #include "common.cuh"
+#include "fastmath.cuh"
 #include "launch.h"
 
 namespace picgb {
@@ -207,10 +208,6 @@ __device__ __forceinline__ int wrap_near_p(int g, int n) { return g < 0 ? g + n 
 
 // FP32 uses the hardware reciprocal square root and fast division (relative error ~1e-7, inside
 // the 1e-5 per-step bar); FP64 keeps IEEE division and square root.
-__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double fast_rsqrt(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 // Galerkin gather (order 0 along each half-staggered direction, order 1 elsewhere): the nodes are
 // the same for every particle of a cell, so they are read once per lane and each component is an

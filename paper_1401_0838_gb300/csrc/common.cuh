@@ -56,6 +56,13 @@ __device__ __forceinline__ void list_put(const LeaverList<T>& l, long long o, in
   if (l.id) l.id[o] = id;
 }
 
+// Programmatic dependent launch. The kernels of a step are launched with launch_pdl, so a kernel's
+// launch overlaps the completion of the kernel before it in the stream; pdl_wait, the first thing
+// each of them does, holds it until that kernel has completed and its memory is visible (outside
+// such a launch it returns at once). No kernel triggers its dependents early: measured, letting the
+// next grid's blocks take SM resources while a kernel still runs cost 2 % of the step.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Particle tile of the linear push (cells per direction, the shared-memory tiles' size). A run's
 // tiles are at most this (push_tiles); the launchers check it. Tall and narrow, along the drift:
 // few particles leave a tile through a z face per step, and a warp's cell group spans several z

@@ -462,6 +462,7 @@ __device__ __forceinline__ void sep_tile(const SepArgs<T>& a, const int tile, co
 template <typename T, int NDIM, int HZ, int HX>
 __global__ void __launch_bounds__(SEP_THREADS) k_sep_t(const __grid_constant__ SepArgs<T> a, int ntx, int nty,
                                                        int ex, int ey, int ez) {
+  pdl_wait();
   sep_tile<T, NDIM, HZ, HX>(a, blockIdx.x, blockIdx.y, ntx, nty, ex, ey, ez);
 }
 
@@ -510,8 +511,7 @@ static cudaError_t launch_sep_t(const SepArgs<T>& a_in, cudaStream_t st) {
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_t<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)a.ncomp);
-  k_sep_t<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2]);
-  return cudaGetLastError();
+  return launch_pdl(k_sep_t<T, NDIM, HZ, HX>, grid, dim3(SEP_THREADS), sm, st, a, ntx, nty, te[0], te[1], te[2]);
 }
 
 template <typename T, int NDIM, int HX>
@@ -957,6 +957,7 @@ template <typename T, int NDIM, bool CK, bool DIAG>
 __global__ void __launch_bounds__(YEE_THREADS) k_yee_fused(const __grid_constant__ YeeArgs<T> a, int ntx, int nty,
                                                            int ex, int ey, int ez, double* escratch,
                                                            const __grid_constant__ HistCtl hc) {
+  pdl_wait();
   yee_tile<T, NDIM, CK, DIAG>(a, blockIdx.x, ntx, nty, ex, ey, ez, escratch, &hc);
 }
 
@@ -1033,12 +1034,15 @@ static cudaError_t launch_yee_tiles(const YeeArgs<T>& a_in, double* escratch, co
   if (hc) {
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, true>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, NDIM, CK, true><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2], escratch, *hc);
+    e = launch_pdl(k_yee_fused<T, NDIM, CK, true>, dim3(ntiles), dim3(YEE_THREADS), sm, st, a, ntx, nty, te[0], te[1],
+                   te[2], escratch, *hc);
+    if (e != cudaSuccess) return e;
   } else {
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_fused<T, NDIM, CK, false>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_fused<T, NDIM, CK, false><<<ntiles, YEE_THREADS, sm, st>>>(a, ntx, nty, te[0], te[1], te[2], nullptr,
-                                                                     none);
+    e = launch_pdl(k_yee_fused<T, NDIM, CK, false>, dim3(ntiles), dim3(YEE_THREADS), sm, st, a, ntx, nty, te[0],
+                   te[1], te[2], (double*)nullptr, none);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -1213,6 +1213,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
 template <typename T, int NDIM, int SCHEME, int LPC>
 __global__ void __launch_bounds__(PushThreads<T, NDIM>::value, PushMinBlocks<T, NDIM>::value)
     k_push(const __grid_constant__ RunDev<T> r) {
+  pdl_wait();
   push_tile<T, NDIM, SCHEME, LPC>(r, blockIdx.x);
 }
 
@@ -1268,8 +1269,7 @@ static cudaError_t launch_push_t(const RunDev<T>& r, int lpc, cudaStream_t st) {
   auto go = [&](void (*kern)(const RunDev<T>)) -> cudaError_t {
     cudaError_t e = ensure_dynamic_smem((const void*)kern, sm);
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, PushThreads<T, NDIM>::value, sm, st>>>(r);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(ntiles), dim3(PushThreads<T, NDIM>::value), sm, st, r);
   };
   if constexpr (NDIM == 3) {
     if (lpc == 2) return go(k_push<T, NDIM, SCHEME, 2>);
@@ -1459,6 +1459,7 @@ __device__ __forceinline__ void migrate_body(const RunDev<T>& r, int* other_coun
 
 template <typename T>
 __global__ void k_migrate(const __grid_constant__ RunDev<T> r, int* other_count) {
+  pdl_wait();
   migrate_body<T>(r, other_count, blockIdx.x, gridDim.x);
 }
 
@@ -1470,8 +1471,7 @@ __global__ void k_migrate_batch(const RunDev<T>* __restrict__ runs) {
 
 template <typename T>
 cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st) {
-  k_migrate<T><<<152 * 4, 256, 0, st>>>(r, other_count);
-  return cudaGetLastError();
+  return launch_pdl(k_migrate<T>, dim3(152 * 4), dim3(256), 0, st, r, other_count);
 }
 
 template <typename T>

@@ -991,6 +991,7 @@ constexpr int SPILL_THREADS = 256;
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(SPILL_THREADS) k_push_spill(const __grid_constant__ RunDev<T> r, int order,
                                                               int scheme) {
+  pdl_wait();
   push_spill_body<T, NDIM>(r, order, scheme, blockIdx.x, gridDim.x);
 }
 
@@ -1039,9 +1040,8 @@ template <typename T>
 cudaError_t launch_push_spill(const RunDev<T>& r, int order, int scheme, cudaStream_t st) {
   // a fixed grid (the count is on the device): every block exits at once when the list is empty
   constexpr int blocks = 152;
-  if (r.ndim == 2) k_push_spill<T, 2><<<blocks, SPILL_THREADS, 0, st>>>(r, order, scheme);
-  else k_push_spill<T, 3><<<blocks, SPILL_THREADS, 0, st>>>(r, order, scheme);
-  return cudaGetLastError();
+  if (r.ndim == 2) return launch_pdl(k_push_spill<T, 2>, dim3(blocks), dim3(SPILL_THREADS), 0, st, r, order, scheme);
+  return launch_pdl(k_push_spill<T, 3>, dim3(blocks), dim3(SPILL_THREADS), 0, st, r, order, scheme);
 }
 template cudaError_t launch_push_spill<float>(const RunDev<float>&, int, int, cudaStream_t);
 template cudaError_t launch_push_spill<double>(const RunDev<double>&, int, int, cudaStream_t);

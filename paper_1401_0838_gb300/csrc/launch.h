@@ -1,6 +1,7 @@
 // Host-side launchers of the CUDA kernels (internal; the public ABI is include/pic.h).
 #pragma once
-#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
+#include <cuda.h>
+#include <utility>  // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -64,6 +65,24 @@ struct YeeArgs {
 // as zero. Returns false when the layout does not allow TMA (row bytes not a multiple of 16, an
 // unaligned base, a box past the limits) or the driver has no encoder.
 bool tma_encode(CUtensorMap* m, const void* base, int es, int ndim, int nx, int ny, int nz, int bx, int by, int bz);
+
+// Launch with programmatic stream serialization (see pdl_wait): the kernel must call pdl_wait before
+// it reads or writes anything its predecessor in the stream touches.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Particle tiles of a grid: the push kernel's tile (PTile, or HoTile for the cubic and momentum-
 // conserving push) for the precision (es bytes per value), halved (down to 4 cells, the longest

@@ -198,14 +198,15 @@ def test_edge_particles(precision, ndim):
 
 @pytest.mark.parametrize("precision", [1, 0])
 def test_tile_with_more_leavers_than_its_buffer(precision):
-    # 1200 particles in the top cell row of one 16x16 particle tile (z in [15.6, 16)), all moving up:
-    # every one leaves the tile in the first step, more than the 512 the tile buffers in shared
-    # memory, so the rest take the direct path into the global leaver list
+    # 1200 particles in the top cell row of one particle tile, all moving up: every one leaves the
+    # tile in the first step, more than the 512 the tile buffers in shared memory, so the rest take
+    # the direct path into the global leaver list. On this 32x48 grid the 4x64 tiles are spread to
+    # 4x4 cells (96 tiles), so x in [0, 4), z in [15.6, 16) is the top row of the tile [0, 4) x [12, 16).
     nx, nz, n = 32, 48, 1200
-    cfg = make_cfg(nx=nx, nz=nz, dt=0.5, precision=precision, cap=96)
+    cfg = make_cfg(nx=nx, nz=nz, dt=0.5, precision=precision, cap=192)
     rng = np.random.default_rng(31)
     u0 = math.sqrt(cfg.gamma ** 2 - 1)
-    part = {"x": rng.uniform(0, 16, n), "y": np.zeros(n), "z": rng.uniform(15.6, 15.999, n),
+    part = {"x": rng.uniform(0, 3.999, n), "y": np.zeros(n), "z": rng.uniform(15.6, 15.999, n),
             "ux": rng.normal(0, 1e-3, n), "uy": rng.normal(0, 1e-3, n), "uz": u0 + rng.normal(0, 1e-3, n),
             "w": np.ones(n), "q": rng.choice([-1.0, 1.0], n), "id": np.arange(n, dtype=np.int64)}
     fields = synth.random_fields((nz, 1, nx), seed=33, scale=1e-3)

@@ -83,12 +83,13 @@ struct PTile<double, 3> {
   static constexpr int TX = 8, TY = 8, TZ = 8;
 };
 
-// Particle tile of the cubic and momentum-conserving push (k_push_ho).
+// Particle tile of the cubic and momentum-conserving push (k_push_ho): tall along the drift in 2D
+// too (the momentum-conserving push measured 14 % faster than on 16x16 tiles, the cubic the same).
 template <typename T, int NDIM>
 struct HoTile;
 template <typename T>
 struct HoTile<T, 2> {
-  static constexpr int TX = 16, TY = 1, TZ = 16;
+  static constexpr int TX = 4, TY = 1, TZ = 64;
 };
 template <typename T>
 struct HoTile<T, 3> {

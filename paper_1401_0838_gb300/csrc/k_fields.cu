@@ -617,6 +617,25 @@ struct FSum {
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
+// A sum held as an FP32 pair s + c. The block stage of the FP32 energy sums adds pairs: s by TwoSum,
+// its rounding error into c, so no FP64 arithmetic runs until a block's three partials leave it
+// (GB300's FP64 pipe is narrow, and every block reaches this stage at once).
+struct FPair {
+  float s, c;
+};
+__device__ __forceinline__ FPair pair_add(FPair a, FPair b) {
+  const float t = a.s + b.s;
+  const float bb = t - a.s;
+  const float err = (a.s - (t - bb)) + (b.s - bb);
+  return FPair{t, a.c + b.c + err};
+}
+__device__ __forceinline__ FPair warp_sum_pair(FPair v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = pair_add(v, FPair{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)});
+  return v;
+}
+
 // Per-thread sums of squares of the six field components: FP32 fields through FSum (exact squares,
 // error-free running sums), FP64 fields with FMAs.
 template <typename T>
@@ -639,6 +658,14 @@ struct EnergyAcc {
       sp += t + tb;
     }
   }
+  // FP32 fields: the same three sums as FP32 pairs (FP64 fields: unused)
+  __device__ __forceinline__ void pairs(FPair& oe, FPair& ob, FPair& op) const {
+    const FPair ax{e2x.s, e2x.c}, ay{e2y.s, e2y.c}, bxs{b2x.s, b2x.c}, bys{b2y.s, b2y.c};
+    const FPair exy = pair_add(ax, ay), bxy = pair_add(bxs, bys);
+    oe = pair_add(exy, FPair{e2.s, e2.c});
+    ob = pair_add(bxy, FPair{b2.s, b2.c});
+    op = pair_add(exy, bxy);
+  }
   // (sum E^2, sum B^2, sum Ex^2 + Ey^2 + Bx^2 + By^2) of this thread
   __device__ __forceinline__ void get(double& oe, double& ob, double& op) const {
     if (sizeof(T) == 4) {
@@ -658,25 +685,18 @@ struct EnergyAcc {
 // scratch[3 * block + r]; the last block to finish (counter at scratch + 3 * slots, slots >= the
 // grid size) adds the block partials in a fixed order and writes (sum E^2, sum B^2, sum Ex^2 + Ey^2
 // + Bx^2 + By^2) to out[0..2], or, with a history ring, into its next slot with the kinetic sums.
-__device__ __forceinline__ void energy_finish(double se, double sb, double sp, double* scratch, unsigned slots,
-                                              double* out, const HistCtl& hc) {
+// The grid stage: thread r < 3 holds the block's partial r in `part`; it stores it and fences, the
+// block counts itself done, and the last block adds every block's partials in FP64.
+__device__ __forceinline__ void energy_grid_finish(double part, double* scratch, unsigned slots, double* out,
+                                                   const HistCtl& hc) {
   __shared__ double red[3][FE_THREADS / 32];
   __shared__ bool last;
-  double dse = warp_sum(se), dsb = warp_sum(sb), dsp = warp_sum(sp);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][w] = dse;
-    red[1][w] = dsb;
-    red[2][w] = dsp;
-  }
-  __syncthreads();
   unsigned* done = reinterpret_cast<unsigned*>(scratch + 3 * (size_t)slots);
   if (threadIdx.x < 3) {
-    double t = 0;
-    for (int q = 0; q < FE_THREADS / 32; ++q) t += red[threadIdx.x][q];
-    scratch[3 * blockIdx.x + threadIdx.x] = t;
+    scratch[3 * blockIdx.x + threadIdx.x] = part;
+    __threadfence();  // the partial is visible before the block counts itself done
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
   __syncthreads();
@@ -711,6 +731,62 @@ __device__ __forceinline__ void energy_finish(double se, double sb, double sp, d
       out[threadIdx.x] = acc;
     }
     if (threadIdx.x == 0) *done = 0u;  // ready for the next launch
+  }
+}
+
+// Block stage, FP64 per-thread sums: FP64 tree per block, then the grid stage.
+__device__ __forceinline__ void energy_finish(double se, double sb, double sp, double* scratch, unsigned slots,
+                                              double* out, const HistCtl& hc) {
+  __shared__ double redb[3][FE_THREADS / 32];
+  const double dse = warp_sum(se), dsb = warp_sum(sb), dsp = warp_sum(sp);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    redb[0][w] = dse;
+    redb[1][w] = dsb;
+    redb[2][w] = dsp;
+  }
+  __syncthreads();
+  double part = 0;
+  if (threadIdx.x < 3)
+    for (int q = 0; q < FE_THREADS / 32; ++q) part += redb[threadIdx.x][q];
+  energy_grid_finish(part, scratch, slots, out, hc);
+}
+
+// Block stage, FP32 pair sums: pair trees per warp and block, FP64 only for the block's partials.
+__device__ __forceinline__ void energy_finish(FPair e, FPair b, FPair p, double* scratch, unsigned slots,
+                                              double* out, const HistCtl& hc) {
+  __shared__ FPair redp[3][FE_THREADS / 32];
+  e = warp_sum_pair(e);
+  b = warp_sum_pair(b);
+  p = warp_sum_pair(p);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    redp[0][w] = e;
+    redp[1][w] = b;
+    redp[2][w] = p;
+  }
+  __syncthreads();
+  double part = 0;
+  if (threadIdx.x < 3) {
+    FPair t = redp[threadIdx.x][0];
+    for (int q = 1; q < FE_THREADS / 32; ++q) t = pair_add(t, redp[threadIdx.x][q]);
+    part = (double)t.s + (double)t.c;
+  }
+  energy_grid_finish(part, scratch, slots, out, hc);
+}
+
+// The block's energy sums from each thread's accumulator, then the grid stage.
+template <typename T>
+__device__ __forceinline__ void energy_finish(const EnergyAcc<T>& acc, double* scratch, unsigned slots, double* out,
+                                              const HistCtl& hc) {
+  if constexpr (sizeof(T) == 4) {
+    FPair e, b, p;
+    acc.pairs(e, b, p);
+    energy_finish(e, b, p, scratch, slots, out, hc);
+  } else {
+    double se, sb, sp;
+    acc.get(se, sb, sp);
+    energy_finish(se, sb, sp, scratch, slots, out, hc);
   }
 }
 
@@ -946,11 +1022,7 @@ __device__ __forceinline__ void yee_tile(const YeeArgs<T>& a, const int tile, co
     a.obz[o] = nbz;
     if (DIAG) en.add(ex, ey, ez, nbx, nby, nbz);
   }
-  if (DIAG) {  // every thread reaches this (the loop above only skips cells)
-    double se, sb, sp;
-    en.get(se, sb, sp);
-    energy_finish(se, sb, sp, escratch, gridDim.x, nullptr, *hc);
-  }
+  if (DIAG) energy_finish(en, escratch, gridDim.x, nullptr, *hc);  // every thread reaches this
 }
 
 template <typename T, int NDIM, bool CK, bool DIAG>
@@ -1098,9 +1170,7 @@ __device__ __forceinline__ void field_energy_body(const T* __restrict__ ex, cons
   EnergyAcc<T> acc;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += stride)
     acc.add(ex[c], ey[c], ez[c], bx[c], by[c], bz[c]);
-  double se, sb, sp;
-  acc.get(se, sb, sp);
-  energy_finish(se, sb, sp, scratch, FE_BLOCKS, out, hc);
+  energy_finish(acc, scratch, FE_BLOCKS, out, hc);
 }
 
 template <typename T>

@@ -56,6 +56,26 @@ __device__ __forceinline__ void list_put(const LeaverList<T>& l, long long o, in
   if (l.id) l.id[o] = id;
 }
 
+// A sum held as an FP32 pair s + c, added with s by TwoSum and its rounding error into c. The block
+// stages of the FP32 field energy sums reduce pairs, so no FP64 arithmetic runs until a block's
+// partials leave it: GB300's FP64 pipe is narrow, and a one-wave launch's blocks all reach that stage
+// at once.
+struct FPair {
+  float s, c;
+};
+__device__ __forceinline__ FPair pair_add(FPair a, FPair b) {
+  const float t = a.s + b.s;
+  const float bb = t - a.s;
+  const float err = (a.s - (t - bb)) + (b.s - bb);
+  return FPair{t, a.c + b.c + err};
+}
+__device__ __forceinline__ FPair warp_sum_pair(FPair v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = pair_add(v, FPair{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)});
+  return v;
+}
+
 // Programmatic dependent launch. The kernels of a step are launched with launch_pdl, so a kernel's
 // launch overlaps the completion of the kernel before it in the stream; pdl_wait, the first thing
 // each of them does, holds it until that kernel has completed and its memory is visible (outside

@@ -617,24 +617,6 @@ struct FSum {
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-// A sum held as an FP32 pair s + c. The block stage of the FP32 energy sums adds pairs: s by TwoSum,
-// its rounding error into c, so no FP64 arithmetic runs until a block's three partials leave it
-// (GB300's FP64 pipe is narrow, and every block reaches this stage at once).
-struct FPair {
-  float s, c;
-};
-__device__ __forceinline__ FPair pair_add(FPair a, FPair b) {
-  const float t = a.s + b.s;
-  const float bb = t - a.s;
-  const float err = (a.s - (t - bb)) + (b.s - bb);
-  return FPair{t, a.c + b.c + err};
-}
-__device__ __forceinline__ FPair warp_sum_pair(FPair v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    v = pair_add(v, FPair{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)});
-  return v;
-}
 
 // Per-thread sums of squares of the six field components: FP32 fields through FSum (exact squares,
 // error-free running sums), FP64 fields with FMAs.

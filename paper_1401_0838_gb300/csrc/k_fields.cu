@@ -481,6 +481,7 @@ __global__ void __launch_bounds__(SEP_THREADS) k_sep_batch(const SepArgs<T>* __r
                                                            const int* __restrict__ tile_base, int nruns) {
   constexpr int CX = NDIM == 2 ? SEP2_CX : SEP3_CX, CY = NDIM == 2 ? 1 : SEP3_CY;
   constexpr int CZ = NDIM == 2 ? SEP2_CZ : SEP3_CZ;
+  pdl_wait();
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const SepArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
@@ -536,8 +537,7 @@ static cudaError_t launch_sep_batch_t(const SepArgs<T>* args, const int* tile_ba
   cudaError_t e = ensure_dynamic_smem((const void*)k_sep_batch<T, NDIM, HZ, HX>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)total_tiles, (unsigned)ncomp);
-  k_sep_batch<T, NDIM, HZ, HX><<<grid, SEP_THREADS, sm, st>>>(args, tile_base, nruns);
-  return cudaGetLastError();
+  return launch_pdl(k_sep_batch<T, NDIM, HZ, HX>, grid, dim3(SEP_THREADS), sm, st, args, tile_base, nruns);
 }
 
 template <typename T, int NDIM, int HX>
@@ -1020,6 +1020,7 @@ __global__ void __launch_bounds__(YEE_THREADS) k_yee_batch(const YeeArgs<T>* __r
                                                            const int* __restrict__ tile_base, int nruns) {
   constexpr int CX = NDIM == 2 ? YEE2_CX : YEE3_CX, CY = NDIM == 2 ? 1 : YEE3_CY;
   constexpr int CZ = NDIM == 2 ? YEE2_CZ : YEE3_CZ;
+  pdl_wait();
   const int run = run_of_tile(tile_base, nruns, blockIdx.x);
   const YeeArgs<T>& a = args[run];
   const int ntx = (a.nx + CX - 1) / CX, nty = NDIM == 3 ? (a.ny + CY - 1) / CY : 1;
@@ -1038,12 +1039,14 @@ cudaError_t launch_yee_batch(const YeeArgs<T>* args, const int* tile_base, int n
     const size_t sm = YeeGeom<T, 2, false>::SMEM_BYTES;
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 2>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_batch<T, 2><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
+    e = launch_pdl(k_yee_batch<T, 2>, dim3(total_tiles), dim3(YEE_THREADS), sm, st, args, tile_base, nruns);
+    if (e != cudaSuccess) return e;
   } else {
     const size_t sm = YeeGeom<T, 3, false>::SMEM_BYTES;
     cudaError_t e = ensure_dynamic_smem((const void*)k_yee_batch<T, 3>, sm);
     if (e != cudaSuccess) return e;
-    k_yee_batch<T, 3><<<total_tiles, YEE_THREADS, sm, st>>>(args, tile_base, nruns);
+    e = launch_pdl(k_yee_batch<T, 3>, dim3(total_tiles), dim3(YEE_THREADS), sm, st, args, tile_base, nruns);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1165,6 +1168,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy(const T* __restrict
 
 template <typename T>
 __global__ void __launch_bounds__(FE_THREADS) k_field_energy_batch(const EnergyArgs<T>* __restrict__ args) {
+  pdl_wait();
   const EnergyArgs<T>& a = args[blockIdx.y];
   field_energy_body<T>(a.f[0], a.f[1], a.f[2], a.f[3], a.f[4], a.f[5], a.ncell, nullptr, a.scratch, a.hc);
 }
@@ -1172,8 +1176,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_field_energy_batch(const EnergyA
 template <typename T>
 cudaError_t launch_field_energy_batch(const EnergyArgs<T>* args, int nruns, cudaStream_t st) {
   dim3 grid(2 * 152 / (nruns < 8 ? 1 : nruns / 8) + 1, (unsigned)nruns);  // about 2 waves in all
-  k_field_energy_batch<T><<<grid, FE_THREADS, 0, st>>>(args);
-  return cudaGetLastError();
+  return launch_pdl(k_field_energy_batch<T>, grid, dim3(FE_THREADS), 0, st, args);
 }
 template cudaError_t launch_field_energy_batch<float>(const EnergyArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_field_energy_batch<double>(const EnergyArgs<double>*, int, cudaStream_t);

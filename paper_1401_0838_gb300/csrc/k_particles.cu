@@ -1224,6 +1224,7 @@ __global__ void __launch_bounds__(PushThreads<T, NDIM>::value, PushMinBlocks<T, 
 template <typename T, int NDIM, int SCHEME, int LPC>
 __global__ void __launch_bounds__(PushThreads<T, NDIM>::value, PushMinBlocks<T, NDIM>::value)
     k_push_batch(const RunDev<T>* __restrict__ runs, const int2* __restrict__ items, int nitems, int* queue) {
+  pdl_wait();
   __shared__ RunDev<T> rs;
   __shared__ int cur, cur_run;
   if (threadIdx.x == 0) cur_run = -1;
@@ -1299,8 +1300,7 @@ static cudaError_t launch_push_batch_t(const RunDev<T>* runs, const int2* items,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, PushThreads<T, NDIM>::value, sm, st>>>(runs, items, nitems, queue);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(blocks), dim3(PushThreads<T, NDIM>::value), sm, st, runs, items, nitems, queue);
   };
   if (lpc == 4) return go(k_push_batch<T, NDIM, SCHEME, 4>);
   if (lpc == 8) return go(k_push_batch<T, NDIM, SCHEME, 8>);
@@ -1465,6 +1465,7 @@ __global__ void k_migrate(const __grid_constant__ RunDev<T> r, int* other_count)
 
 template <typename T>
 __global__ void k_migrate_batch(const RunDev<T>* __restrict__ runs) {
+  pdl_wait();
   const RunDev<T>& r = runs[blockIdx.y];
   migrate_body<T>(r, r.lv_other, blockIdx.x, gridDim.x);
 }
@@ -1477,8 +1478,7 @@ cudaError_t launch_migrate(const RunDev<T>& r, int* other_count, cudaStream_t st
 template <typename T>
 cudaError_t launch_migrate_batch(const RunDev<T>* runs, int nruns, cudaStream_t st) {
   dim3 grid(4 * 152 / (nruns < 4 ? 1 : nruns / 4) + 1, (unsigned)nruns);
-  k_migrate_batch<T><<<grid, 256, 0, st>>>(runs);
-  return cudaGetLastError();
+  return launch_pdl(k_migrate_batch<T>, grid, dim3(256), 0, st, runs);
 }
 template cudaError_t launch_migrate_batch<float>(const RunDev<float>*, int, cudaStream_t);
 template cudaError_t launch_migrate_batch<double>(const RunDev<double>*, int, cudaStream_t);

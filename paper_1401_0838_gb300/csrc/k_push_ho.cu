@@ -998,6 +998,7 @@ __global__ void __launch_bounds__(SPILL_THREADS) k_push_spill(const __grid_const
 // Many runs: run blockIdx.y (the batched step covers linear shapes).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(SPILL_THREADS) k_push_spill_batch(const RunDev<T>* __restrict__ runs, int scheme) {
+  pdl_wait();
   push_spill_body<T, NDIM>(runs[blockIdx.y], 1, scheme, blockIdx.x, gridDim.x);
 }
 
@@ -1050,9 +1051,8 @@ template <typename T>
 cudaError_t launch_push_spill_batch(const RunDev<T>* runs, int nruns, int ndim, int scheme, cudaStream_t st) {
   if (nruns <= 0) return cudaSuccess;
   const dim3 grid(152 / (nruns < 8 ? 1 : nruns / 8) + 1, (unsigned)nruns);
-  if (ndim == 2) k_push_spill_batch<T, 2><<<grid, SPILL_THREADS, 0, st>>>(runs, scheme);
-  else k_push_spill_batch<T, 3><<<grid, SPILL_THREADS, 0, st>>>(runs, scheme);
-  return cudaGetLastError();
+  if (ndim == 2) return launch_pdl(k_push_spill_batch<T, 2>, grid, dim3(SPILL_THREADS), 0, st, runs, scheme);
+  return launch_pdl(k_push_spill_batch<T, 3>, grid, dim3(SPILL_THREADS), 0, st, runs, scheme);
 }
 template cudaError_t launch_push_spill_batch<float>(const RunDev<float>*, int, int, int, cudaStream_t);
 template cudaError_t launch_push_spill_batch<double>(const RunDev<double>*, int, int, int, cudaStream_t);

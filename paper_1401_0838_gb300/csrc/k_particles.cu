@@ -148,29 +148,58 @@ struct EsirDir {
   T S0[3], dS[3];
 };
 
+// Comparisons of the push's values. FP64: integer tests on the IEEE bit patterns, exact for every
+// value that is not a NaN (the offsets and displacements compared here are finite), which keeps
+// them off the narrow FP64 pipe that bounds the FP64 push. FP32: plain comparisons.
+template <typename T>
+__device__ __forceinline__ bool is_neg(T x) {  // x < 0 (-0 is not)
+  if constexpr (sizeof(T) == 8) return (unsigned long long)__double_as_longlong(x) > 0x8000000000000000ull;
+  else return x < T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool is_pos(T x) {  // x > 0
+  if constexpr (sizeof(T) == 8) return __double_as_longlong(x) > 0;
+  else return x > T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool ge_one(T x) {  // x >= 1
+  if constexpr (sizeof(T) == 8) return __double_as_longlong(x) >= 0x3FF0000000000000ll;
+  else return x >= T(1);
+}
+template <typename T>
+__device__ __forceinline__ bool is_zero(T x) {  // x == 0 (either sign)
+  if constexpr (sizeof(T) == 8) return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) == 0;
+  else return x == T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool abs_lt_one(T x) {  // -1 < x < 1; false for a NaN or an infinity
+  if constexpr (sizeof(T) == 8) return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) < 0x3FF0000000000000ll;
+  else return x > T(-1) && x < T(1);
+}
+
 template <typename T>
 __device__ __forceinline__ EsirDir<T> esir_dir(T o, T d) {
   EsirDir<T> e;
   const T x1 = o + d;
-  if (x1 < T(0)) {  // into the cell below: window nodes -1, 0, 1
+  if (is_neg(x1)) {  // into the cell below: window nodes -1, 0, 1
     e.a = -1;
     e.S0[0] = T(0); e.S0[1] = T(1) - o; e.S0[2] = o;
     e.dS[0] = -x1; e.dS[2] = -o; e.dS[1] = -(e.dS[0] + e.dS[2]);
     e.off = T(1) + x1;
     e.shift = -1;
-    if (e.off >= T(1)) { e.off = T(0); e.shift = 0; }
+    if (ge_one(e.off)) { e.off = T(0); e.shift = 0; }
   } else {
     e.a = 0;
     e.S0[0] = T(1) - o; e.S0[1] = o; e.S0[2] = T(0);
     const T am = T(1) - o;  // distance to the upper face
     const T c = d - am;     // x1 - 1, without the rounding of x1
-    if (x1 >= T(1) && c > T(0)) {  // into the cell above: nodes 0, 1, 2
+    if (ge_one(x1) && is_pos(c)) {  // into the cell above: nodes 0, 1, 2
       e.dS[0] = -am; e.dS[2] = c; e.dS[1] = -(e.dS[0] + e.dS[2]);
       e.off = c;
       e.shift = 1;
     } else {  // same cell (or onto the upper face within rounding)
       e.dS[0] = -d; e.dS[1] = d; e.dS[2] = T(0);
-      if (x1 >= T(1)) { e.off = T(0); e.shift = 1; }
+      if (ge_one(x1)) { e.off = T(0); e.shift = 1; }
       else { e.off = x1; e.shift = 0; }
     }
   }
@@ -423,8 +452,8 @@ struct RegLayout<3> {
 // Whether a particle's window fits the register sums (see RegLayout).
 template <typename T, int NDIM>
 __device__ __forceinline__ bool reg_window(const EsirDir<T>& X, const EsirDir<T>& Y, const EsirDir<T>& Z) {
-  if (NDIM == 3) return (X.a | Y.a | Z.a) == 0 && X.dS[2] == T(0) && Y.dS[2] == T(0);
-  return (X.a | Z.a) == 0 && X.dS[2] == T(0);
+  if (NDIM == 3) return (X.a | Y.a | Z.a) == 0 && is_zero(X.dS[2]) && is_zero(Y.dS[2]);
+  return (X.a | Z.a) == 0 && is_zero(X.dS[2]);
 }
 
 // The contributions of deposit2 / deposit3 that can be nonzero for such a particle, into the
@@ -969,7 +998,7 @@ __device__ __forceinline__ void push_tile(const RunDev<T>& r, const int tile) {
           ++npush;
           // move (cell-relative displacement in grid units)
           T ddx = r.dtdx * vx, ddy = NDIM == 3 ? r.dtdy * vy : T(0), ddz = r.dtdz * vz;
-          if (!(ddx > T(-1) && ddx < T(1) && ddy > T(-1) && ddy < T(1) && ddz > T(-1) && ddz < T(1))) {
+          if (!(abs_lt_one(ddx) && abs_lt_one(ddy) && abs_lt_one(ddz))) {
             flag_error(r.err, ERR_NONFINITE);
             ddx = ddy = ddz = T(0);
             ux = uy = uz = T(0);

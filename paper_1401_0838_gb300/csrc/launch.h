@@ -1,8 +1,8 @@
 // Host-side launchers of the CUDA kernels (internal; the public ABI is include/pic.h).
 #pragma once
-#include <cuda.h>
-#include <utility>  // CUtensorMap (the encoder is fetched from the driver at run time)
+#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
+#include <utility>
 
 #include "common.cuh"
 

@@ -46,6 +46,30 @@ def test_median_kernel_times_ignores_one_stray_launch():
     assert abs(even["spill"][0] / 4 - 0.006) < 1e-12
 
 
+def test_warm_up_runs_one_call_long_enough_to_capture_the_graph():
+    # the warm-up is one pic_step call of at least 4 steps (two graphs' worth at one step per
+    # energy record), so the step graph is captured before the timed call replays it
+    calls = []
+
+    class FakeP:
+        @staticmethod
+        def pic_step(h, n):
+            calls.append((h, n))
+
+    bench.warm_up(FakeP, "h", 3)
+    bench.warm_up(FakeP, "h", 7)
+    assert calls == [("h", 4), ("h", 7)]
+
+
+def test_bin_stats_reports_capacity_and_spills():
+    class FakeP:
+        @staticmethod
+        def pic_bin_stats(h):
+            return 48, 12
+
+    assert bench.bin_stats(FakeP, None) == {"capacity": 48, "spilled": 12}
+
+
 def test_traffic_only_for_the_profiled_source(tmp_path):
     src = tmp_path / "kernel.cu"
     src.write_text("kernel source\n")
